@@ -1,0 +1,104 @@
+"""Oracle: flexible GMRES, the outer solver (Sec. 1 and Sec. 5: "preconditioners
+for FGMRES ... relative convergence tolerance 1e-10").
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Right-preconditioned flexible GMRES with restart length m (Saad's FGMRES):
+the preconditioned directions z_j = M(v_j) are kept in a second basis Z so that
+M may change between steps (the V-cycle is not a fixed linear operator once it
+runs in reduced precision).  Arnoldi uses modified Gram-Schmidt; the small
+least-squares problem is solved with complex Givens rotations.
+
+Readings (the paper fixes none of them): start vector x0 = 0; residual measured
+as ||b - A x||_2 / ||b||_2; the iteration count is the total number of Arnoldi
+steps; the recursive residual estimate only ends a cycle early, and the solve
+stops only when the true residual, recomputed at every restart and at a claimed
+convergence, is below the tolerance.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Callable, List
+
+import numpy as np
+
+
+@dataclass
+class FgmresResult:
+    x: np.ndarray
+    iterations: int
+    true_relres: float
+    converged: bool
+    estimates: List[float] = field(default_factory=list)   # |g_{j+1}| / ||b|| after each step
+    restarts: int = 0
+
+
+def givens(a: complex, b: complex):
+    """(c, s) with c real such that [[c, s], [-conj(s), c]] @ [a, b] = [r, 0]."""
+    if b == 0:
+        return 1.0, 0.0 + 0j
+    if a == 0:
+        return 0.0, 1.0 + 0j
+    r = np.hypot(abs(a), abs(b))
+    c = abs(a) / r
+    s = (a / abs(a)) * np.conj(b) / r
+    return c, s
+
+
+def fgmres(apply_A: Callable[[np.ndarray], np.ndarray],
+           precond: Callable[[np.ndarray], np.ndarray],
+           b: np.ndarray, m: int, tol: float, max_iter: int) -> FgmresResult:
+    n = b.shape[0]
+    x = np.zeros(n, dtype=np.complex128)
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0:
+        return FgmresResult(x, 0, 0.0, True)
+    iters = 0
+    restarts = 0
+    estimates: List[float] = []
+    while True:
+        r = b - apply_A(x)
+        beta = np.linalg.norm(r)
+        if beta <= tol * bnorm:
+            return FgmresResult(x, iters, beta / bnorm, True, estimates, restarts)
+        if iters >= max_iter:
+            return FgmresResult(x, iters, beta / bnorm, False, estimates, restarts)
+        V = np.zeros((m + 1, n), dtype=np.complex128)
+        Z = np.zeros((m, n), dtype=np.complex128)
+        H = np.zeros((m + 1, m), dtype=np.complex128)
+        cs = np.zeros(m)
+        sn = np.zeros(m, dtype=np.complex128)
+        g = np.zeros(m + 1, dtype=np.complex128)
+        g[0] = beta
+        V[0] = r / beta
+        k = 0
+        for j in range(m):
+            Z[j] = precond(V[j])
+            w = apply_A(Z[j])
+            for i in range(j + 1):                       # modified Gram-Schmidt
+                H[i, j] = np.vdot(V[i], w)
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            breakdown = H[j + 1, j] == 0
+            if not breakdown:
+                V[j + 1] = w / H[j + 1, j]
+            for i in range(j):                           # earlier rotations
+                hi, hi1 = H[i, j], H[i + 1, j]
+                H[i, j] = cs[i] * hi + sn[i] * hi1
+                H[i + 1, j] = -np.conj(sn[i]) * hi + cs[i] * hi1
+            cs[j], sn[j] = givens(H[j, j], H[j + 1, j])
+            H[j, j] = cs[j] * H[j, j] + sn[j] * H[j + 1, j]
+            H[j + 1, j] = 0.0
+            g[j + 1] = -np.conj(sn[j]) * g[j]
+            g[j] = cs[j] * g[j]
+            iters += 1
+            k = j + 1
+            estimates.append(abs(g[j + 1]) / bnorm)
+            if abs(g[j + 1]) <= tol * bnorm or iters >= max_iter or breakdown:
+                break
+        # least squares: upper triangular H[:k, :k] y = g[:k]
+        y = np.zeros(k, dtype=np.complex128)
+        for i in range(k - 1, -1, -1):
+            y[i] = (g[i] - H[i, i + 1:k] @ y[i + 1:k]) / H[i, i]
+        x = x + Z[:k].T @ y
+        restarts += 1

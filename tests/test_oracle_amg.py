@@ -1,0 +1,267 @@
+"""Pins of the oracle's SM-AMG hierarchy, smoother and V-cycle (Sec. 2, Sec. 4.1,
+Eqs. (14)-(16), Algorithm 1) to exact properties, dense linear algebra and brute force."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import amg
+from oracle import wilson as W
+from paper_2608_03515_b300 import fixtures as fx
+
+
+def random_links(Nt, Nx, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.exp(1j * rng.uniform(-np.pi, np.pi, size=(2, Nt, Nx)))
+
+
+CASES = [(4, 4, 2), (8, 8, 2), (8, 8, 4), (8, 12, 4)]
+
+
+@pytest.mark.parametrize("Nt,Nx,a", CASES)
+def test_roles_and_ownership_partition(Nt, Nx, a):
+    role = amg.site_roles(Nt, Nx, a)
+    owner = amg.owner_tiles(Nt, Nx, a)
+    Np, Nq = Nt // a, Nx // a
+    # every basket contains 4 vertices, 4(a-1) edge and (a-1)^2 interior sites
+    count = np.zeros(Nt * Nx, dtype=int)
+    for p in range(Np):
+        for q in range(Nq):
+            sites = amg.basket_sites(Nt, Nx, a, p, q)
+            roles = [role[t, x] for (t, x, _, _) in sites]
+            assert roles.count(amg.ROLE_VERTEX) == 4
+            assert roles.count(amg.ROLE_EDGE) == 4 * (a - 1)
+            assert roles.count(amg.ROLE_INTERIOR) == (a - 1) ** 2
+            for (t, x, i, j) in sites:
+                if role[t, x] != amg.ROLE_VERTEX and owner[t, x] == p * Nq + q:
+                    count[t * Nx + x] += 1
+                    assert i < a and j < a
+    # each non-vertex site is owned by exactly one basket that contains it
+    nonvertex = (role.reshape(-1) != amg.ROLE_VERTEX)
+    assert np.all(count[nonvertex] == 1)
+    assert np.all(count[~nonvertex] == 0)
+    # interior sites belong to exactly one basket, edges to two, vertices to four
+    member = np.zeros(Nt * Nx, dtype=int)
+    for p in range(Np):
+        for q in range(Nq):
+            for (t, x, _, _) in amg.basket_sites(Nt, Nx, a, p, q):
+                member[t * Nx + x] += 1
+    expect = {amg.ROLE_VERTEX: 4, amg.ROLE_EDGE: 2, amg.ROLE_INTERIOR: 1}
+    for s in range(Nt * Nx):
+        assert member[s] == expect[role.reshape(-1)[s]]
+
+
+def test_nine_point_basket_matches_the_figure():
+    """a = 2: four vertices (corners), four edges (mid-sides), one interior point (centre)."""
+    role = amg.site_roles(4, 4, 2)
+    sites = amg.basket_sites(4, 4, 2, 0, 0)
+    grid = np.array([role[t, x] for (t, x, _, _) in sites]).reshape(3, 3)
+    V, E, I = amg.ROLE_VERTEX, amg.ROLE_EDGE, amg.ROLE_INTERIOR
+    assert grid.tolist() == [[V, E, V], [E, I, E], [V, E, V]]
+
+
+@pytest.mark.parametrize("Nt,Nx,a", CASES)
+def test_routes_agree_and_ideal_interpolation(Nt, Nx, a):
+    U = random_links(Nt, Nx, 7)
+    D = W.dirac_matrix(U, 0.3)
+    for p in range(Nt // a):
+        for q in range(Nx // a):
+            F_sites, PA = amg.local_interpolation(D, Nt, Nx, a, p, q, "A")
+            _, PB = amg.local_interpolation(D, Nt, Nx, a, p, q, "B")
+            assert np.max(np.abs(PA - PB)) <= 1e-12 * np.max(np.abs(PA))
+            # Eq. (15): F rows of A_W [P_F; I] vanish (zero interior/edge residual)
+            sites = amg.basket_sites(Nt, Nx, a, p, q)
+            corners = sorted([s for s in sites if s[2] in (0, a) and s[3] in (0, a)],
+                             key=lambda s: 2 * (s[2] // a) + (s[3] // a))
+            dof = lambda s: [2 * (s[0] * Nx + s[1]), 2 * (s[0] * Nx + s[1]) + 1]
+            Fd = np.concatenate([dof(s) for s in F_sites])
+            Vd = np.concatenate([dof(s) for s in corners])
+            res = D[Fd][:, Fd].toarray() @ PA + D[Fd][:, Vd].toarray()
+            assert np.max(np.abs(res)) < 1e-12
+
+
+@pytest.mark.parametrize("Nt,Nx,a", CASES)
+def test_interpolator_identity_on_vertices(Nt, Nx, a):
+    U = random_links(Nt, Nx, 8)
+    D = W.dirac_matrix(U, 0.3)
+    P, pat = amg.build_interpolator(D, Nt, Nx, a)
+    role = amg.site_roles(Nt, Nx, a).reshape(-1)
+    Nq = Nx // a
+    Pd = P.toarray()
+    for s in range(Nt * Nx):
+        t, x = divmod(s, Nx)
+        rows = Pd[2 * s:2 * s + 2]
+        if role[s] == amg.ROLE_VERTEX:
+            v = (t // a) * Nq + x // a
+            expect = np.zeros_like(rows)
+            expect[0, 2 * v] = expect[1, 2 * v + 1] = 1.0
+            assert np.array_equal(rows, expect)
+        else:
+            assert pat[2 * s].nnz == 8 and pat[2 * s + 1].nnz == 8
+            assert np.all(np.abs(rows).sum(axis=1) > 0)
+
+
+def test_level1_sparsity_is_21_offsets():
+    """Galerkin sparsity from the boolean product: |dp|, |dq| <= 2 minus the four corners."""
+    Nt = Nx = 32
+    a = 4
+    U = random_links(Nt, Nx, 9)
+    D = W.dirac_matrix(U, 0.3)
+    P, pat = amg.build_interpolator(D, Nt, Nx, a)
+    A_pat = amg.pattern_from_offsets(amg.canonical_offsets(amg.WILSON_OFFSETS_RAW, Nt, Nx), Nt, Nx)
+    offs = amg.coarse_offsets(pat, A_pat, Nt, Nx, a)
+    expect = amg.canonical_offsets([(dp, dq) for dp in range(-2, 3) for dq in range(-2, 3)
+                                    if not (abs(dp) == 2 and abs(dq) == 2)], 8, 8)
+    assert offs == expect and len(offs) == 21
+
+
+@pytest.mark.parametrize("Nt,Nx,a", CASES)
+def test_galerkin_equals_dense_product_and_pattern(Nt, Nx, a):
+    U = random_links(Nt, Nx, 10)
+    D = W.dirac_matrix(U, 0.3)
+    P, pat = amg.build_interpolator(D, Nt, Nx, a)
+    Dc = amg.galerkin(P, D)
+    dense = P.toarray().conj().T @ D.toarray() @ P.toarray()
+    assert np.max(np.abs(Dc.toarray() - dense)) < 1e-13 * np.max(np.abs(dense))
+    A_pat = amg.pattern_from_offsets(amg.canonical_offsets(amg.WILSON_OFFSETS_RAW, Nt, Nx), Nt, Nx)
+    offs = amg.coarse_offsets(pat, A_pat, Nt, Nx, a)
+    sym = amg.pattern_from_offsets(offs, Nt // a, Nx // a).toarray() > 0
+    assert np.all(sym[np.abs(dense) > 1e-14])          # numeric nonzeros inside the symbolic pattern
+    # blocks read back from the stencil layout reproduce the matrix
+    B = amg.block_stencil(Dc, offs, Nt // a, Nx // a)
+    rebuilt = np.zeros_like(dense)
+    Np, Nq = Nt // a, Nx // a
+    for k, (dp, dq) in enumerate(offs):
+        for v in range(Np * Nq):
+            pv, qv = divmod(v, Nq)
+            w = ((pv + dp) % Np) * Nq + (qv + dq) % Nq
+            rebuilt[2 * v:2 * v + 2, 2 * w:2 * w + 2] += B[k, v]
+    assert np.max(np.abs(rebuilt - dense)) < 1e-13 * np.max(np.abs(dense))
+
+
+@pytest.mark.parametrize("Nt,Nx,a", [(8, 8, 2), (8, 8, 4)])
+def test_coarse_grid_correction_is_a_projection(Nt, Nx, a):
+    U = random_links(Nt, Nx, 11)
+    Dd = W.dirac_matrix(U, 0.3).toarray()
+    P, _ = amg.build_interpolator(W.dirac_matrix(U, 0.3), Nt, Nx, a)
+    Pd = P.toarray()
+    Dc = Pd.conj().T @ Dd @ Pd
+    K = np.eye(Dd.shape[0]) - Pd @ np.linalg.solve(Dc, Pd.conj().T @ Dd)
+    assert np.max(np.abs(K @ K - K)) < 1e-12
+    assert np.max(np.abs(Pd.conj().T @ Dd @ K)) < 1e-12
+
+
+@pytest.mark.parametrize("Nt,Nx,a", [(8, 8, 2), (8, 8, 4)])
+def test_interpolator_and_coarse_operator_gauge_covariance(Nt, Nx, a):
+    U = random_links(Nt, Nx, 12)
+    rng = np.random.Generator(np.random.PCG64(13))
+    omega = np.exp(1j * rng.uniform(-np.pi, np.pi, size=(Nt, Nx)))
+    U2 = W.gauge_transform_links(U, omega)
+    D1, D2 = W.dirac_matrix(U, 0.3), W.dirac_matrix(U2, 0.3)
+    P1, _ = amg.build_interpolator(D1, Nt, Nx, a)
+    P2, _ = amg.build_interpolator(D2, Nt, Nx, a)
+    Om = np.diag(np.repeat(omega.reshape(-1), 2))
+    omV = omega[::a, ::a].reshape(-1)
+    OmV = np.diag(np.repeat(omV, 2))
+    assert np.max(np.abs(P2.toarray() - Om @ P1.toarray() @ OmV.conj().T)) < 1e-12
+    Dc1, Dc2 = amg.galerkin(P1, D1).toarray(), amg.galerkin(P2, D2).toarray()
+    assert np.max(np.abs(Dc2 - OmV @ Dc1 @ OmV.conj().T)) < 1e-12
+
+
+def sequential_gs(A, e, r, order):
+    """Brute force: point-block Gauss-Seidel, one site at a time in the given order."""
+    e = e.copy()
+    Ad = A.toarray()
+    for s in order:
+        d = slice(2 * s, 2 * s + 2)
+        res = r[d] - Ad[d] @ e
+        e[d] = e[d] + np.linalg.solve(Ad[d, d], res)
+    return e
+
+
+def test_red_black_sweep_equals_sequential_gs():
+    Nt = Nx = 4
+    U = random_links(Nt, Nx, 14)
+    D = W.dirac_matrix(U, 0.1)
+    colour = amg.colouring(Nt, Nx, fine=True)
+    dinv = amg.diag_block_inverses(D, Nt * Nx)
+    rng = np.random.Generator(np.random.PCG64(15))
+    r = rng.standard_normal(32) + 1j * rng.standard_normal(32)
+    e0 = rng.standard_normal(32) + 1j * rng.standard_normal(32)
+    order = [s for c in (0, 1) for s in range(16) if colour.reshape(-1)[s] == c]
+    assert np.max(np.abs(amg.gs_sweep(D, dinv, colour, e0, r) - sequential_gs(D, e0, r, order))) < 1e-13
+
+
+def test_sixteen_colour_sweep_equals_sequential_gs():
+    Nt = Nx = 16
+    U = random_links(Nt, Nx, 16)
+    D = W.dirac_matrix(U, 0.2)
+    levels = amg.build_hierarchy(D, Nt, Nx, [2, 2])
+    L1 = levels[1]                                   # 8 x 8 coarse level, 16 colours
+    rng = np.random.Generator(np.random.PCG64(17))
+    n = 2 * L1.Nt * L1.Nx
+    r = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    e0 = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    col = L1.colour.reshape(-1)
+    order = [s for c in range(16) for s in range(L1.Nt * L1.Nx) if col[s] == c]
+    got = amg.gs_sweep(L1.A, L1.dinv, L1.colour, e0, r)
+    assert np.max(np.abs(got - sequential_gs(L1.A, e0, r, order))) < 1e-12 * np.max(np.abs(got))
+
+
+def test_gauss_seidel_converges_when_diagonally_dominant():
+    Nt = Nx = 8
+    U = random_links(Nt, Nx, 18)
+    D = W.dirac_matrix(U, 2.0)
+    colour = amg.colouring(Nt, Nx, fine=True)
+    dinv = amg.diag_block_inverses(D, Nt * Nx)
+    rng = np.random.Generator(np.random.PCG64(19))
+    b = rng.standard_normal(128) + 1j * rng.standard_normal(128)
+    e = np.zeros(128, dtype=complex)
+    for _ in range(200):
+        e = amg.gs_sweep(D, dinv, colour, e, b)
+    x = np.linalg.solve(D.toarray(), b)
+    assert np.max(np.abs(e - x)) < 1e-12 * np.max(np.abs(x))
+
+
+def test_coarsest_lu_matches_dense_solve():
+    Nt = Nx = 8
+    U = random_links(Nt, Nx, 20)
+    D = W.dirac_matrix(U, 0.2)
+    levels = amg.build_hierarchy(D, Nt, Nx, [2])
+    rng = np.random.Generator(np.random.PCG64(21))
+    n = levels[-1].A.shape[0]
+    r = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    import scipy.linalg as sla
+    got = sla.lu_solve(levels[-1].lu, r)
+    want = np.linalg.solve(levels[-1].A.toarray(), r)
+    assert np.max(np.abs(got - want)) < 1e-12 * np.max(np.abs(want))
+
+
+def test_vcycle_two_level_on_exact_coarse_space_is_exact_for_coarse_vectors():
+    """With no smoothing, M(D P y) = P y for every coarse vector y (P D_c^{-1} P^H D P = P)."""
+    Nt = Nx = 8
+    U = random_links(Nt, Nx, 22)
+    D = W.dirac_matrix(U, 0.2)
+    levels = amg.build_hierarchy(D, Nt, Nx, [4])
+    rng = np.random.Generator(np.random.PCG64(23))
+    y = rng.standard_normal(levels[1].A.shape[0]) + 1j * rng.standard_normal(levels[1].A.shape[0])
+    Py = levels[0].P @ y
+    got = amg.vcycle(levels, D @ Py, post_smooth=0)
+    assert np.max(np.abs(got - Py)) < 1e-11 * np.max(np.abs(Py))
+
+
+def test_stationary_vcycle_reduces_residual_c1_field():
+    """x <- x + M(b - D x) reduces ||r|| every cycle on the 32^2, beta = 3 field
+    (empirical check of the preconditioner, not a theorem)."""
+    theta = fx.metropolis_u1(32, 32, 3.0, 500, 0)
+    U = fx.links_from_angles(theta)
+    m0 = -0.1383495190759743 + 0.05        # m_crit of this field from the oracle's spectrum
+    D = W.dirac_matrix(U, m0)
+    levels = amg.build_hierarchy(D, 32, 32, [4])
+    b = W.to_flat(fx.gaussian_rhs(1, 32, 32, 1)[0])
+    x = np.zeros_like(b)
+    prev = np.linalg.norm(b)
+    for _ in range(8):
+        x = x + amg.vcycle(levels, b - D @ x)
+        now = np.linalg.norm(b - D @ x)
+        assert now < prev
+        prev = now

@@ -1,0 +1,70 @@
+"""Pins of the oracle's FGMRES and of the whole preconditioned solve."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import amg, krylov
+from oracle import wilson as W
+from paper_2608_03515_b300 import fixtures as fx
+
+
+def random_links(Nt, Nx, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.exp(1j * rng.uniform(-np.pi, np.pi, size=(2, Nt, Nx)))
+
+
+def test_identity_preconditioner_reproduces_gmres():
+    """M = I: flexible GMRES is plain restarted GMRES; compare with scipy's GMRES."""
+    Nt = Nx = 8
+    D = W.dirac_matrix(random_links(Nt, Nx, 30), 0.4)
+    b = W.to_flat(fx.gaussian_rhs(1, Nt, Nx, 31)[0])
+    res = krylov.fgmres(lambda v: D @ v, lambda v: v, b, 10, 1e-10, 2000)
+    assert res.converged and res.true_relres <= 1e-10
+    hist = []
+    x, info = spla.gmres(D, b, restart=10, rtol=1e-10, atol=0.0, maxiter=200,
+                         callback=lambda pr: hist.append(pr), callback_type="pr_norm")
+    assert info == 0
+    # same Krylov spaces: same number of inner steps to reach the tolerance (+-1 for
+    # the different stopping bookkeeping) and the same solution
+    assert abs(len(hist) - res.iterations) <= 1
+    xs = np.linalg.solve(D.toarray(), b)
+    assert np.linalg.norm(res.x - xs) <= 1e-8 * np.linalg.norm(xs)
+    # first restart cycle: relative residual estimates coincide with scipy's
+    k = min(9, len(hist))
+    assert np.allclose(res.estimates[:k], hist[:k], rtol=1e-6)
+
+
+def test_exact_preconditioner_converges_in_one_step():
+    Nt = Nx = 8
+    D = W.dirac_matrix(random_links(Nt, Nx, 32), 0.1)
+    Dd = D.toarray()
+    b = W.to_flat(fx.gaussian_rhs(1, Nt, Nx, 33)[0])
+    res = krylov.fgmres(lambda v: D @ v, lambda v: np.linalg.solve(Dd, v), b, 30, 1e-10, 100)
+    assert res.iterations == 1 and res.converged
+
+
+def test_residual_estimate_non_increasing_within_cycle():
+    Nt = Nx = 16
+    D = W.dirac_matrix(random_links(Nt, Nx, 34), 0.05)
+    b = W.to_flat(fx.gaussian_rhs(1, Nt, Nx, 35)[0])
+    m = 20
+    res = krylov.fgmres(lambda v: D @ v, lambda v: v, b, m, 1e-10, 400)
+    est = np.array(res.estimates)
+    for start in range(0, len(est), m):
+        cyc = est[start:start + m]
+        assert np.all(np.diff(cyc) <= 1e-14)
+
+
+@pytest.mark.parametrize("aggs", [[2], [4], [2, 2]])
+def test_amg_preconditioned_solve_matches_dense_lu(aggs):
+    Nt = Nx = 8
+    D = W.dirac_matrix(random_links(Nt, Nx, 36), 0.1)
+    levels = amg.build_hierarchy(D, Nt, Nx, aggs)
+    b = W.to_flat(fx.gaussian_rhs(1, Nt, Nx, 37)[0])
+    res = krylov.fgmres(lambda v: D @ v, lambda r: amg.vcycle(levels, r), b, 30, 1e-10, 500)
+    xs = np.linalg.solve(D.toarray(), b)
+    assert res.converged and res.true_relres <= 1e-10
+    assert np.linalg.norm(res.x - xs) <= 1e-9 * np.linalg.norm(xs)
+    # the preconditioner helps: fewer steps than plain GMRES
+    plain = krylov.fgmres(lambda v: D @ v, lambda v: v, b, 30, 1e-10, 2000)
+    assert res.iterations < plain.iterations
