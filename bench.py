@@ -1,0 +1,405 @@
+"""Benchmark: SM-AMG preconditioned Wilson-Dirac solves on one B300 (or N replicas).
+
+Workload (one "step" = one pass of the whole solve path over one batch of
+synthetic input): a 256x256 lattice, quenched U(1) gauge field at beta = 6
+(Metropolis, 500 sweeps from a cold start, seed 2); three bare masses
+m0 = m_crit + {0.1, 0.02, 0.005}, each with its own resident 3-level hierarchy
+(tile sides 4 then 2, coarsest 32x32 solved by its FP64 inverse); per step one
+Gaussian right-hand side per mass, FGMRES(30) to a true relative residual of
+1e-10.  Setup is timed separately.  Between steps the L2 cache is flushed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on the
+same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "AM-AMG solves/s at 1e-10 rel. residual, mixed vs FP64; D-apply GB/s; p50/p99"
+L = 256
+BETA = 6.0
+FIELD_SEED = 2
+SWEEPS = 500
+MASS_OFFSETS = [0.1, 0.02, 0.005]
+AGGS = [4, 2]
+RESTART = 30
+TOL = 1e-10
+RHS_SEED0 = 1000
+WORKLOAD = ("256x256 Wilson-Dirac (periodic x, antiperiodic t), quenched U(1) beta=6 seed 2, "
+            "m0 = m_crit + {0.1, 0.02, 0.005}, 3-level SM-AMG (tiles 4, 2), FGMRES(30) to 1e-10, 1 RHS per mass")
+
+
+def load_mcrit():
+    path = os.path.join(ROOT, "tests", "golden", "mcrit.json")
+    table = json.load(open(path))
+    return table[f"L{L}_b{BETA:g}_s{FIELD_SEED}"]["m_crit"]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+# ----------------------------------------------------------------------------- reference arm (oracle)
+
+def oracle_solve_time(theta, m0, psi_flat, reps):
+    from oracle import amg, krylov
+    from oracle import wilson as W
+    from paper_2608_03515_b300 import fixtures as fx
+    U = fx.links_from_angles(theta)
+    D = W.dirac_matrix(U, m0)
+    t0 = time.perf_counter()
+    levels = amg.build_hierarchy(D, L, L, AGGS)
+    setup_s = time.perf_counter() - t0
+    times, iters = [], []
+    for i in range(reps):
+        t0 = time.perf_counter()
+        res = krylov.fgmres(lambda v: D @ v, lambda r: amg.vcycle(levels, r), psi_flat[i], RESTART, TOL, 3000)
+        times.append(time.perf_counter() - t0)
+        iters.append(res.iterations)
+    return setup_s, times, iters
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import wilson as W
+    from paper_2608_03515_b300 import fixtures as fx
+    theta = fx.metropolis_u1(L, L, BETA, SWEEPS, FIELD_SEED)
+    m0 = load_mcrit() + MASS_OFFSETS[0]
+    n = args.warmup + args.steps
+    psi = [W.to_flat(fx.gaussian_rhs(1, L, L, RHS_SEED0 + i)[0]) for i in range(n)]
+    setup_s, times, iters = oracle_solve_time(theta, m0, psi, n)
+    timed = times[args.warmup:]
+    value = len(timed) / sum(timed)
+    sample = (f"oracle (FP64 NumPy/SciPy) solves of the m_crit+0.1 mass only, 1 RHS each, "
+              f"{len(timed)} timed after {args.warmup} warm-up; setup {setup_s:.1f} s excluded")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(timed)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "m_crit+0.1 mass only"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "iterations": iters[args.warmup:],
+    }))
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2608_03515_b300 import build as _b
+    _b.build()
+    from paper_2608_03515_b300 import amamg as A
+    from paper_2608_03515_b300 import fixtures as fx
+
+    theta = fx.metropolis_u1(L, L, BETA, SWEEPS, FIELD_SEED)
+    U = torch.from_numpy(fx.links_from_angles(theta)).to(dev)
+    mcrit = load_mcrit()
+    masses = [mcrit + d for d in MASS_OFFSETS]
+    nsteps = args.warmup + args.steps
+    # right-hand sides resident in HBM before the timed region (replicas draw their own)
+    psis = [torch.from_numpy(fx.gaussian_rhs(1, L, L, RHS_SEED0 + 100000 * rank + i)).to(dev) for i in range(nsteps)]
+    x = torch.empty_like(psis[0])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    def build_hiers(prec):
+        hs, setup_ms = [], []
+        for m0 in masses:
+            h = A.setup(U, m0, A.make_params(AGGS, precision=prec, restart=RESTART, tol=TOL))
+            hs.append(h)
+            setup_ms.append(1e3 * A.setup_seconds(h))
+        return hs, setup_ms
+
+    def run(hs, nst=None, skip=0):
+        """Runs steps; returns per-step device ms (events) and per-solve ms."""
+        stream = torch.cuda.current_stream()
+        step_ms, solve_ms, iters, relres = [], [], [], []
+        for i in range(nst if nst is not None else nsteps):
+            flush.zero_()
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(hs) + 1)]
+            evs[0].record(stream)
+            for k, h in enumerate(hs):
+                info = A.solve(h, psis[i], x)
+                evs[k + 1].record(stream)
+                iters.append(info[0].iterations)
+                relres.append(info[0].true_relres)
+                assert info[0].status == A.OK and info[0].true_relres <= TOL, info
+            torch.cuda.synchronize()
+            if i >= skip:
+                step_ms.append(evs[0].elapsed_time(evs[-1]))
+                solve_ms += [evs[k].elapsed_time(evs[k + 1]) for k in range(len(hs))]
+        return step_ms, solve_ms, iters, relres
+
+    hs64, setup64 = build_hiers(A.SOLVE_FP64)
+    hs32, setup32 = build_hiers(A.SOLVE_MIXED)
+
+    # warm-up, then the timed FP64 region
+    run(hs64, nst=args.warmup)
+    launches0 = sum(A.launch_count(h) for h in hs64)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    # timed steps use the right-hand sides after the warm-up ones
+    psis_w = psis
+    step_ms, solve_ms, iters64, relres64 = [], [], [], []
+    stream = torch.cuda.current_stream()
+    for i in range(args.warmup, nsteps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in hs64]
+        e0.record(stream)
+        prev = e0
+        for k, h in enumerate(hs64):
+            info = A.solve(h, psis_w[i], x)
+            evs[k].record(stream)
+            iters64.append(info[0].iterations)
+            relres64.append(info[0].true_relres)
+            if not (info[0].status == A.OK and info[0].true_relres <= TOL):
+                raise RuntimeError(f"solve did not converge: {info}")
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(evs[-1]))
+        solve_ms += [(e0 if k == 0 else evs[k - 1]).elapsed_time(evs[k]) for k in range(len(hs64))]
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall_s = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    launches = sum(A.launch_count(h) for h in hs64) - launches0
+    total_ms = float(np.sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    solves = args.steps * len(masses) * world
+    value = solves / (total_ms * 1e-3)
+
+    # mixed precision on the same inputs
+    run(hs32, nst=args.warmup)
+    st32, sv32, it32, rr32 = run(hs32, nst=nsteps, skip=args.warmup)
+    for r in rr32:
+        assert r <= TOL
+    mixed_value = len(sv32) / (np.sum(st32) * 1e-3) * world
+
+    # end to end through the public API with host buffers
+    psi_h = [p.cpu().pin_memory() for p in psis]
+    x_h = torch.empty(psis[0].shape, dtype=torch.complex128).pin_memory()
+    psi_d = torch.empty_like(psis[0])
+    e2e_ms = []
+    for i in range(nsteps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for h in hs64:
+            psi_d.copy_(psi_h[i], non_blocking=True)
+            A.solve(h, psi_d, x)
+            x_h.copy_(x, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_value = args.steps * len(masses) * world / (np.sum(e2e_ms) * 1e-3)
+    nbytes = psis[0].numel() * 16
+
+    # per-kernel profile: a replay of the timed steps with event-bracketed launches
+    for h in hs64:
+        A.profile_reset(h)
+        A.profile_enable(h, True)
+    run(hs64, nst=nsteps, skip=args.warmup)
+    cats = {}
+    for h in hs64:
+        A.profile_enable(h, False)
+        for name, n, ms, by in A.profile_get(h):
+            c = cats.setdefault(name, [0, 0.0, 0.0])
+            c[0] += n
+            c[1] += ms
+            c[2] += by
+    peak, peak_kind = measured_peaks()
+    dom = max(cats.items(), key=lambda kv: kv[1][1])
+    dname, (dn, dms, dby) = dom
+    achieved = dby / (dms * 1e-3) / 1e9
+    kernel_share = {k: round(v[1] / sum(c[1] for c in cats.values()), 4) for k, v in
+                    sorted(cats.items(), key=lambda kv: -kv[1][1])}
+
+    # stencil bandwidth on working sets larger than L2 (1024^2, random-phase links)
+    d_apply = {}
+    Nd = 1024
+    rng = np.random.Generator(np.random.PCG64(77))
+    Ud = torch.from_numpy(np.exp(1j * rng.uniform(-np.pi, np.pi, size=(2, Nd, Nd)))).to(dev)
+    hd = A.setup(Ud, 0.1, A.make_params([4, 4, 2]))
+    for prec, R, dt in (("f64", 4, torch.complex128), ("f32", 8, torch.complex64)):
+        xin = torch.randn(R, 2, Nd, Nd, dtype=dt, device=dev)
+        yout = torch.empty_like(xin)
+        for _ in range(3):
+            A.apply_D(hd, xin, yout)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        reps = 20
+        ev[0].record(stream)
+        for _ in range(reps):
+            A.apply_D(hd, xin, yout)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / reps
+        cb = 16 if prec == "f64" else 8
+        by = Nd * Nd * (R * 2 * 2 * cb + 2 * cb)
+        gbs = by / (ms * 1e-3) / 1e9
+        d_apply[prec] = {"lattice": f"{Nd}x{Nd}", "rhs": R, "ms": round(ms, 4), "GB/s": round(gbs, 1),
+                         "frac_of_hbm": round(gbs / peak, 3), "bytes_per_launch": by}
+        del xin, yout
+    del hd
+
+    out = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            from oracle import wilson as W
+            psi_flat = [W.to_flat(psis[args.warmup].cpu().numpy()[0])]
+            setup_s, ot, oit = oracle_solve_time(theta, masses[0], psi_flat, 1)
+            cpu = {"value": 1.0 / ot[0], "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+                   "sample": f"1 oracle solve (m_crit+0.1 mass, {oit[0]} iterations, FP64 NumPy/SciPy, sparse "
+                             f"kernels single-threaded); oracle setup {setup_s:.1f} s excluded"}
+        out = {
+            "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": f"{L}x{L}", "levels": 3, "tiles": AGGS,
+                       "restart": RESTART, "tol": TOL, "rhs_per_mass": 1, "masses": len(masses),
+                       "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) between steps"},
+            "e2e": {"value": round(e2e_value, 3), "unit": "solves/s", "h2d_bytes_per_step": nbytes * len(masses),
+                    "d2h_bytes_per_step": nbytes * len(masses)},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "hbm", "kernel": dname, "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                         "peak_source": f"{peak_kind} hbm_gbs", "launches": dn,
+                         "avg_launch_us": round(1e3 * dms / dn, 3),
+                         "bytes_per_launch": round(dby / dn), "pass": "profiled replay of the timed steps"},
+            "kernel_share": kernel_share,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "mixed": {"value": round(mixed_value, 3), "unit": "solves/s", "speedup_vs_fp64": round(mixed_value / value, 3),
+                      "iterations": it32[-len(masses):], "true_relres_max": max(rr32),
+                      "latency_ms": {"p50": round(float(np.percentile(sv32, 50)), 3),
+                                     "p99": round(float(np.percentile(sv32, 99)), 3)},
+                      "setup_ms": [round(s, 2) for s in setup32]},
+            "latency_ms": {"p50": round(float(np.percentile(solve_ms, 50)), 3),
+                           "p99": round(float(np.percentile(solve_ms, 99)), 3)},
+            "iterations": iters64[-len(masses):],
+            "true_relres_max": max(relres64),
+            "setup_ms": [round(s, 2) for s in setup64],
+            "d_apply": d_apply,
+            "wall_s_timed_region": round(wall_s, 3),
+        }
+        print(json.dumps(out))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * amamg.h - C ABI of the B300 library for the SM-AMG preconditioned
+ * Wilson-Dirac solve of the two-dimensional (Schwinger-model) Wilson operator.
+ *
+ * Problem statement (paper: "A first look at Structured-Multiscale Algebraic
+ * Multigrid for Lattice Field Theory"):
+ *   solve D x = psi (Eq. (1)) with the Wilson-Dirac operator D of Eq. (3)
+ *   (Pauli basis of Eq. (4), periodic in x, antiperiodic in t, Eq. (7)), using
+ *   FGMRES preconditioned by an SM-AMG V-cycle (Algorithm 1, Sec. 4): compact
+ *   wirebasket aggregates with overlapping borders, ideal local interpolation
+ *   (Eqs. (14)-(16)), Galerkin coarse operators A_H = P^H A P (Sec. 2).
+ *
+ * Conventions shared by every call
+ *   - Lattice sites n = (t, x), 0 <= t < Nt, 0 <= x < Nx, site index t*Nx + x.
+ *   - Gauge links U: device array of complex128 (two doubles re, im) laid out
+ *     [mu][t][x], mu = 0 the t direction, mu = 1 the x direction.
+ *   - Fine vectors: device arrays [R][spin 2][Nt][Nx] of complex128
+ *     (AMAMG_F64) or complex64 (AMAMG_F32); R right-hand sides back to back.
+ *   - Level-l vectors (l >= 1): [R][2][Nt_l][Nx_l], Nt_l = Nt / (a_0 ... a_{l-1}).
+ *     The coarse variable of vertex (p, q), spin alpha is element
+ *     [alpha][p][q]; vertex (p, q) is fine site (p*a, q*a) of the level below.
+ *   - All device pointers are caller-owned (e.g. allocated by PyTorch); the
+ *     library never frees them and keeps no pointer to them after a call
+ *     returns.  The hierarchy (interpolators, coarse operators, coarsest
+ *     inverse, solver workspace) is owned by the handle and freed by
+ *     amamg_destroy.
+ *   - Every call is ordered on the caller's stream (a cudaStream_t passed as
+ *     void*, NULL = legacy default stream).  A handle is used by one stream at
+ *     a time.  Calls that return data to the host (amamg_solve's info, the
+ *     export functions) synchronise that stream.
+ *   - Errors: every call returns an int status, AMAMG_OK (0) on success, a
+ *     negative AMAMG_ERR_* on failure (no exception or abort crosses the ABI,
+ *     no device assert or trap is used).  amamg_last_error(handle) gives a
+ *     message for the last failure on that handle.
+ */
+#ifndef AMAMG_H
+#define AMAMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct amamg_ctx* amamg_handle;
+
+/* status codes */
+#define AMAMG_OK                 0
+#define AMAMG_NOT_CONVERGED      1   /* max_iter reached; x holds the last iterate */
+#define AMAMG_ERR_INVALID_ARG   -1
+#define AMAMG_ERR_OOM           -2
+#define AMAMG_ERR_CUDA          -3
+#define AMAMG_ERR_SINGULAR      -4   /* a local or coarsest pivot vanished in setup */
+#define AMAMG_ERR_NONFINITE     -5   /* NaN/Inf in a right-hand side or a residual */
+#define AMAMG_ERR_TIMEOUT       -6
+
+/* vector precision of apply-style calls */
+#define AMAMG_F64 0                  /* complex128 vectors, FP64 operators */
+#define AMAMG_F32 1                  /* complex64 vectors, FP32 links, FP16+scale P and coarse blocks */
+
+/* solve precision */
+#define AMAMG_SOLVE_FP64  0          /* every step in FP64 */
+#define AMAMG_SOLVE_MIXED 1          /* FP64 outer FGMRES, FP32 V-cycle, FP64 coarsest solve */
+
+#define AMAMG_MAX_LEVELS 4
+
+typedef struct {
+    int    nlevels;                  /* 2..4 levels including the fine one */
+    int    agg[AMAMG_MAX_LEVELS];    /* tile side a per coarsening step, 2 or 4; a | N_l, N_l/a >= 2 */
+    int    precision;                /* AMAMG_SOLVE_FP64 or AMAMG_SOLVE_MIXED */
+    int    restart;                  /* FGMRES restart length m, 1..64 */
+    int    max_iter;                 /* total Arnoldi steps before AMAMG_NOT_CONVERGED */
+    int    post_smooth;              /* post-smoothing sweeps per level (paper: 2); no pre-smoothing */
+    double tol;                      /* relative residual ||psi - D x|| / ||psi|| */
+} amamg_params;
+
+typedef struct {
+    int    iterations;               /* Arnoldi steps taken for this right-hand side */
+    int    status;                   /* AMAMG_OK, AMAMG_NOT_CONVERGED or AMAMG_ERR_NONFINITE */
+    double true_relres;              /* ||psi - D x|| / ||psi|| recomputed in FP64 at the end */
+} amamg_solve_info;
+
+/* Fills *p with the defaults: 2 levels, agg {4}, FP64, restart 30,
+ * max_iter 3000, 2 post-smoothing sweeps, tol 1e-10. */
+int amamg_default_params(amamg_params* p);
+
+/* Device bytes the hierarchy of a Nt x Nx lattice needs (setup_bytes) and the
+ * solver workspace per right-hand side (per_rhs_bytes); no GPU work, no
+ * allocation.  Used for admission control. */
+int amamg_query_bytes(const amamg_params* p, int Nt, int Nx, int max_rhs,
+                      size_t* setup_bytes, size_t* per_rhs_bytes);
+
+/* Setup phase (Sec. 2; SM-AMG interpolation Sec. 4.1, Eqs. (14)-(16)).
+ * U: device complex128 [2][Nt][Nx] gauge links (read during the call only).
+ * m0: bare mass.  Builds, on the device: wirebasket structure per level, the
+ * local ideal interpolation of every basket (batched dense solves
+ * -A_FF^{-1} A_FV in FP64), the Galerkin coarse operators P^H A P in
+ * block-stencil form, their FP16+scale copies, the coarse smoother's 2x2
+ * diagonal inverses and the coarsest level's inverse (FP64 LU with partial
+ * pivoting carried to the inverse).  Requires Nt, Nx even and divisible by
+ * every tile side, smoothed coarse levels with extents divisible by 4.
+ * *out receives the handle; AMAMG_ERR_SINGULAR if a pivot vanishes. */
+int amamg_setup(const amamg_params* p, const void* U, int Nt, int Nx, double m0,
+                void* stream, amamg_handle* out);
+
+/* Solve D x_r = psi_r for R right-hand sides (FGMRES(m), right-preconditioned
+ * by one V-cycle per step; Sec. 1 and Sec. 5).  psi, x: device complex128
+ * [R][2][Nt][Nx]; x is overwritten with the solution (start vector 0).
+ * info: host array of R records.  Returns AMAMG_OK when every right-hand side
+ * converged, AMAMG_NOT_CONVERGED if some stopped at max_iter, or an error. */
+int amamg_solve(amamg_handle h, const void* psi, void* x, int R, void* stream,
+                amamg_solve_info* info);
+
+/* out = D in on the fine lattice, Eq. (3).  precision AMAMG_F64 or AMAMG_F32. */
+int amamg_apply_D(amamg_handle h, const void* in, void* out, int R, int precision, void* stream);
+
+/* fine_out = P_l coarse_in: interpolation from level l+1 to level l
+ * (Eq. (16) rows for owned edge/interior sites, identity on vertices). */
+int amamg_apply_P(amamg_handle h, int level, const void* coarse_in, void* fine_out,
+                  int R, int precision, void* stream);
+
+/* coarse_out = P_l^H fine_in: restriction from level l to level l+1 (Sec. 2). */
+int amamg_apply_PH(amamg_handle h, int level, const void* fine_in, void* coarse_out,
+                   int R, int precision, void* stream);
+
+/* out = A_l in with the Galerkin operator of level l >= 1 (A_l = P^H A_{l-1} P). */
+int amamg_apply_coarse(amamg_handle h, int level, const void* in, void* out,
+                       int R, int precision, void* stream);
+
+/* sweeps block Gauss-Seidel sweeps on A_l e = r, starting from the e passed in
+ * (red-black on the fine level, 16 colours (t mod 4, x mod 4) on coarse
+ * levels; "block solver as smoother", Sec. 5). */
+int amamg_smooth(amamg_handle h, int level, const void* r, void* e, int R,
+                 int sweeps, int precision, void* stream);
+
+/* e = A_L^{-1} r on the coarsest level, in FP64 (complex128 vectors). */
+int amamg_coarsest_solve(amamg_handle h, const void* r, void* e, int R, void* stream);
+
+/* e = M(r): one V-cycle of Algorithm 1 on the fine level with start vector 0,
+ * no pre-smoothing and post_smooth sweeps per level. */
+int amamg_vcycle(amamg_handle h, const void* r, void* e, int R, int precision, void* stream);
+
+/* Integer structure of level l (host arrays; bit-exact tests):
+ * role[Nt_l*Nx_l] (0 vertex, 1 edge, 2 interior), owner_tile[Nt_l*Nx_l]
+ * (index p*(Nx_l/a)+q of the basket a site takes its formula from),
+ * nbr_offsets[2*K] canonical (dt mod Nt_{l+1}, dx mod Nx_{l+1}) block offsets of
+ * the level-(l+1) operator, lexicographically sorted, *nbr_count = K.
+ * Arrays may be NULL to skip them; nbr_offsets must hold 2*32 ints. */
+int amamg_export_structure(amamg_handle h, int level, int32_t* role, int32_t* owner_tile,
+                           int32_t* nbr_offsets, int32_t* nbr_count);
+
+/* Lattice extents and block-offset count of level l. */
+int amamg_level_info(amamg_handle h, int level, int* Nt_l, int* Nx_l, int* n_offsets);
+
+/* Copies level-l data to caller device buffers (complex128):
+ * amamg_export_P: P_l tiles [nT][8][2(a^2-1)] (column 2c+beta = corner c of
+ *   the tile's basket, c = 2 di + dj for corner (p+di, q+dj); row 2(l-1)+alpha
+ *   for in-tile site l = i*a + j, l >= 1);
+ * amamg_export_coarse: A_l blocks [K][4][n_l] (entry 2 alpha + beta) for l >= 1. */
+int amamg_export_P(amamg_handle h, int level, void* out, void* stream);
+int amamg_export_coarse(amamg_handle h, int level, void* out, void* stream);
+
+/* Kernel timing for measurement: when enabled, every kernel the handle
+ * launches is bracketed by CUDA events on its stream.  amamg_profile_get
+ * synchronises, then reports for kernel category idx (0..count-1) its name,
+ * launches, summed device time and algorithmic bytes moved.  Returns
+ * AMAMG_ERR_INVALID_ARG past the last category. */
+int amamg_profile_enable(amamg_handle h, int on);
+int amamg_profile_reset(amamg_handle h);
+int amamg_profile_get(amamg_handle h, int idx, const char** name, long long* launches,
+                      double* total_ms, double* bytes);
+
+/* Number of kernels the handle has launched since setup (all categories). */
+long long amamg_launch_count(amamg_handle h);
+
+/* Seconds of device time of the last amamg_setup (measured with events). */
+double amamg_setup_seconds(amamg_handle h);
+
+int amamg_destroy(amamg_handle h);
+const char* amamg_status_string(int status);
+const char* amamg_last_error(amamg_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMAMG_H */

@@ -1,0 +1,896 @@
+// Host engine and C ABI: hierarchy setup (Sec. 2, Sec. 4.1), the V-cycle of
+// Algorithm 1 used as preconditioner, the FP64 flexible GMRES outer solver, and
+// the apply/export entry points declared in include/amamg.h.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <set>
+#include <utility>
+
+#include "context.h"
+
+namespace {
+
+#define CK(call)                                                              \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) {                                                  \
+      h->err = std::string(#call) + ": " + cudaGetErrorString(e_);           \
+      return e_ == cudaErrorMemoryAllocation ? AMAMG_ERR_OOM : AMAMG_ERR_CUDA; \
+    }                                                                         \
+  } while (0)
+
+#define CKS(expr)              \
+  do {                         \
+    int s_ = (expr);           \
+    if (s_ != AMAMG_OK) return s_; \
+  } while (0)
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ----------------------------------------------------------------- profiling
+int cat_id(amamg_ctx* h, const char* name) {
+  for (size_t i = 0; i < h->cats.size(); ++i)
+    if (h->cats[i].name == name) return (int)i;
+  h->cats.push_back(ProfCat{name});
+  return (int)h->cats.size() - 1;
+}
+
+cudaEvent_t take_event(amamg_ctx* h) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    h->ev_pool.push_back(e);
+  }
+  return h->ev_pool[h->ev_used++];
+}
+
+// Wraps one kernel launch: counts it and, when profiling, brackets it with events.
+template <typename F>
+int launch(amamg_ctx* h, const char* name, double bytes, cudaStream_t st, F&& f) {
+  ProfRec rec{-1, nullptr, nullptr, bytes};
+  if (h->prof) {
+    rec.cat = cat_id(h, name);
+    rec.a = take_event(h);
+    rec.b = take_event(h);
+    if (rec.a) cudaEventRecord(rec.a, st);
+  }
+  cudaError_t e = f();
+  if (e != cudaSuccess) {
+    h->err = std::string(name) + ": " + cudaGetErrorString(e);
+    return AMAMG_ERR_CUDA;
+  }
+  h->launches++;
+  if (h->prof && rec.a && rec.b) {
+    cudaEventRecord(rec.b, st);
+    h->recs.push_back(rec);
+  }
+  return AMAMG_OK;
+}
+
+int collect_profile(amamg_ctx* h) {
+  for (auto& r : h->recs) {
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return AMAMG_ERR_CUDA;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    ProfCat& c = h->cats[r.cat];
+    c.launches++;
+    c.ms += ms;
+    c.bytes += r.bytes;
+  }
+  h->recs.clear();
+  h->ev_used = 0;
+  return AMAMG_OK;
+}
+
+template <typename P>
+int dalloc(amamg_ctx* h, P** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return AMAMG_OK;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(P));
+  if (e != cudaSuccess) {
+    h->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    return AMAMG_ERR_OOM;
+  }
+  return AMAMG_OK;
+}
+
+template <typename P>
+void dfree(P*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+// ----------------------------------------------------------------- structure
+Offsets wilson_offsets(int Nt, int Nx) {
+  std::set<std::pair<int, int>> s = {{0, 0}, {1 % Nt, 0}, {(Nt - 1) % Nt, 0}, {0, 1 % Nx}, {0, (Nx - 1) % Nx}};
+  Offsets o{};
+  o.K = 0;
+  for (auto& p : s) { o.dt[o.K] = p.first; o.dx[o.K] = p.second; ++o.K; }
+  return o;
+}
+
+// Block offsets of P^H A P from the structural patterns (translation invariant
+// under the tile ownership rule, so coarse site 0 represents every row): the
+// support of coarse column 0 is its own vertex site plus the owned sites of the
+// four tiles that have it as a corner; A widens it by its offsets; each reached
+// site contributes its vertex (vertex row) or its tile's four corners.
+int coarse_offsets(const Offsets& fine, int Nt, int Nx, int a, Offsets* out) {
+  const int Np = Nt / a, Nq = Nx / a;
+  std::set<std::pair<int, int>> W;
+  std::vector<std::pair<int, int>> supp;
+  supp.push_back({0, 0});
+  for (int c = 0; c < 4; ++c) {
+    const int pT = wrap(-(c >> 1), Np), qT = wrap(-(c & 1), Nq);
+    for (int i = 0; i < a; ++i)
+      for (int j = 0; j < a; ++j)
+        if (i || j) supp.push_back({pT * a + i, qT * a + j});
+  }
+  for (auto& s : supp) {
+    for (int k = 0; k < fine.K; ++k) {
+      const int t = wrap(s.first + fine.dt[k], Nt), x = wrap(s.second + fine.dx[k], Nx);
+      const int pt = t / a, qt = x / a;
+      if (t % a == 0 && x % a == 0) {
+        W.insert({pt, qt});
+      } else {
+        for (int c = 0; c < 4; ++c) W.insert({wrap(pt + (c >> 1), Np), wrap(qt + (c & 1), Nq)});
+      }
+    }
+  }
+  if ((int)W.size() > AMAMG_MAX_OFFSETS) return AMAMG_ERR_INVALID_ARG;
+  Offsets o{};
+  o.K = 0;
+  for (auto& p : W) { o.dt[o.K] = p.first; o.dx[o.K] = p.second; ++o.K; }
+  *out = o;
+  return AMAMG_OK;
+}
+
+// ----------------------------------------------------------------- workspace
+int ensure_vcycle_ws(amamg_ctx* h, int R) {
+  if (R <= h->Rcap) return AMAMG_OK;
+  for (auto& L : h->lv) {
+    dfree(L.r64); dfree(L.e64); dfree(L.r32); dfree(L.e32);
+  }
+  for (size_t l = 1; l < h->lv.size(); ++l) {
+    Level& L = h->lv[l];
+    const size_t m = (size_t)R * 2 * L.n;
+    CKS(dalloc(h, &L.r64, m)); CKS(dalloc(h, &L.e64, m));
+    CKS(dalloc(h, &L.r32, m)); CKS(dalloc(h, &L.e32, m));
+  }
+  h->Rcap = R;
+  return AMAMG_OK;
+}
+
+int ensure_solver_ws(amamg_ctx* h, int R) {
+  const int m = h->prm.restart;
+  if (R <= h->Rsolve && m <= h->mcap) return AMAMG_OK;
+  dfree(h->V); dfree(h->Z64); dfree(h->Z32); dfree(h->v32); dfree(h->w); dfree(h->res);
+  dfree(h->partial); dfree(h->d_h); dfree(h->d_inv); dfree(h->d_y);
+  if (h->h_h) cudaFreeHost(h->h_h);
+  if (h->h_y) cudaFreeHost(h->h_y);
+  h->h_h = h->h_y = nullptr;
+  const size_t len = 2 * (size_t)h->lv[0].n;
+  CKS(dalloc(h, &h->V, (size_t)(m + 1) * R * len));
+  if (h->prm.precision == AMAMG_SOLVE_MIXED) {
+    CKS(dalloc(h, &h->Z32, (size_t)m * R * len));
+    CKS(dalloc(h, &h->v32, (size_t)R * len));
+  } else {
+    CKS(dalloc(h, &h->Z64, (size_t)m * R * len));
+  }
+  CKS(dalloc(h, &h->w, (size_t)R * len));
+  CKS(dalloc(h, &h->res, (size_t)R * len));
+  h->partial_elems = (size_t)R * (m + 1) * dot_blocks((long)len);
+  CKS(dalloc(h, &h->partial, h->partial_elems));
+  CKS(dalloc(h, &h->d_h, (size_t)R * 3 * (m + 2)));
+  CKS(dalloc(h, &h->d_inv, (size_t)R));
+  CKS(dalloc(h, &h->d_y, (size_t)R * m));
+  CK(cudaMallocHost((void**)&h->h_h, sizeof(double2) * (size_t)R * 3 * (m + 2)));
+  CK(cudaMallocHost((void**)&h->h_y, sizeof(double2) * (size_t)R * m));
+  h->Rsolve = R;
+  h->mcap = m;
+  return AMAMG_OK;
+}
+
+// ----------------------------------------------------------------- level operations
+// bytes below are the algorithmic traffic of each launch (each input read once,
+// each output written once), used for the achieved-bandwidth figures.
+
+template <typename T>
+int op_dslash(amamg_ctx* h, const typename cplx<T>::type* in, typename cplx<T>::type* out,
+              const typename cplx<T>::type* b, int R, cudaStream_t st);
+
+template <>
+int op_dslash<double>(amamg_ctx* h, const double2* in, double2* out, const double2* b, int R, cudaStream_t st) {
+  const Level& L = h->lv[0];
+  const double bytes = (double)L.n * (R * (32.0 + 32.0 + (b ? 32.0 : 0.0)) + 32.0);
+  return launch(h, b ? "dslash_residual_f64" : "dslash_f64", bytes, st, [&] {
+    return launch_dslash<double2, double2, double>(in, out, b, h->U64, h->m0 + 2.0, L.Nt, L.Nx, R, st);
+  });
+}
+
+template <>
+int op_dslash<float>(amamg_ctx* h, const float2* in, float2* out, const float2* b, int R, cudaStream_t st) {
+  const Level& L = h->lv[0];
+  const double bytes = (double)L.n * (R * (16.0 + 16.0 + (b ? 16.0 : 0.0)) + 16.0);
+  return launch(h, "dslash_f32", bytes, st, [&] {
+    return launch_dslash<float2, float2, float>(in, out, b, h->U32, (float)(h->m0 + 2.0), L.Nt, L.Nx, R, st);
+  });
+}
+
+template <typename T>
+int op_smooth(amamg_ctx* h, int l, typename cplx<T>::type* e, const typename cplx<T>::type* r, int R, int sweeps,
+              cudaStream_t st);
+
+template <typename T>
+int smooth_impl(amamg_ctx* h, int l, typename cplx<T>::type* e, const typename cplx<T>::type* r, int R, int sweeps,
+                cudaStream_t st) {
+  const Level& L = h->lv[l];
+  constexpr bool f64 = sizeof(T) == 8;
+  const double cb = f64 ? 16.0 : 8.0;
+  if (l == 0) {
+    const T inv = (T)(1.0 / (h->m0 + 2.0));
+    const typename cplx<T>::type* U;
+    if constexpr (f64) U = h->U64; else U = h->U32;
+    // half sweep: read r, read + write e on half the sites, links once
+    const double bytes = (double)L.n / 2 * (R * 2 * 3 * cb) + (double)L.n * 2 * cb / 2;
+    for (int s = 0; s < sweeps; ++s)
+      for (int c = 0; c < 2; ++c)
+        CKS(launch(h, f64 ? "rb_smooth_f64" : "rb_smooth_f32", bytes, st, [&] {
+          return launch_rb_half<T>(e, r, U, inv, L.Nt, L.Nx, c, R, st);
+        }));
+    return AMAMG_OK;
+  }
+  const double blk = f64 ? 16.0 * 4 : (4.0 * 4 + 4.0);
+  const double bytes = (double)L.n / 16 * ((L.off.K - 1) * blk + 4 * cb + R * 2 * 3 * cb);
+  for (int s = 0; s < sweeps; ++s)
+    for (int c = 0; c < 16; ++c) {
+      int rc;
+      if constexpr (f64)
+        rc = launch(h, "coarse_smooth_f64", bytes, st, [&] {
+          return launch_coarse_colour<double, double2>(e, r, L.B64, nullptr, L.Dinv64, L.off, L.Nt, L.Nx, c, R, st);
+        });
+      else
+        rc = launch(h, "coarse_smooth_f32", bytes, st, [&] {
+          return launch_coarse_colour<float, __half2>(e, r, L.B16, L.Bs, L.Dinv32, L.off, L.Nt, L.Nx, c, R, st);
+        });
+      CKS(rc);
+    }
+  return AMAMG_OK;
+}
+
+template <typename T>
+int op_prolong(amamg_ctx* h, int l, const typename cplx<T>::type* ec, typename cplx<T>::type* ef, int R,
+               cudaStream_t st) {
+  const Level& L = h->lv[l];
+  constexpr bool f64 = sizeof(T) == 8;
+  const double cb = f64 ? 16.0 : 8.0;
+  const double pbytes = (double)L.nT * 8 * L.nrows * (f64 ? 16.0 : 4.0) + (f64 ? 0.0 : 4.0 * L.nT);
+  const double bytes = pbytes + (double)R * 2 * (L.n + h->lv[l + 1].n) * cb;
+  if constexpr (f64)
+    return launch(h, "prolong_f64", bytes, st, [&] {
+      return launch_prolong<double, double2>(ec, ef, L.P64, nullptr, L.Nx, L.a, L.Np, L.Nq, R, st);
+    });
+  else
+    return launch(h, "prolong_f32", bytes, st, [&] {
+      return launch_prolong<float, __half2>(ec, ef, L.P16, L.Ps, L.Nx, L.a, L.Np, L.Nq, R, st);
+    });
+}
+
+template <typename T>
+int op_restrict(amamg_ctx* h, int l, const typename cplx<T>::type* ef, typename cplx<T>::type* ec, int R,
+                cudaStream_t st) {
+  const Level& L = h->lv[l];
+  constexpr bool f64 = sizeof(T) == 8;
+  const double cb = f64 ? 16.0 : 8.0;
+  const double pbytes = (double)L.nT * 8 * L.nrows * (f64 ? 16.0 : 4.0) + (f64 ? 0.0 : 4.0 * L.nT);
+  const double bytes = pbytes + (double)R * 2 * (L.n + h->lv[l + 1].n) * cb;
+  if constexpr (f64)
+    return launch(h, "restrict_f64", bytes, st, [&] {
+      return launch_restrict<double, double2>(ef, ec, L.P64, nullptr, L.Nx, L.a, L.Np, L.Nq, R, st);
+    });
+  else
+    return launch(h, "restrict_f32", bytes, st, [&] {
+      return launch_restrict<float, __half2>(ef, ec, L.P16, L.Ps, L.Nx, L.a, L.Np, L.Nq, R, st);
+    });
+}
+
+template <typename T>
+int op_coarse(amamg_ctx* h, int l, const typename cplx<T>::type* in, typename cplx<T>::type* out,
+              const typename cplx<T>::type* b, int R, cudaStream_t st) {
+  const Level& L = h->lv[l];
+  constexpr bool f64 = sizeof(T) == 8;
+  const double cb = f64 ? 16.0 : 8.0;
+  const double blk = f64 ? 16.0 * 4 : (4.0 * 4 + 4.0);
+  const double bytes = (double)L.n * (L.off.K * blk + R * 2 * (b ? 3 : 2) * cb);
+  if constexpr (f64)
+    return launch(h, "coarse_apply_f64", bytes, st, [&] {
+      return launch_coarse_apply<double, double2>(in, out, b, L.B64, nullptr, L.off, L.Nt, L.Nx, R, st);
+    });
+  else
+    return launch(h, "coarse_apply_f32", bytes, st, [&] {
+      return launch_coarse_apply<float, __half2>(in, out, b, L.B16, L.Bs, L.off, L.Nt, L.Nx, R, st);
+    });
+}
+
+template <typename Cv>
+int op_coarsest(amamg_ctx* h, const Cv* r, Cv* e, int R, cudaStream_t st) {
+  const double bytes = (double)h->nd * h->nd * 16.0 + (double)R * 2 * h->nd * sizeof(Cv);
+  return launch(h, "coarsest_gemv_f64", bytes, st,
+                [&] { return launch_dense_gemv<Cv>(h->Ainv, r, e, h->nd, R, st); });
+}
+
+// V-cycle of Algorithm 1 (start vector 0, no pre-smoothing) from level l:
+// e = P M_{l+1}(P^H r), then post-smoothing sweeps on A_l e = r.
+template <typename T>
+int vcycle_from(amamg_ctx* h, int l, const typename cplx<T>::type* r, typename cplx<T>::type* e, int R,
+                cudaStream_t st) {
+  const int Lc = (int)h->lv.size() - 1;
+  if (l == Lc) return op_coarsest(h, r, e, R, st);
+  Level& C = h->lv[l + 1];
+  typename cplx<T>::type *rc, *ec;
+  if constexpr (sizeof(T) == 8) { rc = C.r64; ec = C.e64; } else { rc = C.r32; ec = C.e32; }
+  CKS(op_restrict<T>(h, l, r, rc, R, st));
+  CKS(vcycle_from<T>(h, l + 1, rc, ec, R, st));
+  CKS(op_prolong<T>(h, l, ec, e, R, st));
+  return smooth_impl<T>(h, l, e, r, R, h->prm.post_smooth, st);
+}
+
+// ----------------------------------------------------------------- FGMRES
+int norms(amamg_ctx* h, const double2* X, size_t xr, long len, int R, double2* out, int ldo, int off, double* inv,
+          cudaStream_t st) {
+  const int nb = dot_blocks(len);
+  CKS(launch(h, "gs_dots", (double)R * len * 16.0, st,
+             [&] { return launch_dots(X, 0, xr, X, xr, len, 1, R, h->partial, st); }));
+  return launch(h, "gs_reduce", (double)R * nb * 16.0, st,
+                [&] { return launch_reduce(h->partial, nb, 1, R, out, ldo, off, 1, inv, st); });
+}
+
+// solve the upper-triangular k x k system of the rotated Hessenberg matrix
+void back_solve(const std::vector<double2>& H, int ldh, const std::vector<double2>& g, int k, double2* y) {
+  for (int i = k - 1; i >= 0; --i) {
+    double2 s = g[i];
+    for (int j = i + 1; j < k; ++j) s -= cmul(H[(size_t)i * ldh + j], y[j]);
+    const double2 d = H[(size_t)i * ldh + i];
+    const double dd = d.x * d.x + d.y * d.y;
+    y[i] = make_double2((s.x * d.x + s.y * d.y) / dd, (s.y * d.x - s.x * d.y) / dd);
+  }
+}
+
+int fgmres(amamg_ctx* h, const double2* psi, double2* x, int R, cudaStream_t st, amamg_solve_info* info) {
+  const int m = h->prm.restart;
+  const long len = 2L * h->lv[0].n;
+  const size_t vr = (size_t)len, vi = (size_t)R * len;
+  const bool mixed = h->prm.precision == AMAMG_SOLVE_MIXED;
+  CKS(ensure_vcycle_ws(h, R));
+  CKS(ensure_solver_ws(h, R));
+  const int ldh = 3 * (m + 2);
+  double2* d_h1 = h->d_h;             // [R][ldh]: h1 at 0, h2 at m+2, norm at 2(m+2)
+  // ||psi||
+  CKS(norms(h, psi, vr, len, R, d_h1, ldh, 2 * (m + 2), h->d_inv, st));
+  CK(cudaMemcpyAsync(h->h_h, h->d_h, sizeof(double2) * R * ldh, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  std::vector<double> bnorm(R), relres(R, 0.0);
+  std::vector<int> iters(R, 0), done(R, 0), status(R, AMAMG_OK);
+  int nonfinite = 0;
+  for (int r = 0; r < R; ++r) {
+    bnorm[r] = h->h_h[(size_t)r * ldh + 2 * (m + 2)].x;
+    if (!std::isfinite(bnorm[r])) { status[r] = AMAMG_ERR_NONFINITE; done[r] = 1; nonfinite = 1; }
+    if (bnorm[r] == 0.0) done[r] = 1;
+  }
+  CK(cudaMemsetAsync(x, 0, sizeof(double2) * R * len, st));
+  const double tol = h->prm.tol;
+  int total = 0;
+  // per-RHS Arnoldi state
+  std::vector<std::vector<double2>> H(R, std::vector<double2>((size_t)(m + 1) * m));
+  std::vector<std::vector<double2>> g(R, std::vector<double2>(m + 1));
+  std::vector<std::vector<double>> cs(R, std::vector<double>(m));
+  std::vector<std::vector<double2>> sn(R, std::vector<double2>(m));
+  std::vector<int> k(R), building(R);
+  while (true) {
+    // true residual r = psi - D x and its norm
+    CKS(op_dslash<double>(h, x, h->res, psi, R, st));
+    CKS(norms(h, h->res, vr, len, R, d_h1, ldh, 2 * (m + 2), h->d_inv, st));
+    CK(cudaMemcpyAsync(h->h_h, h->d_h, sizeof(double2) * R * ldh, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    bool all = true;
+    for (int r = 0; r < R; ++r) {
+      if (status[r] == AMAMG_ERR_NONFINITE) continue;
+      const double beta = h->h_h[(size_t)r * ldh + 2 * (m + 2)].x;
+      if (!std::isfinite(beta)) { status[r] = AMAMG_ERR_NONFINITE; done[r] = 1; nonfinite = 1; continue; }
+      relres[r] = bnorm[r] > 0 ? beta / bnorm[r] : 0.0;
+      if (relres[r] <= tol) done[r] = 1;
+      if (!done[r]) all = false;
+      g[r].assign(m + 1, make_double2(0.0, 0.0));
+      g[r][0] = make_double2(beta, 0.0);
+    }
+    if (all || total >= h->prm.max_iter) break;
+    // V[0] = r / beta
+    CKS(launch(h, "scale_copy", (double)R * len * 32.0, st, [&] {
+      return launch_scale_copy<double2>(h->V, vr, h->res, vr, h->d_inv, len, R, st);
+    }));
+    for (int r = 0; r < R; ++r) { k[r] = 0; building[r] = !done[r]; }
+    int j = 0;
+    for (; j < m; ++j) {
+      const double2* vj = h->V + (size_t)j * vi;
+      // z_j = M(v_j)
+      if (mixed) {
+        float2* zj = h->Z32 + (size_t)j * vi;
+        CKS(launch(h, "cast_f64_f32", (double)R * len * 24.0, st,
+                   [&] { return launch_cast<double2, float2>(vj, h->v32, (long)R * len, st); }));
+        CKS(vcycle_from<float>(h, 0, h->v32, zj, R, st));
+        const Level& L = h->lv[0];
+        CKS(launch(h, "dslash_mixed", (double)L.n * (R * (16.0 + 32.0) + 32.0), st, [&] {
+          return launch_dslash<float2, double2, double>(zj, h->w, nullptr, h->U64, h->m0 + 2.0, L.Nt, L.Nx, R, st);
+        }));
+      } else {
+        double2* zj = h->Z64 + (size_t)j * vi;
+        CKS(vcycle_from<double>(h, 0, vj, zj, R, st));
+        CKS(op_dslash<double>(h, zj, h->w, nullptr, R, st));
+      }
+      // classical Gram-Schmidt, twice
+      const int J = j + 1;
+      const int nb = dot_blocks(len);
+      for (int pass = 0; pass < 2; ++pass) {
+        const int off = pass * (m + 2);
+        CKS(launch(h, "gs_dots", (double)R * len * 16.0 * (J + 1), st,
+                   [&] { return launch_dots(h->V, vi, vr, h->w, vr, len, J, R, h->partial, st); }));
+        CKS(launch(h, "gs_reduce", (double)R * J * nb * 16.0, st,
+                   [&] { return launch_reduce(h->partial, nb, J, R, d_h1, ldh, off, 0, nullptr, st); }));
+        CKS(launch(h, "gs_update", (double)R * len * 16.0 * (J + 2), st, [&] {
+          return launch_multi_axpy<double2>(h->w, vr, h->V, vi, vr, d_h1 + off, ldh, J, -1.0, len, R, st);
+        }));
+      }
+      CKS(norms(h, h->w, vr, len, R, d_h1, ldh, 2 * (m + 2), h->d_inv, st));
+      CKS(launch(h, "scale_copy", (double)R * len * 32.0, st, [&] {
+        return launch_scale_copy<double2>(h->V + (size_t)(j + 1) * vi, vr, h->w, vr, h->d_inv, len, R, st);
+      }));
+      CK(cudaMemcpyAsync(h->h_h, h->d_h, sizeof(double2) * R * ldh, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      ++total;
+      bool any = false;
+      for (int r = 0; r < R; ++r) {
+        if (!building[r]) continue;
+        const double2* hh = h->h_h + (size_t)r * ldh;
+        std::vector<double2>& Hr = H[r];
+        for (int i = 0; i <= j; ++i) Hr[(size_t)i * m + j] = hh[i] + hh[(m + 2) + i];
+        const double hn = hh[2 * (m + 2)].x;
+        if (!std::isfinite(hn)) { status[r] = AMAMG_ERR_NONFINITE; done[r] = 1; building[r] = 0; nonfinite = 1; continue; }
+        // earlier rotations, then a new one that annihilates H[j+1][j]
+        for (int i = 0; i < j; ++i) {
+          const double2 a = Hr[(size_t)i * m + j], b = Hr[(size_t)(i + 1) * m + j];
+          Hr[(size_t)i * m + j] = cs[r][i] * a + cmul(sn[r][i], b);
+          Hr[(size_t)(i + 1) * m + j] = cs[r][i] * b - cmulc(sn[r][i], a);
+        }
+        const double2 a = Hr[(size_t)j * m + j];
+        const double aa = std::sqrt(a.x * a.x + a.y * a.y);
+        double c;
+        double2 s;
+        if (hn == 0.0) { c = 1.0; s = make_double2(0.0, 0.0); }
+        else if (aa == 0.0) { c = 0.0; s = make_double2(1.0, 0.0); }
+        else {
+          const double rr = std::hypot(aa, hn);
+          c = aa / rr;
+          s = make_double2(a.x / aa * hn / rr, a.y / aa * hn / rr);   // (a/|a|) conj(hn) / r, hn real
+        }
+        cs[r][j] = c;
+        sn[r][j] = s;
+        Hr[(size_t)j * m + j] = c * a + hn * s;
+        const double2 gj = g[r][j];
+        g[r][j + 1] = -1.0 * cmulc(s, gj);
+        g[r][j] = c * gj;
+        iters[r]++;
+        k[r] = j + 1;
+        const double est = std::sqrt(cabs2(g[r][j + 1]));
+        if (est <= tol * bnorm[r] || hn == 0.0) building[r] = 0;
+        if (building[r]) any = true;
+      }
+      if (!any || total >= h->prm.max_iter) { ++j; break; }
+    }
+    // x += Z y  (per right-hand side k[r] columns; the rest zero)
+    const int jmax = j < m ? j : m;
+    for (int r = 0; r < R; ++r) {
+      double2* y = h->h_y + (size_t)r * m;
+      for (int i = 0; i < m; ++i) y[i] = make_double2(0.0, 0.0);
+      if (k[r] > 0 && status[r] != AMAMG_ERR_NONFINITE) back_solve(H[r], m, g[r], k[r], y);
+    }
+    CK(cudaMemcpyAsync(h->d_y, h->h_y, sizeof(double2) * R * m, cudaMemcpyHostToDevice, st));
+    if (mixed)
+      CKS(launch(h, "x_update", (double)R * len * (8.0 * jmax + 32.0), st, [&] {
+        return launch_multi_axpy<float2>(x, vr, h->Z32, vi, vr, h->d_y, m, jmax, 1.0, len, R, st);
+      }));
+    else
+      CKS(launch(h, "x_update", (double)R * len * (16.0 * jmax + 32.0), st, [&] {
+        return launch_multi_axpy<double2>(x, vr, h->Z64, vi, vr, h->d_y, m, jmax, 1.0, len, R, st);
+      }));
+  }
+  int rc = AMAMG_OK;
+  for (int r = 0; r < R; ++r) {
+    if (status[r] == AMAMG_OK && !done[r]) status[r] = AMAMG_NOT_CONVERGED;
+    if (info) { info[r].iterations = iters[r]; info[r].status = status[r]; info[r].true_relres = relres[r]; }
+    if (status[r] == AMAMG_NOT_CONVERGED && rc == AMAMG_OK) rc = AMAMG_NOT_CONVERGED;
+  }
+  if (nonfinite) { h->err = "non-finite value in a right-hand side or residual"; rc = AMAMG_ERR_NONFINITE; }
+  return rc;
+}
+
+// ----------------------------------------------------------------- setup
+int check_params(const amamg_params* p, int Nt, int Nx, std::string* why) {
+  if (!p) { *why = "params is NULL"; return AMAMG_ERR_INVALID_ARG; }
+  if (p->nlevels < 2 || p->nlevels > AMAMG_MAX_LEVELS) { *why = "nlevels must be 2..4"; return AMAMG_ERR_INVALID_ARG; }
+  if (p->precision != AMAMG_SOLVE_FP64 && p->precision != AMAMG_SOLVE_MIXED) { *why = "bad precision"; return AMAMG_ERR_INVALID_ARG; }
+  if (p->restart < 1 || p->restart > 64) { *why = "restart must be 1..64"; return AMAMG_ERR_INVALID_ARG; }
+  if (p->max_iter < 1 || p->post_smooth < 0 || !(p->tol > 0.0)) { *why = "bad max_iter/post_smooth/tol"; return AMAMG_ERR_INVALID_ARG; }
+  if (Nt < 4 || Nx < 4 || (Nt & 1) || (Nx & 1)) { *why = "Nt, Nx must be even and >= 4"; return AMAMG_ERR_INVALID_ARG; }
+  int nt = Nt, nx = Nx;
+  for (int l = 0; l + 1 < p->nlevels; ++l) {
+    const int a = p->agg[l];
+    if (a != 2 && a != 4) { *why = "tile sides must be 2 or 4"; return AMAMG_ERR_INVALID_ARG; }
+    if (nt % a || nx % a || nt / a < 2 || nx / a < 2) { *why = "tile side does not divide the level extents"; return AMAMG_ERR_INVALID_ARG; }
+    if (l >= 1 && (nt % 4 || nx % 4)) { *why = "smoothed coarse levels need extents divisible by 4"; return AMAMG_ERR_INVALID_ARG; }
+    nt /= a; nx /= a;
+  }
+  const double nd = 2.0 * nt * nx;
+  if (nd > 16384) { *why = "coarsest level too large for the dense inverse (2 Nt_L Nx_L > 16384)"; return AMAMG_ERR_INVALID_ARG; }
+  return AMAMG_OK;
+}
+
+void free_all(amamg_ctx* h) {
+  for (auto& L : h->lv) {
+    dfree(L.B64); dfree(L.B16); dfree(L.Bs); dfree(L.Dinv64); dfree(L.Dinv32);
+    dfree(L.P64); dfree(L.P16); dfree(L.Ps);
+    dfree(L.r64); dfree(L.e64); dfree(L.r32); dfree(L.e32);
+  }
+  dfree(h->U64); dfree(h->U32); dfree(h->Ainv); dfree(h->d_err);
+  dfree(h->V); dfree(h->Z64); dfree(h->Z32); dfree(h->v32); dfree(h->w); dfree(h->res);
+  dfree(h->partial); dfree(h->d_h); dfree(h->d_inv); dfree(h->d_y);
+  if (h->h_h) cudaFreeHost(h->h_h);
+  if (h->h_y) cudaFreeHost(h->h_y);
+  h->h_h = h->h_y = nullptr;
+  for (auto e : h->ev_pool) cudaEventDestroy(e);
+  h->ev_pool.clear();
+}
+
+int do_setup(amamg_ctx* h, const void* Uin, cudaStream_t st) {
+  const int L = h->prm.nlevels;
+  h->lv.resize(L);
+  {
+    Level& F = h->lv[0];
+    F.Nt = h->Nt; F.Nx = h->Nx; F.n = h->Nt * h->Nx;
+  }
+  const size_t nl = 2 * (size_t)h->lv[0].n;
+  CKS(dalloc(h, &h->U64, nl));
+  CKS(dalloc(h, &h->U32, nl));
+  CKS(dalloc(h, &h->d_err, 1));
+  CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+  CK(cudaMemcpyAsync(h->U64, Uin, nl * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  CKS(launch(h, "setup_cast_links", nl * 24.0, st,
+             [&] { return launch_cast<double2, float2>(h->U64, h->U32, (long)nl, st); }));
+  Offsets fine_off = wilson_offsets(h->Nt, h->Nx);
+  for (int l = 0; l + 1 < L; ++l) {
+    Level& F = h->lv[l];
+    Level& C = h->lv[l + 1];
+    F.a = h->prm.agg[l];
+    F.Np = F.Nt / F.a; F.Nq = F.Nx / F.a; F.nT = F.Np * F.Nq; F.nrows = 2 * (F.a * F.a - 1);
+    C.Nt = F.Np; C.Nx = F.Nq; C.n = F.nT;
+    CKS(dalloc(h, &F.P64, (size_t)F.nT * 8 * F.nrows));
+    CKS(dalloc(h, &F.P16, (size_t)F.nT * 8 * F.nrows));
+    CKS(dalloc(h, &F.Ps, (size_t)F.nT));
+    const Offsets& fo = (l == 0) ? fine_off : F.off;
+    if (coarse_offsets(fo, F.Nt, F.Nx, F.a, &C.off) != AMAMG_OK) {
+      h->err = "coarse operator has more than 32 block offsets";
+      return AMAMG_ERR_INVALID_ARG;
+    }
+    CKS(dalloc(h, &C.B64, (size_t)C.off.K * 4 * C.n));
+    if (l == 0) {
+      WilsonOp op{h->U64, h->m0 + 2.0, F.Nt, F.Nx};
+      CKS(launch(h, "setup_local_solve", 0.0, st, [&] { return launch_local_solve(op, F.a, F.Np, F.Nq, F.P64, h->d_err, st); }));
+      CKS(launch(h, "setup_galerkin", 0.0, st, [&] { return launch_galerkin(op, F.P64, F.a, F.Np, F.Nq, C.off, C.B64, st); }));
+    } else {
+      StencilOp op{F.B64, F.off, F.Nt, F.Nx};
+      CKS(launch(h, "setup_local_solve", 0.0, st, [&] { return launch_local_solve(op, F.a, F.Np, F.Nq, F.P64, h->d_err, st); }));
+      CKS(launch(h, "setup_galerkin", 0.0, st, [&] { return launch_galerkin(op, F.P64, F.a, F.Np, F.Nq, C.off, C.B64, st); }));
+    }
+    CKS(launch(h, "setup_pack", 0.0, st, [&] { return launch_pack_P16(F.P64, 8 * F.nrows, F.nT, F.P16, F.Ps, st); }));
+  }
+  for (int l = 1; l < L; ++l) {
+    Level& C = h->lv[l];
+    CKS(dalloc(h, &C.B16, (size_t)C.off.K * 4 * C.n));
+    CKS(dalloc(h, &C.Bs, (size_t)C.off.K * C.n));
+    CKS(launch(h, "setup_pack", 0.0, st, [&] { return launch_pack_B16(C.B64, C.off.K, C.n, C.B16, C.Bs, st); }));
+    if (l + 1 < L) {
+      CKS(dalloc(h, &C.Dinv64, 4 * (size_t)C.n));
+      CKS(dalloc(h, &C.Dinv32, 4 * (size_t)C.n));
+      CKS(launch(h, "setup_diag_inv", 0.0, st, [&] { return launch_diag_inv(C.B64, C.n, C.Dinv64, C.Dinv32, h->d_err, st); }));
+    }
+  }
+  // coarsest: dense matrix and its Gauss-Jordan inverse
+  Level& Cl = h->lv[L - 1];
+  h->nd = 2 * Cl.n;
+  const size_t nd = (size_t)h->nd;
+  double2* X = nullptr;
+  double2* colk = nullptr;
+  int* perm = nullptr;
+  CKS(dalloc(h, &X, nd * nd));
+  int rc = dalloc(h, &h->Ainv, nd * nd);
+  if (rc == AMAMG_OK) rc = dalloc(h, &colk, nd);
+  if (rc == AMAMG_OK) rc = dalloc(h, &perm, nd);
+  if (rc == AMAMG_OK && cudaMemsetAsync(X, 0, nd * nd * sizeof(double2), st) != cudaSuccess) rc = AMAMG_ERR_CUDA;
+  if (rc == AMAMG_OK)
+    rc = launch(h, "setup_coarsest", 0.0, st, [&] { return launch_dense_from_blocks(Cl.B64, Cl.off, Cl.Nt, Cl.Nx, X, st); });
+  for (int k = 0; rc == AMAMG_OK && k < h->nd; ++k)
+    rc = launch(h, "setup_coarsest", 0.0, st, [&] { return launch_gj_step(X, h->nd, k, colk, perm, h->d_err, 1e-300, st); });
+  std::vector<int> hperm(nd), cols(nd);
+  if (rc == AMAMG_OK && cudaMemcpyAsync(hperm.data(), perm, nd * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = AMAMG_ERR_CUDA;
+  if (rc == AMAMG_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = AMAMG_ERR_CUDA;
+  if (rc == AMAMG_OK) {
+    for (size_t i = 0; i < nd; ++i) cols[i] = (int)i;
+    for (int k = h->nd - 1; k >= 0; --k) std::swap(cols[k], cols[hperm[k]]);
+    if (cudaMemcpyAsync(perm, cols.data(), nd * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess) rc = AMAMG_ERR_CUDA;
+  }
+  if (rc == AMAMG_OK)
+    rc = launch(h, "setup_coarsest", 0.0, st, [&] { return launch_gather_cols(X, h->Ainv, perm, h->nd, st); });
+  int herr = 0;
+  if (rc == AMAMG_OK && cudaMemcpyAsync(&herr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = AMAMG_ERR_CUDA;
+  if (rc == AMAMG_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = AMAMG_ERR_CUDA;
+  dfree(X); dfree(colk); dfree(perm);
+  if (rc == AMAMG_ERR_CUDA && h->err.empty()) h->err = cudaGetErrorString(cudaGetLastError());
+  if (rc != AMAMG_OK) return rc;
+  if (herr) {
+    h->err = (herr & 1) ? "vanishing pivot in a local basket solve"
+           : (herr & 2) ? "singular 2x2 diagonal block on a coarse level"
+                        : "vanishing pivot in the coarsest inverse";
+    return AMAMG_ERR_SINGULAR;
+  }
+  return AMAMG_OK;
+}
+
+bool valid_level(amamg_ctx* h, int level, bool need_next) {
+  if (level < 0 || level >= (int)h->lv.size()) return false;
+  if (need_next && level + 1 >= (int)h->lv.size()) return false;
+  return true;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+int amamg_default_params(amamg_params* p) {
+  if (!p) return AMAMG_ERR_INVALID_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->nlevels = 2;
+  p->agg[0] = 4; p->agg[1] = 2; p->agg[2] = 2; p->agg[3] = 2;
+  p->precision = AMAMG_SOLVE_FP64;
+  p->restart = 30;
+  p->max_iter = 3000;
+  p->post_smooth = 2;
+  p->tol = 1e-10;
+  return AMAMG_OK;
+}
+
+int amamg_query_bytes(const amamg_params* p, int Nt, int Nx, int max_rhs, size_t* setup_bytes, size_t* per_rhs_bytes) {
+  std::string why;
+  int rc = check_params(p, Nt, Nx, &why);
+  if (rc != AMAMG_OK) return rc;
+  if (max_rhs < 1) return AMAMG_ERR_INVALID_ARG;
+  size_t sb = 2 * (size_t)Nt * Nx * (16 + 8);   // links FP64 + FP32
+  size_t vb = 0;                                 // V-cycle vectors per RHS
+  int nt = Nt, nx = Nx;
+  Offsets off = wilson_offsets(Nt, Nx);
+  for (int l = 0; l + 1 < p->nlevels; ++l) {
+    const int a = p->agg[l];
+    const size_t nT = (size_t)(nt / a) * (nx / a), nrows = 2 * (a * a - 1);
+    sb += nT * 8 * nrows * (16 + 4) + nT * 4;
+    Offsets c;
+    if (coarse_offsets(off, nt, nx, a, &c) != AMAMG_OK) return AMAMG_ERR_INVALID_ARG;
+    nt /= a; nx /= a;
+    const size_t n = (size_t)nt * nx;
+    sb += (size_t)c.K * n * (4 * 16 + 4 * 4 + 4) + 4 * n * (16 + 8);
+    vb += 2 * n * 2 * (16 + 8);
+    off = c;
+  }
+  const size_t nd = 2 * (size_t)nt * nx;
+  sb += 2 * nd * nd * 16;                        // inverse + its work copy during setup
+  const size_t len = 2 * (size_t)Nt * Nx;
+  const int m = p->restart;
+  size_t rb = vb + (size_t)(m + 1) * len * 16 + 2 * len * 16 +
+              (p->precision == AMAMG_SOLVE_MIXED ? (size_t)(m + 1) * len * 8 : (size_t)m * len * 16);
+  if (setup_bytes) *setup_bytes = sb;
+  if (per_rhs_bytes) *per_rhs_bytes = rb;
+  return AMAMG_OK;
+}
+
+int amamg_setup(const amamg_params* p, const void* U, int Nt, int Nx, double m0, void* stream, amamg_handle* out) {
+  if (!out) return AMAMG_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::string why;
+  int rc = check_params(p, Nt, Nx, &why);
+  if (rc != AMAMG_OK) return rc;
+  if (!U || !std::isfinite(m0)) return AMAMG_ERR_INVALID_ARG;
+  amamg_ctx* h = new amamg_ctx();
+  h->prm = *p;
+  h->Nt = Nt; h->Nx = Nx; h->m0 = m0;
+  cudaStream_t st = S(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  rc = do_setup(h, U, st);
+  if (rc == AMAMG_OK) {
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    h->setup_s = ms * 1e-3;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != AMAMG_OK) {
+    fprintf(stderr, "amamg_setup: %s\n", h->err.c_str());
+    free_all(h);
+    delete h;
+    return rc;
+  }
+  h->recs.clear();
+  h->ev_used = 0;
+  *out = h;
+  return AMAMG_OK;
+}
+
+int amamg_solve(amamg_handle h, const void* psi, void* x, int R, void* stream, amamg_solve_info* info) {
+  if (!h || !psi || !x || R < 1) return AMAMG_ERR_INVALID_ARG;
+  return fgmres(h, (const double2*)psi, (double2*)x, R, S(stream), info);
+}
+
+int amamg_apply_D(amamg_handle h, const void* in, void* out, int R, int precision, void* stream) {
+  if (!h || !in || !out || R < 1) return AMAMG_ERR_INVALID_ARG;
+  if (precision == AMAMG_F64) return op_dslash<double>(h, (const double2*)in, (double2*)out, nullptr, R, S(stream));
+  if (precision == AMAMG_F32) return op_dslash<float>(h, (const float2*)in, (float2*)out, nullptr, R, S(stream));
+  return AMAMG_ERR_INVALID_ARG;
+}
+
+int amamg_apply_P(amamg_handle h, int level, const void* ci, void* fo, int R, int precision, void* stream) {
+  if (!h || !ci || !fo || R < 1 || !valid_level(h, level, true)) return AMAMG_ERR_INVALID_ARG;
+  if (precision == AMAMG_F64) return op_prolong<double>(h, level, (const double2*)ci, (double2*)fo, R, S(stream));
+  if (precision == AMAMG_F32) return op_prolong<float>(h, level, (const float2*)ci, (float2*)fo, R, S(stream));
+  return AMAMG_ERR_INVALID_ARG;
+}
+
+int amamg_apply_PH(amamg_handle h, int level, const void* fi, void* co, int R, int precision, void* stream) {
+  if (!h || !fi || !co || R < 1 || !valid_level(h, level, true)) return AMAMG_ERR_INVALID_ARG;
+  if (precision == AMAMG_F64) return op_restrict<double>(h, level, (const double2*)fi, (double2*)co, R, S(stream));
+  if (precision == AMAMG_F32) return op_restrict<float>(h, level, (const float2*)fi, (float2*)co, R, S(stream));
+  return AMAMG_ERR_INVALID_ARG;
+}
+
+int amamg_apply_coarse(amamg_handle h, int level, const void* in, void* out, int R, int precision, void* stream) {
+  if (!h || !in || !out || R < 1 || level < 1 || !valid_level(h, level, false)) return AMAMG_ERR_INVALID_ARG;
+  if (precision == AMAMG_F64)
+    return op_coarse<double>(h, level, (const double2*)in, (double2*)out, nullptr, R, S(stream));
+  if (precision == AMAMG_F32)
+    return op_coarse<float>(h, level, (const float2*)in, (float2*)out, nullptr, R, S(stream));
+  return AMAMG_ERR_INVALID_ARG;
+}
+
+int amamg_smooth(amamg_handle h, int level, const void* r, void* e, int R, int sweeps, int precision, void* stream) {
+  if (!h || !r || !e || R < 1 || sweeps < 0 || !valid_level(h, level, true)) return AMAMG_ERR_INVALID_ARG;
+  if (precision == AMAMG_F64) return smooth_impl<double>(h, level, (double2*)e, (const double2*)r, R, sweeps, S(stream));
+  if (precision == AMAMG_F32) return smooth_impl<float>(h, level, (float2*)e, (const float2*)r, R, sweeps, S(stream));
+  return AMAMG_ERR_INVALID_ARG;
+}
+
+int amamg_coarsest_solve(amamg_handle h, const void* r, void* e, int R, void* stream) {
+  if (!h || !r || !e || R < 1) return AMAMG_ERR_INVALID_ARG;
+  return op_coarsest<double2>(h, (const double2*)r, (double2*)e, R, S(stream));
+}
+
+int amamg_vcycle(amamg_handle h, const void* r, void* e, int R, int precision, void* stream) {
+  if (!h || !r || !e || R < 1) return AMAMG_ERR_INVALID_ARG;
+  int rc = ensure_vcycle_ws(h, R);
+  if (rc != AMAMG_OK) return rc;
+  if (precision == AMAMG_F64) return vcycle_from<double>(h, 0, (const double2*)r, (double2*)e, R, S(stream));
+  if (precision == AMAMG_F32) return vcycle_from<float>(h, 0, (const float2*)r, (float2*)e, R, S(stream));
+  return AMAMG_ERR_INVALID_ARG;
+}
+
+int amamg_export_structure(amamg_handle h, int level, int32_t* role, int32_t* owner_tile, int32_t* nbr_offsets,
+                           int32_t* nbr_count) {
+  if (!h || !valid_level(h, level, true)) return AMAMG_ERR_INVALID_ARG;
+  const Level& L = h->lv[level];
+  const Level& C = h->lv[level + 1];
+  for (int t = 0; t < L.Nt; ++t)
+    for (int x = 0; x < L.Nx; ++x) {
+      const int s = t * L.Nx + x;
+      const bool t0 = t % L.a == 0, x0 = x % L.a == 0;
+      if (role) role[s] = (t0 && x0) ? 0 : (t0 != x0 ? 1 : 2);
+      if (owner_tile) owner_tile[s] = (t / L.a) * L.Nq + x / L.a;
+    }
+  if (nbr_offsets)
+    for (int k = 0; k < C.off.K; ++k) { nbr_offsets[2 * k] = C.off.dt[k]; nbr_offsets[2 * k + 1] = C.off.dx[k]; }
+  if (nbr_count) *nbr_count = C.off.K;
+  return AMAMG_OK;
+}
+
+int amamg_level_info(amamg_handle h, int level, int* Nt_l, int* Nx_l, int* n_offsets) {
+  if (!h || !valid_level(h, level, false)) return AMAMG_ERR_INVALID_ARG;
+  const Level& L = h->lv[level];
+  if (Nt_l) *Nt_l = L.Nt;
+  if (Nx_l) *Nx_l = L.Nx;
+  if (n_offsets) *n_offsets = level == 0 ? 5 : L.off.K;
+  return AMAMG_OK;
+}
+
+int amamg_export_P(amamg_handle h, int level, void* out, void* stream) {
+  if (!h || !out || !valid_level(h, level, true)) return AMAMG_ERR_INVALID_ARG;
+  const Level& L = h->lv[level];
+  CK(cudaMemcpyAsync(out, L.P64, sizeof(double2) * L.nT * 8 * L.nrows, cudaMemcpyDeviceToDevice, S(stream)));
+  return AMAMG_OK;
+}
+
+int amamg_export_coarse(amamg_handle h, int level, void* out, void* stream) {
+  if (!h || !out || level < 1 || !valid_level(h, level, false)) return AMAMG_ERR_INVALID_ARG;
+  const Level& L = h->lv[level];
+  CK(cudaMemcpyAsync(out, L.B64, sizeof(double2) * L.off.K * 4 * L.n, cudaMemcpyDeviceToDevice, S(stream)));
+  return AMAMG_OK;
+}
+
+int amamg_profile_enable(amamg_handle h, int on) {
+  if (!h) return AMAMG_ERR_INVALID_ARG;
+  if (!on && h->prof) {
+    int rc = collect_profile(h);
+    if (rc != AMAMG_OK) return rc;
+  }
+  h->prof = on != 0;
+  return AMAMG_OK;
+}
+
+int amamg_profile_reset(amamg_handle h) {
+  if (!h) return AMAMG_ERR_INVALID_ARG;
+  int rc = collect_profile(h);
+  h->cats.clear();
+  return rc;
+}
+
+int amamg_profile_get(amamg_handle h, int idx, const char** name, long long* launches, double* total_ms, double* bytes) {
+  if (!h) return AMAMG_ERR_INVALID_ARG;
+  int rc = collect_profile(h);
+  if (rc != AMAMG_OK) return rc;
+  if (idx < 0 || idx >= (int)h->cats.size()) return AMAMG_ERR_INVALID_ARG;
+  const ProfCat& c = h->cats[idx];
+  if (name) *name = c.name.c_str();
+  if (launches) *launches = c.launches;
+  if (total_ms) *total_ms = c.ms;
+  if (bytes) *bytes = c.bytes;
+  return AMAMG_OK;
+}
+
+long long amamg_launch_count(amamg_handle h) { return h ? h->launches : -1; }
+
+double amamg_setup_seconds(amamg_handle h) { return h ? h->setup_s : -1.0; }
+
+int amamg_destroy(amamg_handle h) {
+  if (!h) return AMAMG_ERR_INVALID_ARG;
+  cudaDeviceSynchronize();
+  free_all(h);
+  delete h;
+  return AMAMG_OK;
+}
+
+const char* amamg_status_string(int s) {
+  switch (s) {
+    case AMAMG_OK: return "ok";
+    case AMAMG_NOT_CONVERGED: return "not converged (max_iter reached)";
+    case AMAMG_ERR_INVALID_ARG: return "invalid argument";
+    case AMAMG_ERR_OOM: return "out of device memory";
+    case AMAMG_ERR_CUDA: return "CUDA error";
+    case AMAMG_ERR_SINGULAR: return "singular pivot in setup";
+    case AMAMG_ERR_NONFINITE: return "non-finite value";
+    case AMAMG_ERR_TIMEOUT: return "timeout";
+    default: return "unknown status";
+  }
+}
+
+const char* amamg_last_error(amamg_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+}  // extern "C"

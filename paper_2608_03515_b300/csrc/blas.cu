@@ -1,0 +1,168 @@
+// Krylov vector kernels of the FP64 outer FGMRES (Gram-Schmidt inner products,
+// multi-vector updates, norms, scaling) and precision casts.
+//
+// A basis is one allocation [J][R][len] (vector i of right-hand side r at
+// base + (i*R + r)*len).  Inner products are two-pass and deterministic: each
+// block writes a partial sum, a second kernel adds the partials in a fixed tree
+// order.  len counts complex elements.
+#include "kernels.h"
+
+namespace {
+
+constexpr int DOT_THREADS = 256;
+
+template <typename C>
+__device__ __forceinline__ C block_reduce(C v, C* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  if (wid == 0) {
+    v = lane < nw ? sh[lane] : czero<C>();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+      v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+  }
+  return v;
+}
+
+// partial[(r*J + i)*nb + blk] = sum over the block's chunk of conj(V_i,r) w_r
+__global__ void __launch_bounds__(DOT_THREADS)
+k_dots(const double2* __restrict__ V, size_t vi, size_t vr, const double2* __restrict__ w, size_t wr,
+       long len, long chunk, double2* __restrict__ partial, int J) {
+  __shared__ double2 sh[32];
+  const int i = blockIdx.y, r = blockIdx.z, nb = gridDim.x;
+  const double2* a = V + i * vi + r * vr;
+  const double2* b = w + r * wr;
+  const long start = (long)blockIdx.x * chunk;
+  const long end = min(start + chunk, len);
+  double2 acc = make_double2(0.0, 0.0);
+  for (long k = start + threadIdx.x; k < end; k += blockDim.x) acc += cmulc(a[k], b[k]);
+  acc = block_reduce(acc, sh);
+  if (threadIdx.x == 0) partial[((size_t)r * J + i) * nb + blockIdx.x] = acc;
+}
+
+// out[r*ldo + off + i] = sum_b partial[(r*J + i)*nb + b]  (+ optional norm form)
+// mode 0: store the complex sum; mode 1: the sum is <w, w>: store sqrt(re) in
+// out and 1/sqrt(re) (0 when the norm is 0) in inv.
+__global__ void __launch_bounds__(256)
+k_reduce_partials(const double2* __restrict__ partial, int nb, int J, double2* __restrict__ out, int ldo,
+                  int off, int mode, double* __restrict__ inv) {
+  __shared__ double2 sh[32];
+  const int i = blockIdx.x, r = blockIdx.y;
+  const double2* p = partial + ((size_t)r * J + i) * nb;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += p[b];
+  acc = block_reduce(acc, sh);
+  if (threadIdx.x == 0) {
+    if (mode == 0) {
+      out[(size_t)r * ldo + off + i] = acc;
+    } else {
+      // NaN propagates (a NaN or Inf entry must surface as a non-finite norm)
+      const double nrm = (acc.x >= 0.0) ? sqrt(acc.x) : ((acc.x < 0.0) ? 0.0 : acc.x);
+      out[(size_t)r * ldo + off + i] = make_double2(nrm, 0.0);
+      if (inv) inv[r] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    }
+  }
+}
+
+// y_r += sign * sum_{i<J} coef[r*ldc + i] * X_{i,r}
+template <typename Cx>
+__global__ void __launch_bounds__(256)
+k_multi_axpy(double2* __restrict__ y, size_t yr, const Cx* __restrict__ X, size_t xi, size_t xr,
+             const double2* __restrict__ coef, int ldc, int J, double sign, long len) {
+  const int r = blockIdx.y;
+  const double2* c = coef + (size_t)r * ldc;
+  for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < len; k += (long)gridDim.x * blockDim.x) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int i = 0; i < J; ++i) acc += cmul(c[i], to_c(X[i * xi + r * xr + k], double()));
+    y[r * yr + k] += sign * acc;
+  }
+}
+
+// dst_r = src_r * scale[r]   (scale from device memory)
+template <typename Cd>
+__global__ void __launch_bounds__(256)
+k_scale_copy(Cd* __restrict__ dst, size_t dr, const double2* __restrict__ src, size_t sr,
+             const double* __restrict__ scale, long len) {
+  const int r = blockIdx.y;
+  const double s = scale[r];
+  for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < len; k += (long)gridDim.x * blockDim.x)
+    dst[r * dr + k] = to_c(s * src[r * sr + k], typename real_of<Cd>::type());
+}
+
+template <typename Cs, typename Cd>
+__global__ void __launch_bounds__(256) k_cast(const Cs* __restrict__ src, Cd* __restrict__ dst, long len) {
+  for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < len; k += (long)gridDim.x * blockDim.x)
+    dst[k] = to_c(src[k], typename real_of<Cd>::type());
+}
+
+inline int grid_for(long len) {
+  long g = (len + 255) / 256;
+  if (g > 148 * 16) g = 148 * 16;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+int dot_blocks(long len) {
+  long nb = (len + 4095) / 4096;
+  if (nb > 296) nb = 296;
+  return (int)(nb < 1 ? 1 : nb);
+}
+
+cudaError_t launch_dots(const double2* V, size_t vi, size_t vr, const double2* w, size_t wr, long len, int J,
+                        int R, double2* partial, cudaStream_t st) {
+  const int nb = dot_blocks(len);
+  const long chunk = (len + nb - 1) / nb;
+  dim3 grid(nb, J, R);
+  k_dots<<<grid, DOT_THREADS, 0, st>>>(V, vi, vr, w, wr, len, chunk, partial, J);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const double2* partial, int nb, int J, int R, double2* out, int ldo, int off, int mode,
+                          double* inv, cudaStream_t st) {
+  dim3 grid(J, R);
+  k_reduce_partials<<<grid, 256, 0, st>>>(partial, nb, J, out, ldo, off, mode, inv);
+  return cudaGetLastError();
+}
+
+template <typename Cx>
+cudaError_t launch_multi_axpy(double2* y, size_t yr, const Cx* X, size_t xi, size_t xr, const double2* coef, int ldc,
+                              int J, double sign, long len, int R, cudaStream_t st) {
+  dim3 grid(grid_for(len), R);
+  k_multi_axpy<Cx><<<grid, 256, 0, st>>>(y, yr, X, xi, xr, coef, ldc, J, sign, len);
+  return cudaGetLastError();
+}
+
+template <typename Cd>
+cudaError_t launch_scale_copy(Cd* dst, size_t dr, const double2* src, size_t sr, const double* scale, long len, int R,
+                              cudaStream_t st) {
+  dim3 grid(grid_for(len), R);
+  k_scale_copy<Cd><<<grid, 256, 0, st>>>(dst, dr, src, sr, scale, len);
+  return cudaGetLastError();
+}
+
+template <typename Cs, typename Cd>
+cudaError_t launch_cast(const Cs* src, Cd* dst, long len, cudaStream_t st) {
+  k_cast<Cs, Cd><<<grid_for(len), 256, 0, st>>>(src, dst, len);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_multi_axpy<double2>(double2*, size_t, const double2*, size_t, size_t, const double2*, int,
+                                                int, double, long, int, cudaStream_t);
+template cudaError_t launch_multi_axpy<float2>(double2*, size_t, const float2*, size_t, size_t, const double2*, int,
+                                               int, double, long, int, cudaStream_t);
+template cudaError_t launch_scale_copy<double2>(double2*, size_t, const double2*, size_t, const double*, long, int,
+                                                cudaStream_t);
+template cudaError_t launch_scale_copy<float2>(float2*, size_t, const double2*, size_t, const double*, long, int,
+                                               cudaStream_t);
+template cudaError_t launch_cast<double2, float2>(const double2*, float2*, long, cudaStream_t);
+template cudaError_t launch_cast<float2, double2>(const float2*, double2*, long, cudaStream_t);

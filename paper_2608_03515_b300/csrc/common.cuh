@@ -1,0 +1,65 @@
+// Shared device helpers: complex arithmetic on double2 / float2, precision traits,
+// FP16+scale decoding.  Nothing here is specific to one kernel.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+template <typename T> struct cplx;
+template <> struct cplx<double> { using type = double2; };
+template <> struct cplx<float>  { using type = float2; };
+
+__host__ __device__ __forceinline__ double2 mk(double r, double i) { return make_double2(r, i); }
+__host__ __device__ __forceinline__ float2  mk(float r, float i)  { return make_float2(r, i); }
+
+template <typename C> __host__ __device__ __forceinline__ C czero();
+template <> __host__ __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
+template <> __host__ __device__ __forceinline__ float2  czero<float2>()  { return make_float2(0.f, 0.f); }
+
+#define CPLX_OPS(C, R)                                                                         \
+  __host__ __device__ __forceinline__ C operator+(C a, C b) { return mk(a.x + b.x, a.y + b.y); } \
+  __host__ __device__ __forceinline__ C operator-(C a, C b) { return mk(a.x - b.x, a.y - b.y); } \
+  __host__ __device__ __forceinline__ C operator-(C a) { return mk(-a.x, -a.y); }               \
+  __host__ __device__ __forceinline__ C operator*(R s, C a) { return mk(s * a.x, s * a.y); }     \
+  __host__ __device__ __forceinline__ C& operator+=(C& a, C b) { a.x += b.x; a.y += b.y; return a; } \
+  __host__ __device__ __forceinline__ C& operator-=(C& a, C b) { a.x -= b.x; a.y -= b.y; return a; } \
+  __host__ __device__ __forceinline__ C cmul(C a, C b) { return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); } \
+  /* conj(a) * b */                                                                             \
+  __host__ __device__ __forceinline__ C cmulc(C a, C b) { return mk(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x); } \
+  /* a * conj(b) */                                                                             \
+  __host__ __device__ __forceinline__ C cmul_conjb(C a, C b) { return mk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y); } \
+  __host__ __device__ __forceinline__ C cconj(C a) { return mk(a.x, -a.y); }                    \
+  /* i * a */                                                                                   \
+  __host__ __device__ __forceinline__ C ci(C a) { return mk(-a.y, a.x); }                        \
+  __host__ __device__ __forceinline__ R cabs2(C a) { return a.x * a.x + a.y * a.y; }
+
+CPLX_OPS(double2, double)
+CPLX_OPS(float2, float)
+#undef CPLX_OPS
+
+// element conversions between vector precisions
+__device__ __forceinline__ double2 to_c(double2 a, double) { return a; }
+__device__ __forceinline__ double2 to_c(float2 a, double) { return make_double2(a.x, a.y); }
+__device__ __forceinline__ float2 to_c(float2 a, float) { return a; }
+__device__ __forceinline__ float2 to_c(double2 a, float) { return make_float2((float)a.x, (float)a.y); }
+
+template <typename C> struct real_of;
+template <> struct real_of<double2> { using type = double; };
+template <> struct real_of<float2> { using type = float; };
+
+// FP16 pair + FP32 scale -> complex of compute precision
+template <typename T>
+__device__ __forceinline__ typename cplx<T>::type h2c(__half2 h, float s) {
+  float2 f = __half22float2(h);
+  return mk((T)(f.x * s), (T)(f.y * s));
+}
+
+// canonical (mod N) block offsets of a level operator, passed by value to kernels
+#define AMAMG_MAX_OFFSETS 32
+struct Offsets {
+  int K;
+  int dt[AMAMG_MAX_OFFSETS];
+  int dx[AMAMG_MAX_OFFSETS];
+};
+
+__host__ __device__ __forceinline__ int wrap(int v, int n) { v %= n; return v < 0 ? v + n : v; }

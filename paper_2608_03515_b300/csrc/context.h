@@ -1,0 +1,81 @@
+// Host-side state of one hierarchy (the object behind amamg_handle).
+#pragma once
+#include <string>
+#include <vector>
+
+#include "../../include/amamg.h"
+#include "kernels.h"
+
+struct Level {
+  int Nt = 0, Nx = 0, n = 0;            // sites of this level
+  // coarsening to the next level (unused on the coarsest)
+  int a = 0, Np = 0, Nq = 0, nT = 0, nrows = 0;
+  // this level's operator for l >= 1: canonical offsets and blocks
+  Offsets off{};
+  double2* B64 = nullptr;
+  __half2* B16 = nullptr;
+  float* Bs = nullptr;
+  double2* Dinv64 = nullptr;
+  float2* Dinv32 = nullptr;
+  // interpolation to the next level
+  double2* P64 = nullptr;
+  __half2* P16 = nullptr;
+  float* Ps = nullptr;
+  // V-cycle work vectors (capacity Rcap right-hand sides)
+  double2* r64 = nullptr;
+  double2* e64 = nullptr;
+  float2* r32 = nullptr;
+  float2* e32 = nullptr;
+};
+
+struct ProfCat {
+  std::string name;
+  long long launches = 0;
+  double ms = 0.0;
+  double bytes = 0.0;
+};
+
+struct ProfRec {
+  int cat;
+  cudaEvent_t a, b;
+  double bytes;
+};
+
+struct amamg_ctx {
+  amamg_params prm{};
+  int Nt = 0, Nx = 0;
+  double m0 = 0.0;
+  std::vector<Level> lv;
+  double2* U64 = nullptr;
+  float2* U32 = nullptr;
+  double2* Ainv = nullptr;   // coarsest inverse, nd x nd row-major
+  int nd = 0;
+  int* d_err = nullptr;
+
+  // solver workspace
+  int Rcap = 0;              // V-cycle work vectors
+  int Rsolve = 0;            // FGMRES basis capacity
+  int mcap = 0;
+  double2* V = nullptr;      // [m+1][R][len]
+  double2* Z64 = nullptr;    // [m][R][len]
+  float2* Z32 = nullptr;     // [m][R][len]
+  float2* v32 = nullptr;     // [R][len]
+  double2* w = nullptr;      // [R][len]
+  double2* res = nullptr;    // [R][len]
+  double2* partial = nullptr;
+  size_t partial_elems = 0;
+  double2* d_h = nullptr;    // [R][3 (m+2)] device: h1 | h2 | norms
+  double* d_inv = nullptr;   // [R]
+  double2* d_y = nullptr;    // [R][m]
+  double2* h_h = nullptr;    // pinned host mirror of d_h
+  double2* h_y = nullptr;    // pinned host mirror of d_y
+
+  std::string err;
+  long long launches = 0;
+  bool prof = false;
+  std::vector<ProfCat> cats;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  double setup_s = 0.0;
+};

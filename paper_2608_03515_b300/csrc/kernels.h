@@ -1,0 +1,74 @@
+// Kernel launchers of the library (one declaration per kernel family).
+// Every launcher enqueues on the given stream and returns cudaGetLastError().
+#pragma once
+#include "common.cuh"
+
+// level operators as seen by the setup kernels
+struct WilsonOp {          // fine level, Eq. (3)
+  const double2* U;        // [2][Nt][Nx]
+  double diag;             // m0 + 2
+  int Nt, Nx;
+};
+struct StencilOp {         // Galerkin level, [K][4][n] blocks
+  const double2* B;
+  Offsets off;
+  int Nt, Nx;
+};
+
+// dslash.cu
+template <typename Cin, typename Cout, typename T>
+cudaError_t launch_dslash(const Cin* in, Cout* out, const Cout* b, const typename cplx<T>::type* U, T diag, int Nt,
+                          int Nx, int R, cudaStream_t st);
+template <typename T>
+cudaError_t launch_rb_half(typename cplx<T>::type* e, const typename cplx<T>::type* r, const typename cplx<T>::type* U,
+                           T inv_diag, int Nt, int Nx, int colour, int R, cudaStream_t st);
+
+// transfer.cu
+template <typename T, typename PT>
+cudaError_t launch_prolong(const typename cplx<T>::type* ec, typename cplx<T>::type* ef, const PT* P,
+                           const float* Pscale, int Nxf, int a, int Np, int Nq, int R, cudaStream_t st);
+template <typename T, typename PT>
+cudaError_t launch_restrict(const typename cplx<T>::type* ef, typename cplx<T>::type* ec, const PT* P,
+                            const float* Pscale, int Nxf, int a, int Np, int Nq, int R, cudaStream_t st);
+
+// coarse.cu
+template <typename T, typename BT>
+cudaError_t launch_coarse_apply(const typename cplx<T>::type* in, typename cplx<T>::type* out,
+                                const typename cplx<T>::type* b, const BT* B, const float* Bs, const Offsets& off,
+                                int Nt, int Nx, int R, cudaStream_t st);
+template <typename T, typename BT>
+cudaError_t launch_coarse_colour(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* B,
+                                 const float* Bs, const typename cplx<T>::type* Dinv, const Offsets& off, int Nt,
+                                 int Nx, int colour, int R, cudaStream_t st);
+template <typename Cv>
+cudaError_t launch_dense_gemv(const double2* A, const Cv* x, Cv* y, int nd, int R, cudaStream_t st);
+
+// blas.cu
+int dot_blocks(long len);
+cudaError_t launch_dots(const double2* V, size_t vi, size_t vr, const double2* w, size_t wr, long len, int J, int R,
+                        double2* partial, cudaStream_t st);
+cudaError_t launch_reduce(const double2* partial, int nb, int J, int R, double2* out, int ldo, int off, int mode,
+                          double* inv, cudaStream_t st);
+template <typename Cx>
+cudaError_t launch_multi_axpy(double2* y, size_t yr, const Cx* X, size_t xi, size_t xr, const double2* coef, int ldc,
+                              int J, double sign, long len, int R, cudaStream_t st);
+template <typename Cd>
+cudaError_t launch_scale_copy(Cd* dst, size_t dr, const double2* src, size_t sr, const double* scale, long len, int R,
+                              cudaStream_t st);
+template <typename Cs, typename Cd>
+cudaError_t launch_cast(const Cs* src, Cd* dst, long len, cudaStream_t st);
+
+// setup.cu
+template <typename Op>
+cudaError_t launch_local_solve(const Op& op, int a, int Np, int Nq, double2* P, int* err, cudaStream_t st);
+template <typename Op>
+cudaError_t launch_galerkin(const Op& op, const double2* P, int a, int Np, int Nq, const Offsets& offc, double2* Bc,
+                            cudaStream_t st);
+cudaError_t launch_diag_inv(const double2* B, int n, double2* D64, float2* D32, int* err, cudaStream_t st);
+cudaError_t launch_dense_from_blocks(const double2* B, const Offsets& off, int Nt, int Nx, double2* Ad,
+                                     cudaStream_t st);
+cudaError_t launch_gj_step(double2* A, int nd, int k, double2* colk, int* perm, int* err, double tol2,
+                           cudaStream_t st);
+cudaError_t launch_gather_cols(const double2* X, double2* Y, const int* cols, int nd, cudaStream_t st);
+cudaError_t launch_pack_P16(const double2* P, int per_tile, int ntiles, __half2* P16, float* scale, cudaStream_t st);
+cudaError_t launch_pack_B16(const double2* B, int K, int n, __half2* B16, float* scale, cudaStream_t st);

@@ -1,0 +1,140 @@
+// Transfer kernels between level l and level l+1 (Sec. 2; interpolator of
+// Sec. 4.1, Eq. (16)).
+//
+// P_l is stored per tile T = (p, q) (the a x a sites whose non-vertex rows take
+// their formula from basket W(p, q)) as a dense [8][nrows] column-major block:
+// column 2c + beta is corner c (= 2 di + dj, vertex (p+di, q+dj)), spin beta;
+// row 2(l-1) + alpha is in-tile site l = i*a + j (l >= 1), spin alpha.  The
+// tile's vertex (l = 0) interpolates by identity and is not stored.
+//   FP64: double2 entries.  FP32 path: __half2 entries times one FP32 scale per tile.
+#include "kernels.h"
+
+namespace {
+
+template <typename T, typename PT>
+__device__ __forceinline__ typename cplx<T>::type p_load(const PT* P, const float* scale, size_t idx, int tile);
+
+template <>
+__device__ __forceinline__ double2 p_load<double, double2>(const double2* P, const float*, size_t idx, int) {
+  return P[idx];
+}
+template <>
+__device__ __forceinline__ float2 p_load<float, __half2>(const __half2* P, const float* scale, size_t idx, int tile) {
+  return h2c<float>(P[idx], scale[tile]);
+}
+
+// e_fine = P e_coarse.  One thread per (tile, row); rows nrows, nrows+1 are the
+// vertex's two spins (identity).
+template <typename T, typename PT>
+__global__ void __launch_bounds__(256)
+k_prolong(const typename cplx<T>::type* __restrict__ ec, typename cplx<T>::type* __restrict__ ef,
+          const PT* __restrict__ P, const float* __restrict__ Pscale,
+          int Nxf, int a, int nrows, int Np, int Nq) {
+  using C = typename cplx<T>::type;
+  const int rows_tot = nrows + 2;
+  const int nc = Np * Nq;
+  const int nf = nc * a * a;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nc * rows_tot) return;
+  const int tile = g / rows_tot;
+  const int lr = g - tile * rows_tot;
+  const int p = tile / Nq, q = tile - (tile / Nq) * Nq;
+  const C* e0 = ec + (size_t)blockIdx.y * 2 * nc;
+  C* f0 = ef + (size_t)blockIdx.y * 2 * nf;
+  if (lr >= nrows) {
+    const int alpha = lr - nrows;
+    f0[(size_t)alpha * nf + (p * a) * Nxf + q * a] = e0[(size_t)alpha * nc + tile];
+    return;
+  }
+  const int l = (lr >> 1) + 1, alpha = lr & 1;
+  const int i = l / a, j = l - (l / a) * a;
+  const int p1 = (p + 1 == Np) ? 0 : p + 1, q1 = (q + 1 == Nq) ? 0 : q + 1;
+  const int vtx[4] = {p * Nq + q, p * Nq + q1, p1 * Nq + q, p1 * Nq + q1};
+  C acc = czero<C>();
+  const size_t base = (size_t)tile * 8 * nrows + lr;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    acc += cmul(p_load<T, PT>(P, Pscale, base + (size_t)(2 * c) * nrows, tile), e0[vtx[c]]);
+    acc += cmul(p_load<T, PT>(P, Pscale, base + (size_t)(2 * c + 1) * nrows, tile), e0[nc + vtx[c]]);
+  }
+  f0[(size_t)alpha * nf + (p * a + i) * Nxf + q * a + j] = acc;
+}
+
+// e_coarse = P^H e_fine.  One warp per coarse vertex v = (p, q): it gathers the
+// rows of the four tiles that have v as a corner (tile (p-di, q-dj) sees v as
+// its corner c = 2 di + dj) plus v's own fine site (identity row), so every
+// coarse value is written once and no atomics are needed.
+template <typename T, typename PT>
+__global__ void __launch_bounds__(256)
+k_restrict(const typename cplx<T>::type* __restrict__ ef, typename cplx<T>::type* __restrict__ ec,
+           const PT* __restrict__ P, const float* __restrict__ Pscale,
+           int Nxf, int a, int nrows, int Np, int Nq) {
+  using C = typename cplx<T>::type;
+  const int nc = Np * Nq;
+  const int nf = nc * a * a;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= nc) return;
+  const int p = warp / Nq, q = warp - (warp / Nq) * Nq;
+  const C* f0 = ef + (size_t)blockIdx.y * 2 * nf;
+  C acc0 = czero<C>(), acc1 = czero<C>();
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int di = c >> 1, dj = c & 1;
+    const int pT = (p - di < 0) ? Np - 1 : p - di;
+    const int qT = (q - dj < 0) ? Nq - 1 : q - dj;
+    const int tile = pT * Nq + qT;
+    const size_t base = (size_t)tile * 8 * nrows + (size_t)(2 * c) * nrows;
+    for (int lr = lane; lr < nrows; lr += 32) {
+      const int l = (lr >> 1) + 1, alpha = lr & 1;
+      const int i = l / a, j = l - (l / a) * a;
+      const C f = f0[(size_t)alpha * nf + (pT * a + i) * Nxf + qT * a + j];
+      acc0 += cmulc(p_load<T, PT>(P, Pscale, base + lr, tile), f);
+      acc1 += cmulc(p_load<T, PT>(P, Pscale, base + nrows + lr, tile), f);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    acc0.x += __shfl_xor_sync(0xffffffffu, acc0.x, o);
+    acc0.y += __shfl_xor_sync(0xffffffffu, acc0.y, o);
+    acc1.x += __shfl_xor_sync(0xffffffffu, acc1.x, o);
+    acc1.y += __shfl_xor_sync(0xffffffffu, acc1.y, o);
+  }
+  if (lane == 0) {
+    const int sv = (p * a) * Nxf + q * a;
+    C* e0 = ec + (size_t)blockIdx.y * 2 * nc;
+    e0[warp] = acc0 + f0[sv];
+    e0[nc + warp] = acc1 + f0[nf + sv];
+  }
+}
+
+}  // namespace
+
+template <typename T, typename PT>
+cudaError_t launch_prolong(const typename cplx<T>::type* ec, typename cplx<T>::type* ef, const PT* P,
+                           const float* Pscale, int Nxf, int a, int Np, int Nq, int R, cudaStream_t st) {
+  const int nrows = 2 * (a * a - 1);
+  const int total = Np * Nq * (nrows + 2);
+  dim3 grid((total + 255) / 256, R);
+  k_prolong<T, PT><<<grid, 256, 0, st>>>(ec, ef, P, Pscale, Nxf, a, nrows, Np, Nq);
+  return cudaGetLastError();
+}
+
+template <typename T, typename PT>
+cudaError_t launch_restrict(const typename cplx<T>::type* ef, typename cplx<T>::type* ec, const PT* P,
+                            const float* Pscale, int Nxf, int a, int Np, int Nq, int R, cudaStream_t st) {
+  const int nrows = 2 * (a * a - 1);
+  const int nc = Np * Nq;
+  dim3 grid((nc * 32 + 255) / 256, R);
+  k_restrict<T, PT><<<grid, 256, 0, st>>>(ef, ec, P, Pscale, Nxf, a, nrows, Np, Nq);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_prolong<double, double2>(const double2*, double2*, const double2*, const float*, int,
+                                                     int, int, int, int, cudaStream_t);
+template cudaError_t launch_prolong<float, __half2>(const float2*, float2*, const __half2*, const float*, int, int,
+                                                    int, int, int, cudaStream_t);
+template cudaError_t launch_restrict<double, double2>(const double2*, double2*, const double2*, const float*, int,
+                                                      int, int, int, int, cudaStream_t);
+template cudaError_t launch_restrict<float, __half2>(const float2*, float2*, const __half2*, const float*, int,
+                                                     int, int, int, int, cudaStream_t);

@@ -1,0 +1,303 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element.
+
+Tolerances: FP64 kernels 1e-13 relative (max-norm over the output), setup
+products (P, coarse blocks) 1e-12, FP32 stencil 2e-6; whole solves reach the
+1e-10 true relative residual with iteration counts within 10 % of the oracle's.
+"""
+import numpy as np
+import pytest
+
+from oracle import amg, krylov
+from oracle import wilson as W
+from paper_2608_03515_b300 import fixtures as fx
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2608_03515_b300 import build  # noqa: E402
+
+build.build()
+from paper_2608_03515_b300 import amamg as A  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def random_links(Nt, Nx, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.exp(1j * rng.uniform(-np.pi, np.pi, size=(2, Nt, Nx)))
+
+
+def dev(a, dtype=torch.complex128):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV).to(dtype)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def relerr(got, want):
+    return np.max(np.abs(got - want)) / max(np.max(np.abs(want)), 1e-300)
+
+
+def lattice_vec(flat, Nt, Nx):
+    return W.from_flat(flat, Nt, Nx)
+
+
+def oracle_P_tiles(P, Nt, Nx, a):
+    """Oracle interpolator in the library's per-tile [8][nrows] layout."""
+    Np, Nq = Nt // a, Nx // a
+    nrows = 2 * (a * a - 1)
+    Pd = P.tocsr()
+    out = np.zeros((Np * Nq, 8, nrows), dtype=complex)
+    for p in range(Np):
+        for q in range(Nq):
+            tile = p * Nq + q
+            for lr in range(nrows):
+                l, alpha = lr // 2 + 1, lr % 2
+                t, x = p * a + l // a, q * a + l % a
+                row = 2 * (t * Nx + x) + alpha
+                for c in range(4):
+                    v = amg.corner_vertex(Nt, Nx, a, p, q, c)
+                    for beta in range(2):
+                        out[tile, 2 * c + beta, lr] = Pd[row, 2 * v + beta]
+    return out
+
+
+def make(Nt, Nx, aggs, m0=0.1, seed=1, U=None, precision=0, restart=30):
+    U = random_links(Nt, Nx, seed) if U is None else U
+    params = A.make_params(aggs, precision=precision, restart=restart)
+    hier = A.setup(dev(U), m0, params)
+    D = W.dirac_matrix(U, m0)
+    levels = amg.build_hierarchy(D, Nt, Nx, aggs)
+    return U, D, hier, levels
+
+
+# ------------------------------------------------------------------ Wilson stencil
+
+@pytest.mark.parametrize("Nt,Nx,R", [(8, 8, 1), (16, 32, 3), (34, 18, 2)])
+def test_apply_D_fp64_and_fp32(Nt, Nx, R):
+    U = random_links(Nt, Nx, 3)
+    hier = A.setup(dev(U), 0.07, A.make_params([2]))
+    psi = fx.gaussian_rhs(R, Nt, Nx, 4)
+    out = torch.empty(R, 2, Nt, Nx, dtype=torch.complex128, device=DEV)
+    A.apply_D(hier, dev(psi), out)
+    got = host(out)
+    want = np.stack([W.apply_dirac(U, 0.07, psi[r]) for r in range(R)])
+    assert relerr(got, want) <= 1e-13
+    D = W.dirac_matrix(U, 0.07)
+    for r in range(R):
+        assert relerr(got[r], lattice_vec(D @ W.to_flat(psi[r]), Nt, Nx)) <= 1e-13
+    # FP32: inputs rounded to complex64, reference in FP64 on the rounded inputs
+    psi32 = psi.astype(np.complex64)
+    out32 = torch.empty(R, 2, Nt, Nx, dtype=torch.complex64, device=DEV)
+    A.apply_D(hier, dev(psi32, torch.complex64), out32)
+    U32 = U.astype(np.complex64).astype(np.complex128)
+    want32 = np.stack([W.apply_dirac(U32, 0.07, psi32[r].astype(np.complex128)) for r in range(R)])
+    assert relerr(host(out32), want32) <= 2e-6
+
+
+def test_apply_D_full_size_256_properties():
+    """256^2 (the benchmark lattice): full comparison with the matrix-free oracle."""
+    Nt = Nx = 256
+    theta = fx.metropolis_u1(Nt, Nx, 6.0, 20, 2)
+    U = fx.links_from_angles(theta)
+    hier = A.setup(dev(U), 0.03, A.make_params([4, 2]))
+    psi = fx.gaussian_rhs(1, Nt, Nx, 3)
+    out = torch.empty(1, 2, Nt, Nx, dtype=torch.complex128, device=DEV)
+    A.apply_D(hier, dev(psi), out)
+    assert relerr(host(out)[0], W.apply_dirac(U, 0.03, psi[0])) <= 1e-13
+
+
+# ------------------------------------------------------------------ structure and setup
+
+@pytest.mark.parametrize("Nt,Nx,aggs", [(8, 8, [4]), (16, 16, [2, 2]), (32, 32, [4, 2]), (16, 24, [4])])
+def test_structure_bit_exact(Nt, Nx, aggs):
+    U, D, hier, levels = make(Nt, Nx, aggs)
+    for l in range(len(aggs)):
+        role, owner, offs = A.export_structure(hier, l)
+        L = levels[l]
+        assert np.array_equal(role, amg.site_roles(L.Nt, L.Nx, aggs[l]))
+        assert np.array_equal(owner, amg.owner_tiles(L.Nt, L.Nx, aggs[l]))
+        assert offs == [tuple(o) for o in levels[l + 1].offsets]
+        assert hier.level_info(l + 1)[:2] == (levels[l + 1].Nt, levels[l + 1].Nx)
+
+
+@pytest.mark.parametrize("Nt,Nx,aggs", [(8, 8, [4]), (8, 8, [2]), (16, 16, [2, 2]), (32, 32, [4, 2]),
+                                        (32, 16, [4, 2])])
+def test_interpolator_and_galerkin_fp64(Nt, Nx, aggs):
+    U, D, hier, levels = make(Nt, Nx, aggs, m0=0.05, seed=5)
+    for l, a in enumerate(aggs):
+        L = levels[l]
+        want = oracle_P_tiles(L.P, L.Nt, L.Nx, a)
+        got = torch.empty(want.shape, dtype=torch.complex128, device=DEV)
+        A.export_P(hier, l, got)
+        assert relerr(host(got), want) <= 1e-12
+        C = levels[l + 1]
+        Bw = amg.block_stencil(C.A, C.offsets, C.Nt, C.Nx)            # [K, n, 2, 2]
+        Bw = np.transpose(Bw.reshape(len(C.offsets), C.Nt * C.Nx, 4), (0, 2, 1))
+        Bg = torch.empty(Bw.shape, dtype=torch.complex128, device=DEV)
+        A.export_coarse(hier, l + 1, Bg)
+        assert relerr(host(Bg), Bw) <= 1e-12
+
+
+# ------------------------------------------------------------------ transfers, coarse operator
+
+@pytest.mark.parametrize("Nt,Nx,aggs,R", [(16, 16, [4], 2), (32, 32, [4, 2], 1), (16, 24, [2, 2], 3)])
+def test_transfers_and_coarse_apply_fp64(Nt, Nx, aggs, R):
+    U, D, hier, levels = make(Nt, Nx, aggs, m0=0.2, seed=6)
+    rng = np.random.Generator(np.random.PCG64(7))
+    for l in range(len(aggs)):
+        F, C = levels[l], levels[l + 1]
+        ec = rng.standard_normal((R, 2, C.Nt, C.Nx)) + 1j * rng.standard_normal((R, 2, C.Nt, C.Nx))
+        ef = rng.standard_normal((R, 2, F.Nt, F.Nx)) + 1j * rng.standard_normal((R, 2, F.Nt, F.Nx))
+        out_f = torch.empty(R, 2, F.Nt, F.Nx, dtype=torch.complex128, device=DEV)
+        out_c = torch.empty(R, 2, C.Nt, C.Nx, dtype=torch.complex128, device=DEV)
+        A.apply_P(hier, l, dev(ec), out_f)
+        A.apply_PH(hier, l, dev(ef), out_c)
+        gf, gc = host(out_f), host(out_c)
+        for r in range(R):
+            wf = lattice_vec(F.P @ W.to_flat(ec[r]), F.Nt, F.Nx)
+            wc = lattice_vec(F.P.conj().T @ W.to_flat(ef[r]), C.Nt, C.Nx)
+            assert relerr(gf[r], wf) <= 1e-13
+            assert relerr(gc[r], wc) <= 1e-13
+        A.apply_coarse(hier, l + 1, dev(ec), out_c)
+        gc = host(out_c)
+        for r in range(R):
+            assert relerr(gc[r], lattice_vec(C.A @ W.to_flat(ec[r]), C.Nt, C.Nx)) <= 1e-12
+
+
+# ------------------------------------------------------------------ smoother, coarsest, V-cycle
+
+@pytest.mark.parametrize("sweeps", [1, 2])
+def test_smoothers_fp64(sweeps):
+    Nt = Nx = 32
+    U, D, hier, levels = make(Nt, Nx, [2, 2], m0=0.1, seed=8)
+    rng = np.random.Generator(np.random.PCG64(9))
+    for l in range(2):
+        L = levels[l]
+        r = rng.standard_normal((1, 2, L.Nt, L.Nx)) + 1j * rng.standard_normal((1, 2, L.Nt, L.Nx))
+        e0 = rng.standard_normal((1, 2, L.Nt, L.Nx)) + 1j * rng.standard_normal((1, 2, L.Nt, L.Nx))
+        e = dev(e0)
+        A.smooth(hier, l, dev(r), e, sweeps)
+        want = W.to_flat(e0[0])
+        for _ in range(sweeps):
+            want = amg.gs_sweep(L.A, L.dinv, L.colour, want, W.to_flat(r[0]))
+        assert relerr(host(e)[0], lattice_vec(want, L.Nt, L.Nx)) <= 1e-12
+
+
+def test_coarsest_solve_and_vcycle_fp64():
+    Nt = Nx = 32
+    U, D, hier, levels = make(Nt, Nx, [4, 2], m0=0.05, seed=10)
+    C = levels[-1]
+    rng = np.random.Generator(np.random.PCG64(11))
+    rc = rng.standard_normal((2, 2, C.Nt, C.Nx)) + 1j * rng.standard_normal((2, 2, C.Nt, C.Nx))
+    ec = torch.empty(rc.shape, dtype=torch.complex128, device=DEV)
+    A.coarsest_solve(hier, dev(rc), ec)
+    import scipy.linalg as sla
+    got = host(ec)
+    cond = np.linalg.cond(C.A.toarray())
+    for r in range(2):
+        want = lattice_vec(sla.lu_solve(C.lu, W.to_flat(rc[r])), C.Nt, C.Nx)
+        assert relerr(got[r], want) <= 1e-15 * cond * 10
+    psi = fx.gaussian_rhs(2, Nt, Nx, 12)
+    e = torch.empty(psi.shape, dtype=torch.complex128, device=DEV)
+    A.vcycle(hier, dev(psi), e)
+    got = host(e)
+    for r in range(2):
+        want = lattice_vec(amg.vcycle(levels, W.to_flat(psi[r])), Nt, Nx)
+        assert relerr(got[r], want) <= 1e-11
+
+
+# ------------------------------------------------------------------ whole solves
+
+def oracle_solve(D, levels, b, m, tol=1e-10):
+    return krylov.fgmres(lambda v: D @ v, lambda r: amg.vcycle(levels, r), b, m, tol, 5000)
+
+
+@pytest.mark.parametrize("aggs", [[4], [4, 2]])
+def test_solve_fp64_matches_oracle_c1_field(aggs):
+    """32^2, beta = 3 quenched field, m0 = m_crit + 0.05 (m_crit from the oracle's spectrum)."""
+    Nt = Nx = 32
+    theta = fx.metropolis_u1(Nt, Nx, 3.0, 500, 0)
+    U = fx.links_from_angles(theta)
+    m0 = -0.1383495190759743 + 0.05
+    U_, D, hier, levels = make(Nt, Nx, aggs, m0=m0, U=U)
+    psi = fx.gaussian_rhs(1, Nt, Nx, 1)
+    x = torch.empty(psi.shape, dtype=torch.complex128, device=DEV)
+    info = A.solve(hier, dev(psi), x)
+    ref = oracle_solve(D, levels, W.to_flat(psi[0]), 30)
+    assert info[0].status == A.OK
+    xg = host(x)[0]
+    # independent FP64 check of the returned solution
+    res = np.linalg.norm(W.to_flat(psi[0]) - D @ W.to_flat(xg)) / np.linalg.norm(psi[0])
+    assert res <= 1e-10 and info[0].true_relres <= 1e-10
+    assert abs(info[0].iterations - ref.iterations) <= max(1, 0.1 * ref.iterations)
+    assert relerr(xg, lattice_vec(ref.x, Nt, Nx)) <= 1e-7
+
+
+def test_solve_multi_rhs_each_equals_single():
+    Nt = Nx = 16
+    U, D, hier, levels = make(Nt, Nx, [2, 2], m0=0.05, seed=13)
+    psi = fx.gaussian_rhs(3, Nt, Nx, 14)
+    x = torch.empty(psi.shape, dtype=torch.complex128, device=DEV)
+    info = A.solve(hier, dev(psi), x)
+    xb = host(x)
+    for r in range(3):
+        x1 = torch.empty((1,) + psi.shape[1:], dtype=torch.complex128, device=DEV)
+        i1 = A.solve(hier, dev(psi[r:r + 1]), x1)
+        assert i1[0].iterations == info[r].iterations
+        assert relerr(host(x1)[0], xb[r]) <= 1e-12
+        assert info[r].true_relres <= 1e-10
+
+
+def test_solve_mixed_precision_reaches_tolerance():
+    Nt = Nx = 32
+    theta = fx.metropolis_u1(Nt, Nx, 3.0, 500, 0)
+    U = fx.links_from_angles(theta)
+    m0 = -0.1383495190759743 + 0.05
+    hier64 = A.setup(dev(U), m0, A.make_params([4, 2]))
+    hier32 = A.setup(dev(U), m0, A.make_params([4, 2], precision=A.SOLVE_MIXED))
+    psi = fx.gaussian_rhs(1, Nt, Nx, 1)
+    x64 = torch.empty(psi.shape, dtype=torch.complex128, device=DEV)
+    x32 = torch.empty(psi.shape, dtype=torch.complex128, device=DEV)
+    i64 = A.solve(hier64, dev(psi), x64)
+    i32 = A.solve(hier32, dev(psi), x32)
+    assert i32[0].status == A.OK and i32[0].true_relres <= 1e-10
+    D = W.dirac_matrix(U, m0)
+    res = np.linalg.norm(W.to_flat(psi[0]) - D @ W.to_flat(host(x32)[0])) / np.linalg.norm(psi[0])
+    assert res <= 1e-10
+    assert i32[0].iterations <= 1.1 * i64[0].iterations + 1
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_zero_and_nonfinite_rhs():
+    Nt = Nx = 16
+    U, D, hier, levels = make(Nt, Nx, [4], m0=0.1, seed=15)
+    psi = np.zeros((2, 2, Nt, Nx), dtype=complex)
+    psi[1] = fx.gaussian_rhs(1, Nt, Nx, 16)[0]
+    x = torch.full(psi.shape, 7.0, dtype=torch.complex128, device=DEV)
+    info = A.solve(hier, dev(psi), x)
+    assert info[0].status == A.OK and info[0].iterations == 0
+    assert np.all(host(x)[0] == 0)
+    assert info[1].status == A.OK and info[1].true_relres <= 1e-10
+    psi[1, 0, 3, 3] = np.nan
+    with pytest.raises(A.AmamgError) as ei:
+        A.solve(hier, dev(psi), x)
+    assert ei.value.status == A.ERR_NONFINITE
+
+
+def test_invalid_arguments_rejected():
+    Nt = Nx = 16
+    U, D, hier, levels = make(Nt, Nx, [4], m0=0.1, seed=17)
+    v = torch.zeros(1, 2, Nt, Nx, dtype=torch.complex128, device=DEV)
+    with pytest.raises(A.AmamgError):
+        A.apply_P(hier, 1, v, v)          # level 1 is the coarsest: nothing below it
+    with pytest.raises(A.AmamgError):
+        A.apply_coarse(hier, 0, v, v)     # level 0 is the Wilson operator
+    L = A.lib()
+    assert L.amamg_apply_D(hier.h, None, None, 1, 0, None) == A.ERR_INVALID_ARG
