@@ -162,6 +162,46 @@ def run_reference(args):
     }))
 
 
+# ----------------------------------------------------------------------------- kernel probe
+
+def run_probe(args):
+    """A small, self-contained case of one kernel family, e.g. for an ncu capture:
+    random-phase links on an L x L lattice, tiles 4 then 2 (4, 4, 2 from 1024 up)."""
+    import torch
+    from paper_2608_03515_b300 import build as _b
+    _b.build()
+    from paper_2608_03515_b300 import amamg as A
+    dev = torch.device("cuda:0")
+    Lp = args.lattice
+    rng = np.random.Generator(np.random.PCG64(5))
+    U = torch.from_numpy(np.exp(1j * rng.uniform(-np.pi, np.pi, size=(2, Lp, Lp)))).to(dev)
+    aggs = [4, 4, 2] if Lp >= 1024 else [4, 2]
+    prec = A.SOLVE_MIXED if args.prec == "f32" else A.SOLVE_FP64
+    h = A.setup(U, 0.1, A.make_params(aggs, precision=prec))
+    dt = torch.complex64 if args.prec == "f32" else torch.complex128
+    x = torch.randn(args.rhs, 2, Lp, Lp, dtype=dt, device=dev)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for rep in range(args.reps + 1):
+        if rep == 1:
+            ev[0].record(stream)
+        if args.probe == "apply_D":
+            A.apply_D(h, x, y)
+        elif args.probe == "vcycle":
+            A.vcycle(h, x, y)
+        elif args.probe == "coarsest":
+            nt, nx, _ = h.level_info(len(aggs))
+            xc = torch.randn(args.rhs, 2, nt, nx, dtype=torch.complex128, device=dev)
+            A.coarsest_solve(h, xc, torch.empty_like(xc))
+        else:
+            A.solve(h, x.to(torch.complex128), torch.empty(x.shape, dtype=torch.complex128, device=dev))
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    print(json.dumps({"probe": args.probe, "lattice": Lp, "rhs": args.rhs, "prec": args.prec,
+                      "ms_per_rep": ev[0].elapsed_time(ev[1]) / max(args.reps, 1)}))
+
+
 # ----------------------------------------------------------------------------- our arm
 
 def main():
@@ -171,11 +211,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--probe", default=None, choices=["apply_D", "vcycle", "solve", "coarsest"],
+                    help="time one kernel family on a small random-phase case (for profiler captures)")
+    ap.add_argument("--lattice", type=int, default=512)
+    ap.add_argument("--rhs", type=int, default=1)
+    ap.add_argument("--prec", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.probe:
+        run_probe(args)
         return
 
     import torch
@@ -243,6 +292,8 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")
+    torch.cuda.profiler.start()          # profiler window (ncu --profile-from-start off) = timed region
     t_wall = time.perf_counter()
     # timed steps use the right-hand sides after the warm-up ones
     psis_w = psis
@@ -268,6 +319,8 @@ def main():
     if world > 1:
         dist.barrier()
     wall_s = time.perf_counter() - t_wall
+    torch.cuda.profiler.stop()
+    torch.cuda.nvtx.range_pop()
     clk = clocks.stop()
     launches = sum(A.launch_count(h) for h in hs64) - launches0
     total_ms = float(np.sum(step_ms))

@@ -147,8 +147,17 @@ int coarse_offsets(const Offsets& fine, int Nt, int Nx, int a, Offsets* out) {
 }
 
 // ----------------------------------------------------------------- workspace
+void clear_graphs(amamg_ctx* h) {
+  for (auto g : h->step_graphs)
+    if (g) cudaGraphExecDestroy(g);
+  h->step_graphs.clear();
+  h->step_graph_kernels.clear();
+  h->graph_R = 0;
+}
+
 int ensure_vcycle_ws(amamg_ctx* h, int R) {
   if (R <= h->Rcap) return AMAMG_OK;
+  clear_graphs(h);
   for (auto& L : h->lv) {
     dfree(L.r64); dfree(L.e64); dfree(L.r32); dfree(L.e32);
   }
@@ -165,6 +174,7 @@ int ensure_vcycle_ws(amamg_ctx* h, int R) {
 int ensure_solver_ws(amamg_ctx* h, int R) {
   const int m = h->prm.restart;
   if (R <= h->Rsolve && m <= h->mcap) return AMAMG_OK;
+  clear_graphs(h);
   dfree(h->V); dfree(h->Z64); dfree(h->Z32); dfree(h->v32); dfree(h->w); dfree(h->res);
   dfree(h->partial); dfree(h->d_h); dfree(h->d_inv); dfree(h->d_y);
   if (h->h_h) cudaFreeHost(h->h_h);
@@ -243,6 +253,19 @@ int smooth_impl(amamg_ctx* h, int l, typename cplx<T>::type* e, const typename c
   }
   const double blk = f64 ? 16.0 * 4 : (4.0 * 4 + 4.0);
   const double bytes = (double)L.n / 16 * ((L.off.K - 1) * blk + 4 * cb + R * 2 * 3 * cb);
+  if (sweeps > 0 && cluster_sweep_threads(L.n) <= 1024) {
+    // every colour of every sweep in one clustered launch
+    if constexpr (f64)
+      return launch(h, "coarse_smooth_f64", bytes * 16 * sweeps, st, [&] {
+        return launch_coarse_sweeps_cluster<double, double2>(e, r, L.B64, nullptr, L.Dinv64, L.off, L.Nt, L.Nx,
+                                                             sweeps, R, st);
+      });
+    else
+      return launch(h, "coarse_smooth_f32", bytes * 16 * sweeps, st, [&] {
+        return launch_coarse_sweeps_cluster<float, __half2>(e, r, L.B16, L.Bs, L.Dinv32, L.off, L.Nt, L.Nx, sweeps,
+                                                            R, st);
+      });
+  }
   for (int s = 0; s < sweeps; ++s)
     for (int c = 0; c < 16; ++c) {
       int rc;
@@ -320,13 +343,24 @@ int op_coarsest(amamg_ctx* h, const Cv* r, Cv* e, int R, cudaStream_t st) {
                 [&] { return launch_dense_gemv<Cv>(h->Ainv, r, e, h->nd, R, st); });
 }
 
+// coarsest level inside a V-cycle: FP64 inverse for FP64 vectors, its FP32
+// rounding for the FP32 (mixed-precision) V-cycle
+int vcycle_coarsest(amamg_ctx* h, const double2* r, double2* e, int R, cudaStream_t st) {
+  return op_coarsest<double2>(h, r, e, R, st);
+}
+int vcycle_coarsest(amamg_ctx* h, const float2* r, float2* e, int R, cudaStream_t st) {
+  const double bytes = (double)h->nd * h->nd * 8.0 + (double)R * 2 * h->nd * 8.0;
+  return launch(h, "coarsest_gemv_f32", bytes, st,
+                [&] { return launch_dense_gemv32(h->Ainv32, r, e, h->nd, R, st); });
+}
+
 // V-cycle of Algorithm 1 (start vector 0, no pre-smoothing) from level l:
 // e = P M_{l+1}(P^H r), then post-smoothing sweeps on A_l e = r.
 template <typename T>
 int vcycle_from(amamg_ctx* h, int l, const typename cplx<T>::type* r, typename cplx<T>::type* e, int R,
                 cudaStream_t st) {
   const int Lc = (int)h->lv.size() - 1;
-  if (l == Lc) return op_coarsest(h, r, e, R, st);
+  if (l == Lc) return vcycle_coarsest(h, r, e, R, st);
   Level& C = h->lv[l + 1];
   typename cplx<T>::type *rc, *ec;
   if constexpr (sizeof(T) == 8) { rc = C.r64; ec = C.e64; } else { rc = C.r32; ec = C.e32; }
@@ -357,7 +391,91 @@ void back_solve(const std::vector<double2>& H, int ldh, const std::vector<double
   }
 }
 
-int fgmres(amamg_ctx* h, const double2* psi, double2* x, int R, cudaStream_t st, amamg_solve_info* info) {
+// One Arnoldi step j for all R right-hand sides, entirely on the device:
+// z_j = M(v_j), w = D z_j, two classical Gram-Schmidt passes against v_0..v_j,
+// ||w||, v_{j+1} = w / ||w||, and the copy of the new Hessenberg column and norm
+// to pinned host memory.  Capturable as one CUDA graph.
+int arnoldi_step(amamg_ctx* h, int j, int R, cudaStream_t st) {
+  const int m = h->prm.restart;
+  const long len = 2L * h->lv[0].n;
+  const size_t vr = (size_t)len, vi = (size_t)R * len;
+  const int ldh = 3 * (m + 2);
+  double2* d_h1 = h->d_h;
+  const double2* vj = h->V + (size_t)j * vi;
+  if (h->prm.precision == AMAMG_SOLVE_MIXED) {
+    float2* zj = h->Z32 + (size_t)j * vi;
+    CKS(launch(h, "cast_f64_f32", (double)R * len * 24.0, st,
+               [&] { return launch_cast<double2, float2>(vj, h->v32, (long)R * len, st); }));
+    CKS(vcycle_from<float>(h, 0, h->v32, zj, R, st));
+    const Level& L = h->lv[0];
+    CKS(launch(h, "dslash_mixed", (double)L.n * (R * (16.0 + 32.0) + 32.0), st, [&] {
+      return launch_dslash<float2, double2, double>(zj, h->w, nullptr, h->U64, h->m0 + 2.0, L.Nt, L.Nx, R, st);
+    }));
+  } else {
+    double2* zj = h->Z64 + (size_t)j * vi;
+    CKS(vcycle_from<double>(h, 0, vj, zj, R, st));
+    CKS(op_dslash<double>(h, zj, h->w, nullptr, R, st));
+  }
+  const int J = j + 1;
+  const int nb = dot_blocks(len);
+  for (int pass = 0; pass < 2; ++pass) {
+    const int off = pass * (m + 2);
+    CKS(launch(h, "gs_dots", (double)R * len * 16.0 * (J + 1), st,
+               [&] { return launch_dots(h->V, vi, vr, h->w, vr, len, J, R, h->partial, st); }));
+    CKS(launch(h, "gs_reduce", (double)R * J * nb * 16.0, st,
+               [&] { return launch_reduce(h->partial, nb, J, R, d_h1, ldh, off, 0, nullptr, st); }));
+    CKS(launch(h, "gs_update", (double)R * len * 16.0 * (J + 2), st, [&] {
+      return launch_multi_axpy<double2>(h->w, vr, h->V, vi, vr, d_h1 + off, ldh, J, -1.0, len, R, st);
+    }));
+  }
+  CKS(norms(h, h->w, vr, len, R, d_h1, ldh, 2 * (m + 2), h->d_inv, st));
+  CKS(launch(h, "scale_copy", (double)R * len * 32.0, st, [&] {
+    return launch_scale_copy<double2>(h->V + (size_t)(j + 1) * vi, vr, h->w, vr, h->d_inv, len, R, st);
+  }));
+  CK(cudaMemcpyAsync(h->h_h, h->d_h, sizeof(double2) * R * ldh, cudaMemcpyDeviceToHost, st));
+  return AMAMG_OK;
+}
+
+// Runs Arnoldi step j: replays its captured graph (capturing it on first use),
+// or launches eagerly when kernel profiling is on.
+int run_step(amamg_ctx* h, int j, int R, cudaStream_t st) {
+  if (h->prof || !h->use_graphs) return arnoldi_step(h, j, R, st);
+  if (h->graph_R != R) {
+    clear_graphs(h);
+    h->graph_R = R;
+  }
+  if ((int)h->step_graphs.size() <= j) {
+    h->step_graphs.resize(j + 1, nullptr);
+    h->step_graph_kernels.resize(j + 1, 0);
+  }
+  if (!h->step_graphs[j]) {
+    const long long l0 = h->launches;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const int rc = arnoldi_step(h, j, R, st);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(st, &g);
+    if (rc != AMAMG_OK || ec != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      if (h->err.empty()) h->err = std::string("graph capture: ") + cudaGetErrorString(ec);
+      return rc != AMAMG_OK ? rc : AMAMG_ERR_CUDA;
+    }
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      h->err = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ei);
+      return AMAMG_ERR_CUDA;
+    }
+    h->step_graphs[j] = ex;
+    h->step_graph_kernels[j] = h->launches - l0;
+    h->launches = l0;
+  }
+  CK(cudaGraphLaunch(h->step_graphs[j], st));
+  h->launches += h->step_graph_kernels[j];
+  return AMAMG_OK;
+}
+
+int fgmres_on(amamg_ctx* h, const double2* psi, double2* x, int R, cudaStream_t st, amamg_solve_info* info) {
   const int m = h->prm.restart;
   const long len = 2L * h->lv[0].n;
   const size_t vr = (size_t)len, vi = (size_t)R * len;
@@ -412,40 +530,7 @@ int fgmres(amamg_ctx* h, const double2* psi, double2* x, int R, cudaStream_t st,
     for (int r = 0; r < R; ++r) { k[r] = 0; building[r] = !done[r]; }
     int j = 0;
     for (; j < m; ++j) {
-      const double2* vj = h->V + (size_t)j * vi;
-      // z_j = M(v_j)
-      if (mixed) {
-        float2* zj = h->Z32 + (size_t)j * vi;
-        CKS(launch(h, "cast_f64_f32", (double)R * len * 24.0, st,
-                   [&] { return launch_cast<double2, float2>(vj, h->v32, (long)R * len, st); }));
-        CKS(vcycle_from<float>(h, 0, h->v32, zj, R, st));
-        const Level& L = h->lv[0];
-        CKS(launch(h, "dslash_mixed", (double)L.n * (R * (16.0 + 32.0) + 32.0), st, [&] {
-          return launch_dslash<float2, double2, double>(zj, h->w, nullptr, h->U64, h->m0 + 2.0, L.Nt, L.Nx, R, st);
-        }));
-      } else {
-        double2* zj = h->Z64 + (size_t)j * vi;
-        CKS(vcycle_from<double>(h, 0, vj, zj, R, st));
-        CKS(op_dslash<double>(h, zj, h->w, nullptr, R, st));
-      }
-      // classical Gram-Schmidt, twice
-      const int J = j + 1;
-      const int nb = dot_blocks(len);
-      for (int pass = 0; pass < 2; ++pass) {
-        const int off = pass * (m + 2);
-        CKS(launch(h, "gs_dots", (double)R * len * 16.0 * (J + 1), st,
-                   [&] { return launch_dots(h->V, vi, vr, h->w, vr, len, J, R, h->partial, st); }));
-        CKS(launch(h, "gs_reduce", (double)R * J * nb * 16.0, st,
-                   [&] { return launch_reduce(h->partial, nb, J, R, d_h1, ldh, off, 0, nullptr, st); }));
-        CKS(launch(h, "gs_update", (double)R * len * 16.0 * (J + 2), st, [&] {
-          return launch_multi_axpy<double2>(h->w, vr, h->V, vi, vr, d_h1 + off, ldh, J, -1.0, len, R, st);
-        }));
-      }
-      CKS(norms(h, h->w, vr, len, R, d_h1, ldh, 2 * (m + 2), h->d_inv, st));
-      CKS(launch(h, "scale_copy", (double)R * len * 32.0, st, [&] {
-        return launch_scale_copy<double2>(h->V + (size_t)(j + 1) * vi, vr, h->w, vr, h->d_inv, len, R, st);
-      }));
-      CK(cudaMemcpyAsync(h->h_h, h->d_h, sizeof(double2) * R * ldh, cudaMemcpyDeviceToHost, st));
+      CKS(run_step(h, j, R, st));
       CK(cudaStreamSynchronize(st));
       ++total;
       bool any = false;
@@ -514,6 +599,17 @@ int fgmres(amamg_ctx* h, const double2* psi, double2* x, int R, cudaStream_t st,
   return rc;
 }
 
+// The solve runs on the handle's own stream, ordered after the caller's stream
+// and before anything the caller enqueues afterwards.
+int fgmres(amamg_ctx* h, const double2* psi, double2* x, int R, cudaStream_t st, amamg_solve_info* info) {
+  CK(cudaEventRecord(h->ev_in, st));
+  CK(cudaStreamWaitEvent(h->ws, h->ev_in, 0));
+  const int rc = fgmres_on(h, psi, x, R, h->ws, info);
+  CK(cudaEventRecord(h->ev_out, h->ws));
+  CK(cudaStreamWaitEvent(st, h->ev_out, 0));
+  return rc;
+}
+
 // ----------------------------------------------------------------- setup
 int check_params(const amamg_params* p, int Nt, int Nx, std::string* why) {
   if (!p) { *why = "params is NULL"; return AMAMG_ERR_INVALID_ARG; }
@@ -541,7 +637,12 @@ void free_all(amamg_ctx* h) {
     dfree(L.P64); dfree(L.P16); dfree(L.Ps);
     dfree(L.r64); dfree(L.e64); dfree(L.r32); dfree(L.e32);
   }
-  dfree(h->U64); dfree(h->U32); dfree(h->Ainv); dfree(h->d_err);
+  clear_graphs(h);
+  if (h->ws) cudaStreamDestroy(h->ws);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
+  h->ws = nullptr; h->ev_in = h->ev_out = nullptr;
+  dfree(h->U64); dfree(h->U32); dfree(h->Ainv); dfree(h->Ainv32); dfree(h->d_err);
   dfree(h->V); dfree(h->Z64); dfree(h->Z32); dfree(h->v32); dfree(h->w); dfree(h->res);
   dfree(h->partial); dfree(h->d_h); dfree(h->d_inv); dfree(h->d_y);
   if (h->h_h) cudaFreeHost(h->h_h);
@@ -559,6 +660,9 @@ int do_setup(amamg_ctx* h, const void* Uin, cudaStream_t st) {
     F.Nt = h->Nt; F.Nx = h->Nx; F.n = h->Nt * h->Nx;
   }
   const size_t nl = 2 * (size_t)h->lv[0].n;
+  CK(cudaStreamCreateWithFlags(&h->ws, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
   CKS(dalloc(h, &h->U64, nl));
   CKS(dalloc(h, &h->U32, nl));
   CKS(dalloc(h, &h->d_err, 1));
@@ -630,6 +734,9 @@ int do_setup(amamg_ctx* h, const void* Uin, cudaStream_t st) {
   }
   if (rc == AMAMG_OK)
     rc = launch(h, "setup_coarsest", 0.0, st, [&] { return launch_gather_cols(X, h->Ainv, perm, h->nd, st); });
+  if (rc == AMAMG_OK) rc = dalloc(h, &h->Ainv32, nd * nd);
+  if (rc == AMAMG_OK)
+    rc = launch(h, "setup_cast", 0.0, st, [&] { return launch_cast<double2, float2>(h->Ainv, h->Ainv32, (long)(nd * nd), st); });
   int herr = 0;
   if (rc == AMAMG_OK && cudaMemcpyAsync(&herr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = AMAMG_ERR_CUDA;
   if (rc == AMAMG_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = AMAMG_ERR_CUDA;

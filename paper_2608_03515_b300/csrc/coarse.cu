@@ -6,7 +6,11 @@
 // consecutive sites).  Offsets are the canonical (dt mod Nt, dx mod Nx) pairs,
 // sorted, with (0, 0) first.  FP32 path: __half2 entries with one FP32 scale per
 // block ([K][n]).
+#include <cooperative_groups.h>
+
 #include "kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -53,70 +57,173 @@ k_coarse_apply(const typename cplx<T>::type* __restrict__ in, typename cplx<T>::
   o[n + v] = y1;
 }
 
-// One colour of the 16-colour block Gauss-Seidel sweep on A e = r:
-// sites (t, x) with (t mod 4, x mod 4) = (c / 4, c % 4):
-// e_v <- A_vv^{-1} (r_v - sum_{k >= 1} A_{v, v+off_k} e_{v+off_k}).
+// Block Gauss-Seidel update of one coarse site v on A e = r, by one warp:
+// lane k (1 <= k < K) forms A_{v, v+off_k} e_{v+off_k}; the warp sums the lanes
+// (xor-shuffle tree, fixed order) and lane 0 writes
+// e_v = A_vv^{-1} (r_v - sum_{k >= 1} A_{v, v+off_k} e_{v+off_k}).
+// Neighbour values are read through L2 (ld.global.cg) so that the kernel is also
+// correct when other thread blocks of a cluster updated them.
+template <typename T, typename BT>
+__device__ __forceinline__ void gs_site_warp(typename cplx<T>::type* __restrict__ e0,
+                                             const typename cplx<T>::type* __restrict__ r0,
+                                             const BT* __restrict__ B, const float* __restrict__ Bs,
+                                             const typename cplx<T>::type* __restrict__ Dinv, const Offsets& off,
+                                             int Nt, int Nx, int t, int x, int lane) {
+  using C = typename cplx<T>::type;
+  const int n = Nt * Nx;
+  const int v = t * Nx + x;
+  C s0 = czero<C>(), s1 = czero<C>();
+  if (lane >= 1 && lane < off.K) {
+    int tw = t + off.dt[lane]; tw -= (tw >= Nt) ? Nt : 0;
+    int xw = x + off.dx[lane]; xw -= (xw >= Nx) ? Nx : 0;
+    const int w = tw * Nx + xw;
+    const C x0 = __ldcg(e0 + w), x1 = __ldcg(e0 + n + w);
+    s0 = cmul(b_load<T, BT>(B, Bs, lane, 0, n, v), x0) + cmul(b_load<T, BT>(B, Bs, lane, 1, n, v), x1);
+    s1 = cmul(b_load<T, BT>(B, Bs, lane, 2, n, v), x0) + cmul(b_load<T, BT>(B, Bs, lane, 3, n, v), x1);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0.x += __shfl_xor_sync(0xffffffffu, s0.x, o);
+    s0.y += __shfl_xor_sync(0xffffffffu, s0.y, o);
+    s1.x += __shfl_xor_sync(0xffffffffu, s1.x, o);
+    s1.y += __shfl_xor_sync(0xffffffffu, s1.y, o);
+  }
+  if (lane == 0) {
+    const C a0 = r0[v] - s0, a1 = r0[n + v] - s1;
+    const C d00 = Dinv[v], d01 = Dinv[n + v], d10 = Dinv[2 * n + v], d11 = Dinv[3 * n + v];
+    __stcg(e0 + v, cmul(d00, a0) + cmul(d01, a1));
+    __stcg(e0 + n + v, cmul(d10, a0) + cmul(d11, a1));
+  }
+}
+
+// One colour of the 16-colour sweep, sites (t, x) with (t mod 4, x mod 4) =
+// (c / 4, c % 4); one warp per site.
 template <typename T, typename BT>
 __global__ void __launch_bounds__(256)
 k_coarse_colour(typename cplx<T>::type* __restrict__ e, const typename cplx<T>::type* __restrict__ r,
                 const BT* __restrict__ B, const float* __restrict__ Bs,
                 const typename cplx<T>::type* __restrict__ Dinv, Offsets off, int Nt, int Nx, int colour) {
-  using C = typename cplx<T>::type;
   const int n = Nt * Nx;
   const int qx = Nx >> 2;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int idx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (idx >= (n >> 4)) return;
   const int ti = idx / qx;
   const int t = 4 * ti + (colour >> 2);
   const int x = 4 * (idx - ti * qx) + (colour & 3);
-  const int v = t * Nx + x;
   const size_t roff = (size_t)blockIdx.y * 2 * n;
-  C* e0 = e + roff;
-  C s0 = r[roff + v], s1 = r[roff + n + v];
-  for (int k = 1; k < off.K; ++k) {
-    int tw = t + off.dt[k]; tw -= (tw >= Nt) ? Nt : 0;
-    int xw = x + off.dx[k]; xw -= (xw >= Nx) ? Nx : 0;
-    const int w = tw * Nx + xw;
-    const C x0 = e0[w], x1 = e0[n + w];
-    s0 -= cmul(b_load<T, BT>(B, Bs, k, 0, n, v), x0) + cmul(b_load<T, BT>(B, Bs, k, 1, n, v), x1);
-    s1 -= cmul(b_load<T, BT>(B, Bs, k, 2, n, v), x0) + cmul(b_load<T, BT>(B, Bs, k, 3, n, v), x1);
+  gs_site_warp<T, BT>(e + roff, r + roff, B, Bs, Dinv, off, Nt, Nx, t, x, lane);
+}
+
+// All colours of `sweeps` sweeps in one launch: one thread block cluster per
+// right-hand side, one warp per site, and a cluster barrier (barrier.cluster,
+// release/acquire) between colours.  Same arithmetic as k_coarse_colour.
+template <typename T, typename BT>
+__global__ void __launch_bounds__(1024)
+k_coarse_sweeps_cluster(typename cplx<T>::type* __restrict__ e, const typename cplx<T>::type* __restrict__ r,
+                        const BT* __restrict__ B, const float* __restrict__ Bs,
+                        const typename cplx<T>::type* __restrict__ Dinv, Offsets off, int Nt, int Nx, int sweeps) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int n = Nt * Nx;
+  const int qx = Nx >> 2;
+  const int per_colour = n >> 4;
+  const int rank = (int)cluster.block_rank();
+  const int csize = (int)cluster.num_blocks();
+  const int rhs = blockIdx.x / csize;
+  const size_t roff = (size_t)rhs * 2 * n;
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  const int stride = csize * wpb;
+  for (int sw = 0; sw < sweeps; ++sw) {
+    for (int colour = 0; colour < 16; ++colour) {
+      for (int idx = rank * wpb + (threadIdx.x >> 5); idx < per_colour; idx += stride) {
+        const int ti = idx / qx;
+        const int t = 4 * ti + (colour >> 2);
+        const int x = 4 * (idx - ti * qx) + (colour & 3);
+        gs_site_warp<T, BT>(e + roff, r + roff, B, Bs, Dinv, off, Nt, Nx, t, x, lane);
+      }
+      cluster.sync();
+    }
   }
-  const C d00 = Dinv[v], d01 = Dinv[n + v], d10 = Dinv[2 * n + v], d11 = Dinv[3 * n + v];
-  e0[v] = cmul(d00, s0) + cmul(d01, s1);
-  e0[n + v] = cmul(d10, s0) + cmul(d11, s1);
 }
 
 // y_r = Ainv x_r for the coarsest level: dense FP64 complex matrix, row-major,
 // nd x nd; vectors are contiguous nd-element arrays (the [2][Nt][Nx] layout
-// flattened).  One warp per row; the row is read once for all R right-hand
-// sides (R <= 8 per launch).
-template <typename Cv>
+// flattened).  One warp per row; the row is read once for all RR right-hand
+// sides; four independent row loads per lane are in flight.
+template <typename Cv, int RR>
 __global__ void __launch_bounds__(256)
-k_dense_gemv(const double2* __restrict__ A, const Cv* __restrict__ x, Cv* __restrict__ y, int nd, int R) {
+k_dense_gemv(const double2* __restrict__ A, const Cv* __restrict__ x, Cv* __restrict__ y, int nd) {
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= nd) return;
-  double2 acc[8];
+  double2 acc[RR];
 #pragma unroll
-  for (int r = 0; r < 8; ++r) acc[r] = make_double2(0.0, 0.0);
+  for (int r = 0; r < RR; ++r) acc[r] = make_double2(0.0, 0.0);
   const double2* a = A + (size_t)row * nd;
-  for (int j = lane; j < nd; j += 32) {
+  int j = lane;
+  for (; j + 96 < nd; j += 128) {
+    double2 aj[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) aj[u] = __ldcs(a + j + 32 * u);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int r = 0; r < RR; ++r) acc[r] += cmul(aj[u], to_c(x[(size_t)r * nd + j + 32 * u], double()));
+  }
+  for (; j < nd; j += 32) {
     const double2 aj = a[j];
 #pragma unroll
-    for (int r = 0; r < 8; ++r)
-      if (r < R) acc[r] += cmul(aj, to_c(x[(size_t)r * nd + j], double()));
+    for (int r = 0; r < RR; ++r) acc[r] += cmul(aj, to_c(x[(size_t)r * nd + j], double()));
   }
 #pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    if (r < R) {
-      double re = acc[r].x, im = acc[r].y;
+  for (int r = 0; r < RR; ++r) {
+    double re = acc[r].x, im = acc[r].y;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        re += __shfl_xor_sync(0xffffffffu, re, o);
-        im += __shfl_xor_sync(0xffffffffu, im, o);
-      }
-      if (lane == 0) y[(size_t)r * nd + row] = to_c(make_double2(re, im), typename real_of<Cv>::type());
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
     }
+    if (lane == 0) y[(size_t)r * nd + row] = to_c(make_double2(re, im), typename real_of<Cv>::type());
+  }
+}
+
+// Mixed-precision V-cycle: y_r = Ainv32 x_r with the FP32 rounding of the FP64
+// inverse (the factorisation itself is FP64); FP32 arithmetic.
+template <int RR>
+__global__ void __launch_bounds__(256)
+k_dense_gemv32(const float2* __restrict__ A, const float2* __restrict__ x, float2* __restrict__ y, int nd) {
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= nd) return;
+  float2 acc[RR];
+#pragma unroll
+  for (int r = 0; r < RR; ++r) acc[r] = make_float2(0.f, 0.f);
+  const float2* a = A + (size_t)row * nd;
+  int j = lane;
+  for (; j + 96 < nd; j += 128) {
+    float2 aj[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) aj[u] = __ldcs(a + j + 32 * u);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int r = 0; r < RR; ++r) acc[r] += cmul(aj[u], x[(size_t)r * nd + j + 32 * u]);
+  }
+  for (; j < nd; j += 32) {
+    const float2 aj = a[j];
+#pragma unroll
+    for (int r = 0; r < RR; ++r) acc[r] += cmul(aj, x[(size_t)r * nd + j]);
+  }
+#pragma unroll
+  for (int r = 0; r < RR; ++r) {
+    float re = acc[r].x, im = acc[r].y;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) y[(size_t)r * nd + row] = make_float2(re, im);
   }
 }
 
@@ -136,18 +243,72 @@ template <typename T, typename BT>
 cudaError_t launch_coarse_colour(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* B,
                                  const float* Bs, const typename cplx<T>::type* Dinv, const Offsets& off,
                                  int Nt, int Nx, int colour, int R, cudaStream_t st) {
-  const int m = Nt * Nx / 16;
-  const int bs = m < 256 ? ((m + 31) / 32) * 32 : 256;
-  dim3 grid((m + bs - 1) / bs, R);
+  const long threads = (long)(Nt * Nx / 16) * 32;
+  const int bs = 256;
+  dim3 grid((unsigned)((threads + bs - 1) / bs), R);
   k_coarse_colour<T, BT><<<grid, bs, 0, st>>>(e, r, B, Bs, Dinv, off, Nt, Nx, colour);
   return cudaGetLastError();
 }
 
+int cluster_sweep_threads(int n) {
+  // one warp per site of a colour, at most 16 sites per warp and colour
+  const long per_colour = n / 16;
+  long warps = (per_colour + CLUSTER_BLOCKS - 1) / CLUSTER_BLOCKS;
+  if (warps > 32) {
+    if (per_colour > (long)CLUSTER_BLOCKS * 32 * 16) return 1 << 30;   // too large: per-colour launches
+    warps = 32;
+  }
+  return (int)(warps < 1 ? 32 : warps * 32);
+}
+
+template <typename T, typename BT>
+cudaError_t launch_coarse_sweeps_cluster(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* B,
+                                         const float* Bs, const typename cplx<T>::type* Dinv, const Offsets& off,
+                                         int Nt, int Nx, int sweeps, int R, cudaStream_t st) {
+  const int bs = cluster_sweep_threads(Nt * Nx);
+  if (bs > 1024) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CLUSTER_BLOCKS * R);
+  cfg.blockDim = dim3(bs);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CLUSTER_BLOCKS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_coarse_sweeps_cluster<T, BT>, e, r, B, Bs, Dinv, off, Nt, Nx, sweeps);
+}
+
 template <typename Cv>
 cudaError_t launch_dense_gemv(const double2* A, const Cv* x, Cv* y, int nd, int R, cudaStream_t st) {
-  for (int r0 = 0; r0 < R; r0 += 8) {
-    const int rr = (R - r0) < 8 ? (R - r0) : 8;
-    k_dense_gemv<Cv><<<(nd * 32 + 255) / 256, 256, 0, st>>>(A, x + (size_t)r0 * nd, y + (size_t)r0 * nd, nd, rr);
+  const int blocks = (nd * 32 + 255) / 256;
+  for (int r0 = 0; r0 < R;) {
+    const int left = R - r0;
+    const Cv* xx = x + (size_t)r0 * nd;
+    Cv* yy = y + (size_t)r0 * nd;
+    if (left >= 8) { k_dense_gemv<Cv, 8><<<blocks, 256, 0, st>>>(A, xx, yy, nd); r0 += 8; }
+    else if (left >= 4) { k_dense_gemv<Cv, 4><<<blocks, 256, 0, st>>>(A, xx, yy, nd); r0 += 4; }
+    else if (left >= 2) { k_dense_gemv<Cv, 2><<<blocks, 256, 0, st>>>(A, xx, yy, nd); r0 += 2; }
+    else { k_dense_gemv<Cv, 1><<<blocks, 256, 0, st>>>(A, xx, yy, nd); r0 += 1; }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_dense_gemv32(const float2* A, const float2* x, float2* y, int nd, int R, cudaStream_t st) {
+  const int blocks = (nd * 32 + 255) / 256;
+  for (int r0 = 0; r0 < R;) {
+    const int left = R - r0;
+    const float2* xx = x + (size_t)r0 * nd;
+    float2* yy = y + (size_t)r0 * nd;
+    if (left >= 8) { k_dense_gemv32<8><<<blocks, 256, 0, st>>>(A, xx, yy, nd); r0 += 8; }
+    else if (left >= 4) { k_dense_gemv32<4><<<blocks, 256, 0, st>>>(A, xx, yy, nd); r0 += 4; }
+    else if (left >= 2) { k_dense_gemv32<2><<<blocks, 256, 0, st>>>(A, xx, yy, nd); r0 += 2; }
+    else { k_dense_gemv32<1><<<blocks, 256, 0, st>>>(A, xx, yy, nd); r0 += 1; }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -164,5 +325,11 @@ template cudaError_t launch_coarse_colour<double, double2>(double2*, const doubl
 template cudaError_t launch_coarse_colour<float, __half2>(float2*, const float2*, const __half2*, const float*,
                                                           const float2*, const Offsets&, int, int, int, int,
                                                           cudaStream_t);
+template cudaError_t launch_coarse_sweeps_cluster<double, double2>(double2*, const double2*, const double2*,
+                                                                   const float*, const double2*, const Offsets&, int,
+                                                                   int, int, int, cudaStream_t);
+template cudaError_t launch_coarse_sweeps_cluster<float, __half2>(float2*, const float2*, const __half2*, const float*,
+                                                                  const float2*, const Offsets&, int, int, int, int,
+                                                                  cudaStream_t);
 template cudaError_t launch_dense_gemv<double2>(const double2*, const double2*, double2*, int, int, cudaStream_t);
 template cudaError_t launch_dense_gemv<float2>(const double2*, const float2*, float2*, int, int, cudaStream_t);

@@ -49,6 +49,7 @@ struct amamg_ctx {
   double2* U64 = nullptr;
   float2* U32 = nullptr;
   double2* Ainv = nullptr;   // coarsest inverse, nd x nd row-major
+  float2* Ainv32 = nullptr;  // its FP32 rounding, applied by the mixed-precision V-cycle
   int nd = 0;
   int* d_err = nullptr;
 
@@ -69,6 +70,15 @@ struct amamg_ctx {
   double2* d_y = nullptr;    // [R][m]
   double2* h_h = nullptr;    // pinned host mirror of d_h
   double2* h_y = nullptr;    // pinned host mirror of d_y
+
+  // work stream of the solver (graph capture needs a non-default stream) and the
+  // per-step CUDA graphs of one Arnoldi step j (captured once, replayed)
+  cudaStream_t ws = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::vector<cudaGraphExec_t> step_graphs;
+  std::vector<long long> step_graph_kernels;
+  int graph_R = 0;
+  bool use_graphs = true;
 
   std::string err;
   long long launches = 0;

@@ -40,8 +40,17 @@ template <typename T, typename BT>
 cudaError_t launch_coarse_colour(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* B,
                                  const float* Bs, const typename cplx<T>::type* Dinv, const Offsets& off, int Nt,
                                  int Nx, int colour, int R, cudaStream_t st);
+// all colours of `sweeps` sweeps in one launch, one 8-block cluster per RHS;
+// usable while n / 16 <= 8 * 1024 sites per colour
+constexpr int CLUSTER_BLOCKS = 8;
+int cluster_sweep_threads(int n);
+template <typename T, typename BT>
+cudaError_t launch_coarse_sweeps_cluster(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* B,
+                                         const float* Bs, const typename cplx<T>::type* Dinv, const Offsets& off,
+                                         int Nt, int Nx, int sweeps, int R, cudaStream_t st);
 template <typename Cv>
 cudaError_t launch_dense_gemv(const double2* A, const Cv* x, Cv* y, int nd, int R, cudaStream_t st);
+cudaError_t launch_dense_gemv32(const float2* A, const float2* x, float2* y, int nd, int R, cudaStream_t st);
 
 // blas.cu
 int dot_blocks(long len);

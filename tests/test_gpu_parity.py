@@ -301,3 +301,117 @@ def test_invalid_arguments_rejected():
         A.apply_coarse(hier, 0, v, v)     # level 0 is the Wilson operator
     L = A.lib()
     assert L.amamg_apply_D(hier.h, None, None, 1, 0, None) == A.ERR_INVALID_ARG
+
+
+# ------------------------------------------------------------------ FP32 path (FP16 + scale storage)
+
+def test_fp32_transfers_coarse_and_smoothers_match_emulated_storage():
+    """FP32 kernels against FP64 arithmetic on the emulated FP16+scale operators
+    and complex64-rounded inputs (oracle.mixed): FP32 rounding only."""
+    from oracle import mixed
+    Nt = Nx = 32
+    aggs = [4, 2]
+    U, D, hier, levels = make(Nt, Nx, aggs, m0=0.2, seed=21)
+    rng = np.random.Generator(np.random.PCG64(22))
+    R = 2
+    for l, a in enumerate(aggs):
+        F, C = levels[l], levels[l + 1]
+        Pq = mixed.quantise_tiles(oracle_P_tiles(F.P, F.Nt, F.Nx, a))
+        ec = mixed.round32(rng.standard_normal((R, 2, C.Nt, C.Nx)) + 1j * rng.standard_normal((R, 2, C.Nt, C.Nx)))
+        ef = mixed.round32(rng.standard_normal((R, 2, F.Nt, F.Nx)) + 1j * rng.standard_normal((R, 2, F.Nt, F.Nx)))
+        out_f = torch.empty(R, 2, F.Nt, F.Nx, dtype=torch.complex64, device=DEV)
+        out_c = torch.empty(R, 2, C.Nt, C.Nx, dtype=torch.complex64, device=DEV)
+        A.apply_P(hier, l, dev(ec, torch.complex64), out_f)
+        A.apply_PH(hier, l, dev(ef, torch.complex64), out_c)
+        gf, gc = host(out_f), host(out_c)
+        Np, Nq = F.Nt // a, F.Nx // a
+        nrows = 2 * (a * a - 1)
+        for r in range(R):
+            wf = np.zeros((2, F.Nt, F.Nx), dtype=complex)
+            wc = np.zeros((2, C.Nt, C.Nx), dtype=complex)
+            for p in range(Np):
+                for q in range(Nq):
+                    tile = p * Nq + q
+                    corners = [amg.corner_vertex(F.Nt, F.Nx, a, p, q, c) for c in range(4)]
+                    ecv = np.array([ec[r, beta].reshape(-1)[corners[c]] for c in range(4) for beta in range(2)])
+                    vals = Pq[tile].T @ ecv                                   # [nrows]
+                    for lr in range(nrows):
+                        l_, alpha = lr // 2 + 1, lr % 2
+                        t, x = p * a + l_ // a, q * a + l_ % a
+                        wf[alpha, t, x] = vals[lr]
+                        for c in range(4):
+                            for beta in range(2):
+                                wc[beta].reshape(-1)[corners[c]] += np.conj(Pq[tile, 2 * c + beta, lr]) * ef[r, alpha, t, x]
+                    wf[:, p * a, q * a] = ec[r, :, p, q]
+                    wc[:, p, q] += ef[r, :, p * a, q * a]
+            assert relerr(gf[r], wf) <= 2e-6
+            assert relerr(gc[r], wc) <= 2e-6
+        # coarse operator with FP16 blocks
+        Bq = mixed.quantise_blocks(amg.block_stencil(C.A, C.offsets, C.Nt, C.Nx))
+        A.apply_coarse(hier, l + 1, dev(ec, torch.complex64), out_c)
+        gc = host(out_c)
+        for r in range(R):
+            want = np.zeros((2, C.Nt * C.Nx), dtype=complex)
+            x0 = ec[r].reshape(2, -1)
+            for k, (dt, dx) in enumerate(C.offsets):
+                for v in range(C.Nt * C.Nx):
+                    tv, xv = divmod(v, C.Nx)
+                    w = ((tv + dt) % C.Nt) * C.Nx + (xv + dx) % C.Nx
+                    want[:, v] += Bq[k, v] @ x0[:, w]
+            assert relerr(gc[r], want.reshape(2, C.Nt, C.Nx)) <= 2e-6
+    # fine red-black sweep with FP32 links and (m0 + 2) in FP32
+    L0 = levels[0]
+    r0 = mixed.round32(fx.gaussian_rhs(1, Nt, Nx, 23))
+    e0 = mixed.round32(fx.gaussian_rhs(1, Nt, Nx, 24))
+    e = dev(e0, torch.complex64)
+    A.smooth(hier, 0, dev(r0, torch.complex64), e, 2)
+    D32 = W.dirac_matrix(mixed.round32(U), 0.2)
+    want = W.to_flat(e0[0])
+    for _ in range(2):
+        want = amg.gs_sweep(D32, L0.dinv, L0.colour, want, W.to_flat(r0[0]))
+    assert relerr(host(e)[0], lattice_vec(want, Nt, Nx)) <= 1e-5
+    # coarse 16-colour sweep: FP16 off-diagonal blocks, FP32-rounded diagonal inverses
+    L1 = levels[1]
+    Bq = mixed.quantise_blocks(amg.block_stencil(L1.A, L1.offsets, L1.Nt, L1.Nx))
+    Bex = amg.block_stencil(L1.A, L1.offsets, L1.Nt, L1.Nx)
+    Bq[0] = Bex[0]                                                  # diagonal blocks stay exact
+    n1 = L1.Nt * L1.Nx
+    rows, cols, vals = [], [], []
+    for k, (dt, dx) in enumerate(L1.offsets):
+        for v in range(n1):
+            tv, xv = divmod(v, L1.Nx)
+            w = ((tv + dt) % L1.Nt) * L1.Nx + (xv + dx) % L1.Nx
+            for al in range(2):
+                for be in range(2):
+                    rows.append(2 * v + al); cols.append(2 * w + be); vals.append(Bq[k, v, al, be])
+    import scipy.sparse as sp
+    Aq = sp.csr_matrix((vals, (rows, cols)), shape=(2 * n1, 2 * n1))
+    dinv32 = mixed.round32(L1.dinv)
+    r1 = mixed.round32(rng.standard_normal((1, 2, L1.Nt, L1.Nx)) + 1j * rng.standard_normal((1, 2, L1.Nt, L1.Nx)))
+    e1 = mixed.round32(rng.standard_normal((1, 2, L1.Nt, L1.Nx)) + 1j * rng.standard_normal((1, 2, L1.Nt, L1.Nx)))
+    eg = dev(e1, torch.complex64)
+    A.smooth(hier, 1, dev(r1, torch.complex64), eg, 2)
+    want = W.to_flat(e1[0])
+    for _ in range(2):
+        want = amg.gs_sweep(Aq, dinv32, L1.colour, want, W.to_flat(r1[0]))
+    assert relerr(host(eg)[0], lattice_vec(want, L1.Nt, L1.Nx)) <= 1e-5
+
+
+def test_graph_replay_matches_eager_profiled_solve():
+    """The captured-graph Arnoldi steps and the eager (profiled) path give the same solve."""
+    Nt = Nx = 32
+    U, D, hier, levels = make(Nt, Nx, [4, 2], m0=0.05, seed=25)
+    psi = fx.gaussian_rhs(2, Nt, Nx, 26)
+    x1 = torch.empty(psi.shape, dtype=torch.complex128, device=DEV)
+    x2 = torch.empty(psi.shape, dtype=torch.complex128, device=DEV)
+    i1 = A.solve(hier, dev(psi), x1)
+    A.profile_enable(hier, True)
+    i2 = A.solve(hier, dev(psi), x2)
+    A.profile_enable(hier, False)
+    prof = A.profile_get(hier)
+    assert any(name.startswith("dslash") for name, *_ in prof)
+    assert [i.iterations for i in i1] == [i.iterations for i in i2]
+    assert relerr(host(x1), host(x2)) <= 1e-13
+    n0 = A.launch_count(hier)
+    A.solve(hier, dev(psi), x1)
+    assert A.launch_count(hier) > n0
