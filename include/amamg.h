@@ -141,6 +141,28 @@ int amamg_coarsest_solve(amamg_handle h, const void* r, void* e, int R, void* st
  * no pre-smoothing and post_smooth sweeps per level. */
 int amamg_vcycle(amamg_handle h, const void* r, void* e, int R, int precision, void* stream);
 
+/* Size of the fixed device array behind amamg_vcycle_noalloc (8 MiB). */
+#define AMAMG_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* amamg_vcycle without any device allocation.  The paper has no counterpart:
+ * this exists for callers that cannot call cudaMalloc while they run (a host
+ * callback, a region recorded for replay with fixed addresses, an application
+ * whose memory pool forbids allocations after start-up).  Same arguments and
+ * the same result as amamg_vcycle; the coarse-level work vectors live in one
+ * file-scope __device__ array of AMAMG_NOALLOC_SCRATCH_BYTES that every GPU
+ * loading the library holds until the process exits.
+ *   - Needs 2 * R * 2 * (n_1 + ... + n_L) complex elements (each level's
+ *     vectors rounded up to 256 bytes); larger requests return
+ *     AMAMG_ERR_INVALID_ARG with the sizes in amamg_last_error.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture.
+ *   - Every call on a device shares the one array and leaves its contents
+ *     behind; nothing in it has to start at zero (each level's vectors are
+ *     written before they are read).  Calls that overlap on the GPU (other
+ *     streams, other handles) race on it: serialise them. */
+int amamg_vcycle_noalloc(amamg_handle h, const void* r, void* e, int R, int precision, void* stream);
+
 /* Integer structure of level l (host arrays; bit-exact tests):
  * role[Nt_l*Nx_l] (0 vertex, 1 edge, 2 interior), owner_tile[Nt_l*Nx_l]
  * (index p*(Nx_l/a)+q of the basket a site takes its formula from),
