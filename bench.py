@@ -38,6 +38,7 @@ AGGS = [4, 2]
 RESTART = 30
 TOL = 1e-10
 RHS_SEED0 = 1000
+FP64_PEAK_GFLOPS = 1250.0      # nominal B300 FP64 rate
 WORKLOAD = ("256x256 Wilson-Dirac (periodic x, antiperiodic t), quenched U(1) beta=6 seed 2, "
             "m0 = m_crit + {0.1, 0.02, 0.005}, 3-level SM-AMG (tiles 4, 2), FGMRES(30) to 1e-10, 1 RHS per mass")
 
@@ -361,24 +362,41 @@ def main():
     nbytes = psis[0].numel() * 16
 
     # per-kernel profile: a replay of the timed steps with event-bracketed launches
-    for h in hs64:
-        A.profile_reset(h)
-        A.profile_enable(h, True)
-    run(hs64, nst=nsteps, skip=args.warmup)
-    cats = {}
-    for h in hs64:
-        A.profile_enable(h, False)
-        for name, n, ms, by in A.profile_get(h):
-            c = cats.setdefault(name, [0, 0.0, 0.0])
-            c[0] += n
-            c[1] += ms
-            c[2] += by
     peak, peak_kind = measured_peaks()
-    dom = max(cats.items(), key=lambda kv: kv[1][1])
-    dname, (dn, dms, dby) = dom
-    achieved = dby / (dms * 1e-3) / 1e9
-    kernel_share = {k: round(v[1] / sum(c[1] for c in cats.values()), 4) for k, v in
-                    sorted(cats.items(), key=lambda kv: -kv[1][1])}
+
+    def profile(hs):
+        for h in hs:
+            A.profile_reset(h)
+            A.profile_enable(h, True)
+        run(hs, nst=nsteps, skip=args.warmup)
+        cats = {}
+        for h in hs:
+            A.profile_enable(h, False)
+            for name, n, ms, by, fl in A.profile_get(h):
+                c = cats.setdefault(name, [0, 0.0, 0.0, 0.0])
+                c[0] += n
+                c[1] += ms
+                c[2] += by
+                c[3] += fl
+        tot = sum(c[1] for c in cats.values())
+        share = {k: round(v[1] / tot, 4) for k, v in sorted(cats.items(), key=lambda kv: -kv[1][1])}
+        dname, (dn, dms, dby, dfl) = max(cats.items(), key=lambda kv: kv[1][1])
+        gbs = dby / (dms * 1e-3) / 1e9
+        gflops = dfl / (dms * 1e-3) / 1e9
+        fp64 = dname.endswith("f64") or dname.startswith("gs")
+        roof = {"bound": "hbm", "kernel": dname, "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(gbs / peak, 4), "traffic": None, "peak_source": f"{peak_kind} hbm_gbs",
+                "launches": dn, "avg_launch_us": round(1e3 * dms / dn, 3), "bytes_per_launch": round(dby / dn),
+                "flops_per_launch": round(dfl / dn), "pass": "profiled replay of the timed steps"}
+        if fp64 and gflops / FP64_PEAK_GFLOPS > gbs / peak:
+            roof.update({"bound": "alu", "achieved": round(gflops, 1), "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                         "frac": round(gflops / FP64_PEAK_GFLOPS, 4),
+                         "peak_source": "nominal B300 FP64 rate (no measured FP64 figure)",
+                         "hbm_GB/s": round(gbs, 1), "hbm_frac": round(gbs / peak, 4)})
+        return roof, share
+
+    roofline, kernel_share = profile(hs64)
+    roofline_mixed, kernel_share_mixed = profile(hs32)
 
     # stencil bandwidth on working sets larger than L2 (1024^2, random-phase links)
     d_apply = {}
@@ -427,12 +445,10 @@ def main():
             "e2e": {"value": round(e2e_value, 3), "unit": "solves/s", "h2d_bytes_per_step": nbytes * len(masses),
                     "d2h_bytes_per_step": nbytes * len(masses)},
             "gpu_launches": int(launches),
-            "roofline": {"bound": "hbm", "kernel": dname, "achieved": round(achieved, 1), "peak": peak,
-                         "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
-                         "peak_source": f"{peak_kind} hbm_gbs", "launches": dn,
-                         "avg_launch_us": round(1e3 * dms / dn, 3),
-                         "bytes_per_launch": round(dby / dn), "pass": "profiled replay of the timed steps"},
+            "roofline": roofline,
             "kernel_share": kernel_share,
+            "roofline_mixed": roofline_mixed,
+            "kernel_share_mixed": kernel_share_mixed,
             "cpu_baseline": cpu,
             "clocks": clk,
             "mixed": {"value": round(mixed_value, 3), "unit": "solves/s", "speedup_vs_fp64": round(mixed_value / value, 3),

@@ -112,6 +112,38 @@ int amamg_setup(const amamg_params* p, const void* U, int Nt, int Nx, double m0,
 int amamg_solve(amamg_handle h, const void* psi, void* x, int R, void* stream,
                 amamg_solve_info* info);
 
+/* ---- Slot batches: continuous batching of solves on one hierarchy ----------
+ * A batch owns S right-hand-side slots (device buffers for b and x).  Callers
+ * admit a right-hand side into a free slot at any time between cycles, run
+ * restart cycles of the outer FGMRES (Sec. 1 and Sec. 5) over every occupied
+ * slot at once, and retire slots whose right-hand side is done, so that new
+ * requests join while others are in flight.  Each slot carries its own bare
+ * mass m0: the fine operator is D(m0_slot) = D(m0_setup) + (m0_slot - m0_setup) I
+ * (Eq. (3)); the interpolators and coarse operators stay those of the setup
+ * mass (the flexible outer solver tolerates the preconditioner's mass offset).
+ * One batch per handle at a time (it uses the handle's solver workspace). */
+typedef struct amamg_batch* amamg_batch_handle;
+
+typedef struct {
+    int    active;                   /* slot holds a right-hand side */
+    int    done;                     /* converged, out of iterations, or failed */
+    int    status;                   /* AMAMG_OK, AMAMG_NOT_CONVERGED or AMAMG_ERR_NONFINITE */
+    int    iterations;               /* Arnoldi steps taken since admission */
+    double true_relres;              /* ||b - D(m0) x|| / ||b|| at the start of the last cycle */
+} amamg_slot_info;
+
+/* Creates a batch of `slots` slots on hierarchy h (allocates its buffers). */
+int amamg_batch_create(amamg_handle h, int slots, amamg_batch_handle* out);
+/* Copies psi (device complex128 [2][Nt][Nx]) into free slot `slot` with mass m0,
+ * on the caller's stream; AMAMG_ERR_INVALID_ARG if the slot is occupied. */
+int amamg_batch_admit(amamg_batch_handle b, int slot, const void* psi, double m0, void* stream);
+/* One restart cycle (at most `restart` Arnoldi steps) over every occupied,
+ * unfinished slot; fills info[0..slots-1] (host) and synchronises the stream. */
+int amamg_batch_cycle(amamg_batch_handle b, void* stream, amamg_slot_info* info);
+/* Copies the slot's iterate to x (device complex128 [2][Nt][Nx]) and frees it. */
+int amamg_batch_retire(amamg_batch_handle b, int slot, void* x, void* stream);
+int amamg_batch_destroy(amamg_batch_handle b);
+
 /* out = D in on the fine lattice, Eq. (3).  precision AMAMG_F64 or AMAMG_F32. */
 int amamg_apply_D(amamg_handle h, const void* in, void* out, int R, int precision, void* stream);
 
@@ -184,14 +216,16 @@ int amamg_export_P(amamg_handle h, int level, void* out, void* stream);
 int amamg_export_coarse(amamg_handle h, int level, void* out, void* stream);
 
 /* Kernel timing for measurement: when enabled, every kernel the handle
- * launches is bracketed by CUDA events on its stream.  amamg_profile_get
+ * launches is bracketed by CUDA events on its stream (and the solver's
+ * Arnoldi steps run eagerly instead of as graphs).  amamg_profile_get
  * synchronises, then reports for kernel category idx (0..count-1) its name,
- * launches, summed device time and algorithmic bytes moved.  Returns
- * AMAMG_ERR_INVALID_ARG past the last category. */
+ * launches, summed device time, and the algorithmic bytes moved and
+ * floating-point operations done (each input read once, each output written
+ * once).  Returns AMAMG_ERR_INVALID_ARG past the last category. */
 int amamg_profile_enable(amamg_handle h, int on);
 int amamg_profile_reset(amamg_handle h);
 int amamg_profile_get(amamg_handle h, int idx, const char** name, long long* launches,
-                      double* total_ms, double* bytes);
+                      double* total_ms, double* bytes, double* flops);
 
 /* Number of kernels the handle has launched since setup (all categories). */
 long long amamg_launch_count(amamg_handle h);

@@ -35,6 +35,7 @@ EXPORTED = [
     "amamg_vcycle", "amamg_vcycle_noalloc", "amamg_export_structure", "amamg_level_info", "amamg_export_P", "amamg_export_coarse",
     "amamg_profile_enable", "amamg_profile_reset", "amamg_profile_get", "amamg_launch_count",
     "amamg_setup_seconds", "amamg_destroy", "amamg_status_string", "amamg_last_error",
+    "amamg_batch_create", "amamg_batch_admit", "amamg_batch_cycle", "amamg_batch_retire", "amamg_batch_destroy",
 ]
 
 
@@ -48,6 +49,11 @@ class Params(ctypes.Structure):
         ("post_smooth", ctypes.c_int),
         ("tol", ctypes.c_double),
     ]
+
+
+class SlotInfo(ctypes.Structure):
+    _fields_ = [("active", ctypes.c_int), ("done", ctypes.c_int), ("status", ctypes.c_int),
+                ("iterations", ctypes.c_int), ("true_relres", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -81,12 +87,17 @@ def _load() -> ctypes.CDLL:
         "amamg_profile_enable": ([vp, ci], ci),
         "amamg_profile_reset": ([vp], ci),
         "amamg_profile_get": ([vp, ci, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_longlong),
-                               ctypes.POINTER(cd), ctypes.POINTER(cd)], ci),
+                               ctypes.POINTER(cd), ctypes.POINTER(cd), ctypes.POINTER(cd)], ci),
         "amamg_launch_count": ([vp], ctypes.c_longlong),
         "amamg_setup_seconds": ([vp], cd),
         "amamg_destroy": ([vp], ci),
         "amamg_status_string": ([ci], ctypes.c_char_p),
         "amamg_last_error": ([vp], ctypes.c_char_p),
+        "amamg_batch_create": ([vp, ci, ctypes.POINTER(vp)], ci),
+        "amamg_batch_admit": ([vp, ci, vp, cd, vp], ci),
+        "amamg_batch_cycle": ([vp, vp, ctypes.POINTER(SlotInfo)], ci),
+        "amamg_batch_retire": ([vp, ci, vp, vp], ci),
+        "amamg_batch_destroy": ([vp], ci),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -305,7 +316,7 @@ def profile_reset(hier: Hierarchy):
 
 
 def profile_get(hier: Hierarchy):
-    """[(name, launches, total_ms, bytes)] for every kernel category seen."""
+    """[(name, launches, total_ms, bytes, flops)] for every kernel category seen."""
     out = []
     i = 0
     while True:
@@ -313,10 +324,12 @@ def profile_get(hier: Hierarchy):
         n = ctypes.c_longlong()
         ms = ctypes.c_double()
         by = ctypes.c_double()
-        st = _lib.amamg_profile_get(hier.h, i, ctypes.byref(name), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by))
+        fl = ctypes.c_double()
+        st = _lib.amamg_profile_get(hier.h, i, ctypes.byref(name), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by),
+                                    ctypes.byref(fl))
         if st != OK:
             break
-        out.append((name.value.decode(), n.value, ms.value, by.value))
+        out.append((name.value.decode(), n.value, ms.value, by.value, fl.value))
         i += 1
     return out
 
@@ -331,3 +344,41 @@ def setup_seconds(hier: Hierarchy) -> float:
 
 def destroy(hier: Hierarchy):
     hier.destroy()
+
+
+class Batch:
+    """amamg_batch_*: S right-hand-side slots on one hierarchy (continuous batching).
+
+    admit() puts a right-hand side (device complex128 [2, Nt, Nx]) with its own
+    mass into a free slot, cycle() runs one FGMRES restart cycle over all
+    occupied slots, retire() copies a slot's solution out and frees the slot."""
+
+    def __init__(self, hier: Hierarchy, slots: int):
+        self.hier = hier
+        self.slots = slots
+        self.b = ctypes.c_void_p()
+        hier._check(_lib.amamg_batch_create(hier.h, slots, ctypes.byref(self.b)), "amamg_batch_create")
+
+    def admit(self, slot: int, psi, m0: float, stream=None):
+        self.hier._check(_lib.amamg_batch_admit(self.b, slot, _ptr(psi), float(m0), _stream(stream)),
+                         "amamg_batch_admit")
+
+    def cycle(self, stream=None):
+        info = (SlotInfo * self.slots)()
+        self.hier._check(_lib.amamg_batch_cycle(self.b, _stream(stream), info), "amamg_batch_cycle")
+        return [(i.active, i.done, i.status, i.iterations, i.true_relres) for i in info]
+
+    def retire(self, slot: int, x=None, stream=None):
+        self.hier._check(_lib.amamg_batch_retire(self.b, slot, _ptr(x) if x is not None else None,
+                                                 _stream(stream)), "amamg_batch_retire")
+
+    def destroy(self):
+        if self.b is not None and self.b.value:
+            _lib.amamg_batch_destroy(self.b)
+            self.b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

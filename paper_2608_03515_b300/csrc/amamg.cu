@@ -47,8 +47,8 @@ cudaEvent_t take_event(amamg_ctx* h) {
 
 // Wraps one kernel launch: counts it and, when profiling, brackets it with events.
 template <typename F>
-int launch(amamg_ctx* h, const char* name, double bytes, cudaStream_t st, F&& f) {
-  ProfRec rec{-1, nullptr, nullptr, bytes};
+int launch(amamg_ctx* h, const char* name, double bytes, cudaStream_t st, F&& f, double flops = 0.0) {
+  ProfRec rec{-1, nullptr, nullptr, bytes, flops};
   if (h->prof) {
     rec.cat = cat_id(h, name);
     rec.a = take_event(h);
@@ -77,6 +77,7 @@ int collect_profile(amamg_ctx* h) {
     c.launches++;
     c.ms += ms;
     c.bytes += r.bytes;
+    c.flops += r.flops;
   }
   h->recs.clear();
   h->ev_used = 0;
@@ -176,7 +177,8 @@ int ensure_solver_ws(amamg_ctx* h, int R) {
   if (R <= h->Rsolve && m <= h->mcap) return AMAMG_OK;
   clear_graphs(h);
   dfree(h->V); dfree(h->Z64); dfree(h->Z32); dfree(h->v32); dfree(h->w); dfree(h->res);
-  dfree(h->partial); dfree(h->d_h); dfree(h->d_inv); dfree(h->d_y);
+  dfree(h->partial); dfree(h->d_h); dfree(h->d_inv); dfree(h->d_flag); dfree(h->d_y);
+  dfree(h->d_diag64); dfree(h->d_inv64); dfree(h->d_inv32);
   if (h->h_h) cudaFreeHost(h->h_h);
   if (h->h_y) cudaFreeHost(h->h_y);
   h->h_h = h->h_y = nullptr;
@@ -190,10 +192,14 @@ int ensure_solver_ws(amamg_ctx* h, int R) {
   }
   CKS(dalloc(h, &h->w, (size_t)R * len));
   CKS(dalloc(h, &h->res, (size_t)R * len));
-  h->partial_elems = (size_t)R * (m + 1) * dot_blocks((long)len);
+  h->partial_elems = (size_t)R * (m + 2) * dot_blocks((long)len);
   CKS(dalloc(h, &h->partial, h->partial_elems));
   CKS(dalloc(h, &h->d_h, (size_t)R * 3 * (m + 2)));
   CKS(dalloc(h, &h->d_inv, (size_t)R));
+  CKS(dalloc(h, &h->d_flag, (size_t)R));
+  CKS(dalloc(h, &h->d_diag64, (size_t)R));
+  CKS(dalloc(h, &h->d_inv64, (size_t)R));
+  CKS(dalloc(h, &h->d_inv32, (size_t)R));
   CKS(dalloc(h, &h->d_y, (size_t)R * m));
   CK(cudaMallocHost((void**)&h->h_h, sizeof(double2) * (size_t)R * 3 * (m + 2)));
   CK(cudaMallocHost((void**)&h->h_y, sizeof(double2) * (size_t)R * m));
@@ -215,8 +221,8 @@ int op_dslash<double>(amamg_ctx* h, const double2* in, double2* out, const doubl
   const Level& L = h->lv[0];
   const double bytes = (double)L.n * (R * (32.0 + 32.0 + (b ? 32.0 : 0.0)) + 32.0);
   return launch(h, b ? "dslash_residual_f64" : "dslash_f64", bytes, st, [&] {
-    return launch_dslash<double2, double2, double>(in, out, b, h->U64, h->m0 + 2.0, L.Nt, L.Nx, R, st);
-  });
+    return launch_dslash<double2, double2, double>(in, out, b, h->U64, h->m0 + 2.0, L.Nt, L.Nx, R, st, h->cur_diag64);
+  }, (double)L.n * R * (b ? 60.0 : 56.0));
 }
 
 template <>
@@ -225,7 +231,7 @@ int op_dslash<float>(amamg_ctx* h, const float2* in, float2* out, const float2* 
   const double bytes = (double)L.n * (R * (16.0 + 16.0 + (b ? 16.0 : 0.0)) + 16.0);
   return launch(h, "dslash_f32", bytes, st, [&] {
     return launch_dslash<float2, float2, float>(in, out, b, h->U32, (float)(h->m0 + 2.0), L.Nt, L.Nx, R, st);
-  });
+  }, (double)L.n * R * (b ? 60.0 : 56.0));
 }
 
 template <typename T>
@@ -241,30 +247,32 @@ int smooth_impl(amamg_ctx* h, int l, typename cplx<T>::type* e, const typename c
   if (l == 0) {
     const T inv = (T)(1.0 / (h->m0 + 2.0));
     const typename cplx<T>::type* U;
-    if constexpr (f64) U = h->U64; else U = h->U32;
+    const T* inv_r;
+    if constexpr (f64) { U = h->U64; inv_r = h->cur_inv64; } else { U = h->U32; inv_r = h->cur_inv32; }
     // half sweep: read r, read + write e on half the sites, links once
     const double bytes = (double)L.n / 2 * (R * 2 * 3 * cb) + (double)L.n * 2 * cb / 2;
     for (int s = 0; s < sweeps; ++s)
       for (int c = 0; c < 2; ++c)
         CKS(launch(h, f64 ? "rb_smooth_f64" : "rb_smooth_f32", bytes, st, [&] {
-          return launch_rb_half<T>(e, r, U, inv, L.Nt, L.Nx, c, R, st);
-        }));
+          return launch_rb_half<T>(e, r, U, inv, L.Nt, L.Nx, c, R, st, inv_r);
+        }, (double)L.n / 2 * R * 56.0));
     return AMAMG_OK;
   }
   const double blk = f64 ? 16.0 * 4 : (4.0 * 4 + 4.0);
   const double bytes = (double)L.n / 16 * ((L.off.K - 1) * blk + 4 * cb + R * 2 * 3 * cb);
-  if (sweeps > 0 && cluster_sweep_threads(L.n) <= 1024) {
+  const double flops = (double)L.n / 16 * R * ((L.off.K - 1) * 32.0 + 36.0);   // one colour
+  if (sweeps > 0 && use_cluster_sweeps<T>(L.n)) {
     // every colour of every sweep in one clustered launch
     if constexpr (f64)
       return launch(h, "coarse_smooth_f64", bytes * 16 * sweeps, st, [&] {
         return launch_coarse_sweeps_cluster<double, double2>(e, r, L.B64, nullptr, L.Dinv64, L.off, L.Nt, L.Nx,
                                                              sweeps, R, st);
-      });
+      }, flops * 16 * sweeps);
     else
       return launch(h, "coarse_smooth_f32", bytes * 16 * sweeps, st, [&] {
         return launch_coarse_sweeps_cluster<float, __half2>(e, r, L.B16, L.Bs, L.Dinv32, L.off, L.Nt, L.Nx, sweeps,
                                                             R, st);
-      });
+      }, flops * 16 * sweeps);
   }
   for (int s = 0; s < sweeps; ++s)
     for (int c = 0; c < 16; ++c) {
@@ -272,11 +280,11 @@ int smooth_impl(amamg_ctx* h, int l, typename cplx<T>::type* e, const typename c
       if constexpr (f64)
         rc = launch(h, "coarse_smooth_f64", bytes, st, [&] {
           return launch_coarse_colour<double, double2>(e, r, L.B64, nullptr, L.Dinv64, L.off, L.Nt, L.Nx, c, R, st);
-        });
+        }, flops);
       else
         rc = launch(h, "coarse_smooth_f32", bytes, st, [&] {
           return launch_coarse_colour<float, __half2>(e, r, L.B16, L.Bs, L.Dinv32, L.off, L.Nt, L.Nx, c, R, st);
-        });
+        }, flops);
       CKS(rc);
     }
   return AMAMG_OK;
@@ -293,11 +301,11 @@ int op_prolong(amamg_ctx* h, int l, const typename cplx<T>::type* ec, typename c
   if constexpr (f64)
     return launch(h, "prolong_f64", bytes, st, [&] {
       return launch_prolong<double, double2>(ec, ef, L.P64, nullptr, L.Nx, L.a, L.Np, L.Nq, R, st);
-    });
+    }, (double)L.nT * L.nrows * 64.0 * R);
   else
     return launch(h, "prolong_f32", bytes, st, [&] {
       return launch_prolong<float, __half2>(ec, ef, L.P16, L.Ps, L.Nx, L.a, L.Np, L.Nq, R, st);
-    });
+    }, (double)L.nT * L.nrows * 64.0 * R);
 }
 
 template <typename T>
@@ -311,11 +319,11 @@ int op_restrict(amamg_ctx* h, int l, const typename cplx<T>::type* ef, typename 
   if constexpr (f64)
     return launch(h, "restrict_f64", bytes, st, [&] {
       return launch_restrict<double, double2>(ef, ec, L.P64, nullptr, L.Nx, L.a, L.Np, L.Nq, R, st);
-    });
+    }, (double)L.nT * L.nrows * 64.0 * R);
   else
     return launch(h, "restrict_f32", bytes, st, [&] {
       return launch_restrict<float, __half2>(ef, ec, L.P16, L.Ps, L.Nx, L.a, L.Np, L.Nq, R, st);
-    });
+    }, (double)L.nT * L.nrows * 64.0 * R);
 }
 
 template <typename T>
@@ -329,18 +337,19 @@ int op_coarse(amamg_ctx* h, int l, const typename cplx<T>::type* in, typename cp
   if constexpr (f64)
     return launch(h, "coarse_apply_f64", bytes, st, [&] {
       return launch_coarse_apply<double, double2>(in, out, b, L.B64, nullptr, L.off, L.Nt, L.Nx, R, st);
-    });
+    }, (double)L.n * R * L.off.K * 32.0);
   else
     return launch(h, "coarse_apply_f32", bytes, st, [&] {
       return launch_coarse_apply<float, __half2>(in, out, b, L.B16, L.Bs, L.off, L.Nt, L.Nx, R, st);
-    });
+    }, (double)L.n * R * L.off.K * 32.0);
 }
 
 template <typename Cv>
 int op_coarsest(amamg_ctx* h, const Cv* r, Cv* e, int R, cudaStream_t st) {
   const double bytes = (double)h->nd * h->nd * 16.0 + (double)R * 2 * h->nd * sizeof(Cv);
   return launch(h, "coarsest_gemv_f64", bytes, st,
-                [&] { return launch_dense_gemv<Cv>(h->Ainv, r, e, h->nd, R, st); });
+                [&] { return launch_dense_gemv<Cv>(h->Ainv, r, e, h->nd, R, st); },
+                (double)h->nd * h->nd * 8.0 * R);
 }
 
 // coarsest level inside a V-cycle: FP64 inverse for FP64 vectors, its FP32
@@ -351,7 +360,8 @@ int vcycle_coarsest(amamg_ctx* h, const double2* r, double2* e, int R, cudaStrea
 int vcycle_coarsest(amamg_ctx* h, const float2* r, float2* e, int R, cudaStream_t st) {
   const double bytes = (double)h->nd * h->nd * 8.0 + (double)R * 2 * h->nd * 8.0;
   return launch(h, "coarsest_gemv_f32", bytes, st,
-                [&] { return launch_dense_gemv32(h->Ainv32, r, e, h->nd, R, st); });
+                [&] { return launch_dense_gemv32(h->Ainv32, r, e, h->nd, R, st); },
+                (double)h->nd * h->nd * 8.0 * R);
 }
 
 // V-cycle of Algorithm 1 (start vector 0, no pre-smoothing) from level l:
@@ -409,26 +419,50 @@ int arnoldi_step(amamg_ctx* h, int j, int R, cudaStream_t st) {
     CKS(vcycle_from<float>(h, 0, h->v32, zj, R, st));
     const Level& L = h->lv[0];
     CKS(launch(h, "dslash_mixed", (double)L.n * (R * (16.0 + 32.0) + 32.0), st, [&] {
-      return launch_dslash<float2, double2, double>(zj, h->w, nullptr, h->U64, h->m0 + 2.0, L.Nt, L.Nx, R, st);
+      return launch_dslash<float2, double2, double>(zj, h->w, nullptr, h->U64, h->m0 + 2.0, L.Nt, L.Nx, R, st,
+                                                    h->cur_diag64);
     }));
   } else {
     double2* zj = h->Z64 + (size_t)j * vi;
     CKS(vcycle_from<double>(h, 0, vj, zj, R, st));
     CKS(op_dslash<double>(h, zj, h->w, nullptr, R, st));
   }
+  // Classical Gram-Schmidt with the DGKS criterion: one pass, and a second
+  // pass only for right-hand sides whose norm dropped below 1/sqrt(2) of its
+  // value before orthogonalisation (the second-pass kernels are gated per RHS).
   const int J = j + 1;
   const int nb = dot_blocks(len);
-  for (int pass = 0; pass < 2; ++pass) {
-    const int off = pass * (m + 2);
-    CKS(launch(h, "gs_dots", (double)R * len * 16.0 * (J + 1), st,
-               [&] { return launch_dots(h->V, vi, vr, h->w, vr, len, J, R, h->partial, st); }));
-    CKS(launch(h, "gs_reduce", (double)R * J * nb * 16.0, st,
-               [&] { return launch_reduce(h->partial, nb, J, R, d_h1, ldh, off, 0, nullptr, st); }));
-    CKS(launch(h, "gs_update", (double)R * len * 16.0 * (J + 2), st, [&] {
-      return launch_multi_axpy<double2>(h->w, vr, h->V, vi, vr, d_h1 + off, ldh, J, -1.0, len, R, st);
-    }));
-  }
-  CKS(norms(h, h->w, vr, len, R, d_h1, ldh, 2 * (m + 2), h->d_inv, st));
+  const int nrm_off = 2 * (m + 2);
+  CKS(launch(h, "gs_dots", (double)R * len * 16.0 * (J + 1), st, [&] {
+    return launch_dots(h->V, vi, vr, h->w, vr, len, J, R, h->partial, st, true);
+  }, (double)R * len * 8.0 * (J + 1)));
+  CKS(launch(h, "gs_reduce", (double)R * (J + 1) * nb * 16.0, st,
+             [&] { return launch_reduce(h->partial, nb, J + 1, R, d_h1, ldh, 0, 0, nullptr, st); }));
+  CKS(launch(h, "gs_update", (double)R * len * 16.0 * (J + 2), st, [&] {
+    return launch_multi_axpy<double2>(h->w, vr, h->V, vi, vr, d_h1, ldh, J, -1.0, len, R, st);
+  }, (double)R * len * 8.0 * J));
+  CKS(launch(h, "gs_dots", (double)R * len * 16.0, st,
+             [&] { return launch_dots(h->w, 0, vr, h->w, vr, len, 1, R, h->partial, st); }));
+  CKS(launch(h, "gs_reduce", (double)R * nb * 16.0, st, [&] {
+    return launch_reduce(h->partial, nb, 1, R, d_h1, ldh, nrm_off, 2, h->d_inv, st, h->d_flag, J, 0.5);
+  }));
+  // second pass, gated by the DGKS flag (h2 = 0 where it is not needed); the
+  // byte counts of these categories assume the pass runs (upper bounds)
+  CKS(launch(h, "gs2_dots_gated", (double)R * len * 16.0 * (J + 1), st, [&] {
+    return launch_dots(h->V, vi, vr, h->w, vr, len, J, R, h->partial, st, false, h->d_flag);
+  }));
+  CKS(launch(h, "gs2_reduce_gated", (double)R * J * nb * 16.0, st, [&] {
+    return launch_reduce(h->partial, nb, J, R, d_h1, ldh, m + 2, 0, nullptr, st, h->d_flag);
+  }));
+  CKS(launch(h, "gs2_update_gated", (double)R * len * 16.0 * (J + 2), st, [&] {
+    return launch_multi_axpy<double2>(h->w, vr, h->V, vi, vr, d_h1 + (m + 2), ldh, J, -1.0, len, R, st, h->d_flag);
+  }));
+  CKS(launch(h, "gs2_dots_gated", (double)R * len * 16.0, st, [&] {
+    return launch_dots(h->w, 0, vr, h->w, vr, len, 1, R, h->partial, st, false, h->d_flag);
+  }));
+  CKS(launch(h, "gs2_reduce_gated", (double)R * nb * 16.0, st, [&] {
+    return launch_reduce(h->partial, nb, 1, R, d_h1, ldh, nrm_off, 1, h->d_inv, st, h->d_flag);
+  }));
   CKS(launch(h, "scale_copy", (double)R * len * 32.0, st, [&] {
     return launch_scale_copy<double2>(h->V + (size_t)(j + 1) * vi, vr, h->w, vr, h->d_inv, len, R, st);
   }));
@@ -475,125 +509,173 @@ int run_step(amamg_ctx* h, int j, int R, cudaStream_t st) {
   return AMAMG_OK;
 }
 
-int fgmres_on(amamg_ctx* h, const double2* psi, double2* x, int R, cudaStream_t st, amamg_solve_info* info) {
+// One restart cycle of the FP64 flexible GMRES for R right-hand sides b_r with
+// iterates x_r (both [R][len] on the device), using the per-RHS host state st_.
+// Recomputes the true residual r = b - D x, marks converged right-hand sides,
+// runs Arnoldi steps (one captured graph each) until every still-active
+// right-hand side meets its residual estimate or m steps are done, and adds
+// Z y to x.  Returns AMAMG_OK; *any_left tells whether some right-hand side is
+// still unconverged and within its iteration budget.
+int fgmres_cycle(amamg_ctx* h, const double2* b, double2* x, int R, cudaStream_t st, std::vector<SlotState>& sl,
+                 bool* any_left) {
   const int m = h->prm.restart;
   const long len = 2L * h->lv[0].n;
   const size_t vr = (size_t)len, vi = (size_t)R * len;
   const bool mixed = h->prm.precision == AMAMG_SOLVE_MIXED;
-  CKS(ensure_vcycle_ws(h, R));
-  CKS(ensure_solver_ws(h, R));
   const int ldh = 3 * (m + 2);
-  double2* d_h1 = h->d_h;             // [R][ldh]: h1 at 0, h2 at m+2, norm at 2(m+2)
-  // ||psi||
-  CKS(norms(h, psi, vr, len, R, d_h1, ldh, 2 * (m + 2), h->d_inv, st));
+  const int nrm_off = 2 * (m + 2);
+  double2* d_h1 = h->d_h;
+  const double tol = h->prm.tol;
+  OuterState& o = h->outer;
+  o.resize(R, m);
+  // true residual and the norms of r and b
+  CKS(op_dslash<double>(h, x, h->res, b, R, st));
+  CKS(norms(h, h->res, vr, len, R, d_h1, ldh, nrm_off, h->d_inv, st));
+  CKS(norms(h, b, vr, len, R, d_h1, ldh, nrm_off + 1, nullptr, st));
   CK(cudaMemcpyAsync(h->h_h, h->d_h, sizeof(double2) * R * ldh, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  std::vector<double> bnorm(R), relres(R, 0.0);
-  std::vector<int> iters(R, 0), done(R, 0), status(R, AMAMG_OK);
-  int nonfinite = 0;
+  bool left = false;
   for (int r = 0; r < R; ++r) {
-    bnorm[r] = h->h_h[(size_t)r * ldh + 2 * (m + 2)].x;
-    if (!std::isfinite(bnorm[r])) { status[r] = AMAMG_ERR_NONFINITE; done[r] = 1; nonfinite = 1; }
-    if (bnorm[r] == 0.0) done[r] = 1;
+    SlotState& q = sl[r];
+    o.k[r] = 0;
+    o.building[r] = 0;
+    if (!q.active || q.done) continue;
+    if (q.fresh) {
+      q.bnorm = h->h_h[(size_t)r * ldh + nrm_off + 1].x;
+      q.fresh = 0;
+      if (!std::isfinite(q.bnorm)) { q.status = AMAMG_ERR_NONFINITE; q.done = 1; continue; }
+    }
+    const double beta = h->h_h[(size_t)r * ldh + nrm_off].x;
+    if (!std::isfinite(beta)) { q.status = AMAMG_ERR_NONFINITE; q.done = 1; continue; }
+    q.relres = q.bnorm > 0 ? beta / q.bnorm : 0.0;
+    if (q.relres <= tol) { q.done = 1; q.status = AMAMG_OK; continue; }
+    if (q.iters >= h->prm.max_iter) { q.done = 1; q.status = AMAMG_NOT_CONVERGED; continue; }
+    o.g[r].assign(m + 1, make_double2(0.0, 0.0));
+    o.g[r][0] = make_double2(beta, 0.0);
+    o.building[r] = 1;
+    left = true;
   }
-  CK(cudaMemsetAsync(x, 0, sizeof(double2) * R * len, st));
-  const double tol = h->prm.tol;
-  int total = 0;
-  // per-RHS Arnoldi state
-  std::vector<std::vector<double2>> H(R, std::vector<double2>((size_t)(m + 1) * m));
-  std::vector<std::vector<double2>> g(R, std::vector<double2>(m + 1));
-  std::vector<std::vector<double>> cs(R, std::vector<double>(m));
-  std::vector<std::vector<double2>> sn(R, std::vector<double2>(m));
-  std::vector<int> k(R), building(R);
-  while (true) {
-    // true residual r = psi - D x and its norm
-    CKS(op_dslash<double>(h, x, h->res, psi, R, st));
-    CKS(norms(h, h->res, vr, len, R, d_h1, ldh, 2 * (m + 2), h->d_inv, st));
-    CK(cudaMemcpyAsync(h->h_h, h->d_h, sizeof(double2) * R * ldh, cudaMemcpyDeviceToHost, st));
+  *any_left = left;
+  if (!left) return AMAMG_OK;
+  // V[0] = r / beta (zero for right-hand sides that are not building: their inv is
+  // set by the norm of a zero or converged residual and they are ignored below)
+  CKS(launch(h, "scale_copy", (double)R * len * 32.0, st, [&] {
+    return launch_scale_copy<double2>(h->V, vr, h->res, vr, h->d_inv, len, R, st);
+  }));
+  int j = 0;
+  for (; j < m; ++j) {
+    CKS(run_step(h, j, R, st));
     CK(cudaStreamSynchronize(st));
-    bool all = true;
+    bool any = false;
     for (int r = 0; r < R; ++r) {
-      if (status[r] == AMAMG_ERR_NONFINITE) continue;
-      const double beta = h->h_h[(size_t)r * ldh + 2 * (m + 2)].x;
-      if (!std::isfinite(beta)) { status[r] = AMAMG_ERR_NONFINITE; done[r] = 1; nonfinite = 1; continue; }
-      relres[r] = bnorm[r] > 0 ? beta / bnorm[r] : 0.0;
-      if (relres[r] <= tol) done[r] = 1;
-      if (!done[r]) all = false;
-      g[r].assign(m + 1, make_double2(0.0, 0.0));
-      g[r][0] = make_double2(beta, 0.0);
-    }
-    if (all || total >= h->prm.max_iter) break;
-    // V[0] = r / beta
-    CKS(launch(h, "scale_copy", (double)R * len * 32.0, st, [&] {
-      return launch_scale_copy<double2>(h->V, vr, h->res, vr, h->d_inv, len, R, st);
-    }));
-    for (int r = 0; r < R; ++r) { k[r] = 0; building[r] = !done[r]; }
-    int j = 0;
-    for (; j < m; ++j) {
-      CKS(run_step(h, j, R, st));
-      CK(cudaStreamSynchronize(st));
-      ++total;
-      bool any = false;
-      for (int r = 0; r < R; ++r) {
-        if (!building[r]) continue;
-        const double2* hh = h->h_h + (size_t)r * ldh;
-        std::vector<double2>& Hr = H[r];
-        for (int i = 0; i <= j; ++i) Hr[(size_t)i * m + j] = hh[i] + hh[(m + 2) + i];
-        const double hn = hh[2 * (m + 2)].x;
-        if (!std::isfinite(hn)) { status[r] = AMAMG_ERR_NONFINITE; done[r] = 1; building[r] = 0; nonfinite = 1; continue; }
-        // earlier rotations, then a new one that annihilates H[j+1][j]
-        for (int i = 0; i < j; ++i) {
-          const double2 a = Hr[(size_t)i * m + j], b = Hr[(size_t)(i + 1) * m + j];
-          Hr[(size_t)i * m + j] = cs[r][i] * a + cmul(sn[r][i], b);
-          Hr[(size_t)(i + 1) * m + j] = cs[r][i] * b - cmulc(sn[r][i], a);
-        }
-        const double2 a = Hr[(size_t)j * m + j];
-        const double aa = std::sqrt(a.x * a.x + a.y * a.y);
-        double c;
-        double2 s;
-        if (hn == 0.0) { c = 1.0; s = make_double2(0.0, 0.0); }
-        else if (aa == 0.0) { c = 0.0; s = make_double2(1.0, 0.0); }
-        else {
-          const double rr = std::hypot(aa, hn);
-          c = aa / rr;
-          s = make_double2(a.x / aa * hn / rr, a.y / aa * hn / rr);   // (a/|a|) conj(hn) / r, hn real
-        }
-        cs[r][j] = c;
-        sn[r][j] = s;
-        Hr[(size_t)j * m + j] = c * a + hn * s;
-        const double2 gj = g[r][j];
-        g[r][j + 1] = -1.0 * cmulc(s, gj);
-        g[r][j] = c * gj;
-        iters[r]++;
-        k[r] = j + 1;
-        const double est = std::sqrt(cabs2(g[r][j + 1]));
-        if (est <= tol * bnorm[r] || hn == 0.0) building[r] = 0;
-        if (building[r]) any = true;
+      if (!o.building[r]) continue;
+      SlotState& q = sl[r];
+      const double2* hh = h->h_h + (size_t)r * ldh;
+      std::vector<double2>& Hr = o.H[r];
+      for (int i = 0; i <= j; ++i) Hr[(size_t)i * m + j] = hh[i] + hh[(m + 2) + i];
+      const double hn = hh[nrm_off].x;
+      if (!std::isfinite(hn)) { q.status = AMAMG_ERR_NONFINITE; q.done = 1; o.building[r] = 0; o.k[r] = 0; continue; }
+      // earlier rotations, then a new one that annihilates H[j+1][j]
+      for (int i = 0; i < j; ++i) {
+        const double2 a = Hr[(size_t)i * m + j], bb = Hr[(size_t)(i + 1) * m + j];
+        Hr[(size_t)i * m + j] = o.cs[r][i] * a + cmul(o.sn[r][i], bb);
+        Hr[(size_t)(i + 1) * m + j] = o.cs[r][i] * bb - cmulc(o.sn[r][i], a);
       }
-      if (!any || total >= h->prm.max_iter) { ++j; break; }
+      const double2 a = Hr[(size_t)j * m + j];
+      const double aa = std::sqrt(a.x * a.x + a.y * a.y);
+      double c;
+      double2 sv;
+      if (hn == 0.0) { c = 1.0; sv = make_double2(0.0, 0.0); }
+      else if (aa == 0.0) { c = 0.0; sv = make_double2(1.0, 0.0); }
+      else {
+        const double rr = std::hypot(aa, hn);
+        c = aa / rr;
+        sv = make_double2(a.x / aa * hn / rr, a.y / aa * hn / rr);   // (a/|a|) conj(hn) / r, hn real
+      }
+      o.cs[r][j] = c;
+      o.sn[r][j] = sv;
+      Hr[(size_t)j * m + j] = c * a + hn * sv;
+      const double2 gj = o.g[r][j];
+      o.g[r][j + 1] = -1.0 * cmulc(sv, gj);
+      o.g[r][j] = c * gj;
+      q.iters++;
+      o.k[r] = j + 1;
+      const double est = std::sqrt(cabs2(o.g[r][j + 1]));
+      if (est <= tol * q.bnorm || hn == 0.0 || q.iters >= h->prm.max_iter) o.building[r] = 0;
+      if (o.building[r]) any = true;
     }
-    // x += Z y  (per right-hand side k[r] columns; the rest zero)
-    const int jmax = j < m ? j : m;
-    for (int r = 0; r < R; ++r) {
-      double2* y = h->h_y + (size_t)r * m;
-      for (int i = 0; i < m; ++i) y[i] = make_double2(0.0, 0.0);
-      if (k[r] > 0 && status[r] != AMAMG_ERR_NONFINITE) back_solve(H[r], m, g[r], k[r], y);
-    }
-    CK(cudaMemcpyAsync(h->d_y, h->h_y, sizeof(double2) * R * m, cudaMemcpyHostToDevice, st));
-    if (mixed)
-      CKS(launch(h, "x_update", (double)R * len * (8.0 * jmax + 32.0), st, [&] {
-        return launch_multi_axpy<float2>(x, vr, h->Z32, vi, vr, h->d_y, m, jmax, 1.0, len, R, st);
-      }));
-    else
-      CKS(launch(h, "x_update", (double)R * len * (16.0 * jmax + 32.0), st, [&] {
-        return launch_multi_axpy<double2>(x, vr, h->Z64, vi, vr, h->d_y, m, jmax, 1.0, len, R, st);
-      }));
+    if (!any) { ++j; break; }
+  }
+  // x += Z y  (per right-hand side k[r] columns; the rest zero)
+  const int jmax = j < m ? j : m;
+  for (int r = 0; r < R; ++r) {
+    double2* y = h->h_y + (size_t)r * m;
+    for (int i = 0; i < m; ++i) y[i] = make_double2(0.0, 0.0);
+    if (o.k[r] > 0 && sl[r].status != AMAMG_ERR_NONFINITE) back_solve(o.H[r], m, o.g[r], o.k[r], y);
+  }
+  CK(cudaMemcpyAsync(h->d_y, h->h_y, sizeof(double2) * R * m, cudaMemcpyHostToDevice, st));
+  if (mixed)
+    CKS(launch(h, "x_update", (double)R * len * (8.0 * jmax + 32.0), st, [&] {
+      return launch_multi_axpy<float2>(x, vr, h->Z32, vi, vr, h->d_y, m, jmax, 1.0, len, R, st);
+    }));
+  else
+    CKS(launch(h, "x_update", (double)R * len * (16.0 * jmax + 32.0), st, [&] {
+      return launch_multi_axpy<double2>(x, vr, h->Z64, vi, vr, h->d_y, m, jmax, 1.0, len, R, st);
+    }));
+  return AMAMG_OK;
+}
+
+// Per-RHS masses of the fine operator for the next cycles: diag = m0_r + 2 and
+// its inverse in FP64 and FP32, copied to the solver's device arrays.
+int set_masses(amamg_ctx* h, const double* m0, int R, cudaStream_t st) {
+  std::vector<double> d(R), i64(R);
+  std::vector<float> i32(R);
+  for (int r = 0; r < R; ++r) {
+    d[r] = m0[r] + 2.0;
+    i64[r] = 1.0 / d[r];
+    i32[r] = (float)i64[r];
+  }
+  CK(cudaMemcpyAsync(h->d_diag64, d.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(h->d_inv64, i64.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(h->d_inv32, i32.data(), sizeof(float) * R, cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));   // the host vectors go out of scope
+  return AMAMG_OK;
+}
+
+// Solver kernels read the per-RHS mass arrays while this guard is alive.
+struct MassGuard {
+  amamg_ctx* h;
+  explicit MassGuard(amamg_ctx* hh) : h(hh) {
+    h->cur_diag64 = h->d_diag64;
+    h->cur_inv64 = h->d_inv64;
+    h->cur_inv32 = h->d_inv32;
+  }
+  ~MassGuard() { h->cur_diag64 = nullptr; h->cur_inv64 = nullptr; h->cur_inv32 = nullptr; }
+};
+
+int fgmres_on(amamg_ctx* h, const double2* psi, double2* x, int R, cudaStream_t st, amamg_solve_info* info) {
+  const long len = 2L * h->lv[0].n;
+  CKS(ensure_vcycle_ws(h, R));
+  CKS(ensure_solver_ws(h, R));
+  std::vector<double> masses(R, h->m0);
+  CKS(set_masses(h, masses.data(), R, st));
+  MassGuard guard(h);
+  std::vector<SlotState> sl(R);
+  for (auto& q : sl) { q.active = 1; q.fresh = 1; q.done = 0; }
+  CK(cudaMemsetAsync(x, 0, sizeof(double2) * R * len, st));
+  int cycles = 0;
+  while (true) {
+    bool left = false;
+    CKS(fgmres_cycle(h, psi, x, R, st, sl, &left));
+    if (!left) break;
+    if (++cycles > h->prm.max_iter + 1) break;   // every cycle takes at least one step
   }
   int rc = AMAMG_OK;
+  bool nonfinite = false;
   for (int r = 0; r < R; ++r) {
-    if (status[r] == AMAMG_OK && !done[r]) status[r] = AMAMG_NOT_CONVERGED;
-    if (info) { info[r].iterations = iters[r]; info[r].status = status[r]; info[r].true_relres = relres[r]; }
-    if (status[r] == AMAMG_NOT_CONVERGED && rc == AMAMG_OK) rc = AMAMG_NOT_CONVERGED;
+    if (info) { info[r].iterations = sl[r].iters; info[r].status = sl[r].status; info[r].true_relres = sl[r].relres; }
+    if (sl[r].status == AMAMG_NOT_CONVERGED && rc == AMAMG_OK) rc = AMAMG_NOT_CONVERGED;
+    if (sl[r].status == AMAMG_ERR_NONFINITE) nonfinite = true;
   }
   if (nonfinite) { h->err = "non-finite value in a right-hand side or residual"; rc = AMAMG_ERR_NONFINITE; }
   return rc;
@@ -644,7 +726,8 @@ void free_all(amamg_ctx* h) {
   h->ws = nullptr; h->ev_in = h->ev_out = nullptr;
   dfree(h->U64); dfree(h->U32); dfree(h->Ainv); dfree(h->Ainv32); dfree(h->d_err);
   dfree(h->V); dfree(h->Z64); dfree(h->Z32); dfree(h->v32); dfree(h->w); dfree(h->res);
-  dfree(h->partial); dfree(h->d_h); dfree(h->d_inv); dfree(h->d_y);
+  dfree(h->partial); dfree(h->d_h); dfree(h->d_inv); dfree(h->d_flag); dfree(h->d_y);
+  dfree(h->d_diag64); dfree(h->d_inv64); dfree(h->d_inv32);
   if (h->h_h) cudaFreeHost(h->h_h);
   if (h->h_y) cudaFreeHost(h->h_y);
   h->h_h = h->h_y = nullptr;
@@ -850,6 +933,101 @@ int amamg_solve(amamg_handle h, const void* psi, void* x, int R, void* stream, a
   return fgmres(h, (const double2*)psi, (double2*)x, R, S(stream), info);
 }
 
+int amamg_batch_create(amamg_handle h, int slots, amamg_batch_handle* out) {
+  if (!h || !out || slots < 1) return AMAMG_ERR_INVALID_ARG;
+  *out = nullptr;
+  int rc = ensure_vcycle_ws(h, slots);
+  if (rc == AMAMG_OK) rc = ensure_solver_ws(h, slots);
+  if (rc != AMAMG_OK) return rc;
+  amamg_batch* b = new amamg_batch();
+  b->h = h;
+  b->S = slots;
+  const size_t n = (size_t)slots * 2 * (size_t)h->lv[0].n;   // slots x len complex elements
+  if (cudaMalloc((void**)&b->B, n * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc((void**)&b->X, n * sizeof(double2)) != cudaSuccess) {
+    cudaGetLastError();
+    if (b->B) cudaFree(b->B);
+    if (b->X) cudaFree(b->X);
+    delete b;
+    h->err = "amamg_batch_create: out of device memory";
+    return AMAMG_ERR_OOM;
+  }
+  cudaMemset(b->B, 0, n * sizeof(double2));
+  cudaMemset(b->X, 0, n * sizeof(double2));
+  b->sl.assign(slots, SlotState());
+  b->mass.assign(slots, h->m0);
+  *out = b;
+  return AMAMG_OK;
+}
+
+int amamg_batch_admit(amamg_batch_handle b, int slot, const void* psi, double m0, void* stream) {
+  if (!b || !psi || slot < 0 || slot >= b->S || !std::isfinite(m0)) return AMAMG_ERR_INVALID_ARG;
+  amamg_ctx* h = b->h;
+  if (b->sl[slot].active) { h->err = "amamg_batch_admit: slot is occupied"; return AMAMG_ERR_INVALID_ARG; }
+  const size_t len = 2 * (size_t)h->lv[0].n;
+  cudaStream_t st = S(stream);
+  CK(cudaMemcpyAsync(b->B + slot * len, psi, len * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemsetAsync(b->X + slot * len, 0, len * sizeof(double2), st));
+  SlotState q;
+  q.active = 1; q.fresh = 1; q.done = 0;
+  b->sl[slot] = q;
+  b->mass[slot] = m0;
+  return AMAMG_OK;
+}
+
+int amamg_batch_cycle(amamg_batch_handle b, void* stream, amamg_slot_info* info) {
+  if (!b) return AMAMG_ERR_INVALID_ARG;
+  amamg_ctx* h = b->h;
+  cudaStream_t st = S(stream);
+  const int R = b->S;
+  int rc = ensure_vcycle_ws(h, R);
+  if (rc == AMAMG_OK) rc = ensure_solver_ws(h, R);
+  if (rc != AMAMG_OK) return rc;
+  CK(cudaEventRecord(h->ev_in, st));
+  CK(cudaStreamWaitEvent(h->ws, h->ev_in, 0));
+  rc = set_masses(h, b->mass.data(), R, h->ws);
+  bool left = false;
+  if (rc == AMAMG_OK) {
+    MassGuard guard(h);
+    rc = fgmres_cycle(h, b->B, b->X, R, h->ws, b->sl, &left);
+  }
+  CK(cudaEventRecord(h->ev_out, h->ws));
+  CK(cudaStreamWaitEvent(st, h->ev_out, 0));
+  CK(cudaStreamSynchronize(st));
+  if (info)
+    for (int r = 0; r < R; ++r) {
+      const SlotState& q = b->sl[r];
+      info[r].active = q.active;
+      info[r].done = q.active ? q.done : 1;
+      info[r].status = q.status;
+      info[r].iterations = q.iters;
+      info[r].true_relres = q.relres;
+    }
+  return rc;
+}
+
+int amamg_batch_retire(amamg_batch_handle b, int slot, void* x, void* stream) {
+  if (!b || slot < 0 || slot >= b->S) return AMAMG_ERR_INVALID_ARG;
+  amamg_ctx* h = b->h;
+  const size_t len = 2 * (size_t)h->lv[0].n;
+  cudaStream_t st = S(stream);
+  if (x) CK(cudaMemcpyAsync(x, b->X + slot * len, len * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemsetAsync(b->B + slot * len, 0, len * sizeof(double2), st));
+  CK(cudaMemsetAsync(b->X + slot * len, 0, len * sizeof(double2), st));
+  b->sl[slot] = SlotState();
+  b->mass[slot] = h->m0;
+  return AMAMG_OK;
+}
+
+int amamg_batch_destroy(amamg_batch_handle b) {
+  if (!b) return AMAMG_ERR_INVALID_ARG;
+  cudaDeviceSynchronize();
+  if (b->B) cudaFree(b->B);
+  if (b->X) cudaFree(b->X);
+  delete b;
+  return AMAMG_OK;
+}
+
 int amamg_apply_D(amamg_handle h, const void* in, void* out, int R, int precision, void* stream) {
   if (!h || !in || !out || R < 1) return AMAMG_ERR_INVALID_ARG;
   if (precision == AMAMG_F64) return op_dslash<double>(h, (const double2*)in, (double2*)out, nullptr, R, S(stream));
@@ -959,7 +1137,8 @@ int amamg_profile_reset(amamg_handle h) {
   return rc;
 }
 
-int amamg_profile_get(amamg_handle h, int idx, const char** name, long long* launches, double* total_ms, double* bytes) {
+int amamg_profile_get(amamg_handle h, int idx, const char** name, long long* launches, double* total_ms, double* bytes,
+                      double* flops) {
   if (!h) return AMAMG_ERR_INVALID_ARG;
   int rc = collect_profile(h);
   if (rc != AMAMG_OK) return rc;
@@ -969,6 +1148,7 @@ int amamg_profile_get(amamg_handle h, int idx, const char** name, long long* lau
   if (launches) *launches = c.launches;
   if (total_ms) *total_ms = c.ms;
   if (bytes) *bytes = c.bytes;
+  if (flops) *flops = c.flops;
   return AMAMG_OK;
 }
 

@@ -33,30 +33,42 @@ __device__ __forceinline__ C block_reduce(C v, C* sh) {
   return v;
 }
 
-// partial[(r*J + i)*nb + blk] = sum over the block's chunk of conj(V_i,r) w_r
+// partial[(r*Jt + i)*nb + blk] = sum over the block's chunk of conj(V_i,r) w_r for
+// i < J, and conj(w_r) w_r for i == J when the grid has J + 1 rows (Jt = gridDim.y).
+// gate (optional): per right-hand side flag; a block whose flag is 0 does nothing.
 __global__ void __launch_bounds__(DOT_THREADS)
 k_dots(const double2* __restrict__ V, size_t vi, size_t vr, const double2* __restrict__ w, size_t wr,
-       long len, long chunk, double2* __restrict__ partial, int J) {
+       long len, long chunk, double2* __restrict__ partial, int J, const int* __restrict__ gate) {
   __shared__ double2 sh[32];
-  const int i = blockIdx.y, r = blockIdx.z, nb = gridDim.x;
-  const double2* a = V + i * vi + r * vr;
+  const int i = blockIdx.y, r = blockIdx.z, nb = gridDim.x, Jt = gridDim.y;
+  if (gate && gate[r] == 0) return;
+  const double2* a = (i < J) ? V + i * vi + r * vr : w + r * wr;
   const double2* b = w + r * wr;
   const long start = (long)blockIdx.x * chunk;
   const long end = min(start + chunk, len);
   double2 acc = make_double2(0.0, 0.0);
-  for (long k = start + threadIdx.x; k < end; k += blockDim.x) acc += cmulc(a[k], b[k]);
+  for (long k = start + threadIdx.x; k < end; k += blockDim.x) cmacc(acc, a[k], b[k]);
   acc = block_reduce(acc, sh);
-  if (threadIdx.x == 0) partial[((size_t)r * J + i) * nb + blockIdx.x] = acc;
+  if (threadIdx.x == 0) partial[((size_t)r * Jt + i) * nb + blockIdx.x] = acc;
 }
 
-// out[r*ldo + off + i] = sum_b partial[(r*J + i)*nb + b]  (+ optional norm form)
-// mode 0: store the complex sum; mode 1: the sum is <w, w>: store sqrt(re) in
-// out and 1/sqrt(re) (0 when the norm is 0) in inv.
+// out[r*ldo + off + i] = sum_b partial[(r*J + i)*nb + b]
+// mode 0: store the complex sum (0 for a right-hand side whose gate flag is 0);
+// mode 1: the sum is <w, w>: store sqrt(re) in out and 1/sqrt(re) (0 when the
+//   norm is 0) in inv; with a gate, only where the flag is set;
+// mode 2: as mode 1, and set flag[r] = (<w, w> < eta^2 * ref) where ref =
+//   out[r*ldo + ref_off].x is the squared norm before the first Gram-Schmidt
+//   pass (DGKS criterion for a second pass).
 __global__ void __launch_bounds__(256)
 k_reduce_partials(const double2* __restrict__ partial, int nb, int J, double2* __restrict__ out, int ldo,
-                  int off, int mode, double* __restrict__ inv) {
+                  int off, int mode, double* __restrict__ inv, int* __restrict__ flag, int ref_off, double eta2) {
   __shared__ double2 sh[32];
   const int i = blockIdx.x, r = blockIdx.y;
+  const bool gated = flag && mode != 2 && flag[r] == 0;
+  if (gated) {
+    if (threadIdx.x == 0 && mode == 0) out[(size_t)r * ldo + off + i] = make_double2(0.0, 0.0);
+    return;
+  }
   const double2* p = partial + ((size_t)r * J + i) * nb;
   double2 acc = make_double2(0.0, 0.0);
   for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += p[b];
@@ -69,6 +81,7 @@ k_reduce_partials(const double2* __restrict__ partial, int nb, int J, double2* _
       const double nrm = (acc.x >= 0.0) ? sqrt(acc.x) : ((acc.x < 0.0) ? 0.0 : acc.x);
       out[(size_t)r * ldo + off + i] = make_double2(nrm, 0.0);
       if (inv) inv[r] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+      if (mode == 2) flag[r] = (acc.x < eta2 * out[(size_t)r * ldo + ref_off].x) ? 1 : 0;
     }
   }
 }
@@ -77,12 +90,13 @@ k_reduce_partials(const double2* __restrict__ partial, int nb, int J, double2* _
 template <typename Cx>
 __global__ void __launch_bounds__(256)
 k_multi_axpy(double2* __restrict__ y, size_t yr, const Cx* __restrict__ X, size_t xi, size_t xr,
-             const double2* __restrict__ coef, int ldc, int J, double sign, long len) {
+             const double2* __restrict__ coef, int ldc, int J, double sign, long len, const int* __restrict__ gate) {
   const int r = blockIdx.y;
+  if (gate && gate[r] == 0) return;
   const double2* c = coef + (size_t)r * ldc;
   for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < len; k += (long)gridDim.x * blockDim.x) {
     double2 acc = make_double2(0.0, 0.0);
-    for (int i = 0; i < J; ++i) acc += cmul(c[i], to_c(X[i * xi + r * xr + k], double()));
+    for (int i = 0; i < J; ++i) cmac(acc, c[i], to_c(X[i * xi + r * xr + k], double()));
     y[r * yr + k] += sign * acc;
   }
 }
@@ -119,26 +133,26 @@ int dot_blocks(long len) {
 }
 
 cudaError_t launch_dots(const double2* V, size_t vi, size_t vr, const double2* w, size_t wr, long len, int J,
-                        int R, double2* partial, cudaStream_t st) {
+                        int R, double2* partial, cudaStream_t st, bool with_self, const int* gate) {
   const int nb = dot_blocks(len);
   const long chunk = (len + nb - 1) / nb;
-  dim3 grid(nb, J, R);
-  k_dots<<<grid, DOT_THREADS, 0, st>>>(V, vi, vr, w, wr, len, chunk, partial, J);
+  dim3 grid(nb, J + (with_self ? 1 : 0), R);
+  k_dots<<<grid, DOT_THREADS, 0, st>>>(V, vi, vr, w, wr, len, chunk, partial, J, gate);
   return cudaGetLastError();
 }
 
 cudaError_t launch_reduce(const double2* partial, int nb, int J, int R, double2* out, int ldo, int off, int mode,
-                          double* inv, cudaStream_t st) {
+                          double* inv, cudaStream_t st, int* flag, int ref_off, double eta2) {
   dim3 grid(J, R);
-  k_reduce_partials<<<grid, 256, 0, st>>>(partial, nb, J, out, ldo, off, mode, inv);
+  k_reduce_partials<<<grid, 256, 0, st>>>(partial, nb, J, out, ldo, off, mode, inv, flag, ref_off, eta2);
   return cudaGetLastError();
 }
 
 template <typename Cx>
 cudaError_t launch_multi_axpy(double2* y, size_t yr, const Cx* X, size_t xi, size_t xr, const double2* coef, int ldc,
-                              int J, double sign, long len, int R, cudaStream_t st) {
+                              int J, double sign, long len, int R, cudaStream_t st, const int* gate) {
   dim3 grid(grid_for(len), R);
-  k_multi_axpy<Cx><<<grid, 256, 0, st>>>(y, yr, X, xi, xr, coef, ldc, J, sign, len);
+  k_multi_axpy<Cx><<<grid, 256, 0, st>>>(y, yr, X, xi, xr, coef, ldc, J, sign, len, gate);
   return cudaGetLastError();
 }
 
@@ -157,9 +171,9 @@ cudaError_t launch_cast(const Cs* src, Cd* dst, long len, cudaStream_t st) {
 }
 
 template cudaError_t launch_multi_axpy<double2>(double2*, size_t, const double2*, size_t, size_t, const double2*, int,
-                                                int, double, long, int, cudaStream_t);
+                                                int, double, long, int, cudaStream_t, const int*);
 template cudaError_t launch_multi_axpy<float2>(double2*, size_t, const float2*, size_t, size_t, const double2*, int,
-                                               int, double, long, int, cudaStream_t);
+                                               int, double, long, int, cudaStream_t, const int*);
 template cudaError_t launch_scale_copy<double2>(double2*, size_t, const double2*, size_t, const double*, long, int,
                                                 cudaStream_t);
 template cudaError_t launch_scale_copy<float2>(float2*, size_t, const double2*, size_t, const double*, long, int,

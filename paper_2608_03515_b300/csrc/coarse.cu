@@ -45,8 +45,10 @@ k_coarse_apply(const typename cplx<T>::type* __restrict__ in, typename cplx<T>::
     int xw = x + off.dx[k]; xw -= (xw >= Nx) ? Nx : 0;
     const int w = tw * Nx + xw;
     const C x0 = i0[w], x1 = i0[n + w];
-    y0 += cmul(b_load<T, BT>(B, Bs, k, 0, n, v), x0) + cmul(b_load<T, BT>(B, Bs, k, 1, n, v), x1);
-    y1 += cmul(b_load<T, BT>(B, Bs, k, 2, n, v), x0) + cmul(b_load<T, BT>(B, Bs, k, 3, n, v), x1);
+    cmac(y0, b_load<T, BT>(B, Bs, k, 0, n, v), x0);
+    cmac(y0, b_load<T, BT>(B, Bs, k, 1, n, v), x1);
+    cmac(y1, b_load<T, BT>(B, Bs, k, 2, n, v), x0);
+    cmac(y1, b_load<T, BT>(B, Bs, k, 3, n, v), x1);
   }
   C* o = out + roff;
   if (b) {
@@ -57,38 +59,43 @@ k_coarse_apply(const typename cplx<T>::type* __restrict__ in, typename cplx<T>::
   o[n + v] = y1;
 }
 
-// Block Gauss-Seidel update of one coarse site v on A e = r, by one warp:
-// lane k (1 <= k < K) forms A_{v, v+off_k} e_{v+off_k}; the warp sums the lanes
-// (xor-shuffle tree, fixed order) and lane 0 writes
+// Block Gauss-Seidel update of one coarse site v on A e = r by a group of LPS
+// lanes: lane g of the group forms A_{v, v+off_k} e_{v+off_k} for
+// k = 1 + g, 1 + g + LPS, ...; the group sums its lanes (xor-shuffle tree, fixed
+// order) and its lane 0 writes
 // e_v = A_vv^{-1} (r_v - sum_{k >= 1} A_{v, v+off_k} e_{v+off_k}).
 // Neighbour values are read through L2 (ld.global.cg) so that the kernel is also
 // correct when other thread blocks of a cluster updated them.
-template <typename T, typename BT>
-__device__ __forceinline__ void gs_site_warp(typename cplx<T>::type* __restrict__ e0,
-                                             const typename cplx<T>::type* __restrict__ r0,
-                                             const BT* __restrict__ B, const float* __restrict__ Bs,
-                                             const typename cplx<T>::type* __restrict__ Dinv, const Offsets& off,
-                                             int Nt, int Nx, int t, int x, int lane) {
+template <typename T, typename BT, int LPS>
+__device__ __forceinline__ void gs_site(typename cplx<T>::type* __restrict__ e0,
+                                        const typename cplx<T>::type* __restrict__ r0,
+                                        const BT* __restrict__ B, const float* __restrict__ Bs,
+                                        const typename cplx<T>::type* __restrict__ Dinv, const Offsets& off,
+                                        int Nt, int Nx, int t, int x, int g, bool valid) {
+  // every lane of the warp calls this (the shuffles need all 32); lanes of
+  // groups without a site pass valid = false and only take part in the shuffles
   using C = typename cplx<T>::type;
   const int n = Nt * Nx;
   const int v = t * Nx + x;
   C s0 = czero<C>(), s1 = czero<C>();
-  if (lane >= 1 && lane < off.K) {
-    int tw = t + off.dt[lane]; tw -= (tw >= Nt) ? Nt : 0;
-    int xw = x + off.dx[lane]; xw -= (xw >= Nx) ? Nx : 0;
+  for (int k = 1 + g; valid && k < off.K; k += LPS) {
+    int tw = t + off.dt[k]; tw -= (tw >= Nt) ? Nt : 0;
+    int xw = x + off.dx[k]; xw -= (xw >= Nx) ? Nx : 0;
     const int w = tw * Nx + xw;
     const C x0 = __ldcg(e0 + w), x1 = __ldcg(e0 + n + w);
-    s0 = cmul(b_load<T, BT>(B, Bs, lane, 0, n, v), x0) + cmul(b_load<T, BT>(B, Bs, lane, 1, n, v), x1);
-    s1 = cmul(b_load<T, BT>(B, Bs, lane, 2, n, v), x0) + cmul(b_load<T, BT>(B, Bs, lane, 3, n, v), x1);
+    cmac(s0, b_load<T, BT>(B, Bs, k, 0, n, v), x0);
+    cmac(s0, b_load<T, BT>(B, Bs, k, 1, n, v), x1);
+    cmac(s1, b_load<T, BT>(B, Bs, k, 2, n, v), x0);
+    cmac(s1, b_load<T, BT>(B, Bs, k, 3, n, v), x1);
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
+  for (int o = LPS / 2; o > 0; o >>= 1) {
     s0.x += __shfl_xor_sync(0xffffffffu, s0.x, o);
     s0.y += __shfl_xor_sync(0xffffffffu, s0.y, o);
     s1.x += __shfl_xor_sync(0xffffffffu, s1.x, o);
     s1.y += __shfl_xor_sync(0xffffffffu, s1.y, o);
   }
-  if (lane == 0) {
+  if (valid && g == 0) {
     const C a0 = r0[v] - s0, a1 = r0[n + v] - s1;
     const C d00 = Dinv[v], d01 = Dinv[n + v], d10 = Dinv[2 * n + v], d11 = Dinv[3 * n + v];
     __stcg(e0 + v, cmul(d00, a0) + cmul(d01, a1));
@@ -96,33 +103,42 @@ __device__ __forceinline__ void gs_site_warp(typename cplx<T>::type* __restrict_
   }
 }
 
+// Lanes per site: 4 in FP64 (B300's FP64 pipe is narrow: few lanes per site
+// and the sites of a colour spread over all SMs), 32 in FP32 (all offsets of a
+// site loaded at once: the clustered sweep is latency bound).
+template <typename T> struct GsLanes { static constexpr int value = 32; };
+template <> struct GsLanes<double> { static constexpr int value = 4; };
+
 // One colour of the 16-colour sweep, sites (t, x) with (t mod 4, x mod 4) =
-// (c / 4, c % 4); one warp per site.
+// (c / 4, c % 4); LPS lanes per site.
 template <typename T, typename BT>
 __global__ void __launch_bounds__(256)
 k_coarse_colour(typename cplx<T>::type* __restrict__ e, const typename cplx<T>::type* __restrict__ r,
                 const BT* __restrict__ B, const float* __restrict__ Bs,
                 const typename cplx<T>::type* __restrict__ Dinv, Offsets off, int Nt, int Nx, int colour) {
+  constexpr int LPS = GsLanes<T>::value;
   const int n = Nt * Nx;
   const int qx = Nx >> 2;
-  const int idx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (idx >= (n >> 4)) return;
-  const int ti = idx / qx;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int idx = tid / LPS;
+  const int g = tid & (LPS - 1);
+  const bool valid = idx < (n >> 4);
+  const int ti = valid ? idx / qx : 0;
   const int t = 4 * ti + (colour >> 2);
-  const int x = 4 * (idx - ti * qx) + (colour & 3);
+  const int x = valid ? 4 * (idx - ti * qx) + (colour & 3) : 0;
   const size_t roff = (size_t)blockIdx.y * 2 * n;
-  gs_site_warp<T, BT>(e + roff, r + roff, B, Bs, Dinv, off, Nt, Nx, t, x, lane);
+  gs_site<T, BT, LPS>(e + roff, r + roff, B, Bs, Dinv, off, Nt, Nx, t, x, g, valid);
 }
 
 // All colours of `sweeps` sweeps in one launch: one thread block cluster per
-// right-hand side, one warp per site, and a cluster barrier (barrier.cluster,
+// right-hand side, LPS lanes per site, and a cluster barrier (barrier.cluster,
 // release/acquire) between colours.  Same arithmetic as k_coarse_colour.
 template <typename T, typename BT>
 __global__ void __launch_bounds__(1024)
 k_coarse_sweeps_cluster(typename cplx<T>::type* __restrict__ e, const typename cplx<T>::type* __restrict__ r,
                         const BT* __restrict__ B, const float* __restrict__ Bs,
                         const typename cplx<T>::type* __restrict__ Dinv, Offsets off, int Nt, int Nx, int sweeps) {
+  constexpr int LPS = GsLanes<T>::value;
   cg::cluster_group cluster = cg::this_cluster();
   const int n = Nt * Nx;
   const int qx = Nx >> 2;
@@ -131,16 +147,19 @@ k_coarse_sweeps_cluster(typename cplx<T>::type* __restrict__ e, const typename c
   const int csize = (int)cluster.num_blocks();
   const int rhs = blockIdx.x / csize;
   const size_t roff = (size_t)rhs * 2 * n;
-  const int lane = threadIdx.x & 31;
-  const int wpb = blockDim.x >> 5;
-  const int stride = csize * wpb;
+  const int g = threadIdx.x & (LPS - 1);
+  const int gpb = blockDim.x / LPS;
+  const int stride = csize * gpb;
   for (int sw = 0; sw < sweeps; ++sw) {
     for (int colour = 0; colour < 16; ++colour) {
-      for (int idx = rank * wpb + (threadIdx.x >> 5); idx < per_colour; idx += stride) {
-        const int ti = idx / qx;
+      // every group runs the same number of iterations (shuffles stay converged)
+      for (int base = 0; base < per_colour; base += stride) {
+        const int idx = base + rank * gpb + threadIdx.x / LPS;
+        const bool valid = idx < per_colour;
+        const int ti = valid ? idx / qx : 0;
         const int t = 4 * ti + (colour >> 2);
-        const int x = 4 * (idx - ti * qx) + (colour & 3);
-        gs_site_warp<T, BT>(e + roff, r + roff, B, Bs, Dinv, off, Nt, Nx, t, x, lane);
+        const int x = valid ? 4 * (idx - ti * qx) + (colour & 3) : 0;
+        gs_site<T, BT, LPS>(e + roff, r + roff, B, Bs, Dinv, off, Nt, Nx, t, x, g, valid);
       }
       cluster.sync();
     }
@@ -169,12 +188,12 @@ k_dense_gemv(const double2* __restrict__ A, const Cv* __restrict__ x, Cv* __rest
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int r = 0; r < RR; ++r) acc[r] += cmul(aj[u], to_c(x[(size_t)r * nd + j + 32 * u], double()));
+      for (int r = 0; r < RR; ++r) cmac(acc[r], aj[u], to_c(x[(size_t)r * nd + j + 32 * u], double()));
   }
   for (; j < nd; j += 32) {
     const double2 aj = a[j];
 #pragma unroll
-    for (int r = 0; r < RR; ++r) acc[r] += cmul(aj, to_c(x[(size_t)r * nd + j], double()));
+    for (int r = 0; r < RR; ++r) cmac(acc[r], aj, to_c(x[(size_t)r * nd + j], double()));
   }
 #pragma unroll
   for (int r = 0; r < RR; ++r) {
@@ -208,12 +227,12 @@ k_dense_gemv32(const float2* __restrict__ A, const float2* __restrict__ x, float
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int r = 0; r < RR; ++r) acc[r] += cmul(aj[u], x[(size_t)r * nd + j + 32 * u]);
+      for (int r = 0; r < RR; ++r) cmac(acc[r], aj[u], x[(size_t)r * nd + j + 32 * u]);
   }
   for (; j < nd; j += 32) {
     const float2 aj = a[j];
 #pragma unroll
-    for (int r = 0; r < RR; ++r) acc[r] += cmul(aj, x[(size_t)r * nd + j]);
+    for (int r = 0; r < RR; ++r) cmac(acc[r], aj, x[(size_t)r * nd + j]);
   }
 #pragma unroll
   for (int r = 0; r < RR; ++r) {
@@ -243,15 +262,15 @@ template <typename T, typename BT>
 cudaError_t launch_coarse_colour(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* B,
                                  const float* Bs, const typename cplx<T>::type* Dinv, const Offsets& off,
                                  int Nt, int Nx, int colour, int R, cudaStream_t st) {
-  const long threads = (long)(Nt * Nx / 16) * 32;
-  const int bs = 256;
+  const long threads = (long)(Nt * Nx / 16) * GsLanes<T>::value;
+  const int bs = sizeof(T) == 8 ? 64 : 256;      // FP64: spread the colour over many SMs
   dim3 grid((unsigned)((threads + bs - 1) / bs), R);
   k_coarse_colour<T, BT><<<grid, bs, 0, st>>>(e, r, B, Bs, Dinv, off, Nt, Nx, colour);
   return cudaGetLastError();
 }
 
 int cluster_sweep_threads(int n) {
-  // one warp per site of a colour, at most 16 sites per warp and colour
+  // FP32 sweep: 32 lanes per site, at most 16 sites per warp and colour
   const long per_colour = n / 16;
   long warps = (per_colour + CLUSTER_BLOCKS - 1) / CLUSTER_BLOCKS;
   if (warps > 32) {

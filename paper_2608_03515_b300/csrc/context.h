@@ -33,12 +33,42 @@ struct ProfCat {
   long long launches = 0;
   double ms = 0.0;
   double bytes = 0.0;
+  double flops = 0.0;
 };
 
 struct ProfRec {
   int cat;
   cudaEvent_t a, b;
   double bytes;
+  double flops;
+};
+
+// per right-hand side state of the outer FGMRES (host side)
+struct SlotState {
+  double bnorm = 0.0, relres = 0.0;
+  int iters = 0;
+  int status = AMAMG_OK;
+  int active = 0;   // slot holds a right-hand side
+  int fresh = 0;    // ||b|| not yet measured
+  int done = 1;     // converged, out of iterations, or failed
+};
+
+// Arnoldi scratch of one restart cycle (host side), R right-hand sides x m steps
+struct OuterState {
+  int R = 0, m = 0;
+  std::vector<std::vector<double2>> H, g, sn;
+  std::vector<std::vector<double>> cs;
+  std::vector<int> k, building;
+  void resize(int R_, int m_) {
+    if (R_ == R && m_ == m) return;
+    R = R_; m = m_;
+    H.assign(R, std::vector<double2>((size_t)(m + 1) * m));
+    g.assign(R, std::vector<double2>(m + 1));
+    sn.assign(R, std::vector<double2>(m));
+    cs.assign(R, std::vector<double>(m));
+    k.assign(R, 0);
+    building.assign(R, 0);
+  }
 };
 
 struct amamg_ctx {
@@ -67,6 +97,15 @@ struct amamg_ctx {
   size_t partial_elems = 0;
   double2* d_h = nullptr;    // [R][3 (m+2)] device: h1 | h2 | norms
   double* d_inv = nullptr;   // [R]
+  int* d_flag = nullptr;     // [R] second Gram-Schmidt pass needed (DGKS)
+  double* d_diag64 = nullptr;  // [R] m0_r + 2 of each right-hand side
+  double* d_inv64 = nullptr;   // [R] 1 / (m0_r + 2)
+  float* d_inv32 = nullptr;    // [R] its FP32 rounding
+  // the arrays above while a solve or batch cycle runs (nullptr: the handle's m0)
+  const double* cur_diag64 = nullptr;
+  const double* cur_inv64 = nullptr;
+  const float* cur_inv32 = nullptr;
+  OuterState outer;
   double2* d_y = nullptr;    // [R][m]
   double2* h_h = nullptr;    // pinned host mirror of d_h
   double2* h_y = nullptr;    // pinned host mirror of d_y
@@ -88,4 +127,14 @@ struct amamg_ctx {
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   double setup_s = 0.0;
+};
+
+// a batch of right-hand-side slots on one hierarchy (continuous batching)
+struct amamg_batch {
+  amamg_ctx* h = nullptr;
+  int S = 0;
+  double2* B = nullptr;   // [S][len] right-hand sides
+  double2* X = nullptr;   // [S][len] iterates
+  std::vector<SlotState> sl;
+  std::vector<double> mass;
 };

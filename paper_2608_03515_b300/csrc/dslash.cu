@@ -54,8 +54,9 @@ __device__ __forceinline__ void hop_sum(const Cin* __restrict__ p0, const Cin* _
 template <typename Cin, typename Cout, typename T>
 __global__ void __launch_bounds__(256)
 k_dslash(const Cin* __restrict__ in, Cout* __restrict__ out, const Cout* __restrict__ b,
-         const typename cplx<T>::type* __restrict__ U, T diag, int Nt, int Nx) {
+         const typename cplx<T>::type* __restrict__ U, T diag_s, const T* __restrict__ diag_r, int Nt, int Nx) {
   using C = typename cplx<T>::type;
+  const T diag = diag_r ? diag_r[blockIdx.y] : diag_s;   // m0 + 2, per right-hand side when given
   const int n = Nt * Nx;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
@@ -83,8 +84,10 @@ k_dslash(const Cin* __restrict__ in, Cout* __restrict__ out, const Cout* __restr
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_rb_half(typename cplx<T>::type* __restrict__ e, const typename cplx<T>::type* __restrict__ r,
-          const typename cplx<T>::type* __restrict__ U, T inv_diag, int Nt, int Nx, int colour) {
+          const typename cplx<T>::type* __restrict__ U, T inv_diag_s, const T* __restrict__ inv_diag_r, int Nt,
+          int Nx, int colour) {
   using C = typename cplx<T>::type;
+  const T inv_diag = inv_diag_r ? inv_diag_r[blockIdx.y] : inv_diag_s;
   const int n = Nt * Nx;
   const int hx = Nx >> 1;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -105,30 +108,33 @@ k_rb_half(typename cplx<T>::type* __restrict__ e, const typename cplx<T>::type* 
 
 template <typename Cin, typename Cout, typename T>
 cudaError_t launch_dslash(const Cin* in, Cout* out, const Cout* b, const typename cplx<T>::type* U,
-                          T diag, int Nt, int Nx, int R, cudaStream_t st) {
+                          T diag, int Nt, int Nx, int R, cudaStream_t st, const T* diag_r) {
   const int n = Nt * Nx;
   dim3 grid((n + 255) / 256, R);
-  k_dslash<Cin, Cout, T><<<grid, 256, 0, st>>>(in, out, b, U, diag, Nt, Nx);
+  k_dslash<Cin, Cout, T><<<grid, 256, 0, st>>>(in, out, b, U, diag, diag_r, Nt, Nx);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_rb_half(typename cplx<T>::type* e, const typename cplx<T>::type* r,
                            const typename cplx<T>::type* U, T inv_diag, int Nt, int Nx, int colour,
-                           int R, cudaStream_t st) {
+                           int R, cudaStream_t st, const T* inv_diag_r) {
   const int half = Nt * Nx / 2;
   dim3 grid((half + 255) / 256, R);
-  k_rb_half<T><<<grid, 256, 0, st>>>(e, r, U, inv_diag, Nt, Nx, colour);
+  k_rb_half<T><<<grid, 256, 0, st>>>(e, r, U, inv_diag, inv_diag_r, Nt, Nx, colour);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_dslash<double2, double2, double>(const double2*, double2*, const double2*,
-                                                             const double2*, double, int, int, int, cudaStream_t);
+                                                             const double2*, double, int, int, int, cudaStream_t,
+                                                             const double*);
 template cudaError_t launch_dslash<float2, float2, float>(const float2*, float2*, const float2*,
-                                                          const float2*, float, int, int, int, cudaStream_t);
+                                                          const float2*, float, int, int, int, cudaStream_t,
+                                                          const float*);
 template cudaError_t launch_dslash<float2, double2, double>(const float2*, double2*, const double2*,
-                                                            const double2*, double, int, int, int, cudaStream_t);
+                                                            const double2*, double, int, int, int, cudaStream_t,
+                                                            const double*);
 template cudaError_t launch_rb_half<double>(double2*, const double2*, const double2*, double, int, int, int,
-                                            int, cudaStream_t);
+                                            int, cudaStream_t, const double*);
 template cudaError_t launch_rb_half<float>(float2*, const float2*, const float2*, float, int, int, int, int,
-                                           cudaStream_t);
+                                           cudaStream_t, const float*);

@@ -16,12 +16,15 @@ struct StencilOp {         // Galerkin level, [K][4][n] blocks
 };
 
 // dslash.cu
+// diag = m0 + 2 (inv_diag = its inverse) for every right-hand side, or per
+// right-hand side from a device array when diag_r / inv_diag_r is given
 template <typename Cin, typename Cout, typename T>
 cudaError_t launch_dslash(const Cin* in, Cout* out, const Cout* b, const typename cplx<T>::type* U, T diag, int Nt,
-                          int Nx, int R, cudaStream_t st);
+                          int Nx, int R, cudaStream_t st, const T* diag_r = nullptr);
 template <typename T>
 cudaError_t launch_rb_half(typename cplx<T>::type* e, const typename cplx<T>::type* r, const typename cplx<T>::type* U,
-                           T inv_diag, int Nt, int Nx, int colour, int R, cudaStream_t st);
+                           T inv_diag, int Nt, int Nx, int colour, int R, cudaStream_t st,
+                           const T* inv_diag_r = nullptr);
 
 // transfer.cu
 template <typename T, typename PT>
@@ -44,6 +47,12 @@ cudaError_t launch_coarse_colour(typename cplx<T>::type* e, const typename cplx<
 // usable while n / 16 <= 8 * 1024 sites per colour
 constexpr int CLUSTER_BLOCKS = 8;
 int cluster_sweep_threads(int n);
+// The clustered sweep is used in FP32 only: in FP64 the eight SMs of a cluster
+// are FP64-pipe bound, so FP64 colours are launched one by one over all SMs.
+template <typename T>
+inline bool use_cluster_sweeps(int n) {
+  return sizeof(T) == 4 && cluster_sweep_threads(n) <= 1024;
+}
 template <typename T, typename BT>
 cudaError_t launch_coarse_sweeps_cluster(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* B,
                                          const float* Bs, const typename cplx<T>::type* Dinv, const Offsets& off,
@@ -54,13 +63,15 @@ cudaError_t launch_dense_gemv32(const float2* A, const float2* x, float2* y, int
 
 // blas.cu
 int dot_blocks(long len);
+// dots of w with V_0..V_{J-1} (and with itself when with_self); blocks of a
+// right-hand side whose gate flag is 0 do nothing
 cudaError_t launch_dots(const double2* V, size_t vi, size_t vr, const double2* w, size_t wr, long len, int J, int R,
-                        double2* partial, cudaStream_t st);
+                        double2* partial, cudaStream_t st, bool with_self = false, const int* gate = nullptr);
 cudaError_t launch_reduce(const double2* partial, int nb, int J, int R, double2* out, int ldo, int off, int mode,
-                          double* inv, cudaStream_t st);
+                          double* inv, cudaStream_t st, int* flag = nullptr, int ref_off = 0, double eta2 = 0.5);
 template <typename Cx>
 cudaError_t launch_multi_axpy(double2* y, size_t yr, const Cx* X, size_t xi, size_t xr, const double2* coef, int ldc,
-                              int J, double sign, long len, int R, cudaStream_t st);
+                              int J, double sign, long len, int R, cudaStream_t st, const int* gate = nullptr);
 template <typename Cd>
 cudaError_t launch_scale_copy(Cd* dst, size_t dr, const double2* src, size_t sr, const double* scale, long len, int R,
                               cudaStream_t st);

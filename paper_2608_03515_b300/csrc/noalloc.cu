@@ -97,7 +97,7 @@ cudaError_t vcycle_level(amamg_ctx* h, int l, const typename cplx<T>::type* r, t
       }
     return cudaSuccess;
   }
-  if (sweeps > 0 && cluster_sweep_threads(L.n) <= 1024) {
+  if (sweeps > 0 && use_cluster_sweeps<T>(L.n)) {
     if constexpr (f64)
       err = launch_coarse_sweeps_cluster<double, double2>(e, r, L.B64, nullptr, L.Dinv64, L.off, L.Nt, L.Nx, sweeps, R, st);
     else

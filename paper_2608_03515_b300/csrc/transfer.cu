@@ -54,8 +54,8 @@ k_prolong(const typename cplx<T>::type* __restrict__ ec, typename cplx<T>::type*
   const size_t base = (size_t)tile * 8 * nrows + lr;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    acc += cmul(p_load<T, PT>(P, Pscale, base + (size_t)(2 * c) * nrows, tile), e0[vtx[c]]);
-    acc += cmul(p_load<T, PT>(P, Pscale, base + (size_t)(2 * c + 1) * nrows, tile), e0[nc + vtx[c]]);
+    cmac(acc, p_load<T, PT>(P, Pscale, base + (size_t)(2 * c) * nrows, tile), e0[vtx[c]]);
+    cmac(acc, p_load<T, PT>(P, Pscale, base + (size_t)(2 * c + 1) * nrows, tile), e0[nc + vtx[c]]);
   }
   f0[(size_t)alpha * nf + (p * a + i) * Nxf + q * a + j] = acc;
 }
@@ -89,8 +89,8 @@ k_restrict(const typename cplx<T>::type* __restrict__ ef, typename cplx<T>::type
       const int l = (lr >> 1) + 1, alpha = lr & 1;
       const int i = l / a, j = l - (l / a) * a;
       const C f = f0[(size_t)alpha * nf + (pT * a + i) * Nxf + qT * a + j];
-      acc0 += cmulc(p_load<T, PT>(P, Pscale, base + lr, tile), f);
-      acc1 += cmulc(p_load<T, PT>(P, Pscale, base + nrows + lr, tile), f);
+      cmacc(acc0, p_load<T, PT>(P, Pscale, base + lr, tile), f);
+      cmacc(acc1, p_load<T, PT>(P, Pscale, base + nrows + lr, tile), f);
     }
   }
 #pragma unroll
