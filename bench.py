@@ -203,6 +203,50 @@ def run_probe(args):
                       "ms_per_rep": ev[0].elapsed_time(ev[1]) / max(args.reps, 1)}))
 
 
+# ----------------------------------------------------------------------------- serving stream
+
+SERVING_SIZES = (64, 128, 256, 512, 1024)
+
+
+def serving_fields_available():
+    """(L, k) pairs whose critical mass is in the table (beta_k = 2 + 10 k / 7, seed 10 + k)."""
+    table = json.load(open(os.path.join(ROOT, "tests", "golden", "mcrit.json")))
+    out = {}
+    for L in SERVING_SIZES:
+        for k in range(8):
+            beta = round(2.0 + 10.0 * k / 7.0, 12)
+            key = f"L{L}_b{beta:g}_s{10 + k}"
+            if key in table:
+                out[(L, k)] = (beta, table[key]["m_crit"])
+    return out
+
+
+def run_serving(n_requests, rate, dev, mem_budget):
+    import torch
+    from paper_2608_03515_b300 import fixtures as fx
+    from paper_2608_03515_b300 import serving
+    avail = serving_fields_available()
+    sizes = sorted({L for (L, _) in avail})
+    fields_k = sorted({k for (_, k) in avail})
+    fields, mcrit = {}, {}
+    for (L, k), (beta, mc) in avail.items():
+        U = torch.from_numpy(fx.links_from_angles(fx.metropolis_u1(L, L, beta, SWEEPS, 10 + k))).to(dev)
+        fields[(L, k)] = (U, mc + 0.005)            # hierarchy at the lowest serving mass
+        mcrit[(L, k)] = mc
+    if rate <= 0:
+        # calibration: a saturated burst (all requests at t = 0) measures the service rate
+        calib = serving.poisson_requests(min(40, n_requests), 1e9, sizes, fields_k, mcrit, seed=99)
+        srv = serving.Server(fields, mem_budget)
+        c = serving.serve(srv, calib)
+        rate = 0.8 * c["requests_per_s"]
+    srv = serving.Server(fields, mem_budget)
+    reqs = serving.poisson_requests(n_requests, rate, sizes, fields_k, mcrit, seed=100)
+    out = serving.serve(srv, reqs)
+    out.update({"rate_req_per_s": rate, "sizes": sizes, "fields": len(fields),
+                "setup_s_total": sum(g.setup_s for g in srv.groups.values())})
+    return out
+
+
 # ----------------------------------------------------------------------------- our arm
 
 def main():
@@ -218,6 +262,10 @@ def main():
     ap.add_argument("--rhs", type=int, default=1)
     ap.add_argument("--prec", default="f64", choices=["f64", "f32"])
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--serving", type=int, default=0,
+                    help="also run a serving stream of this many requests (continuous batching, mixed precision)")
+    ap.add_argument("--serving-rate", type=float, default=0.0,
+                    help="Poisson arrival rate in requests/s (0: 0.8 x the calibrated saturated rate)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -425,6 +473,11 @@ def main():
         del xin, yout
     del hd
 
+    serving_out = None
+    if args.serving > 0:
+        free, total = torch.cuda.mem_get_info()
+        serving_out = run_serving(args.serving, args.serving_rate, dev, int(0.7 * free))
+
     out = None
     if rank == 0:
         cpu = None
@@ -464,6 +517,8 @@ def main():
             "d_apply": d_apply,
             "wall_s_timed_region": round(wall_s, 3),
         }
+        if serving_out is not None:
+            out["serving"] = serving_out
         print(json.dumps(out))
     if world > 1:
         dist.barrier()

@@ -3,6 +3,7 @@
 // the apply/export entry points declared in include/amamg.h.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <set>
 #include <utility>
@@ -261,6 +262,13 @@ int smooth_impl(amamg_ctx* h, int l, typename cplx<T>::type* e, const typename c
   const double blk = f64 ? 16.0 * 4 : (4.0 * 4 + 4.0);
   const double bytes = (double)L.n / 16 * ((L.off.K - 1) * blk + 4 * cb + R * 2 * 3 * cb);
   const double flops = (double)L.n / 16 * R * ((L.off.K - 1) * 32.0 + 36.0);   // one colour
+  if constexpr (!f64) {
+    if (sweeps > 0 && use_smem_sweeps<T>(L.n))
+      return launch(h, "coarse_smooth_f32", bytes * 16 * sweeps, st, [&] {
+        return launch_coarse_sweeps_smem<float, __half2>(e, r, L.B16, L.Bs, L.Dinv32, L.off, L.Nt, L.Nx, sweeps, R,
+                                                         st);
+      }, flops * 16 * sweeps);
+  }
   if (sweeps > 0 && use_cluster_sweeps<T>(L.n)) {
     // every colour of every sweep in one clustered launch
     if constexpr (f64)
@@ -900,6 +908,9 @@ int amamg_setup(const amamg_params* p, const void* U, int Nt, int Nx, double m0,
   if (!U || !std::isfinite(m0)) return AMAMG_ERR_INVALID_ARG;
   amamg_ctx* h = new amamg_ctx();
   h->prm = *p;
+  // AMAMG_GRAPHS=0 runs the Arnoldi steps as plain launches instead of CUDA
+  // graphs (same kernels; for profilers that handle graph nodes slowly)
+  if (const char* g = std::getenv("AMAMG_GRAPHS")) h->use_graphs = std::strcmp(g, "0") != 0;
   h->Nt = Nt; h->Nx = Nx; h->m0 = m0;
   cudaStream_t st = S(stream);
   cudaEvent_t e0 = nullptr, e1 = nullptr;

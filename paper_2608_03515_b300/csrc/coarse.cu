@@ -64,9 +64,12 @@ k_coarse_apply(const typename cplx<T>::type* __restrict__ in, typename cplx<T>::
 // k = 1 + g, 1 + g + LPS, ...; the group sums its lanes (xor-shuffle tree, fixed
 // order) and its lane 0 writes
 // e_v = A_vv^{-1} (r_v - sum_{k >= 1} A_{v, v+off_k} e_{v+off_k}).
-// Neighbour values are read through L2 (ld.global.cg) so that the kernel is also
-// correct when other thread blocks of a cluster updated them.
-template <typename T, typename BT, int LPS>
+// ESMEM: e0 points to shared memory (one block owns the whole level); otherwise
+// e0 is global and neighbour values are read through L2 (ld.global.cg) so that
+// the kernel is also correct when other thread blocks of a cluster updated them.
+// The loop over a lane's offsets is unrolled so that all its loads are in flight
+// together; r_v and A_vv^{-1} are loaded before the reduction.
+template <typename T, typename BT, int LPS, bool ESMEM>
 __device__ __forceinline__ void gs_site(typename cplx<T>::type* __restrict__ e0,
                                         const typename cplx<T>::type* __restrict__ r0,
                                         const BT* __restrict__ B, const float* __restrict__ Bs,
@@ -77,16 +80,28 @@ __device__ __forceinline__ void gs_site(typename cplx<T>::type* __restrict__ e0,
   using C = typename cplx<T>::type;
   const int n = Nt * Nx;
   const int v = t * Nx + x;
+  C rv0 = czero<C>(), rv1 = czero<C>(), d00 = czero<C>(), d01 = czero<C>(), d10 = czero<C>(), d11 = czero<C>();
+  if (valid && g == 0) {
+    rv0 = r0[v]; rv1 = r0[n + v];
+    d00 = Dinv[v]; d01 = Dinv[n + v]; d10 = Dinv[2 * n + v]; d11 = Dinv[3 * n + v];
+  }
   C s0 = czero<C>(), s1 = czero<C>();
-  for (int k = 1 + g; valid && k < off.K; k += LPS) {
-    int tw = t + off.dt[k]; tw -= (tw >= Nt) ? Nt : 0;
-    int xw = x + off.dx[k]; xw -= (xw >= Nx) ? Nx : 0;
-    const int w = tw * Nx + xw;
-    const C x0 = __ldcg(e0 + w), x1 = __ldcg(e0 + n + w);
-    cmac(s0, b_load<T, BT>(B, Bs, k, 0, n, v), x0);
-    cmac(s0, b_load<T, BT>(B, Bs, k, 1, n, v), x1);
-    cmac(s1, b_load<T, BT>(B, Bs, k, 2, n, v), x0);
-    cmac(s1, b_load<T, BT>(B, Bs, k, 3, n, v), x1);
+  constexpr int IT = (AMAMG_MAX_OFFSETS + LPS - 1) / LPS;
+#pragma unroll
+  for (int i = 0; i < IT; ++i) {
+    const int k = 1 + g + i * LPS;
+    if (valid && k < off.K) {
+      int tw = t + off.dt[k]; tw -= (tw >= Nt) ? Nt : 0;
+      int xw = x + off.dx[k]; xw -= (xw >= Nx) ? Nx : 0;
+      const int w = tw * Nx + xw;
+      C x0, x1;
+      if constexpr (ESMEM) { x0 = e0[w]; x1 = e0[n + w]; }
+      else { x0 = __ldcg(e0 + w); x1 = __ldcg(e0 + n + w); }
+      cmac(s0, b_load<T, BT>(B, Bs, k, 0, n, v), x0);
+      cmac(s0, b_load<T, BT>(B, Bs, k, 1, n, v), x1);
+      cmac(s1, b_load<T, BT>(B, Bs, k, 2, n, v), x0);
+      cmac(s1, b_load<T, BT>(B, Bs, k, 3, n, v), x1);
+    }
   }
 #pragma unroll
   for (int o = LPS / 2; o > 0; o >>= 1) {
@@ -96,10 +111,10 @@ __device__ __forceinline__ void gs_site(typename cplx<T>::type* __restrict__ e0,
     s1.y += __shfl_xor_sync(0xffffffffu, s1.y, o);
   }
   if (valid && g == 0) {
-    const C a0 = r0[v] - s0, a1 = r0[n + v] - s1;
-    const C d00 = Dinv[v], d01 = Dinv[n + v], d10 = Dinv[2 * n + v], d11 = Dinv[3 * n + v];
-    __stcg(e0 + v, cmul(d00, a0) + cmul(d01, a1));
-    __stcg(e0 + n + v, cmul(d10, a0) + cmul(d11, a1));
+    const C a0 = rv0 - s0, a1 = rv1 - s1;
+    const C y0 = cmul(d00, a0) + cmul(d01, a1), y1 = cmul(d10, a0) + cmul(d11, a1);
+    if constexpr (ESMEM) { e0[v] = y0; e0[n + v] = y1; }
+    else { __stcg(e0 + v, y0); __stcg(e0 + n + v, y1); }
   }
 }
 
@@ -127,7 +142,7 @@ k_coarse_colour(typename cplx<T>::type* __restrict__ e, const typename cplx<T>::
   const int t = 4 * ti + (colour >> 2);
   const int x = valid ? 4 * (idx - ti * qx) + (colour & 3) : 0;
   const size_t roff = (size_t)blockIdx.y * 2 * n;
-  gs_site<T, BT, LPS>(e + roff, r + roff, B, Bs, Dinv, off, Nt, Nx, t, x, g, valid);
+  gs_site<T, BT, LPS, false>(e + roff, r + roff, B, Bs, Dinv, off, Nt, Nx, t, x, g, valid);
 }
 
 // All colours of `sweeps` sweeps in one launch: one thread block cluster per
@@ -159,11 +174,49 @@ k_coarse_sweeps_cluster(typename cplx<T>::type* __restrict__ e, const typename c
         const int ti = valid ? idx / qx : 0;
         const int t = 4 * ti + (colour >> 2);
         const int x = valid ? 4 * (idx - ti * qx) + (colour & 3) : 0;
-        gs_site<T, BT, LPS>(e + roff, r + roff, B, Bs, Dinv, off, Nt, Nx, t, x, g, valid);
+        gs_site<T, BT, LPS, false>(e + roff, r + roff, B, Bs, Dinv, off, Nt, Nx, t, x, g, valid);
       }
       cluster.sync();
     }
   }
+}
+
+// All colours of `sweeps` sweeps in one block per right-hand side, with the
+// level's e held in shared memory (levels of at most SMEM_SWEEP_MAX_SITES sites):
+// a colour costs one round of block loads and a __syncthreads.  4 lanes per site.
+template <typename T, typename BT>
+__global__ void __launch_bounds__(1024)
+k_coarse_sweeps_smem(typename cplx<T>::type* __restrict__ e, const typename cplx<T>::type* __restrict__ r,
+                     const BT* __restrict__ B, const float* __restrict__ Bs,
+                     const typename cplx<T>::type* __restrict__ Dinv, Offsets off, int Nt, int Nx, int sweeps) {
+  using C = typename cplx<T>::type;
+  constexpr int LPS = 4;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* es = reinterpret_cast<C*>(smem_raw);
+  const int n = Nt * Nx;
+  const int qx = Nx >> 2;
+  const int per_colour = n >> 4;
+  const size_t roff = (size_t)blockIdx.x * 2 * n;
+  C* e0 = e + roff;
+  const C* r0 = r + roff;
+  for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) es[i] = e0[i];
+  __syncthreads();
+  const int g = threadIdx.x & (LPS - 1);
+  const int groups = blockDim.x / LPS;
+  for (int sw = 0; sw < sweeps; ++sw) {
+    for (int colour = 0; colour < 16; ++colour) {
+      for (int base = 0; base < per_colour; base += groups) {
+        const int idx = base + threadIdx.x / LPS;
+        const bool valid = idx < per_colour;
+        const int ti = valid ? idx / qx : 0;
+        const int t = 4 * ti + (colour >> 2);
+        const int x = valid ? 4 * (idx - ti * qx) + (colour & 3) : 0;
+        gs_site<T, BT, LPS, true>(es, r0, B, Bs, Dinv, off, Nt, Nx, t, x, g, valid);
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) e0[i] = es[i];
 }
 
 // y_r = Ainv x_r for the coarsest level: dense FP64 complex matrix, row-major,
@@ -263,7 +316,7 @@ cudaError_t launch_coarse_colour(typename cplx<T>::type* e, const typename cplx<
                                  const float* Bs, const typename cplx<T>::type* Dinv, const Offsets& off,
                                  int Nt, int Nx, int colour, int R, cudaStream_t st) {
   const long threads = (long)(Nt * Nx / 16) * GsLanes<T>::value;
-  const int bs = sizeof(T) == 8 ? 64 : 256;      // FP64: spread the colour over many SMs
+  const int bs = sizeof(T) == 8 ? 32 : 256;      // FP64: spread the colour over many SMs
   dim3 grid((unsigned)((threads + bs - 1) / bs), R);
   k_coarse_colour<T, BT><<<grid, bs, 0, st>>>(e, r, B, Bs, Dinv, off, Nt, Nx, colour);
   return cudaGetLastError();
@@ -299,6 +352,23 @@ cudaError_t launch_coarse_sweeps_cluster(typename cplx<T>::type* e, const typena
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_coarse_sweeps_cluster<T, BT>, e, r, B, Bs, Dinv, off, Nt, Nx, sweeps);
+}
+
+template <typename T, typename BT>
+cudaError_t launch_coarse_sweeps_smem(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* B,
+                                      const float* Bs, const typename cplx<T>::type* Dinv, const Offsets& off,
+                                      int Nt, int Nx, int sweeps, int R, cudaStream_t st) {
+  const int n = Nt * Nx;
+  const size_t smem = (size_t)2 * n * sizeof(typename cplx<T>::type);
+  if (n > SMEM_SWEEP_MAX_SITES) return cudaErrorInvalidValue;
+  cudaError_t err = cudaFuncSetAttribute(k_coarse_sweeps_smem<T, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+  if (err != cudaSuccess) return err;
+  const int per_colour = n / 16;
+  int threads = ((per_colour * 4 + 31) / 32) * 32;
+  threads = threads < 32 ? 32 : (threads > 1024 ? 1024 : threads);
+  k_coarse_sweeps_smem<T, BT><<<R, threads, smem, st>>>(e, r, B, Bs, Dinv, off, Nt, Nx, sweeps);
+  return cudaGetLastError();
 }
 
 template <typename Cv>
@@ -350,5 +420,8 @@ template cudaError_t launch_coarse_sweeps_cluster<double, double2>(double2*, con
 template cudaError_t launch_coarse_sweeps_cluster<float, __half2>(float2*, const float2*, const __half2*, const float*,
                                                                   const float2*, const Offsets&, int, int, int, int,
                                                                   cudaStream_t);
+template cudaError_t launch_coarse_sweeps_smem<float, __half2>(float2*, const float2*, const __half2*, const float*,
+                                                               const float2*, const Offsets&, int, int, int, int,
+                                                               cudaStream_t);
 template cudaError_t launch_dense_gemv<double2>(const double2*, const double2*, double2*, int, int, cudaStream_t);
 template cudaError_t launch_dense_gemv<float2>(const double2*, const float2*, float2*, int, int, cudaStream_t);

@@ -47,12 +47,23 @@ cudaError_t launch_coarse_colour(typename cplx<T>::type* e, const typename cplx<
 // usable while n / 16 <= 8 * 1024 sites per colour
 constexpr int CLUSTER_BLOCKS = 8;
 int cluster_sweep_threads(int n);
-// The clustered sweep is used in FP32 only: in FP64 the eight SMs of a cluster
-// are FP64-pipe bound, so FP64 colours are launched one by one over all SMs.
+// FP32 levels of at most SMEM_SWEEP_MAX_SITES sites run every colour in one
+// block with e in shared memory; larger FP32 levels use the clustered sweep.
+// In FP64 the few SMs of one block or cluster are FP64-pipe bound, so FP64
+// colours are launched one by one over all SMs.
+constexpr int SMEM_SWEEP_MAX_SITES = 12288;
+template <typename T>
+inline bool use_smem_sweeps(int n) {
+  return sizeof(T) == 4 && n <= SMEM_SWEEP_MAX_SITES;
+}
 template <typename T>
 inline bool use_cluster_sweeps(int n) {
-  return sizeof(T) == 4 && cluster_sweep_threads(n) <= 1024;
+  return sizeof(T) == 4 && !use_smem_sweeps<T>(n) && cluster_sweep_threads(n) <= 1024;
 }
+template <typename T, typename BT>
+cudaError_t launch_coarse_sweeps_smem(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* B,
+                                      const float* Bs, const typename cplx<T>::type* Dinv, const Offsets& off,
+                                      int Nt, int Nx, int sweeps, int R, cudaStream_t st);
 template <typename T, typename BT>
 cudaError_t launch_coarse_sweeps_cluster(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* B,
                                          const float* Bs, const typename cplx<T>::type* Dinv, const Offsets& off,

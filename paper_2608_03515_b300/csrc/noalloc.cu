@@ -97,6 +97,13 @@ cudaError_t vcycle_level(amamg_ctx* h, int l, const typename cplx<T>::type* r, t
       }
     return cudaSuccess;
   }
+  if constexpr (!f64) {
+    if (sweeps > 0 && use_smem_sweeps<T>(L.n)) {
+      err = launch_coarse_sweeps_smem<float, __half2>(e, r, L.B16, L.Bs, L.Dinv32, L.off, L.Nt, L.Nx, sweeps, R, st);
+      h->launches++;
+      return err;
+    }
+  }
   if (sweeps > 0 && use_cluster_sweeps<T>(L.n)) {
     if constexpr (f64)
       err = launch_coarse_sweeps_cluster<double, double2>(e, r, L.B64, nullptr, L.Dinv64, L.off, L.Nt, L.Nx, sweeps, R, st);

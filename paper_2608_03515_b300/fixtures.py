@@ -117,6 +117,17 @@ def gaussian_rhs(R: int, Nt: int, Nx: int, seed: int) -> np.ndarray:
     return (z[..., 0] + 1j * z[..., 1]).astype(np.complex128)
 
 
+def gaussian_rhs_device(Nt: int, Nx: int, seed: int, device):
+    """One right-hand side [2, Nt, Nx] complex128 drawn on the device (torch's
+    Philox generator seeded with `seed`; Re, Im iid N(0, 1)) -- for request
+    streams too large to draw on the host."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    z = torch.randn(2, 2, Nt, Nx, dtype=torch.float64, device=device, generator=g)
+    return torch.complex(z[0], z[1]).contiguous()
+
+
 def field_seed_for(k: int) -> int:
     """Seed of resident field k in the serving mix (fields 0..7 use seeds 10..17)."""
     return 10 + int(k)

@@ -46,8 +46,11 @@ def main(sizes=None, serving=False):
         t0 = time.time()
         theta = fx.metropolis_u1(L, L, beta, SWEEPS, seed)
         mc = spectrum.critical_mass(fx.links_from_angles(theta))
-        table[k] = {"L": L, "beta": beta, "seed": seed, "sweeps": SWEEPS, "m_crit": mc}
+        entry = {"L": L, "beta": beta, "seed": seed, "sweeps": SWEEPS, "m_crit": mc}
         print(k, mc, f"{time.time() - t0:.1f}s", flush=True)
+        # merge with what other runs wrote meanwhile
+        table = json.load(open(OUT)) if os.path.exists(OUT) else {}
+        table[k] = entry
         with open(OUT, "w") as f:
             json.dump(table, f, indent=1, sort_keys=True)
 
