@@ -227,7 +227,6 @@ def run_serving(n_requests, rate, dev, mem_budget):
     from paper_2608_03515_b300 import serving
     avail = serving_fields_available()
     sizes = sorted({L for (L, _) in avail})
-    fields_k = sorted({k for (_, k) in avail})
     fields, mcrit = {}, {}
     for (L, k), (beta, mc) in avail.items():
         U = torch.from_numpy(fx.links_from_angles(fx.metropolis_u1(L, L, beta, SWEEPS, 10 + k))).to(dev)
@@ -235,12 +234,12 @@ def run_serving(n_requests, rate, dev, mem_budget):
         mcrit[(L, k)] = mc
     if rate <= 0:
         # calibration: a saturated burst (all requests at t = 0) measures the service rate
-        calib = serving.poisson_requests(min(40, n_requests), 1e9, sizes, fields_k, mcrit, seed=99)
+        calib = serving.poisson_requests(min(40, n_requests), 1e9, list(avail), mcrit, seed=99)
         srv = serving.Server(fields, mem_budget)
         c = serving.serve(srv, calib)
         rate = 0.8 * c["requests_per_s"]
     srv = serving.Server(fields, mem_budget)
-    reqs = serving.poisson_requests(n_requests, rate, sizes, fields_k, mcrit, seed=100)
+    reqs = serving.poisson_requests(n_requests, rate, list(avail), mcrit, seed=100)
     out = serving.serve(srv, reqs)
     out.update({"rate_req_per_s": rate, "sizes": sizes, "fields": len(fields),
                 "setup_s_total": sum(g.setup_s for g in srv.groups.values())})

@@ -12,7 +12,7 @@ vectors, relative tolerance 1e-6, which fixes m_crit far better than the mass
 offsets it is used for).  Shift-invert around a real shift is not used: on
 quenched fields the leftmost eigenvalue can carry a sizeable imaginary part
 and then is not among the eigenvalues nearest a real shift.  The tests compare
-this route with dense eigenvalues on 32^2 and 48^2 fields.
+this route with dense eigenvalues on 32^2 and 40^2 fields.
 """
 from __future__ import annotations
 

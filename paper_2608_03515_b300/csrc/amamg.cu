@@ -265,20 +265,15 @@ int smooth_impl(amamg_ctx* h, int l, typename cplx<T>::type* e, const typename c
   if constexpr (!f64) {
     if (sweeps > 0 && use_smem_sweeps<T>(L.n))
       return launch(h, "coarse_smooth_f32", bytes * 16 * sweeps, st, [&] {
-        return launch_coarse_sweeps_smem<float, __half2>(e, r, L.B16, L.Bs, L.Dinv32, L.off, L.Nt, L.Nx, sweeps, R,
+        return launch_coarse_sweeps_smem<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, sweeps, R,
                                                          st);
       }, flops * 16 * sweeps);
   }
-  if (sweeps > 0 && use_cluster_sweeps<T>(L.n)) {
-    // every colour of every sweep in one clustered launch
-    if constexpr (f64)
-      return launch(h, "coarse_smooth_f64", bytes * 16 * sweeps, st, [&] {
-        return launch_coarse_sweeps_cluster<double, double2>(e, r, L.B64, nullptr, L.Dinv64, L.off, L.Nt, L.Nx,
-                                                             sweeps, R, st);
-      }, flops * 16 * sweeps);
-    else
+  if constexpr (!f64) {
+    if (sweeps > 0 && use_cluster_sweeps<T>(L.n))
+      // every colour of every sweep in one clustered launch
       return launch(h, "coarse_smooth_f32", bytes * 16 * sweeps, st, [&] {
-        return launch_coarse_sweeps_cluster<float, __half2>(e, r, L.B16, L.Bs, L.Dinv32, L.off, L.Nt, L.Nx, sweeps,
+        return launch_coarse_sweeps_cluster<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, sweeps,
                                                             R, st);
       }, flops * 16 * sweeps);
   }
@@ -287,11 +282,11 @@ int smooth_impl(amamg_ctx* h, int l, typename cplx<T>::type* e, const typename c
       int rc;
       if constexpr (f64)
         rc = launch(h, "coarse_smooth_f64", bytes, st, [&] {
-          return launch_coarse_colour<double, double2>(e, r, L.B64, nullptr, L.Dinv64, L.off, L.Nt, L.Nx, c, R, st);
+          return launch_coarse_colour<double, double2>(e, r, L.Bc64, nullptr, L.Dc64, L.off, L.Nt, L.Nx, c, R, st);
         }, flops);
       else
         rc = launch(h, "coarse_smooth_f32", bytes, st, [&] {
-          return launch_coarse_colour<float, __half2>(e, r, L.B16, L.Bs, L.Dinv32, L.off, L.Nt, L.Nx, c, R, st);
+          return launch_coarse_colour<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, c, R, st);
         }, flops);
       CKS(rc);
     }
@@ -724,6 +719,7 @@ int check_params(const amamg_params* p, int Nt, int Nx, std::string* why) {
 void free_all(amamg_ctx* h) {
   for (auto& L : h->lv) {
     dfree(L.B64); dfree(L.B16); dfree(L.Bs); dfree(L.Dinv64); dfree(L.Dinv32);
+    dfree(L.Bc64); dfree(L.Bc16); dfree(L.Bcs); dfree(L.Dc64); dfree(L.Dc32);
     dfree(L.P64); dfree(L.P16); dfree(L.Ps);
     dfree(L.r64); dfree(L.e64); dfree(L.r32); dfree(L.e32);
   }
@@ -772,8 +768,8 @@ int do_setup(amamg_ctx* h, const void* Uin, cudaStream_t st) {
     CKS(dalloc(h, &F.P16, (size_t)F.nT * 8 * F.nrows));
     CKS(dalloc(h, &F.Ps, (size_t)F.nT));
     const Offsets& fo = (l == 0) ? fine_off : F.off;
-    if (coarse_offsets(fo, F.Nt, F.Nx, F.a, &C.off) != AMAMG_OK) {
-      h->err = "coarse operator has more than 32 block offsets";
+    if (coarse_offsets(fo, F.Nt, F.Nx, F.a, &C.off) != AMAMG_OK || C.off.K - 1 > GS_MAX_OFFDIAG) {
+      h->err = "coarse operator has more block offsets than the smoother supports (25)";
       return AMAMG_ERR_INVALID_ARG;
     }
     CKS(dalloc(h, &C.B64, (size_t)C.off.K * 4 * C.n));
@@ -797,6 +793,16 @@ int do_setup(amamg_ctx* h, const void* Uin, cudaStream_t st) {
       CKS(dalloc(h, &C.Dinv64, 4 * (size_t)C.n));
       CKS(dalloc(h, &C.Dinv32, 4 * (size_t)C.n));
       CKS(launch(h, "setup_diag_inv", 0.0, st, [&] { return launch_diag_inv(C.B64, C.n, C.Dinv64, C.Dinv32, h->d_err, st); }));
+      const size_t nb = (size_t)(C.off.K - 1) * C.n;      // 16 colours x (K-1) offsets x n/16 sites
+      CKS(dalloc(h, &C.Bc64, 4 * nb));
+      CKS(dalloc(h, &C.Bc16, 4 * nb));
+      CKS(dalloc(h, &C.Bcs, nb));
+      CKS(dalloc(h, &C.Dc64, 4 * (size_t)C.n));
+      CKS(dalloc(h, &C.Dc32, 4 * (size_t)C.n));
+      CKS(launch(h, "setup_pack", 0.0, st, [&] {
+        return launch_pack_colour_major(C.B64, C.B16, C.Bs, C.Dinv64, C.Dinv32, C.off.K, C.Nt, C.Nx, C.Bc64, C.Bc16,
+                                        C.Bcs, C.Dc64, C.Dc32, st);
+      }));
     }
   }
   // coarsest: dense matrix and its Gauss-Jordan inverse

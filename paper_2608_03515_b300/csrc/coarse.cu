@@ -59,7 +59,35 @@ k_coarse_apply(const typename cplx<T>::type* __restrict__ in, typename cplx<T>::
   o[n + v] = y1;
 }
 
-// Block Gauss-Seidel update of one coarse site v on A e = r by a group of LPS
+// Colour-major copies of a smoothed level's operator (built in setup): for
+// colour c (sites (t, x) with (t mod 4, x mod 4) = (c / 4, c % 4)), site j of the
+// colour (t = 4 (j / (Nx/4)) + c / 4, x = 4 (j % (Nx/4)) + c % 4, m = n / 16 sites)
+// and off-diagonal offset k = 1..K-1:
+//   Bc[((c (K-1) + k - 1) m + j) 4 + e]   the 2x2 block entries e = 2 alpha + beta,
+//   Sc[(c (K-1) + k - 1) m + j]           its FP32 scale (FP16 copy only),
+//   Dc[(c m + j) 4 + e]                    the inverse of the diagonal block.
+// The four entries of a block are contiguous and consecutive sites of a colour
+// are adjacent, so the lanes of a warp read whole sectors.
+template <typename T, typename BT>
+__device__ __forceinline__ void cm_block(const BT* __restrict__ Bc, const float* __restrict__ Sc, size_t blk,
+                                         typename cplx<T>::type (&b)[4]);
+template <>
+__device__ __forceinline__ void cm_block<double, double2>(const double2* __restrict__ Bc, const float*, size_t blk,
+                                                          double2 (&b)[4]) {
+#pragma unroll
+  for (int e = 0; e < 4; ++e) b[e] = Bc[blk * 4 + e];
+}
+template <>
+__device__ __forceinline__ void cm_block<float, __half2>(const __half2* __restrict__ Bc, const float* __restrict__ Sc,
+                                                         size_t blk, float2 (&b)[4]) {
+  const uint4 q = *reinterpret_cast<const uint4*>(Bc + blk * 4);      // 16 bytes: the block's 4 half2
+  const float sc = Sc[blk];
+  const __half2* h = reinterpret_cast<const __half2*>(&q);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) b[e] = h2c<float>(h[e], sc);
+}
+
+// Block Gauss-Seidel update of site j of colour c on A e = r by a group of LPS
 // lanes: lane g of the group forms A_{v, v+off_k} e_{v+off_k} for
 // k = 1 + g, 1 + g + LPS, ...; the group sums its lanes (xor-shuffle tree, fixed
 // order) and its lane 0 writes
@@ -72,21 +100,29 @@ k_coarse_apply(const typename cplx<T>::type* __restrict__ in, typename cplx<T>::
 template <typename T, typename BT, int LPS, bool ESMEM>
 __device__ __forceinline__ void gs_site(typename cplx<T>::type* __restrict__ e0,
                                         const typename cplx<T>::type* __restrict__ r0,
-                                        const BT* __restrict__ B, const float* __restrict__ Bs,
-                                        const typename cplx<T>::type* __restrict__ Dinv, const Offsets& off,
-                                        int Nt, int Nx, int t, int x, int g, bool valid) {
+                                        const BT* __restrict__ Bc, const float* __restrict__ Sc,
+                                        const typename cplx<T>::type* __restrict__ Dc, const Offsets& off,
+                                        int Nt, int Nx, int colour, int j, int g, bool valid) {
   // every lane of the warp calls this (the shuffles need all 32); lanes of
   // groups without a site pass valid = false and only take part in the shuffles
   using C = typename cplx<T>::type;
   const int n = Nt * Nx;
+  const int m = n >> 4;
+  const int qx = Nx >> 2;
+  const int ti = valid ? j / qx : 0;
+  const int t = 4 * ti + (colour >> 2);
+  const int x = valid ? 4 * (j - ti * qx) + (colour & 3) : 0;
   const int v = t * Nx + x;
-  C rv0 = czero<C>(), rv1 = czero<C>(), d00 = czero<C>(), d01 = czero<C>(), d10 = czero<C>(), d11 = czero<C>();
+  const int K1 = off.K - 1;
+  C rv0 = czero<C>(), rv1 = czero<C>(), d[4] = {czero<C>(), czero<C>(), czero<C>(), czero<C>()};
   if (valid && g == 0) {
     rv0 = r0[v]; rv1 = r0[n + v];
-    d00 = Dinv[v]; d01 = Dinv[n + v]; d10 = Dinv[2 * n + v]; d11 = Dinv[3 * n + v];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) d[e] = Dc[((size_t)colour * m + j) * 4 + e];
   }
-  C s0 = czero<C>(), s1 = czero<C>();
-  constexpr int IT = (AMAMG_MAX_OFFSETS + LPS - 1) / LPS;
+  // all of this lane's loads first (they are independent), then the arithmetic
+  constexpr int IT = (GS_MAX_OFFDIAG + LPS - 1) / LPS;
+  C xv[IT][2], bb[IT][4];
 #pragma unroll
   for (int i = 0; i < IT; ++i) {
     const int k = 1 + g + i * LPS;
@@ -94,14 +130,21 @@ __device__ __forceinline__ void gs_site(typename cplx<T>::type* __restrict__ e0,
       int tw = t + off.dt[k]; tw -= (tw >= Nt) ? Nt : 0;
       int xw = x + off.dx[k]; xw -= (xw >= Nx) ? Nx : 0;
       const int w = tw * Nx + xw;
-      C x0, x1;
-      if constexpr (ESMEM) { x0 = e0[w]; x1 = e0[n + w]; }
-      else { x0 = __ldcg(e0 + w); x1 = __ldcg(e0 + n + w); }
-      cmac(s0, b_load<T, BT>(B, Bs, k, 0, n, v), x0);
-      cmac(s0, b_load<T, BT>(B, Bs, k, 1, n, v), x1);
-      cmac(s1, b_load<T, BT>(B, Bs, k, 2, n, v), x0);
-      cmac(s1, b_load<T, BT>(B, Bs, k, 3, n, v), x1);
+      if constexpr (ESMEM) { xv[i][0] = e0[w]; xv[i][1] = e0[n + w]; }
+      else { xv[i][0] = __ldcg(e0 + w); xv[i][1] = __ldcg(e0 + n + w); }
+      cm_block<T, BT>(Bc, Sc, ((size_t)colour * K1 + (k - 1)) * m + j, bb[i]);
+    } else {
+      xv[i][0] = xv[i][1] = czero<C>();
+      bb[i][0] = bb[i][1] = bb[i][2] = bb[i][3] = czero<C>();
     }
+  }
+  C s0 = czero<C>(), s1 = czero<C>();
+#pragma unroll
+  for (int i = 0; i < IT; ++i) {
+    cmac(s0, bb[i][0], xv[i][0]);
+    cmac(s0, bb[i][1], xv[i][1]);
+    cmac(s1, bb[i][2], xv[i][0]);
+    cmac(s1, bb[i][3], xv[i][1]);
   }
 #pragma unroll
   for (int o = LPS / 2; o > 0; o >>= 1) {
@@ -112,17 +155,17 @@ __device__ __forceinline__ void gs_site(typename cplx<T>::type* __restrict__ e0,
   }
   if (valid && g == 0) {
     const C a0 = rv0 - s0, a1 = rv1 - s1;
-    const C y0 = cmul(d00, a0) + cmul(d01, a1), y1 = cmul(d10, a0) + cmul(d11, a1);
+    const C y0 = cmul(d[0], a0) + cmul(d[1], a1), y1 = cmul(d[2], a0) + cmul(d[3], a1);
     if constexpr (ESMEM) { e0[v] = y0; e0[n + v] = y1; }
     else { __stcg(e0 + v, y0); __stcg(e0 + n + v, y1); }
   }
 }
 
-// Lanes per site: 4 in FP64 (B300's FP64 pipe is narrow: few lanes per site
-// and the sites of a colour spread over all SMs), 32 in FP32 (all offsets of a
+// Lanes per site: 8 in FP64 (B300's FP64 pipe is narrow: the sites of a colour
+// spread over many SMs, three offsets per lane), 32 in FP32 (all offsets of a
 // site loaded at once: the clustered sweep is latency bound).
 template <typename T> struct GsLanes { static constexpr int value = 32; };
-template <> struct GsLanes<double> { static constexpr int value = 4; };
+template <> struct GsLanes<double> { static constexpr int value = 8; };
 
 // One colour of the 16-colour sweep, sites (t, x) with (t mod 4, x mod 4) =
 // (c / 4, c % 4); LPS lanes per site.
@@ -133,16 +176,12 @@ k_coarse_colour(typename cplx<T>::type* __restrict__ e, const typename cplx<T>::
                 const typename cplx<T>::type* __restrict__ Dinv, Offsets off, int Nt, int Nx, int colour) {
   constexpr int LPS = GsLanes<T>::value;
   const int n = Nt * Nx;
-  const int qx = Nx >> 2;
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int idx = tid / LPS;
   const int g = tid & (LPS - 1);
   const bool valid = idx < (n >> 4);
-  const int ti = valid ? idx / qx : 0;
-  const int t = 4 * ti + (colour >> 2);
-  const int x = valid ? 4 * (idx - ti * qx) + (colour & 3) : 0;
   const size_t roff = (size_t)blockIdx.y * 2 * n;
-  gs_site<T, BT, LPS, false>(e + roff, r + roff, B, Bs, Dinv, off, Nt, Nx, t, x, g, valid);
+  gs_site<T, BT, LPS, false>(e + roff, r + roff, B, Bs, Dinv, off, Nt, Nx, colour, idx, g, valid);
 }
 
 // All colours of `sweeps` sweeps in one launch: one thread block cluster per
@@ -156,8 +195,7 @@ k_coarse_sweeps_cluster(typename cplx<T>::type* __restrict__ e, const typename c
   constexpr int LPS = GsLanes<T>::value;
   cg::cluster_group cluster = cg::this_cluster();
   const int n = Nt * Nx;
-  const int qx = Nx >> 2;
-  const int per_colour = n >> 4;
+    const int per_colour = n >> 4;
   const int rank = (int)cluster.block_rank();
   const int csize = (int)cluster.num_blocks();
   const int rhs = blockIdx.x / csize;
@@ -171,10 +209,7 @@ k_coarse_sweeps_cluster(typename cplx<T>::type* __restrict__ e, const typename c
       for (int base = 0; base < per_colour; base += stride) {
         const int idx = base + rank * gpb + threadIdx.x / LPS;
         const bool valid = idx < per_colour;
-        const int ti = valid ? idx / qx : 0;
-        const int t = 4 * ti + (colour >> 2);
-        const int x = valid ? 4 * (idx - ti * qx) + (colour & 3) : 0;
-        gs_site<T, BT, LPS, false>(e + roff, r + roff, B, Bs, Dinv, off, Nt, Nx, t, x, g, valid);
+        gs_site<T, BT, LPS, false>(e + roff, r + roff, B, Bs, Dinv, off, Nt, Nx, colour, idx, g, valid);
       }
       cluster.sync();
     }
@@ -183,19 +218,18 @@ k_coarse_sweeps_cluster(typename cplx<T>::type* __restrict__ e, const typename c
 
 // All colours of `sweeps` sweeps in one block per right-hand side, with the
 // level's e held in shared memory (levels of at most SMEM_SWEEP_MAX_SITES sites):
-// a colour costs one round of block loads and a __syncthreads.  4 lanes per site.
+// a colour costs one round of block loads and a __syncthreads.  8 lanes per site.
 template <typename T, typename BT>
 __global__ void __launch_bounds__(1024)
 k_coarse_sweeps_smem(typename cplx<T>::type* __restrict__ e, const typename cplx<T>::type* __restrict__ r,
                      const BT* __restrict__ B, const float* __restrict__ Bs,
                      const typename cplx<T>::type* __restrict__ Dinv, Offsets off, int Nt, int Nx, int sweeps) {
   using C = typename cplx<T>::type;
-  constexpr int LPS = 4;
+  constexpr int LPS = 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* es = reinterpret_cast<C*>(smem_raw);
   const int n = Nt * Nx;
-  const int qx = Nx >> 2;
-  const int per_colour = n >> 4;
+    const int per_colour = n >> 4;
   const size_t roff = (size_t)blockIdx.x * 2 * n;
   C* e0 = e + roff;
   const C* r0 = r + roff;
@@ -208,10 +242,7 @@ k_coarse_sweeps_smem(typename cplx<T>::type* __restrict__ e, const typename cplx
       for (int base = 0; base < per_colour; base += groups) {
         const int idx = base + threadIdx.x / LPS;
         const bool valid = idx < per_colour;
-        const int ti = valid ? idx / qx : 0;
-        const int t = 4 * ti + (colour >> 2);
-        const int x = valid ? 4 * (idx - ti * qx) + (colour & 3) : 0;
-        gs_site<T, BT, LPS, true>(es, r0, B, Bs, Dinv, off, Nt, Nx, t, x, g, valid);
+        gs_site<T, BT, LPS, true>(es, r0, B, Bs, Dinv, off, Nt, Nx, colour, idx, g, valid);
       }
       __syncthreads();
     }
@@ -365,7 +396,7 @@ cudaError_t launch_coarse_sweeps_smem(typename cplx<T>::type* e, const typename 
                                          (int)smem);
   if (err != cudaSuccess) return err;
   const int per_colour = n / 16;
-  int threads = ((per_colour * 4 + 31) / 32) * 32;
+  int threads = ((per_colour * 8 + 31) / 32) * 32;
   threads = threads < 32 ? 32 : (threads > 1024 ? 1024 : threads);
   k_coarse_sweeps_smem<T, BT><<<R, threads, smem, st>>>(e, r, B, Bs, Dinv, off, Nt, Nx, sweeps);
   return cudaGetLastError();
@@ -414,9 +445,6 @@ template cudaError_t launch_coarse_colour<double, double2>(double2*, const doubl
 template cudaError_t launch_coarse_colour<float, __half2>(float2*, const float2*, const __half2*, const float*,
                                                           const float2*, const Offsets&, int, int, int, int,
                                                           cudaStream_t);
-template cudaError_t launch_coarse_sweeps_cluster<double, double2>(double2*, const double2*, const double2*,
-                                                                   const float*, const double2*, const Offsets&, int,
-                                                                   int, int, int, cudaStream_t);
 template cudaError_t launch_coarse_sweeps_cluster<float, __half2>(float2*, const float2*, const __half2*, const float*,
                                                                   const float2*, const Offsets&, int, int, int, int,
                                                                   cudaStream_t);

@@ -17,6 +17,12 @@ struct Level {
   float* Bs = nullptr;
   double2* Dinv64 = nullptr;
   float2* Dinv32 = nullptr;
+  // colour-major copies for the Gauss-Seidel kernels (smoothed coarse levels)
+  double2* Bc64 = nullptr;
+  __half2* Bc16 = nullptr;
+  float* Bcs = nullptr;
+  double2* Dc64 = nullptr;
+  float2* Dc32 = nullptr;
   // interpolation to the next level
   double2* P64 = nullptr;
   __half2* P16 = nullptr;

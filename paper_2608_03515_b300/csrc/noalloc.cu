@@ -99,25 +99,24 @@ cudaError_t vcycle_level(amamg_ctx* h, int l, const typename cplx<T>::type* r, t
   }
   if constexpr (!f64) {
     if (sweeps > 0 && use_smem_sweeps<T>(L.n)) {
-      err = launch_coarse_sweeps_smem<float, __half2>(e, r, L.B16, L.Bs, L.Dinv32, L.off, L.Nt, L.Nx, sweeps, R, st);
+      err = launch_coarse_sweeps_smem<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, sweeps, R, st);
       h->launches++;
       return err;
     }
   }
-  if (sweeps > 0 && use_cluster_sweeps<T>(L.n)) {
-    if constexpr (f64)
-      err = launch_coarse_sweeps_cluster<double, double2>(e, r, L.B64, nullptr, L.Dinv64, L.off, L.Nt, L.Nx, sweeps, R, st);
-    else
-      err = launch_coarse_sweeps_cluster<float, __half2>(e, r, L.B16, L.Bs, L.Dinv32, L.off, L.Nt, L.Nx, sweeps, R, st);
-    h->launches++;
-    return err;
+  if constexpr (!f64) {
+    if (sweeps > 0 && use_cluster_sweeps<T>(L.n)) {
+      err = launch_coarse_sweeps_cluster<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, sweeps, R, st);
+      h->launches++;
+      return err;
+    }
   }
   for (int s = 0; s < sweeps; ++s)
     for (int c = 0; c < 16; ++c) {
       if constexpr (f64)
-        err = launch_coarse_colour<double, double2>(e, r, L.B64, nullptr, L.Dinv64, L.off, L.Nt, L.Nx, c, R, st);
+        err = launch_coarse_colour<double, double2>(e, r, L.Bc64, nullptr, L.Dc64, L.off, L.Nt, L.Nx, c, R, st);
       else
-        err = launch_coarse_colour<float, __half2>(e, r, L.B16, L.Bs, L.Dinv32, L.off, L.Nt, L.Nx, c, R, st);
+        err = launch_coarse_colour<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, c, R, st);
       if (err != cudaSuccess) return err;
       h->launches++;
     }

@@ -202,17 +202,18 @@ def serve(server: Server, requests: List[Request], time_scale: float = 1.0) -> d
     }
 
 
-def poisson_requests(n: int, rate: float, sizes, fields, mcrit, seed: int = 100, max_rhs: int = 16,
+def poisson_requests(n: int, rate: float, pairs, mcrit, seed: int = 100, max_rhs: int = 16,
                      dm=(0.005, 0.1)) -> List[Request]:
     """n requests with exponential inter-arrival times (rate per second); each draws
-    its lattice, field, mass offset m0 - m_crit ~ U[dm] and R ~ U{1..max_rhs}."""
+    its (lattice, field) pair uniformly from `pairs` (the resident hierarchies),
+    its mass offset m0 - m_crit ~ U[dm] and R ~ U{1..max_rhs}."""
     rng = np.random.Generator(np.random.PCG64(seed))
+    pairs = sorted(pairs)
     t = 0.0
     out = []
     for i in range(n):
         t += rng.exponential(1.0 / rate)
-        L = int(rng.choice(sizes))
-        k = int(rng.choice(fields))
+        L, k = pairs[int(rng.integers(0, len(pairs)))]
         m0 = mcrit[(L, k)] + rng.uniform(*dm)
         R = int(rng.integers(1, max_rhs + 1))
         out.append(Request(i, L, k, float(m0), R, t, rhs_seed=1_000_000 + 100 * i))

@@ -70,8 +70,8 @@ def test_server_stream_converges_and_reports_latency():
             mcrit[(L, k)] = -0.05          # a safe lower bound for these fields: masses sit well above it
             fields[(L, k)] = (torch.from_numpy(U).to(DEV), mcrit[(L, k)] + 0.05)
     srv = serving.Server(fields, mem_budget_bytes=8 << 30, max_slots=4)
-    reqs = serving.poisson_requests(12, rate=200.0, sizes=[32, 64], fields=[0, 1], mcrit=mcrit, seed=7,
-                                    max_rhs=3, dm=(0.05, 0.1))
+    reqs = serving.poisson_requests(12, rate=200.0, pairs=list(fields), mcrit=mcrit, seed=7, max_rhs=3,
+                                    dm=(0.05, 0.1))
     out = serving.serve(srv, reqs)
     assert out["requests"] == 12 and out["not_converged"] == 0
     assert out["max_true_relres"] <= 1e-10
