@@ -262,11 +262,18 @@ int smooth_impl(amamg_ctx* h, int l, typename cplx<T>::type* e, const typename c
   const double blk = f64 ? 16.0 * 4 : (4.0 * 4 + 4.0);
   const double bytes = (double)L.n / 16 * ((L.off.K - 1) * blk + 4 * cb + R * 2 * 3 * cb);
   const double flops = (double)L.n / 16 * R * ((L.off.K - 1) * 32.0 + 36.0);   // one colour
-  if constexpr (!f64) {
-    if (sweeps > 0 && use_smem_sweeps<T>(L.n))
+  if (sweeps > 0 && (f64 ? L.dsmem64 : L.dsmem32)) {
+    // every colour of every sweep on one 16-block cluster, level in shared memory
+    const bool bsm = dsmem_blocks_in_smem<T>(L.n, L.off.K);
+    if constexpr (f64)
+      return launch(h, "coarse_smooth_f64", bytes * 16 * sweeps, st, [&] {
+        return launch_coarse_sweeps_dsmem<double, double2>(e, r, L.Bc64, nullptr, L.Dc64, L.off, L.Nt, L.Nx, sweeps,
+                                                           R, bsm, st);
+      }, flops * 16 * sweeps);
+    else
       return launch(h, "coarse_smooth_f32", bytes * 16 * sweeps, st, [&] {
-        return launch_coarse_sweeps_smem<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, sweeps, R,
-                                                         st);
+        return launch_coarse_sweeps_dsmem<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, sweeps, R,
+                                                          bsm, st);
       }, flops * 16 * sweeps);
   }
   if constexpr (!f64) {
@@ -803,6 +810,8 @@ int do_setup(amamg_ctx* h, const void* Uin, cudaStream_t st) {
         return launch_pack_colour_major(C.B64, C.B16, C.Bs, C.Dinv64, C.Dinv32, C.off.K, C.Nt, C.Nx, C.Bc64, C.Bc16,
                                         C.Bcs, C.Dc64, C.Dc32, st);
       }));
+      C.dsmem64 = dsmem_sweeps_possible<double, double2>(C.n, C.off.K, false);
+      C.dsmem32 = dsmem_sweeps_possible<float, __half2>(C.n, C.off.K, dsmem_blocks_in_smem<float>(C.n, C.off.K));
     }
   }
   // coarsest: dense matrix and its Gauss-Jordan inverse

@@ -216,38 +216,125 @@ k_coarse_sweeps_cluster(typename cplx<T>::type* __restrict__ e, const typename c
   }
 }
 
-// All colours of `sweeps` sweeps in one block per right-hand side, with the
-// level's e held in shared memory (levels of at most SMEM_SWEEP_MAX_SITES sites):
-// a colour costs one round of block loads and a __syncthreads.  8 lanes per site.
-template <typename T, typename BT>
-__global__ void __launch_bounds__(1024)
-k_coarse_sweeps_smem(typename cplx<T>::type* __restrict__ e, const typename cplx<T>::type* __restrict__ r,
-                     const BT* __restrict__ B, const float* __restrict__ Bs,
-                     const typename cplx<T>::type* __restrict__ Dinv, Offsets off, int Nt, int Nx, int sweeps) {
+// All colours of `sweeps` sweeps in one launch on a 16-block thread-block
+// cluster per right-hand side, the level distributed over the cluster's shared
+// memory.  Block q of the cluster owns sites j in [q per, (q+1) per) of every
+// colour (per = n / 256): it keeps their e, r and diagonal inverses (and, with
+// BSMEM, their off-diagonal blocks) in its shared memory for the whole launch.
+// A colour phase reads neighbour values from the owning blocks' shared memory
+// (distributed shared memory), writes its own sites locally, and ends with a
+// cluster barrier (release/acquire), so no phase touches L2 for e.
+template <typename T, typename BT, bool BSMEM>
+__global__ void __launch_bounds__(512)
+k_coarse_sweeps_dsmem(typename cplx<T>::type* __restrict__ e, const typename cplx<T>::type* __restrict__ r,
+                      const BT* __restrict__ Bc, const float* __restrict__ Sc,
+                      const typename cplx<T>::type* __restrict__ Dc, Offsets off, int Nt, int Nx, int sweeps) {
   using C = typename cplx<T>::type;
   constexpr int LPS = 8;
+  constexpr int IT = (GS_MAX_OFFDIAG + LPS - 1) / LPS;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int q = (int)cluster.block_rank();
+  const int rhs = blockIdx.x / DSMEM_CLUSTER;
+  const int n = Nt * Nx, m = n >> 4, qx = Nx >> 2, per = m / DSMEM_CLUSTER, K1 = off.K - 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* es = reinterpret_cast<C*>(smem_raw);
-  const int n = Nt * Nx;
-    const int per_colour = n >> 4;
-  const size_t roff = (size_t)blockIdx.x * 2 * n;
+  C* es = reinterpret_cast<C*>(smem_raw);                 // [16 colours][per][2]
+  C* rs = es + 32 * per;                                  // [16][per][2]
+  C* ds = rs + 32 * per;                                  // [16][per][4]
+  BT* bs = reinterpret_cast<BT*>(ds + 64 * per);          // [16][K1][per][4]      (BSMEM)
+  float* ss = reinterpret_cast<float*>(bs + (BSMEM ? 64 * K1 * per : 0));   // [16][K1][per]  (BSMEM, FP16)
+  const size_t roff = (size_t)rhs * 2 * n;
   C* e0 = e + roff;
   const C* r0 = r + roff;
-  for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) es[i] = e0[i];
-  __syncthreads();
+  // load this block's part of the level
+  for (int i = threadIdx.x; i < 16 * per; i += blockDim.x) {
+    const int c = i / per, jj = i - (i / per) * per, j = q * per + jj;
+    const int t = 4 * (j / qx) + (c >> 2), x = 4 * (j % qx) + (c & 3), v = t * Nx + x;
+    es[2 * i] = e0[v]; es[2 * i + 1] = e0[n + v];
+    rs[2 * i] = r0[v]; rs[2 * i + 1] = r0[n + v];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) ds[4 * i + d] = Dc[((size_t)c * m + j) * 4 + d];
+  }
+  if constexpr (BSMEM) {
+    for (int i = threadIdx.x; i < 16 * K1 * per; i += blockDim.x) {
+      const int ck = i / per, jj = i - (i / per) * per;               // ck = c K1 + (k - 1)
+      const size_t src = (size_t)ck * m + q * per + jj;
+#pragma unroll
+      for (int d = 0; d < 4; ++d) bs[4 * i + d] = Bc[src * 4 + d];
+      if (Sc) ss[i] = Sc[src];
+    }
+  }
+  cluster.sync();
   const int g = threadIdx.x & (LPS - 1);
   const int groups = blockDim.x / LPS;
   for (int sw = 0; sw < sweeps; ++sw) {
     for (int colour = 0; colour < 16; ++colour) {
-      for (int base = 0; base < per_colour; base += groups) {
-        const int idx = base + threadIdx.x / LPS;
-        const bool valid = idx < per_colour;
-        gs_site<T, BT, LPS, true>(es, r0, B, Bs, Dinv, off, Nt, Nx, colour, idx, g, valid);
+      for (int base = 0; base < per; base += groups) {
+        const int jj = base + threadIdx.x / LPS;
+        const bool valid = jj < per;
+        const int j = q * per + (valid ? jj : 0);
+        const int t = 4 * (j / qx) + (colour >> 2), x = 4 * (j % qx) + (colour & 3);
+        C xv[IT][2], bb[IT][4];
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+          const int k = 1 + g + it * LPS;
+          if (valid && k < off.K) {
+            int tw = t + off.dt[k]; tw -= (tw >= Nt) ? Nt : 0;
+            int xw = x + off.dx[k]; xw -= (xw >= Nx) ? Nx : 0;
+            const int cw = ((tw & 3) << 2) | (xw & 3);
+            const int jw = (tw >> 2) * qx + (xw >> 2);
+            const int qw = jw / per, jjw = jw - qw * per;
+            const C* rem = cluster.map_shared_rank(es, qw);
+            xv[it][0] = rem[2 * (cw * per + jjw)];
+            xv[it][1] = rem[2 * (cw * per + jjw) + 1];
+            if constexpr (BSMEM) {
+              const int li = (colour * K1 + (k - 1)) * per + jj;
+              if constexpr (sizeof(T) == 4) {
+#pragma unroll
+                for (int d = 0; d < 4; ++d) bb[it][d] = h2c<float>(bs[4 * li + d], ss[li]);
+              } else {
+#pragma unroll
+                for (int d = 0; d < 4; ++d) bb[it][d] = to_c(bs[4 * li + d], T());
+              }
+            } else {
+              cm_block<T, BT>(Bc, Sc, ((size_t)colour * K1 + (k - 1)) * m + j, bb[it]);
+            }
+          } else {
+            xv[it][0] = xv[it][1] = czero<C>();
+            bb[it][0] = bb[it][1] = bb[it][2] = bb[it][3] = czero<C>();
+          }
+        }
+        C s0 = czero<C>(), s1 = czero<C>();
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+          cmac(s0, bb[it][0], xv[it][0]);
+          cmac(s0, bb[it][1], xv[it][1]);
+          cmac(s1, bb[it][2], xv[it][0]);
+          cmac(s1, bb[it][3], xv[it][1]);
+        }
+#pragma unroll
+        for (int o = LPS / 2; o > 0; o >>= 1) {
+          s0.x += __shfl_xor_sync(0xffffffffu, s0.x, o);
+          s0.y += __shfl_xor_sync(0xffffffffu, s0.y, o);
+          s1.x += __shfl_xor_sync(0xffffffffu, s1.x, o);
+          s1.y += __shfl_xor_sync(0xffffffffu, s1.y, o);
+        }
+        if (valid && g == 0) {
+          const int i = colour * per + jj;
+          const C a0 = rs[2 * i] - s0, a1 = rs[2 * i + 1] - s1;
+          es[2 * i] = cmul(ds[4 * i], a0) + cmul(ds[4 * i + 1], a1);
+          es[2 * i + 1] = cmul(ds[4 * i + 2], a0) + cmul(ds[4 * i + 3], a1);
+        }
       }
-      __syncthreads();
+      cluster.sync();
     }
   }
-  for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) e0[i] = es[i];
+  // write this block's sites back (no block reads remote shared memory after the last barrier)
+  for (int i = threadIdx.x; i < 16 * per; i += blockDim.x) {
+    const int c = i / per, jj = i - (i / per) * per, j = q * per + jj;
+    const int t = 4 * (j / qx) + (c >> 2), x = 4 * (j % qx) + (c & 3), v = t * Nx + x;
+    e0[v] = es[2 * i];
+    e0[n + v] = es[2 * i + 1];
+  }
 }
 
 // y_r = Ainv x_r for the coarsest level: dense FP64 complex matrix, row-major,
@@ -385,21 +472,77 @@ cudaError_t launch_coarse_sweeps_cluster(typename cplx<T>::type* e, const typena
   return cudaLaunchKernelEx(&cfg, k_coarse_sweeps_cluster<T, BT>, e, r, B, Bs, Dinv, off, Nt, Nx, sweeps);
 }
 
+size_t dsmem_sweep_bytes(int n, int K, size_t cbytes, bool bsmem, size_t bt_bytes) {
+  const size_t per = (size_t)n / 256;
+  size_t b = per * 16 * (2 + 2 + 4) * cbytes;
+  if (bsmem) b += per * 16 * (K - 1) * (4 * bt_bytes + 4);
+  return b;
+}
+
+// Whether a 16-block cluster with this shared-memory size can be resident on
+// the device (queried once per level in setup; the sweep falls back to the
+// per-colour kernels otherwise).
 template <typename T, typename BT>
-cudaError_t launch_coarse_sweeps_smem(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* B,
-                                      const float* Bs, const typename cplx<T>::type* Dinv, const Offsets& off,
-                                      int Nt, int Nx, int sweeps, int R, cudaStream_t st) {
+bool dsmem_sweeps_possible(int n, int K, bool bsmem) {
+  if (n % 256 || n / 256 > 64) return false;
+  const size_t smem = dsmem_sweep_bytes(n, K, sizeof(typename cplx<T>::type), bsmem, sizeof(BT));
+  if (smem > 200 * 1024) return false;
+  auto kern = bsmem ? k_coarse_sweeps_dsmem<T, BT, true> : k_coarse_sweeps_dsmem<T, BT, false>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const int per = n / 256;
+  int threads = ((per * 8 + 31) / 32) * 32;
+  threads = threads > 512 ? 512 : threads;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(DSMEM_CLUSTER);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = DSMEM_CLUSTER;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, (void*)kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return clusters >= 1;
+}
+
+template <typename T, typename BT>
+cudaError_t launch_coarse_sweeps_dsmem(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* Bc,
+                                       const float* Sc, const typename cplx<T>::type* Dc, const Offsets& off,
+                                       int Nt, int Nx, int sweeps, int R, bool bsmem, cudaStream_t st) {
   const int n = Nt * Nx;
-  const size_t smem = (size_t)2 * n * sizeof(typename cplx<T>::type);
-  if (n > SMEM_SWEEP_MAX_SITES) return cudaErrorInvalidValue;
-  cudaError_t err = cudaFuncSetAttribute(k_coarse_sweeps_smem<T, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+  if (n % 256 || n / 256 > 64) return cudaErrorInvalidValue;
+  const size_t smem = dsmem_sweep_bytes(n, off.K, sizeof(typename cplx<T>::type), bsmem, sizeof(BT));
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  auto kern = bsmem ? k_coarse_sweeps_dsmem<T, BT, true> : k_coarse_sweeps_dsmem<T, BT, false>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (err == cudaSuccess) err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  const int per_colour = n / 16;
-  int threads = ((per_colour * 8 + 31) / 32) * 32;
-  threads = threads < 32 ? 32 : (threads > 1024 ? 1024 : threads);
-  k_coarse_sweeps_smem<T, BT><<<R, threads, smem, st>>>(e, r, B, Bs, Dinv, off, Nt, Nx, sweeps);
-  return cudaGetLastError();
+  const int per = n / 256;
+  int threads = ((per * 8 + 31) / 32) * 32;
+  threads = threads > 512 ? 512 : threads;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(DSMEM_CLUSTER * R);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = DSMEM_CLUSTER;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, e, r, Bc, Sc, Dc, off, Nt, Nx, sweeps);
 }
 
 template <typename Cv>
@@ -448,8 +591,13 @@ template cudaError_t launch_coarse_colour<float, __half2>(float2*, const float2*
 template cudaError_t launch_coarse_sweeps_cluster<float, __half2>(float2*, const float2*, const __half2*, const float*,
                                                                   const float2*, const Offsets&, int, int, int, int,
                                                                   cudaStream_t);
-template cudaError_t launch_coarse_sweeps_smem<float, __half2>(float2*, const float2*, const __half2*, const float*,
-                                                               const float2*, const Offsets&, int, int, int, int,
-                                                               cudaStream_t);
+template bool dsmem_sweeps_possible<float, __half2>(int, int, bool);
+template bool dsmem_sweeps_possible<double, double2>(int, int, bool);
+template cudaError_t launch_coarse_sweeps_dsmem<float, __half2>(float2*, const float2*, const __half2*, const float*,
+                                                                const float2*, const Offsets&, int, int, int, int, bool,
+                                                                cudaStream_t);
+template cudaError_t launch_coarse_sweeps_dsmem<double, double2>(double2*, const double2*, const double2*,
+                                                                 const float*, const double2*, const Offsets&, int, int,
+                                                                 int, int, bool, cudaStream_t);
 template cudaError_t launch_dense_gemv<double2>(const double2*, const double2*, double2*, int, int, cudaStream_t);
 template cudaError_t launch_dense_gemv<float2>(const double2*, const float2*, float2*, int, int, cudaStream_t);

@@ -17,6 +17,8 @@ struct Level {
   float* Bs = nullptr;
   double2* Dinv64 = nullptr;
   float2* Dinv32 = nullptr;
+  // the distributed-shared-memory cluster sweep can run on this level (FP64, FP32)
+  bool dsmem64 = false, dsmem32 = false;
   // colour-major copies for the Gauss-Seidel kernels (smoothed coarse levels)
   double2* Bc64 = nullptr;
   __half2* Bc16 = nullptr;

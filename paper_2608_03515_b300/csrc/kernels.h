@@ -47,27 +47,31 @@ cudaError_t launch_coarse_colour(typename cplx<T>::type* e, const typename cplx<
 // usable while n / 16 <= 8 * 1024 sites per colour
 constexpr int CLUSTER_BLOCKS = 8;
 int cluster_sweep_threads(int n);
-// FP32 levels of at most SMEM_SWEEP_MAX_SITES sites run every colour in one
-// block with e in shared memory; larger FP32 levels use the clustered sweep.
-// In FP64 the few SMs of one block or cluster are FP64-pipe bound, so FP64
-// colours are launched one by one over all SMs.
-constexpr int SMEM_SWEEP_MAX_SITES = 12288;
-template <typename T>
-inline bool use_smem_sweeps(int n) {
-  return sizeof(T) == 4 && n <= SMEM_SWEEP_MAX_SITES;
-}
-template <typename T>
-inline bool use_cluster_sweeps(int n) {
-  return sizeof(T) == 4 && !use_smem_sweeps<T>(n) && cluster_sweep_threads(n) <= 1024;
-}
-template <typename T, typename BT>
-cudaError_t launch_coarse_sweeps_smem(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* B,
-                                      const float* Bs, const typename cplx<T>::type* Dinv, const Offsets& off,
-                                      int Nt, int Nx, int sweeps, int R, cudaStream_t st);
 template <typename T, typename BT>
 cudaError_t launch_coarse_sweeps_cluster(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* B,
                                          const float* Bs, const typename cplx<T>::type* Dinv, const Offsets& off,
                                          int Nt, int Nx, int sweeps, int R, cudaStream_t st);
+// Coarse Gauss-Seidel kernel choice.  Levels with n = 256 per sites (per <= 64)
+// run all colours on one 16-block cluster with the level in distributed shared
+// memory; in FP32 also the off-diagonal blocks live in shared memory when they
+// fit (n <= 8192).  Other FP32 levels use the L2-based clustered sweep, other
+// FP64 levels one launch per colour spread over all SMs.
+constexpr int DSMEM_CLUSTER = 16;
+size_t dsmem_sweep_bytes(int n, int K, size_t cbytes, bool bsmem, size_t bt_bytes);
+template <typename T, typename BT>
+bool dsmem_sweeps_possible(int n, int K, bool bsmem);
+template <typename T>
+inline bool dsmem_blocks_in_smem(int n, int K) {
+  return sizeof(T) == 4 && dsmem_sweep_bytes(n, K, 8, true, 4) <= 200 * 1024;
+}
+template <typename T>
+inline bool use_cluster_sweeps(int n) {
+  return sizeof(T) == 4 && cluster_sweep_threads(n) <= 1024;
+}
+template <typename T, typename BT>
+cudaError_t launch_coarse_sweeps_dsmem(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* Bc,
+                                       const float* Sc, const typename cplx<T>::type* Dc, const Offsets& off,
+                                       int Nt, int Nx, int sweeps, int R, bool bsmem, cudaStream_t st);
 template <typename Cv>
 cudaError_t launch_dense_gemv(const double2* A, const Cv* x, Cv* y, int nd, int R, cudaStream_t st);
 cudaError_t launch_dense_gemv32(const float2* A, const float2* x, float2* y, int nd, int R, cudaStream_t st);

@@ -97,12 +97,16 @@ cudaError_t vcycle_level(amamg_ctx* h, int l, const typename cplx<T>::type* r, t
       }
     return cudaSuccess;
   }
-  if constexpr (!f64) {
-    if (sweeps > 0 && use_smem_sweeps<T>(L.n)) {
-      err = launch_coarse_sweeps_smem<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, sweeps, R, st);
-      h->launches++;
-      return err;
-    }
+  if (sweeps > 0 && (f64 ? L.dsmem64 : L.dsmem32)) {
+    const bool bsm = dsmem_blocks_in_smem<T>(L.n, L.off.K);
+    if constexpr (f64)
+      err = launch_coarse_sweeps_dsmem<double, double2>(e, r, L.Bc64, nullptr, L.Dc64, L.off, L.Nt, L.Nx, sweeps, R,
+                                                        bsm, st);
+    else
+      err = launch_coarse_sweeps_dsmem<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, sweeps, R, bsm,
+                                                       st);
+    h->launches++;
+    return err;
   }
   if constexpr (!f64) {
     if (sweeps > 0 && use_cluster_sweeps<T>(L.n)) {

@@ -172,9 +172,11 @@ def test_transfers_and_coarse_apply_fp64(Nt, Nx, aggs, R):
 
 # ------------------------------------------------------------------ smoother, coarsest, V-cycle
 
-@pytest.mark.parametrize("sweeps", [1, 2])
-def test_smoothers_fp64(sweeps):
-    Nt = Nx = 32
+@pytest.mark.parametrize("sweeps,Nt", [(1, 32), (2, 32), (2, 128)])
+def test_smoothers_fp64(sweeps, Nt):
+    """Level 1 is 16^2 at Nt = 32 and 64^2 at Nt = 128 (cluster sweeps with the
+    level in distributed shared memory, 1 and 16 sites per block and colour)."""
+    Nx = Nt
     U, D, hier, levels = make(Nt, Nx, [2, 2], m0=0.1, seed=8)
     rng = np.random.Generator(np.random.PCG64(9))
     for l in range(2):
@@ -305,11 +307,14 @@ def test_invalid_arguments_rejected():
 
 # ------------------------------------------------------------------ FP32 path (FP16 + scale storage)
 
-def test_fp32_transfers_coarse_and_smoothers_match_emulated_storage():
+@pytest.mark.parametrize("Nt", [32, 64])
+def test_fp32_transfers_coarse_and_smoothers_match_emulated_storage(Nt):
     """FP32 kernels against FP64 arithmetic on the emulated FP16+scale operators
-    and complex64-rounded inputs (oracle.mixed): FP32 rounding only."""
+    and complex64-rounded inputs (oracle.mixed): FP32 rounding only.  The
+    coarse level is 8^2 (L2-based sweep) at Nt = 32 and 16^2 (cluster sweep
+    with the level in distributed shared memory) at Nt = 64."""
     from oracle import mixed
-    Nt = Nx = 32
+    Nx = Nt
     aggs = [4, 2]
     U, D, hier, levels = make(Nt, Nx, aggs, m0=0.2, seed=21)
     rng = np.random.Generator(np.random.PCG64(22))
