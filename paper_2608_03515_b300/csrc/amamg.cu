@@ -178,7 +178,7 @@ int ensure_solver_ws(amamg_ctx* h, int R) {
   if (R <= h->Rsolve && m <= h->mcap) return AMAMG_OK;
   clear_graphs(h);
   dfree(h->V); dfree(h->Z64); dfree(h->Z32); dfree(h->v32); dfree(h->w); dfree(h->res);
-  dfree(h->partial); dfree(h->d_h); dfree(h->d_inv); dfree(h->d_flag); dfree(h->d_y);
+  dfree(h->partial); dfree(h->d_h); dfree(h->d_inv); dfree(h->d_flag); dfree(h->d_y); dfree(h->d_tickets); dfree(h->d_npart);
   dfree(h->d_diag64); dfree(h->d_inv64); dfree(h->d_inv32);
   if (h->h_h) cudaFreeHost(h->h_h);
   if (h->h_y) cudaFreeHost(h->h_y);
@@ -198,6 +198,9 @@ int ensure_solver_ws(amamg_ctx* h, int R) {
   CKS(dalloc(h, &h->d_h, (size_t)R * 3 * (m + 2)));
   CKS(dalloc(h, &h->d_inv, (size_t)R));
   CKS(dalloc(h, &h->d_flag, (size_t)R));
+  CKS(dalloc(h, &h->d_tickets, (size_t)R * (m + 3)));
+  CK(cudaMemset(h->d_tickets, 0, sizeof(unsigned) * (size_t)R * (m + 3)));
+  CKS(dalloc(h, &h->d_npart, (size_t)R * axpy_norm_blocks((long)len)));
   CKS(dalloc(h, &h->d_diag64, (size_t)R));
   CKS(dalloc(h, &h->d_inv64, (size_t)R));
   CKS(dalloc(h, &h->d_inv32, (size_t)R));
@@ -440,39 +443,29 @@ int arnoldi_step(amamg_ctx* h, int j, int R, cudaStream_t st) {
   // Classical Gram-Schmidt with the DGKS criterion: one pass, and a second
   // pass only for right-hand sides whose norm dropped below 1/sqrt(2) of its
   // value before orthogonalisation (the second-pass kernels are gated per RHS).
+  // Each pass is two kernels with their reductions fused in: the inner
+  // products (pass 1 also ||w||^2), then the update with the new norm.
   const int J = j + 1;
-  const int nb = dot_blocks(len);
   const int nrm_off = 2 * (m + 2);
+  unsigned* tk_dots = h->d_tickets;
+  unsigned* tk_norm = h->d_tickets + (size_t)R * (m + 2);
   CKS(launch(h, "gs_dots", (double)R * len * 16.0 * (J + 1), st, [&] {
-    return launch_dots(h->V, vi, vr, h->w, vr, len, J, R, h->partial, st, true);
+    return launch_dots_fused(h->V, vi, vr, h->w, vr, len, J, R, h->partial, true, nullptr, tk_dots, d_h1, ldh, 0, st);
   }, (double)R * len * 8.0 * (J + 1)));
-  CKS(launch(h, "gs_reduce", (double)R * (J + 1) * nb * 16.0, st,
-             [&] { return launch_reduce(h->partial, nb, J + 1, R, d_h1, ldh, 0, 0, nullptr, st); }));
-  CKS(launch(h, "gs_update", (double)R * len * 16.0 * (J + 2), st, [&] {
-    return launch_multi_axpy<double2>(h->w, vr, h->V, vi, vr, d_h1, ldh, J, -1.0, len, R, st);
-  }, (double)R * len * 8.0 * J));
-  CKS(launch(h, "gs_dots", (double)R * len * 16.0, st,
-             [&] { return launch_dots(h->w, 0, vr, h->w, vr, len, 1, R, h->partial, st); }));
-  CKS(launch(h, "gs_reduce", (double)R * nb * 16.0, st, [&] {
-    return launch_reduce(h->partial, nb, 1, R, d_h1, ldh, nrm_off, 2, h->d_inv, st, h->d_flag, J, 0.5);
-  }));
+  CKS(launch(h, "gs_update_norm", (double)R * len * 16.0 * (J + 2), st, [&] {
+    return launch_axpy_norm(h->w, vr, h->V, vi, vr, d_h1, ldh, J, len, R, nullptr, h->d_npart, tk_norm, d_h1, ldh,
+                            nrm_off, h->d_inv, h->d_flag, J, 0.5, 2, st);
+  }, (double)R * len * 8.0 * (J + 1)));
   // second pass, gated by the DGKS flag (h2 = 0 where it is not needed); the
   // byte counts of these categories assume the pass runs (upper bounds)
   CKS(launch(h, "gs2_dots_gated", (double)R * len * 16.0 * (J + 1), st, [&] {
-    return launch_dots(h->V, vi, vr, h->w, vr, len, J, R, h->partial, st, false, h->d_flag);
-  }));
-  CKS(launch(h, "gs2_reduce_gated", (double)R * J * nb * 16.0, st, [&] {
-    return launch_reduce(h->partial, nb, J, R, d_h1, ldh, m + 2, 0, nullptr, st, h->d_flag);
-  }));
-  CKS(launch(h, "gs2_update_gated", (double)R * len * 16.0 * (J + 2), st, [&] {
-    return launch_multi_axpy<double2>(h->w, vr, h->V, vi, vr, d_h1 + (m + 2), ldh, J, -1.0, len, R, st, h->d_flag);
-  }));
-  CKS(launch(h, "gs2_dots_gated", (double)R * len * 16.0, st, [&] {
-    return launch_dots(h->w, 0, vr, h->w, vr, len, 1, R, h->partial, st, false, h->d_flag);
-  }));
-  CKS(launch(h, "gs2_reduce_gated", (double)R * nb * 16.0, st, [&] {
-    return launch_reduce(h->partial, nb, 1, R, d_h1, ldh, nrm_off, 1, h->d_inv, st, h->d_flag);
-  }));
+    return launch_dots_fused(h->V, vi, vr, h->w, vr, len, J, R, h->partial, false, h->d_flag, tk_dots, d_h1, ldh,
+                             m + 2, st);
+  }, (double)R * len * 8.0 * J));
+  CKS(launch(h, "gs2_update_norm_gated", (double)R * len * 16.0 * (J + 2), st, [&] {
+    return launch_axpy_norm(h->w, vr, h->V, vi, vr, d_h1 + (m + 2), ldh, J, len, R, h->d_flag, h->d_npart, tk_norm,
+                            d_h1, ldh, nrm_off, h->d_inv, nullptr, 0, 0.0, 1, st);
+  }, (double)R * len * 8.0 * (J + 1)));
   CKS(launch(h, "scale_copy", (double)R * len * 32.0, st, [&] {
     return launch_scale_copy<double2>(h->V + (size_t)(j + 1) * vi, vr, h->w, vr, h->d_inv, len, R, st);
   }));
@@ -737,7 +730,7 @@ void free_all(amamg_ctx* h) {
   h->ws = nullptr; h->ev_in = h->ev_out = nullptr;
   dfree(h->U64); dfree(h->U32); dfree(h->Ainv); dfree(h->Ainv32); dfree(h->d_err);
   dfree(h->V); dfree(h->Z64); dfree(h->Z32); dfree(h->v32); dfree(h->w); dfree(h->res);
-  dfree(h->partial); dfree(h->d_h); dfree(h->d_inv); dfree(h->d_flag); dfree(h->d_y);
+  dfree(h->partial); dfree(h->d_h); dfree(h->d_inv); dfree(h->d_flag); dfree(h->d_y); dfree(h->d_tickets); dfree(h->d_npart);
   dfree(h->d_diag64); dfree(h->d_inv64); dfree(h->d_inv32);
   if (h->h_h) cudaFreeHost(h->h_h);
   if (h->h_y) cudaFreeHost(h->h_y);

@@ -118,6 +118,107 @@ __global__ void __launch_bounds__(256) k_cast(const Cs* __restrict__ src, Cd* __
     dst[k] = to_c(src[k], typename real_of<Cd>::type());
 }
 
+__device__ __forceinline__ double block_reduce_real(double v, double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  if (wid == 0) {
+    v = lane < nw ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+// Inner products with the reduction fused in: like k_dots, then the last block
+// of each (row, RHS) to finish (atomic ticket after a fence) adds the partials
+// in a fixed order, so the result is deterministic, writes it to
+// out[r*ldo + off + i] and resets the ticket.  A right-hand side whose gate
+// flag is 0 gets zeros.
+__global__ void __launch_bounds__(DOT_THREADS)
+k_dots_fused(const double2* __restrict__ V, size_t vi, size_t vr, const double2* __restrict__ w, size_t wr,
+             long len, long chunk, double2* __restrict__ partial, int J, const int* __restrict__ gate,
+             unsigned* __restrict__ tickets, double2* __restrict__ out, int ldo, int off) {
+  __shared__ double2 sh[32];
+  __shared__ bool last;
+  const int i = blockIdx.y, r = blockIdx.z, nb = gridDim.x, Jt = gridDim.y;
+  if (gate && gate[r] == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[(size_t)r * ldo + off + i] = make_double2(0.0, 0.0);
+    return;
+  }
+  const double2* a = (i < J) ? V + i * vi + r * vr : w + r * wr;
+  const double2* b = w + r * wr;
+  const long start = (long)blockIdx.x * chunk;
+  const long end = min(start + chunk, len);
+  double2 acc = make_double2(0.0, 0.0);
+  for (long k = start + threadIdx.x; k < end; k += blockDim.x) cmacc(acc, a[k], b[k]);
+  acc = block_reduce(acc, sh);
+  const size_t slot = (size_t)r * Jt + i;
+  if (threadIdx.x == 0) {
+    partial[slot * nb + blockIdx.x] = acc;
+    __threadfence();
+    last = atomicAdd(&tickets[slot], 1u) == (unsigned)(nb - 1);
+  }
+  __syncthreads();
+  if (last) {
+    double2 t = make_double2(0.0, 0.0);
+    for (int bb = threadIdx.x; bb < nb; bb += blockDim.x) t += __ldcg(&partial[slot * nb + bb]);
+    t = block_reduce(t, sh);
+    if (threadIdx.x == 0) {
+      out[(size_t)r * ldo + off + i] = t;
+      tickets[slot] = 0;
+    }
+  }
+}
+
+// y_r -= sum_{i<J} coef[r*ldc + i] X_{i,r}, and ||y_r|| of the result with the
+// same last-block reduction: out[r*ldo + nrm_off] = ||y_r||, inv[r] = 1/||y_r||
+// (0 for a zero vector); mode 2 also sets flag[r] = (||y_r||^2 < eta2 *
+// out[r*ldo + ref_off].x) (the DGKS test against the norm before the pass).
+// A right-hand side whose gate flag is 0 is left untouched.
+__global__ void __launch_bounds__(256)
+k_axpy_norm(double2* __restrict__ y, size_t yr, const double2* __restrict__ X, size_t xi, size_t xr,
+            const double2* __restrict__ coef, int ldc, int J, long len, const int* __restrict__ gate,
+            double* __restrict__ partial, unsigned* __restrict__ tickets, double2* __restrict__ out, int ldo,
+            int nrm_off, double* __restrict__ inv, int* __restrict__ flag, int ref_off, double eta2, int mode) {
+  __shared__ double sh[32];
+  __shared__ bool last;
+  const int r = blockIdx.y, nb = gridDim.x;
+  if (gate && gate[r] == 0) return;
+  const double2* c = coef + (size_t)r * ldc;
+  double ss = 0.0;
+  for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < len; k += (long)gridDim.x * blockDim.x) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int i = 0; i < J; ++i) cmac(acc, c[i], X[i * xi + r * xr + k]);
+    const double2 v = y[r * yr + k] - acc;
+    y[r * yr + k] = v;
+    ss = fma(v.x, v.x, fma(v.y, v.y, ss));
+  }
+  ss = block_reduce_real(ss, sh);
+  if (threadIdx.x == 0) {
+    partial[(size_t)r * nb + blockIdx.x] = ss;
+    __threadfence();
+    last = atomicAdd(&tickets[r], 1u) == (unsigned)(nb - 1);
+  }
+  __syncthreads();
+  if (last) {
+    double t = 0.0;
+    for (int bb = threadIdx.x; bb < nb; bb += blockDim.x) t += __ldcg(&partial[(size_t)r * nb + bb]);
+    t = block_reduce_real(t, sh);
+    if (threadIdx.x == 0) {
+      // NaN propagates (a NaN or Inf entry must surface as a non-finite norm)
+      const double nrm = (t >= 0.0) ? sqrt(t) : ((t < 0.0) ? 0.0 : t);
+      out[(size_t)r * ldo + nrm_off] = make_double2(nrm, 0.0);
+      inv[r] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+      if (mode == 2) flag[r] = (t < eta2 * out[(size_t)r * ldo + ref_off].x) ? 1 : 0;
+      tickets[r] = 0;
+    }
+  }
+}
+
 inline int grid_for(long len) {
   long g = (len + 255) / 256;
   if (g > 148 * 16) g = 148 * 16;
@@ -145,6 +246,28 @@ cudaError_t launch_reduce(const double2* partial, int nb, int J, int R, double2*
                           double* inv, cudaStream_t st, int* flag, int ref_off, double eta2) {
   dim3 grid(J, R);
   k_reduce_partials<<<grid, 256, 0, st>>>(partial, nb, J, out, ldo, off, mode, inv, flag, ref_off, eta2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dots_fused(const double2* V, size_t vi, size_t vr, const double2* w, size_t wr, long len, int J,
+                              int R, double2* partial, bool with_self, const int* gate, unsigned* tickets,
+                              double2* out, int ldo, int off, cudaStream_t st) {
+  const int nb = dot_blocks(len);
+  const long chunk = (len + nb - 1) / nb;
+  dim3 grid(nb, J + (with_self ? 1 : 0), R);
+  k_dots_fused<<<grid, DOT_THREADS, 0, st>>>(V, vi, vr, w, wr, len, chunk, partial, J, gate, tickets, out, ldo, off);
+  return cudaGetLastError();
+}
+
+int axpy_norm_blocks(long len) { return grid_for(len); }
+
+cudaError_t launch_axpy_norm(double2* y, size_t yr, const double2* X, size_t xi, size_t xr, const double2* coef,
+                             int ldc, int J, long len, int R, const int* gate, double* partial, unsigned* tickets,
+                             double2* out, int ldo, int nrm_off, double* inv, int* flag, int ref_off, double eta2,
+                             int mode, cudaStream_t st) {
+  dim3 grid(grid_for(len), R);
+  k_axpy_norm<<<grid, 256, 0, st>>>(y, yr, X, xi, xr, coef, ldc, J, len, gate, partial, tickets, out, ldo, nrm_off,
+                                    inv, flag, ref_off, eta2, mode);
   return cudaGetLastError();
 }
 

@@ -106,6 +106,8 @@ struct amamg_ctx {
   double2* d_h = nullptr;    // [R][3 (m+2)] device: h1 | h2 | norms
   double* d_inv = nullptr;   // [R]
   int* d_flag = nullptr;     // [R] second Gram-Schmidt pass needed (DGKS)
+  unsigned* d_tickets = nullptr;   // [R (m+2)] dots + [R] norms: last-block tickets (kept zero between uses)
+  double* d_npart = nullptr;       // [R][blocks] partial squared norms
   double* d_diag64 = nullptr;  // [R] m0_r + 2 of each right-hand side
   double* d_inv64 = nullptr;   // [R] 1 / (m0_r + 2)
   float* d_inv32 = nullptr;    // [R] its FP32 rounding

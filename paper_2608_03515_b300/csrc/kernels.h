@@ -84,6 +84,15 @@ cudaError_t launch_dots(const double2* V, size_t vi, size_t vr, const double2* w
                         double2* partial, cudaStream_t st, bool with_self = false, const int* gate = nullptr);
 cudaError_t launch_reduce(const double2* partial, int nb, int J, int R, double2* out, int ldo, int off, int mode,
                           double* inv, cudaStream_t st, int* flag = nullptr, int ref_off = 0, double eta2 = 0.5);
+// Gram-Schmidt kernels with the reductions fused in (last-block tickets)
+cudaError_t launch_dots_fused(const double2* V, size_t vi, size_t vr, const double2* w, size_t wr, long len, int J,
+                              int R, double2* partial, bool with_self, const int* gate, unsigned* tickets,
+                              double2* out, int ldo, int off, cudaStream_t st);
+int axpy_norm_blocks(long len);
+cudaError_t launch_axpy_norm(double2* y, size_t yr, const double2* X, size_t xi, size_t xr, const double2* coef,
+                             int ldc, int J, long len, int R, const int* gate, double* partial, unsigned* tickets,
+                             double2* out, int ldo, int nrm_off, double* inv, int* flag, int ref_off, double eta2,
+                             int mode, cudaStream_t st);
 template <typename Cx>
 cudaError_t launch_multi_axpy(double2* y, size_t yr, const Cx* X, size_t xi, size_t xr, const double2* coef, int ldc,
                               int J, double sign, long len, int R, cudaStream_t st, const int* gate = nullptr);
