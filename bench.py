@@ -182,6 +182,9 @@ def run_probe(args):
     dt = torch.complex64 if args.prec == "f32" else torch.complex128
     x = torch.randn(args.rhs, 2, Lp, Lp, dtype=dt, device=dev)
     y = torch.empty_like(x)
+    nt1, nx1, _ = h.level_info(1)
+    r1 = torch.randn(args.rhs, 2, nt1, nx1, dtype=dt, device=dev)
+    e1 = torch.zeros_like(r1)
     stream = torch.cuda.current_stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     for rep in range(args.reps + 1):
@@ -191,6 +194,8 @@ def run_probe(args):
             A.apply_D(h, x, y)
         elif args.probe == "vcycle":
             A.vcycle(h, x, y)
+        elif args.probe == "smooth1":
+            A.smooth(h, 1, r1, e1, 2)
         elif args.probe == "coarsest":
             nt, nx, _ = h.level_info(len(aggs))
             xc = torch.randn(args.rhs, 2, nt, nx, dtype=torch.complex128, device=dev)
@@ -255,7 +260,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--probe", default=None, choices=["apply_D", "vcycle", "solve", "coarsest"],
+    ap.add_argument("--probe", default=None, choices=["apply_D", "vcycle", "smooth1", "solve", "coarsest"],
                     help="time one kernel family on a small random-phase case (for profiler captures)")
     ap.add_argument("--lattice", type=int, default=512)
     ap.add_argument("--rhs", type=int, default=1)

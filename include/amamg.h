@@ -161,8 +161,10 @@ int amamg_apply_coarse(amamg_handle h, int level, const void* in, void* out,
                        int R, int precision, void* stream);
 
 /* sweeps block Gauss-Seidel sweeps on A_l e = r, starting from the e passed in
- * (red-black on the fine level, 16 colours (t mod 4, x mod 4) on coarse
- * levels; "block solver as smoother", Sec. 5). */
+ * (red-black on the fine level; on coarse levels 8 colours (t + 3x) mod 8
+ * when both extents are multiples of 8 and no coupling (dt, dx) of the level
+ * has dt + 3dx = 0 mod 8, else 16 colours (t mod 4, x mod 4); colours in
+ * increasing order; "block solver as smoother", Sec. 5). */
 int amamg_smooth(amamg_handle h, int level, const void* r, void* e, int R,
                  int sweeps, int precision, void* stream);
 

@@ -32,8 +32,10 @@ Galerkin product (Sec. 2): A_H = P^H A_h P; restriction is P^H.
 
 Smoother: "block solver as smoother, 2 post-smoothing steps" (Sec. 5).  Block =
 one site (its 2 x 2 diagonal block).  The colouring is red-black (t + x parity)
-on the fine Wilson level and 16 colours (t mod 4, x mod 4) on coarse levels,
-visited in increasing colour number; sites of one colour never couple, so each
+on the fine Wilson level; on coarse levels it is c = (t + 3 x) mod 8 when that
+separates every coupled pair (extents multiples of 8; true for the 21-offset
+operator of a first coarse level), else 16 colours (t mod 4, x mod 4).  Colours
+are visited in increasing number; sites of one colour never couple, so each
 colour is a simultaneous block update.
 
 V-cycle (Algorithm 1 used as a preconditioner, start vector 0, no
@@ -257,13 +259,27 @@ def block_stencil(A: sp.csr_matrix, offsets, Nt: int, Nx: int) -> np.ndarray:
 
 # --------------------------------------------------------------------------- smoother
 
-def colouring(Nt: int, Nx: int, fine: bool) -> np.ndarray:
+def eight_colour_valid(Nt: int, Nx: int, offsets) -> bool:
+    """The colouring c = (t + 3 x) mod 8 separates every pair of coupled sites
+    when both extents are multiples of 8 and no off-diagonal offset has
+    dt + 3 dx = 0 (mod 8)."""
+    if Nt % 8 or Nx % 8:
+        return False
+    return all((dt + 3 * dx) % 8 != 0 for dt, dx in offsets if (dt % Nt, dx % Nx) != (0, 0))
+
+
+def colouring(Nt: int, Nx: int, fine: bool, offsets=None) -> np.ndarray:
+    """Gauss-Seidel colours: red-black on the fine level; on coarse levels
+    c = (t + 3 x) mod 8 where that separates all couplings (8 colours), else
+    c = 4 (t mod 4) + (x mod 4) (16 colours)."""
     t = np.arange(Nt)[:, None]
     x = np.arange(Nx)[None, :]
     if fine:
         if Nt % 2 or Nx % 2:
             raise ValueError("red-black colouring needs even extents")
         return ((t + x) % 2).astype(np.int32)
+    if offsets is not None and eight_colour_valid(Nt, Nx, offsets):
+        return ((t + 3 * x) % 8).astype(np.int32)
     if Nt % 4 or Nx % 4:
         raise ValueError("16-colour Gauss-Seidel needs extents divisible by 4")
     return ((t % 4) * 4 + (x % 4)).astype(np.int32)
@@ -334,7 +350,7 @@ def build_hierarchy(D: sp.csr_matrix, Nt: int, Nx: int, aggs: List[int], route: 
         levels.append(nxt)
     if smooth:
         for li, L in enumerate(levels[:-1]):
-            L.colour = colouring(L.Nt, L.Nx, fine=(li == 0))
+            L.colour = colouring(L.Nt, L.Nx, fine=(li == 0), offsets=L.offsets)
             check_colouring(L.colour, L.offsets)
             L.dinv = diag_block_inverses(L.A, L.Nt * L.Nx)
     last = levels[-1]

@@ -148,6 +148,44 @@ int coarse_offsets(const Offsets& fine, int Nt, int Nx, int a, Offsets* out) {
   return AMAMG_OK;
 }
 
+// Colours of the coarse Gauss-Seidel sweep on level L: the 8 classes
+// (t + 3x) mod 8 when both extents are multiples of 8 and no off-diagonal
+// coupling (dt, dx) has dt + 3 dx = 0 mod 8 (then a colour holds no two coupled
+// sites), else the 16 classes (t mod 4, x mod 4).
+int gs_colours(const Level& L) {
+  if (L.Nt % 8 || L.Nx % 8) return 16;
+  for (int k = 0; k < L.off.K; ++k) {
+    const int dt = wrap(L.off.dt[k], L.Nt), dx = wrap(L.off.dx[k], L.Nx);
+    if (dt == 0 && dx == 0) continue;
+    if ((dt + 3 * dx) % 8 == 0) return 16;
+  }
+  return 8;
+}
+
+// Coarse Gauss-Seidel kernel of a smoothed coarse level, per precision.
+// Default: FP64 on the whole GPU (grid barrier), since one cluster has the FP64
+// throughput of only 16 SMs; FP32 on one 16-block cluster with the level in
+// distributed shared memory where it fits, else the L2 cluster sweep, else one
+// launch per colour.  AMAMG_COARSE_GS = colour | cluster | dsmem | grid forces a
+// kernel where it is available (for measurement); results are the same.
+void choose_gs_kernels(Level& C) {
+  const bool grid64 = grid_sweep_blocks<double, double2>(C.n, C.ncol, 1) > 0;
+  const bool grid32 = grid_sweep_blocks<float, __half2>(C.n, C.ncol, 1) > 0;
+  const bool dsm64 = dsmem_sweeps_possible<double, double2>(C.n, C.off.K, C.ncol, false);
+  const bool dsm32 = dsmem_sweeps_possible<float, __half2>(C.n, C.off.K, C.ncol,
+                                                            dsmem_blocks_in_smem<float>(C.n, C.off.K));
+  const bool clu32 = use_cluster_sweeps<float>(C.n, C.ncol);
+  C.gs64 = grid64 ? GS_GRID : dsm64 ? GS_DSMEM : GS_COLOUR;
+  C.gs32 = dsm32 ? GS_DSMEM : clu32 ? GS_CLUSTER : grid32 ? GS_GRID : GS_COLOUR;
+  const char* env = getenv("AMAMG_COARSE_GS");
+  if (!env) return;
+  const std::string want(env);
+  if (want == "colour") { C.gs64 = C.gs32 = GS_COLOUR; }
+  else if (want == "cluster") { C.gs32 = clu32 ? GS_CLUSTER : C.gs32; }
+  else if (want == "dsmem") { C.gs64 = dsm64 ? GS_DSMEM : C.gs64; C.gs32 = dsm32 ? GS_DSMEM : C.gs32; }
+  else if (want == "grid") { C.gs64 = grid64 ? GS_GRID : C.gs64; C.gs32 = grid32 ? GS_GRID : C.gs32; }
+}
+
 // ----------------------------------------------------------------- workspace
 void clear_graphs(amamg_ctx* h) {
   for (auto g : h->step_graphs)
@@ -263,40 +301,56 @@ int smooth_impl(amamg_ctx* h, int l, typename cplx<T>::type* e, const typename c
     return AMAMG_OK;
   }
   const double blk = f64 ? 16.0 * 4 : (4.0 * 4 + 4.0);
-  const double bytes = (double)L.n / 16 * ((L.off.K - 1) * blk + 4 * cb + R * 2 * 3 * cb);
-  const double flops = (double)L.n / 16 * R * ((L.off.K - 1) * 32.0 + 36.0);   // one colour
-  if (sweeps > 0 && (f64 ? L.dsmem64 : L.dsmem32)) {
+  const int nc = L.ncol;
+  const double bytes = (double)L.n / nc * ((L.off.K - 1) * blk + 4 * cb + R * 2 * 3 * cb);
+  const double flops = (double)L.n / nc * R * ((L.off.K - 1) * 32.0 + 36.0);   // one colour
+  const int kind = f64 ? L.gs64 : L.gs32;
+  if (sweeps > 0 && kind == GS_DSMEM) {
     // every colour of every sweep on one 16-block cluster, level in shared memory
     const bool bsm = dsmem_blocks_in_smem<T>(L.n, L.off.K);
     if constexpr (f64)
-      return launch(h, "coarse_smooth_f64", bytes * 16 * sweeps, st, [&] {
-        return launch_coarse_sweeps_dsmem<double, double2>(e, r, L.Bc64, nullptr, L.Dc64, L.off, L.Nt, L.Nx, sweeps,
-                                                           R, bsm, st);
-      }, flops * 16 * sweeps);
+      return launch(h, "coarse_smooth_f64", bytes * nc * sweeps, st, [&] {
+        return launch_coarse_sweeps_dsmem<double, double2>(e, r, L.Bc64, nullptr, L.Dc64, L.off, L.Nt, L.Nx, nc,
+                                                           sweeps, R, bsm, st);
+      }, flops * nc * sweeps);
     else
-      return launch(h, "coarse_smooth_f32", bytes * 16 * sweeps, st, [&] {
-        return launch_coarse_sweeps_dsmem<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, sweeps, R,
-                                                          bsm, st);
-      }, flops * 16 * sweeps);
+      return launch(h, "coarse_smooth_f32", bytes * nc * sweeps, st, [&] {
+        return launch_coarse_sweeps_dsmem<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, nc, sweeps,
+                                                          R, bsm, st);
+      }, flops * nc * sweeps);
+  }
+  if (sweeps > 0 && kind == GS_GRID) {
+    // every colour of every sweep in one cooperative launch over all SMs
+    if constexpr (f64)
+      return launch(h, "coarse_smooth_f64", bytes * nc * sweeps, st, [&] {
+        return launch_coarse_sweeps_grid<double, double2>(e, r, L.Bc64, nullptr, L.Dc64, L.off, L.Nt, L.Nx, nc,
+                                                          sweeps, R, h->d_sync, st);
+      }, flops * nc * sweeps);
+    else
+      return launch(h, "coarse_smooth_f32", bytes * nc * sweeps, st, [&] {
+        return launch_coarse_sweeps_grid<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, nc, sweeps,
+                                                         R, h->d_sync, st);
+      }, flops * nc * sweeps);
   }
   if constexpr (!f64) {
-    if (sweeps > 0 && use_cluster_sweeps<T>(L.n))
+    if (sweeps > 0 && kind == GS_CLUSTER && use_cluster_sweeps<T>(L.n, nc))
       // every colour of every sweep in one clustered launch
-      return launch(h, "coarse_smooth_f32", bytes * 16 * sweeps, st, [&] {
-        return launch_coarse_sweeps_cluster<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, sweeps,
-                                                            R, st);
-      }, flops * 16 * sweeps);
+      return launch(h, "coarse_smooth_f32", bytes * nc * sweeps, st, [&] {
+        return launch_coarse_sweeps_cluster<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, nc,
+                                                            sweeps, R, st);
+      }, flops * nc * sweeps);
   }
   for (int s = 0; s < sweeps; ++s)
-    for (int c = 0; c < 16; ++c) {
+    for (int c = 0; c < nc; ++c) {
       int rc;
       if constexpr (f64)
         rc = launch(h, "coarse_smooth_f64", bytes, st, [&] {
-          return launch_coarse_colour<double, double2>(e, r, L.Bc64, nullptr, L.Dc64, L.off, L.Nt, L.Nx, c, R, st);
+          return launch_coarse_colour<double, double2>(e, r, L.Bc64, nullptr, L.Dc64, L.off, L.Nt, L.Nx, nc, c, R,
+                                                       st);
         }, flops);
       else
         rc = launch(h, "coarse_smooth_f32", bytes, st, [&] {
-          return launch_coarse_colour<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, c, R, st);
+          return launch_coarse_colour<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, nc, c, R, st);
         }, flops);
       CKS(rc);
     }
@@ -645,6 +699,19 @@ int set_masses(amamg_ctx* h, const double* m0, int R, cudaStream_t st) {
   return AMAMG_OK;
 }
 
+// A grid Gauss-Seidel sweep whose barrier timed out left its flag set: report
+// it and re-arm the barrier (cooperative launches keep all blocks resident, so
+// this does not happen in a correct run).
+int check_grid_sync(amamg_ctx* h, cudaStream_t st) {
+  unsigned flag[3] = {0, 0, 0};
+  CK(cudaMemcpyAsync(flag, h->d_sync, sizeof(flag), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (!flag[2]) return AMAMG_OK;
+  CK(cudaMemsetAsync(h->d_sync, 0, sizeof(flag), st));
+  h->err = "coarse Gauss-Seidel grid barrier timed out";
+  return AMAMG_ERR_TIMEOUT;
+}
+
 // Solver kernels read the per-RHS mass arrays while this guard is alive.
 struct MassGuard {
   amamg_ctx* h;
@@ -681,6 +748,7 @@ int fgmres_on(amamg_ctx* h, const double2* psi, double2* x, int R, cudaStream_t 
     if (sl[r].status == AMAMG_ERR_NONFINITE) nonfinite = true;
   }
   if (nonfinite) { h->err = "non-finite value in a right-hand side or residual"; rc = AMAMG_ERR_NONFINITE; }
+  CKS(check_grid_sync(h, st));
   return rc;
 }
 
@@ -728,7 +796,7 @@ void free_all(amamg_ctx* h) {
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
   h->ws = nullptr; h->ev_in = h->ev_out = nullptr;
-  dfree(h->U64); dfree(h->U32); dfree(h->Ainv); dfree(h->Ainv32); dfree(h->d_err);
+  dfree(h->U64); dfree(h->U32); dfree(h->Ainv); dfree(h->Ainv32); dfree(h->d_err); dfree(h->d_sync);
   dfree(h->V); dfree(h->Z64); dfree(h->Z32); dfree(h->v32); dfree(h->w); dfree(h->res);
   dfree(h->partial); dfree(h->d_h); dfree(h->d_inv); dfree(h->d_flag); dfree(h->d_y); dfree(h->d_tickets); dfree(h->d_npart);
   dfree(h->d_diag64); dfree(h->d_inv64); dfree(h->d_inv32);
@@ -754,6 +822,8 @@ int do_setup(amamg_ctx* h, const void* Uin, cudaStream_t st) {
   CKS(dalloc(h, &h->U32, nl));
   CKS(dalloc(h, &h->d_err, 1));
   CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+  CKS(dalloc(h, &h->d_sync, 3));
+  CK(cudaMemsetAsync(h->d_sync, 0, 3 * sizeof(unsigned), st));
   CK(cudaMemcpyAsync(h->U64, Uin, nl * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   CKS(launch(h, "setup_cast_links", nl * 24.0, st,
              [&] { return launch_cast<double2, float2>(h->U64, h->U32, (long)nl, st); }));
@@ -793,18 +863,18 @@ int do_setup(amamg_ctx* h, const void* Uin, cudaStream_t st) {
       CKS(dalloc(h, &C.Dinv64, 4 * (size_t)C.n));
       CKS(dalloc(h, &C.Dinv32, 4 * (size_t)C.n));
       CKS(launch(h, "setup_diag_inv", 0.0, st, [&] { return launch_diag_inv(C.B64, C.n, C.Dinv64, C.Dinv32, h->d_err, st); }));
-      const size_t nb = (size_t)(C.off.K - 1) * C.n;      // 16 colours x (K-1) offsets x n/16 sites
+      C.ncol = gs_colours(C);
+      const size_t nb = (size_t)(C.off.K - 1) * C.n;      // ncol colours x (K-1) offsets x n/ncol sites
       CKS(dalloc(h, &C.Bc64, 4 * nb));
       CKS(dalloc(h, &C.Bc16, 4 * nb));
       CKS(dalloc(h, &C.Bcs, nb));
       CKS(dalloc(h, &C.Dc64, 4 * (size_t)C.n));
       CKS(dalloc(h, &C.Dc32, 4 * (size_t)C.n));
       CKS(launch(h, "setup_pack", 0.0, st, [&] {
-        return launch_pack_colour_major(C.B64, C.B16, C.Bs, C.Dinv64, C.Dinv32, C.off.K, C.Nt, C.Nx, C.Bc64, C.Bc16,
-                                        C.Bcs, C.Dc64, C.Dc32, st);
+        return launch_pack_colour_major(C.B64, C.B16, C.Bs, C.Dinv64, C.Dinv32, C.off.K, C.Nt, C.Nx, C.ncol, C.Bc64,
+                                        C.Bc16, C.Bcs, C.Dc64, C.Dc32, st);
       }));
-      C.dsmem64 = dsmem_sweeps_possible<double, double2>(C.n, C.off.K, false);
-      C.dsmem32 = dsmem_sweeps_possible<float, __half2>(C.n, C.off.K, dsmem_blocks_in_smem<float>(C.n, C.off.K));
+      choose_gs_kernels(C);
     }
   }
   // coarsest: dense matrix and its Gauss-Jordan inverse
@@ -1010,6 +1080,7 @@ int amamg_batch_cycle(amamg_batch_handle b, void* stream, amamg_slot_info* info)
     MassGuard guard(h);
     rc = fgmres_cycle(h, b->B, b->X, R, h->ws, b->sl, &left);
   }
+  if (rc == AMAMG_OK) rc = check_grid_sync(h, h->ws);
   CK(cudaEventRecord(h->ev_out, h->ws));
   CK(cudaStreamWaitEvent(st, h->ev_out, 0));
   CK(cudaStreamSynchronize(st));

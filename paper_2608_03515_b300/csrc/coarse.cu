@@ -1,5 +1,6 @@
 // Coarse-level kernels: the Galerkin operator A_l = P^H A_{l-1} P in block-stencil
-// form, its 16-colour block Gauss-Seidel smoother, and the coarsest direct solve.
+// form, its multicolour block Gauss-Seidel smoother (8 or 16 colours, see
+// colour_site), and the coarsest direct solve.
 //
 // A_l is stored as K blocks of 2x2 complex per coarse site, [K][4][n] (entry
 // 2 alpha + beta, site-major within an entry plane, so consecutive threads read
@@ -60,9 +61,8 @@ k_coarse_apply(const typename cplx<T>::type* __restrict__ in, typename cplx<T>::
 }
 
 // Colour-major copies of a smoothed level's operator (built in setup): for
-// colour c (sites (t, x) with (t mod 4, x mod 4) = (c / 4, c % 4)), site j of the
-// colour (t = 4 (j / (Nx/4)) + c / 4, x = 4 (j % (Nx/4)) + c % 4, m = n / 16 sites)
-// and off-diagonal offset k = 1..K-1:
+// colour c, site j of the colour (colour_site / site_colour below, m = n / ncol
+// sites per colour) and off-diagonal offset k = 1..K-1:
 //   Bc[((c (K-1) + k - 1) m + j) 4 + e]   the 2x2 block entries e = 2 alpha + beta,
 //   Sc[(c (K-1) + k - 1) m + j]           its FP32 scale (FP16 copy only),
 //   Dc[(c m + j) 4 + e]                    the inverse of the diagonal block.
@@ -102,16 +102,15 @@ __device__ __forceinline__ void gs_site(typename cplx<T>::type* __restrict__ e0,
                                         const typename cplx<T>::type* __restrict__ r0,
                                         const BT* __restrict__ Bc, const float* __restrict__ Sc,
                                         const typename cplx<T>::type* __restrict__ Dc, const Offsets& off,
-                                        int Nt, int Nx, int colour, int j, int g, bool valid) {
+                                        int Nt, int Nx, int ncol, int colour, int j, int g, bool valid) {
   // every lane of the warp calls this (the shuffles need all 32); lanes of
   // groups without a site pass valid = false and only take part in the shuffles
   using C = typename cplx<T>::type;
   const int n = Nt * Nx;
-  const int m = n >> 4;
-  const int qx = Nx >> 2;
-  const int ti = valid ? j / qx : 0;
-  const int t = 4 * ti + (colour >> 2);
-  const int x = valid ? 4 * (j - ti * qx) + (colour & 3) : 0;
+  const int m = n / ncol;
+  if (!valid) j = 0;
+  int t, x;
+  colour_site(ncol, colour, j, Nx, t, x);
   const int v = t * Nx + x;
   const int K1 = off.K - 1;
   C rv0 = czero<C>(), rv1 = czero<C>(), d[4] = {czero<C>(), czero<C>(), czero<C>(), czero<C>()};
@@ -167,21 +166,21 @@ __device__ __forceinline__ void gs_site(typename cplx<T>::type* __restrict__ e0,
 template <typename T> struct GsLanes { static constexpr int value = 32; };
 template <> struct GsLanes<double> { static constexpr int value = 8; };
 
-// One colour of the 16-colour sweep, sites (t, x) with (t mod 4, x mod 4) =
-// (c / 4, c % 4); LPS lanes per site.
+// One colour of the multicolour sweep (sites of colour c as colour_site maps
+// them); LPS lanes per site.
 template <typename T, typename BT>
 __global__ void __launch_bounds__(256)
 k_coarse_colour(typename cplx<T>::type* __restrict__ e, const typename cplx<T>::type* __restrict__ r,
                 const BT* __restrict__ B, const float* __restrict__ Bs,
-                const typename cplx<T>::type* __restrict__ Dinv, Offsets off, int Nt, int Nx, int colour) {
+                const typename cplx<T>::type* __restrict__ Dinv, Offsets off, int Nt, int Nx, int ncol, int colour) {
   constexpr int LPS = GsLanes<T>::value;
   const int n = Nt * Nx;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int idx = tid / LPS;
   const int g = tid & (LPS - 1);
-  const bool valid = idx < (n >> 4);
+  const bool valid = idx < n / ncol;
   const size_t roff = (size_t)blockIdx.y * 2 * n;
-  gs_site<T, BT, LPS, false>(e + roff, r + roff, B, Bs, Dinv, off, Nt, Nx, colour, idx, g, valid);
+  gs_site<T, BT, LPS, false>(e + roff, r + roff, B, Bs, Dinv, off, Nt, Nx, ncol, colour, idx, g, valid);
 }
 
 // All colours of `sweeps` sweeps in one launch: one thread block cluster per
@@ -191,11 +190,12 @@ template <typename T, typename BT>
 __global__ void __launch_bounds__(1024)
 k_coarse_sweeps_cluster(typename cplx<T>::type* __restrict__ e, const typename cplx<T>::type* __restrict__ r,
                         const BT* __restrict__ B, const float* __restrict__ Bs,
-                        const typename cplx<T>::type* __restrict__ Dinv, Offsets off, int Nt, int Nx, int sweeps) {
+                        const typename cplx<T>::type* __restrict__ Dinv, Offsets off, int Nt, int Nx, int ncol,
+                        int sweeps) {
   constexpr int LPS = GsLanes<T>::value;
   cg::cluster_group cluster = cg::this_cluster();
   const int n = Nt * Nx;
-    const int per_colour = n >> 4;
+  const int per_colour = n / ncol;
   const int rank = (int)cluster.block_rank();
   const int csize = (int)cluster.num_blocks();
   const int rhs = blockIdx.x / csize;
@@ -204,14 +204,87 @@ k_coarse_sweeps_cluster(typename cplx<T>::type* __restrict__ e, const typename c
   const int gpb = blockDim.x / LPS;
   const int stride = csize * gpb;
   for (int sw = 0; sw < sweeps; ++sw) {
-    for (int colour = 0; colour < 16; ++colour) {
+    for (int colour = 0; colour < ncol; ++colour) {
       // every group runs the same number of iterations (shuffles stay converged)
       for (int base = 0; base < per_colour; base += stride) {
         const int idx = base + rank * gpb + threadIdx.x / LPS;
         const bool valid = idx < per_colour;
-        gs_site<T, BT, LPS, false>(e + roff, r + roff, B, Bs, Dinv, off, Nt, Nx, colour, idx, g, valid);
+        gs_site<T, BT, LPS, false>(e + roff, r + roff, B, Bs, Dinv, off, Nt, Nx, ncol, colour, idx, g, valid);
       }
       cluster.sync();
+    }
+  }
+}
+
+// Software barrier over all blocks of a cooperative launch (co-residency is
+// guaranteed by the launch).  sync = {arrival count, generation, error}: a
+// block's thread 0 reads the generation, arrives, and either (last arrival)
+// resets the count and advances the generation or waits for it to advance,
+// at most GRID_SPIN_LIMIT polls (about a second); on time-out it records the
+// error and the block returns false (its caller stops).  The fences order the
+// block's global stores before its arrival and the other blocks' stores before
+// its reads (which go through L2).
+constexpr unsigned GRID_SPIN_LIMIT = 1u << 23;
+__device__ __forceinline__ bool grid_barrier(unsigned* sync, unsigned nblocks) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = sync + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    ok = 1;
+    if (atomicAdd(sync, 1u) == nblocks - 1) {
+      sync[0] = 0;
+      __threadfence();
+      atomicExch(sync + 1, g + 1);
+    } else {
+      unsigned it = 0;
+      while (*gen == g) {
+        if (++it == GRID_SPIN_LIMIT) {
+          atomicExch(sync + 2, 1u);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// All colours of `sweeps` sweeps in one cooperative launch spread over the
+// whole GPU: work units (right-hand side, site of the colour) are dealt to
+// groups of LPS lanes across all blocks, the colour phases are separated by
+// grid_barrier.  Same arithmetic per site as k_coarse_colour.  For FP64, whose
+// pipe is narrow on this GPU, this spreads a colour over every SM instead of
+// the 16 SMs of one cluster.
+template <typename T, typename BT>
+__global__ void __launch_bounds__(256)
+k_coarse_sweeps_grid(typename cplx<T>::type* __restrict__ e, const typename cplx<T>::type* __restrict__ r,
+                     const BT* __restrict__ B, const float* __restrict__ Bs,
+                     const typename cplx<T>::type* __restrict__ Dinv, Offsets off, int Nt, int Nx, int ncol,
+                     int sweeps, int R, unsigned* sync) {
+  constexpr int LPS = GsLanes<T>::value;
+  const int n = Nt * Nx;
+  const int per_colour = n / ncol;
+  const long units = (long)R * per_colour;
+  const int g = threadIdx.x & (LPS - 1);
+  const int gpb = blockDim.x / LPS;
+  const long stride = (long)gridDim.x * gpb;
+  for (int sw = 0; sw < sweeps; ++sw) {
+    for (int colour = 0; colour < ncol; ++colour) {
+      // every group runs the same number of iterations (shuffles stay converged)
+      for (long base = 0; base < units; base += stride) {
+        const long u = base + (long)blockIdx.x * gpb + threadIdx.x / LPS;
+        const bool valid = u < units;
+        const int rhs = valid ? (int)(u / per_colour) : 0;
+        const int idx = valid ? (int)(u - (long)rhs * per_colour) : 0;
+        const size_t roff = (size_t)rhs * 2 * n;
+        gs_site<T, BT, LPS, false>(e + roff, r + roff, B, Bs, Dinv, off, Nt, Nx, ncol, colour, idx, g, valid);
+      }
+      if (!grid_barrier(sync, gridDim.x)) return;
     }
   }
 }
@@ -219,7 +292,7 @@ k_coarse_sweeps_cluster(typename cplx<T>::type* __restrict__ e, const typename c
 // All colours of `sweeps` sweeps in one launch on a 16-block thread-block
 // cluster per right-hand side, the level distributed over the cluster's shared
 // memory.  Block q of the cluster owns sites j in [q per, (q+1) per) of every
-// colour (per = n / 256): it keeps their e, r and diagonal inverses (and, with
+// colour (per = n / (16 ncol)): it keeps their e, r and diagonal inverses (and, with
 // BSMEM, their off-diagonal blocks) in its shared memory for the whole launch.
 // A colour phase reads neighbour values from the owning blocks' shared memory
 // (distributed shared memory), writes its own sites locally, and ends with a
@@ -228,34 +301,38 @@ template <typename T, typename BT, bool BSMEM>
 __global__ void __launch_bounds__(512)
 k_coarse_sweeps_dsmem(typename cplx<T>::type* __restrict__ e, const typename cplx<T>::type* __restrict__ r,
                       const BT* __restrict__ Bc, const float* __restrict__ Sc,
-                      const typename cplx<T>::type* __restrict__ Dc, Offsets off, int Nt, int Nx, int sweeps) {
+                      const typename cplx<T>::type* __restrict__ Dc, Offsets off, int Nt, int Nx, int ncol,
+                      int sweeps) {
   using C = typename cplx<T>::type;
   constexpr int LPS = 8;
   constexpr int IT = (GS_MAX_OFFDIAG + LPS - 1) / LPS;
   cg::cluster_group cluster = cg::this_cluster();
   const int q = (int)cluster.block_rank();
   const int rhs = blockIdx.x / DSMEM_CLUSTER;
-  const int n = Nt * Nx, m = n >> 4, qx = Nx >> 2, per = m / DSMEM_CLUSTER, K1 = off.K - 1;
+  const int n = Nt * Nx, m = n / ncol, per = m / DSMEM_CLUSTER, K1 = off.K - 1;
+  const int own = ncol * per;                             // sites this block owns (n / 16)
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* es = reinterpret_cast<C*>(smem_raw);                 // [16 colours][per][2]
-  C* rs = es + 32 * per;                                  // [16][per][2]
-  C* ds = rs + 32 * per;                                  // [16][per][4]
-  BT* bs = reinterpret_cast<BT*>(ds + 64 * per);          // [16][K1][per][4]      (BSMEM)
-  float* ss = reinterpret_cast<float*>(bs + (BSMEM ? 64 * K1 * per : 0));   // [16][K1][per]  (BSMEM, FP16)
+  C* es = reinterpret_cast<C*>(smem_raw);                 // [ncol colours][per][2]
+  C* rs = es + 2 * own;                                   // [ncol][per][2]
+  C* ds = rs + 2 * own;                                   // [ncol][per][4]
+  BT* bs = reinterpret_cast<BT*>(ds + 4 * own);           // [ncol][K1][per][4]      (BSMEM)
+  float* ss = reinterpret_cast<float*>(bs + (BSMEM ? 4 * K1 * own : 0));   // [ncol][K1][per]  (BSMEM, FP16)
   const size_t roff = (size_t)rhs * 2 * n;
   C* e0 = e + roff;
   const C* r0 = r + roff;
   // load this block's part of the level
-  for (int i = threadIdx.x; i < 16 * per; i += blockDim.x) {
+  for (int i = threadIdx.x; i < own; i += blockDim.x) {
     const int c = i / per, jj = i - (i / per) * per, j = q * per + jj;
-    const int t = 4 * (j / qx) + (c >> 2), x = 4 * (j % qx) + (c & 3), v = t * Nx + x;
+    int t, x;
+    colour_site(ncol, c, j, Nx, t, x);
+    const int v = t * Nx + x;
     es[2 * i] = e0[v]; es[2 * i + 1] = e0[n + v];
     rs[2 * i] = r0[v]; rs[2 * i + 1] = r0[n + v];
 #pragma unroll
     for (int d = 0; d < 4; ++d) ds[4 * i + d] = Dc[((size_t)c * m + j) * 4 + d];
   }
   if constexpr (BSMEM) {
-    for (int i = threadIdx.x; i < 16 * K1 * per; i += blockDim.x) {
+    for (int i = threadIdx.x; i < K1 * own; i += blockDim.x) {
       const int ck = i / per, jj = i - (i / per) * per;               // ck = c K1 + (k - 1)
       const size_t src = (size_t)ck * m + q * per + jj;
 #pragma unroll
@@ -267,12 +344,13 @@ k_coarse_sweeps_dsmem(typename cplx<T>::type* __restrict__ e, const typename cpl
   const int g = threadIdx.x & (LPS - 1);
   const int groups = blockDim.x / LPS;
   for (int sw = 0; sw < sweeps; ++sw) {
-    for (int colour = 0; colour < 16; ++colour) {
+    for (int colour = 0; colour < ncol; ++colour) {
       for (int base = 0; base < per; base += groups) {
         const int jj = base + threadIdx.x / LPS;
         const bool valid = jj < per;
         const int j = q * per + (valid ? jj : 0);
-        const int t = 4 * (j / qx) + (colour >> 2), x = 4 * (j % qx) + (colour & 3);
+        int t, x;
+        colour_site(ncol, colour, j, Nx, t, x);
         C xv[IT][2], bb[IT][4];
 #pragma unroll
         for (int it = 0; it < IT; ++it) {
@@ -280,8 +358,8 @@ k_coarse_sweeps_dsmem(typename cplx<T>::type* __restrict__ e, const typename cpl
           if (valid && k < off.K) {
             int tw = t + off.dt[k]; tw -= (tw >= Nt) ? Nt : 0;
             int xw = x + off.dx[k]; xw -= (xw >= Nx) ? Nx : 0;
-            const int cw = ((tw & 3) << 2) | (xw & 3);
-            const int jw = (tw >> 2) * qx + (xw >> 2);
+            int cw, jw;
+            site_colour(ncol, tw, xw, Nx, cw, jw);
             const int qw = jw / per, jjw = jw - qw * per;
             const C* rem = cluster.map_shared_rank(es, qw);
             xv[it][0] = rem[2 * (cw * per + jjw)];
@@ -329,9 +407,11 @@ k_coarse_sweeps_dsmem(typename cplx<T>::type* __restrict__ e, const typename cpl
     }
   }
   // write this block's sites back (no block reads remote shared memory after the last barrier)
-  for (int i = threadIdx.x; i < 16 * per; i += blockDim.x) {
+  for (int i = threadIdx.x; i < own; i += blockDim.x) {
     const int c = i / per, jj = i - (i / per) * per, j = q * per + jj;
-    const int t = 4 * (j / qx) + (c >> 2), x = 4 * (j % qx) + (c & 3), v = t * Nx + x;
+    int t, x;
+    colour_site(ncol, c, j, Nx, t, x);
+    const int v = t * Nx + x;
     e0[v] = es[2 * i];
     e0[n + v] = es[2 * i + 1];
   }
@@ -432,17 +512,17 @@ cudaError_t launch_coarse_apply(const typename cplx<T>::type* in, typename cplx<
 template <typename T, typename BT>
 cudaError_t launch_coarse_colour(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* B,
                                  const float* Bs, const typename cplx<T>::type* Dinv, const Offsets& off,
-                                 int Nt, int Nx, int colour, int R, cudaStream_t st) {
-  const long threads = (long)(Nt * Nx / 16) * GsLanes<T>::value;
+                                 int Nt, int Nx, int ncol, int colour, int R, cudaStream_t st) {
+  const long threads = (long)(Nt * Nx / ncol) * GsLanes<T>::value;
   const int bs = sizeof(T) == 8 ? 32 : 256;      // FP64: spread the colour over many SMs
   dim3 grid((unsigned)((threads + bs - 1) / bs), R);
-  k_coarse_colour<T, BT><<<grid, bs, 0, st>>>(e, r, B, Bs, Dinv, off, Nt, Nx, colour);
+  k_coarse_colour<T, BT><<<grid, bs, 0, st>>>(e, r, B, Bs, Dinv, off, Nt, Nx, ncol, colour);
   return cudaGetLastError();
 }
 
-int cluster_sweep_threads(int n) {
+int cluster_sweep_threads(int n, int ncol) {
   // FP32 sweep: 32 lanes per site, at most 16 sites per warp and colour
-  const long per_colour = n / 16;
+  const long per_colour = n / ncol;
   long warps = (per_colour + CLUSTER_BLOCKS - 1) / CLUSTER_BLOCKS;
   if (warps > 32) {
     if (per_colour > (long)CLUSTER_BLOCKS * 32 * 16) return 1 << 30;   // too large: per-colour launches
@@ -454,8 +534,8 @@ int cluster_sweep_threads(int n) {
 template <typename T, typename BT>
 cudaError_t launch_coarse_sweeps_cluster(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* B,
                                          const float* Bs, const typename cplx<T>::type* Dinv, const Offsets& off,
-                                         int Nt, int Nx, int sweeps, int R, cudaStream_t st) {
-  const int bs = cluster_sweep_threads(Nt * Nx);
+                                         int Nt, int Nx, int ncol, int sweeps, int R, cudaStream_t st) {
+  const int bs = cluster_sweep_threads(Nt * Nx, ncol);
   if (bs > 1024) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CLUSTER_BLOCKS * R);
@@ -469,22 +549,75 @@ cudaError_t launch_coarse_sweeps_cluster(typename cplx<T>::type* e, const typena
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_coarse_sweeps_cluster<T, BT>, e, r, B, Bs, Dinv, off, Nt, Nx, sweeps);
+  return cudaLaunchKernelEx(&cfg, k_coarse_sweeps_cluster<T, BT>, e, r, B, Bs, Dinv, off, Nt, Nx, ncol, sweeps);
 }
 
 size_t dsmem_sweep_bytes(int n, int K, size_t cbytes, bool bsmem, size_t bt_bytes) {
-  const size_t per = (size_t)n / 256;
-  size_t b = per * 16 * (2 + 2 + 4) * cbytes;
-  if (bsmem) b += per * 16 * (K - 1) * (4 * bt_bytes + 4);
+  const size_t own = (size_t)n / DSMEM_CLUSTER;            // sites per block
+  size_t b = own * (2 + 2 + 4) * cbytes;
+  if (bsmem) b += own * (K - 1) * (4 * bt_bytes + 4);
   return b;
+}
+
+// Grid sweep: 64 threads per block (8 FP64 sites or 2 FP32 sites per block and
+// pass), as many blocks as the widest colour needs, at most the blocks that
+// can be co-resident (cooperative launch).
+constexpr int GRID_SWEEP_THREADS = 64;
+template <typename T, typename BT>
+int grid_sweep_blocks(int n, int ncol, int R) {
+  static int cap[2] = {-1, -1};                       // per element type, first device queried
+  int& c = cap[sizeof(T) == 8 ? 1 : 0];
+  if (c < 0) {
+    int dev = 0, sms = 0, occ = 0, coop = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_coarse_sweeps_grid<T, BT>, GRID_SWEEP_THREADS, 0) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      c = 0;
+    } else {
+      c = coop ? sms * occ : 0;
+    }
+  }
+  if (c <= 0) return 0;
+  const long groups = (long)R * (n / ncol);
+  const long want = (groups * GsLanes<T>::value + GRID_SWEEP_THREADS - 1) / GRID_SWEEP_THREADS;
+  return (int)(want < c ? want : c);
+}
+
+template <typename T, typename BT>
+cudaError_t launch_coarse_sweeps_grid(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* B,
+                                      const float* Bs, const typename cplx<T>::type* Dinv, const Offsets& off,
+                                      int Nt, int Nx, int ncol, int sweeps, int R, unsigned* sync, cudaStream_t st) {
+  const int nb = grid_sweep_blocks<T, BT>(Nt * Nx, ncol, R);
+  if (nb <= 0) return cudaErrorNotSupported;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nb);
+  cfg.blockDim = dim3(GRID_SWEEP_THREADS);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_coarse_sweeps_grid<T, BT>, e, r, B, Bs, Dinv, off, Nt, Nx, ncol, sweeps, R, sync);
+}
+
+// the distributed-shared-memory sweep needs per = n / (16 ncol) whole sites per
+// block and colour, at most 64
+static bool dsmem_shape_ok(int n, int ncol) {
+  const int m = n / ncol;
+  return n % ncol == 0 && m % DSMEM_CLUSTER == 0 && m / DSMEM_CLUSTER >= 1 && m / DSMEM_CLUSTER <= 64;
 }
 
 // Whether a 16-block cluster with this shared-memory size can be resident on
 // the device (queried once per level in setup; the sweep falls back to the
 // per-colour kernels otherwise).
 template <typename T, typename BT>
-bool dsmem_sweeps_possible(int n, int K, bool bsmem) {
-  if (n % 256 || n / 256 > 64) return false;
+bool dsmem_sweeps_possible(int n, int K, int ncol, bool bsmem) {
+  if (!dsmem_shape_ok(n, ncol)) return false;
   const size_t smem = dsmem_sweep_bytes(n, K, sizeof(typename cplx<T>::type), bsmem, sizeof(BT));
   if (smem > 200 * 1024) return false;
   auto kern = bsmem ? k_coarse_sweeps_dsmem<T, BT, true> : k_coarse_sweeps_dsmem<T, BT, false>;
@@ -493,7 +626,7 @@ bool dsmem_sweeps_possible(int n, int K, bool bsmem) {
     cudaGetLastError();
     return false;
   }
-  const int per = n / 256;
+  const int per = n / ncol / DSMEM_CLUSTER;
   int threads = ((per * 8 + 31) / 32) * 32;
   threads = threads > 512 ? 512 : threads;
   cudaLaunchConfig_t cfg = {};
@@ -518,16 +651,16 @@ bool dsmem_sweeps_possible(int n, int K, bool bsmem) {
 template <typename T, typename BT>
 cudaError_t launch_coarse_sweeps_dsmem(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* Bc,
                                        const float* Sc, const typename cplx<T>::type* Dc, const Offsets& off,
-                                       int Nt, int Nx, int sweeps, int R, bool bsmem, cudaStream_t st) {
+                                       int Nt, int Nx, int ncol, int sweeps, int R, bool bsmem, cudaStream_t st) {
   const int n = Nt * Nx;
-  if (n % 256 || n / 256 > 64) return cudaErrorInvalidValue;
+  if (!dsmem_shape_ok(n, ncol)) return cudaErrorInvalidValue;
   const size_t smem = dsmem_sweep_bytes(n, off.K, sizeof(typename cplx<T>::type), bsmem, sizeof(BT));
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   auto kern = bsmem ? k_coarse_sweeps_dsmem<T, BT, true> : k_coarse_sweeps_dsmem<T, BT, false>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (err == cudaSuccess) err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  const int per = n / 256;
+  const int per = n / ncol / DSMEM_CLUSTER;
   int threads = ((per * 8 + 31) / 32) * 32;
   threads = threads > 512 ? 512 : threads;
   cudaLaunchConfig_t cfg = {};
@@ -542,7 +675,7 @@ cudaError_t launch_coarse_sweeps_dsmem(typename cplx<T>::type* e, const typename
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, e, r, Bc, Sc, Dc, off, Nt, Nx, sweeps);
+  return cudaLaunchKernelEx(&cfg, kern, e, r, Bc, Sc, Dc, off, Nt, Nx, ncol, sweeps);
 }
 
 template <typename Cv>
@@ -583,21 +716,29 @@ template cudaError_t launch_coarse_apply<double, double2>(const double2*, double
 template cudaError_t launch_coarse_apply<float, __half2>(const float2*, float2*, const float2*, const __half2*,
                                                          const float*, const Offsets&, int, int, int, cudaStream_t);
 template cudaError_t launch_coarse_colour<double, double2>(double2*, const double2*, const double2*, const float*,
-                                                           const double2*, const Offsets&, int, int, int, int,
+                                                           const double2*, const Offsets&, int, int, int, int, int,
                                                            cudaStream_t);
 template cudaError_t launch_coarse_colour<float, __half2>(float2*, const float2*, const __half2*, const float*,
-                                                          const float2*, const Offsets&, int, int, int, int,
+                                                          const float2*, const Offsets&, int, int, int, int, int,
                                                           cudaStream_t);
 template cudaError_t launch_coarse_sweeps_cluster<float, __half2>(float2*, const float2*, const __half2*, const float*,
                                                                   const float2*, const Offsets&, int, int, int, int,
-                                                                  cudaStream_t);
-template bool dsmem_sweeps_possible<float, __half2>(int, int, bool);
-template bool dsmem_sweeps_possible<double, double2>(int, int, bool);
+                                                                  int, cudaStream_t);
+template int grid_sweep_blocks<double, double2>(int, int, int);
+template int grid_sweep_blocks<float, __half2>(int, int, int);
+template cudaError_t launch_coarse_sweeps_grid<double, double2>(double2*, const double2*, const double2*, const float*,
+                                                                const double2*, const Offsets&, int, int, int, int,
+                                                                int, unsigned*, cudaStream_t);
+template cudaError_t launch_coarse_sweeps_grid<float, __half2>(float2*, const float2*, const __half2*, const float*,
+                                                               const float2*, const Offsets&, int, int, int, int,
+                                                               int, unsigned*, cudaStream_t);
+template bool dsmem_sweeps_possible<float, __half2>(int, int, int, bool);
+template bool dsmem_sweeps_possible<double, double2>(int, int, int, bool);
 template cudaError_t launch_coarse_sweeps_dsmem<float, __half2>(float2*, const float2*, const __half2*, const float*,
-                                                                const float2*, const Offsets&, int, int, int, int, bool,
-                                                                cudaStream_t);
+                                                                const float2*, const Offsets&, int, int, int, int, int,
+                                                                bool, cudaStream_t);
 template cudaError_t launch_coarse_sweeps_dsmem<double, double2>(double2*, const double2*, const double2*,
                                                                  const float*, const double2*, const Offsets&, int, int,
-                                                                 int, int, bool, cudaStream_t);
+                                                                 int, int, int, bool, cudaStream_t);
 template cudaError_t launch_dense_gemv<double2>(const double2*, const double2*, double2*, int, int, cudaStream_t);
 template cudaError_t launch_dense_gemv<float2>(const double2*, const float2*, float2*, int, int, cudaStream_t);

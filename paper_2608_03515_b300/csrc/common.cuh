@@ -84,3 +84,29 @@ struct Offsets {
 };
 
 __host__ __device__ __forceinline__ int wrap(int v, int n) { v %= n; return v < 0 ? v + n : v; }
+
+// Gauss-Seidel colourings of a coarse level (Sec. 5 leaves the ordering open):
+// site (t, x) of site j of colour c, and the inverse map.  ncol = 16: colour
+// (t mod 4, x mod 4), j = (t / 4) (Nx / 4) + x / 4.  ncol = 8: colour
+// (t + 3 x) mod 8, j = t (Nx / 8) + x / 8 (one x per row and colour, since 3 is
+// invertible mod 8: x = 3 (c - t) mod 8).
+__host__ __device__ __forceinline__ void colour_site(int ncol, int c, int j, int Nx, int& t, int& x) {
+  if (ncol == 16) {
+    const int qx = Nx >> 2;
+    t = 4 * (j / qx) + (c >> 2);
+    x = 4 * (j % qx) + (c & 3);
+  } else {
+    const int ox = Nx >> 3;
+    t = j / ox;
+    x = 8 * (j % ox) + ((3 * (c - t)) & 7);
+  }
+}
+__host__ __device__ __forceinline__ void site_colour(int ncol, int t, int x, int Nx, int& c, int& j) {
+  if (ncol == 16) {
+    c = ((t & 3) << 2) | (x & 3);
+    j = (t >> 2) * (Nx >> 2) + (x >> 2);
+  } else {
+    c = (t + 3 * x) & 7;
+    j = t * (Nx >> 3) + (x >> 3);
+  }
+}

@@ -17,8 +17,12 @@ struct Level {
   float* Bs = nullptr;
   double2* Dinv64 = nullptr;
   float2* Dinv32 = nullptr;
-  // the distributed-shared-memory cluster sweep can run on this level (FP64, FP32)
-  bool dsmem64 = false, dsmem32 = false;
+  // Gauss-Seidel colours of a smoothed coarse level: 8 ((t + 3x) mod 8) where no
+  // coupling joins two sites of one such colour, else 16 ((t mod 4, x mod 4))
+  int ncol = 16;
+  // coarse Gauss-Seidel kernel of this level in FP64 and in FP32 (GsKernel),
+  // chosen in setup
+  int gs64 = 0, gs32 = 0;
   // colour-major copies for the Gauss-Seidel kernels (smoothed coarse levels)
   double2* Bc64 = nullptr;
   __half2* Bc16 = nullptr;
@@ -79,6 +83,12 @@ struct OuterState {
   }
 };
 
+// Coarse Gauss-Seidel kernels (identical arithmetic per site): one launch per
+// colour; all phases on an 8-block cluster with e in L2; all phases on a
+// 16-block cluster with the level in distributed shared memory; all phases in
+// one cooperative launch over the whole GPU with a software grid barrier.
+enum GsKernel : int { GS_COLOUR = 0, GS_CLUSTER = 1, GS_DSMEM = 2, GS_GRID = 3 };
+
 struct amamg_ctx {
   amamg_params prm{};
   int Nt = 0, Nx = 0;
@@ -90,6 +100,7 @@ struct amamg_ctx {
   float2* Ainv32 = nullptr;  // its FP32 rounding, applied by the mixed-precision V-cycle
   int nd = 0;
   int* d_err = nullptr;
+  unsigned* d_sync = nullptr;   // grid barrier of the grid Gauss-Seidel sweep: count, generation, time-out flag
 
   // solver workspace
   int Rcap = 0;              // V-cycle work vectors

@@ -42,16 +42,26 @@ cudaError_t launch_coarse_apply(const typename cplx<T>::type* in, typename cplx<
 template <typename T, typename BT>
 cudaError_t launch_coarse_colour(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* B,
                                  const float* Bs, const typename cplx<T>::type* Dinv, const Offsets& off, int Nt,
-                                 int Nx, int colour, int R, cudaStream_t st);
+                                 int Nx, int ncol, int colour, int R, cudaStream_t st);
 // all colours of `sweeps` sweeps in one launch, one 8-block cluster per RHS;
-// usable while n / 16 <= 8 * 1024 sites per colour
+// usable while n / ncol <= 8 * 1024 sites per colour
 constexpr int CLUSTER_BLOCKS = 8;
-int cluster_sweep_threads(int n);
+int cluster_sweep_threads(int n, int ncol);
 template <typename T, typename BT>
 cudaError_t launch_coarse_sweeps_cluster(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* B,
                                          const float* Bs, const typename cplx<T>::type* Dinv, const Offsets& off,
-                                         int Nt, int Nx, int sweeps, int R, cudaStream_t st);
-// Coarse Gauss-Seidel kernel choice.  Levels with n = 256 per sites (per <= 64)
+                                         int Nt, int Nx, int ncol, int sweeps, int R, cudaStream_t st);
+// all colours of `sweeps` sweeps in one cooperative launch over the whole GPU,
+// colour phases separated by a bounded software grid barrier on
+// sync[0..2] = {count, generation, error} (zeroed before first use; a time-out
+// sets sync[2]); grid_sweep_blocks = 0 when cooperative launches are unavailable
+template <typename T, typename BT>
+int grid_sweep_blocks(int n, int ncol, int R);
+template <typename T, typename BT>
+cudaError_t launch_coarse_sweeps_grid(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* B,
+                                      const float* Bs, const typename cplx<T>::type* Dinv, const Offsets& off,
+                                      int Nt, int Nx, int ncol, int sweeps, int R, unsigned* sync, cudaStream_t st);
+// Coarse Gauss-Seidel kernel choice.  Levels with n = 16 ncol per sites (per <= 64)
 // run all colours on one 16-block cluster with the level in distributed shared
 // memory; in FP32 also the off-diagonal blocks live in shared memory when they
 // fit (n <= 8192).  Other FP32 levels use the L2-based clustered sweep, other
@@ -59,19 +69,19 @@ cudaError_t launch_coarse_sweeps_cluster(typename cplx<T>::type* e, const typena
 constexpr int DSMEM_CLUSTER = 16;
 size_t dsmem_sweep_bytes(int n, int K, size_t cbytes, bool bsmem, size_t bt_bytes);
 template <typename T, typename BT>
-bool dsmem_sweeps_possible(int n, int K, bool bsmem);
+bool dsmem_sweeps_possible(int n, int K, int ncol, bool bsmem);
 template <typename T>
 inline bool dsmem_blocks_in_smem(int n, int K) {
   return sizeof(T) == 4 && dsmem_sweep_bytes(n, K, 8, true, 4) <= 200 * 1024;
 }
 template <typename T>
-inline bool use_cluster_sweeps(int n) {
-  return sizeof(T) == 4 && cluster_sweep_threads(n) <= 1024;
+inline bool use_cluster_sweeps(int n, int ncol) {
+  return sizeof(T) == 4 && cluster_sweep_threads(n, ncol) <= 1024;
 }
 template <typename T, typename BT>
 cudaError_t launch_coarse_sweeps_dsmem(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* Bc,
                                        const float* Sc, const typename cplx<T>::type* Dc, const Offsets& off,
-                                       int Nt, int Nx, int sweeps, int R, bool bsmem, cudaStream_t st);
+                                       int Nt, int Nx, int ncol, int sweeps, int R, bool bsmem, cudaStream_t st);
 template <typename Cv>
 cudaError_t launch_dense_gemv(const double2* A, const Cv* x, Cv* y, int nd, int R, cudaStream_t st);
 cudaError_t launch_dense_gemv32(const float2* A, const float2* x, float2* y, int nd, int R, cudaStream_t st);
@@ -117,5 +127,5 @@ cudaError_t launch_gather_cols(const double2* X, double2* Y, const int* cols, in
 cudaError_t launch_pack_P16(const double2* P, int per_tile, int ntiles, __half2* P16, float* scale, cudaStream_t st);
 cudaError_t launch_pack_B16(const double2* B, int K, int n, __half2* B16, float* scale, cudaStream_t st);
 cudaError_t launch_pack_colour_major(const double2* B64, const __half2* B16, const float* Bs, const double2* D64,
-                                     const float2* D32, int K, int Nt, int Nx, double2* Bc64, __half2* Bc16,
+                                     const float2* D32, int K, int Nt, int Nx, int ncol, double2* Bc64, __half2* Bc16,
                                      float* Bcs, double2* Dc64, float2* Dc32, cudaStream_t st);

@@ -97,30 +97,42 @@ cudaError_t vcycle_level(amamg_ctx* h, int l, const typename cplx<T>::type* r, t
       }
     return cudaSuccess;
   }
-  if (sweeps > 0 && (f64 ? L.dsmem64 : L.dsmem32)) {
+  const int kind = f64 ? L.gs64 : L.gs32;
+  if (sweeps > 0 && kind == GS_DSMEM) {
     const bool bsm = dsmem_blocks_in_smem<T>(L.n, L.off.K);
     if constexpr (f64)
-      err = launch_coarse_sweeps_dsmem<double, double2>(e, r, L.Bc64, nullptr, L.Dc64, L.off, L.Nt, L.Nx, sweeps, R,
-                                                        bsm, st);
+      err = launch_coarse_sweeps_dsmem<double, double2>(e, r, L.Bc64, nullptr, L.Dc64, L.off, L.Nt, L.Nx, L.ncol,
+                                                        sweeps, R, bsm, st);
     else
-      err = launch_coarse_sweeps_dsmem<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, sweeps, R, bsm,
-                                                       st);
+      err = launch_coarse_sweeps_dsmem<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, L.ncol, sweeps,
+                                                       R, bsm, st);
+    h->launches++;
+    return err;
+  }
+  if (sweeps > 0 && kind == GS_GRID) {
+    if constexpr (f64)
+      err = launch_coarse_sweeps_grid<double, double2>(e, r, L.Bc64, nullptr, L.Dc64, L.off, L.Nt, L.Nx, L.ncol,
+                                                       sweeps, R, h->d_sync, st);
+    else
+      err = launch_coarse_sweeps_grid<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, L.ncol, sweeps,
+                                                      R, h->d_sync, st);
     h->launches++;
     return err;
   }
   if constexpr (!f64) {
-    if (sweeps > 0 && use_cluster_sweeps<T>(L.n)) {
-      err = launch_coarse_sweeps_cluster<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, sweeps, R, st);
+    if (sweeps > 0 && kind == GS_CLUSTER && use_cluster_sweeps<T>(L.n, L.ncol)) {
+      err = launch_coarse_sweeps_cluster<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, L.ncol, sweeps,
+                                                         R, st);
       h->launches++;
       return err;
     }
   }
   for (int s = 0; s < sweeps; ++s)
-    for (int c = 0; c < 16; ++c) {
+    for (int c = 0; c < L.ncol; ++c) {
       if constexpr (f64)
-        err = launch_coarse_colour<double, double2>(e, r, L.Bc64, nullptr, L.Dc64, L.off, L.Nt, L.Nx, c, R, st);
+        err = launch_coarse_colour<double, double2>(e, r, L.Bc64, nullptr, L.Dc64, L.off, L.Nt, L.Nx, L.ncol, c, R, st);
       else
-        err = launch_coarse_colour<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, c, R, st);
+        err = launch_coarse_colour<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, L.ncol, c, R, st);
       if (err != cudaSuccess) return err;
       h->launches++;
     }

@@ -447,16 +447,17 @@ __global__ void k_pack_B16(const double2* __restrict__ B, int K, int n, __half2*
 // colour) for the blocks, the diagonal inverses by the threads with offset 0.
 __global__ void k_pack_colour_major(const double2* __restrict__ B64, const __half2* __restrict__ B16,
                                     const float* __restrict__ Bs, const double2* __restrict__ D64,
-                                    const float2* __restrict__ D32, int K, int Nt, int Nx,
+                                    const float2* __restrict__ D32, int K, int Nt, int Nx, int ncol,
                                     double2* __restrict__ Bc64, __half2* __restrict__ Bc16, float* __restrict__ Bcs,
                                     double2* __restrict__ Dc64, float2* __restrict__ Dc32) {
-  const int n = Nt * Nx, m = n >> 4, qx = Nx >> 2, K1 = K - 1;
+  const int n = Nt * Nx, m = n / ncol, K1 = K - 1;
   const long g = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= 16L * K1 * m) return;
+  if (g >= (long)ncol * K1 * m) return;
   const int j = (int)(g % m);
   const int kk = (int)((g / m) % K1);
   const int c = (int)(g / ((long)m * K1));
-  const int t = 4 * (j / qx) + (c >> 2), x = 4 * (j % qx) + (c & 3);
+  int t, x;
+  colour_site(ncol, c, j, Nx, t, x);
   const int v = t * Nx + x, k = kk + 1;
   const size_t blk = ((size_t)c * K1 + kk) * m + j;
 #pragma unroll
@@ -477,11 +478,11 @@ __global__ void k_pack_colour_major(const double2* __restrict__ B64, const __hal
 }  // namespace
 
 cudaError_t launch_pack_colour_major(const double2* B64, const __half2* B16, const float* Bs, const double2* D64,
-                                     const float2* D32, int K, int Nt, int Nx, double2* Bc64, __half2* Bc16,
+                                     const float2* D32, int K, int Nt, int Nx, int ncol, double2* Bc64, __half2* Bc16,
                                      float* Bcs, double2* Dc64, float2* Dc32, cudaStream_t st) {
-  const long total = 16L * (K - 1) * (Nt * Nx / 16);
-  k_pack_colour_major<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(B64, B16, Bs, D64, D32, K, Nt, Nx, Bc64, Bc16,
-                                                                     Bcs, Dc64, Dc32);
+  const long total = (long)ncol * (K - 1) * (Nt * Nx / ncol);
+  k_pack_colour_major<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(B64, B16, Bs, D64, D32, K, Nt, Nx, ncol, Bc64,
+                                                                     Bc16, Bcs, Dc64, Dc32);
   return cudaGetLastError();
 }
 

@@ -174,8 +174,9 @@ def test_transfers_and_coarse_apply_fp64(Nt, Nx, aggs, R):
 
 @pytest.mark.parametrize("sweeps,Nt", [(1, 32), (2, 32), (2, 128)])
 def test_smoothers_fp64(sweeps, Nt):
-    """Level 1 is 16^2 at Nt = 32 and 64^2 at Nt = 128 (cluster sweeps with the
-    level in distributed shared memory, 1 and 16 sites per block and colour)."""
+    """Level 1 (21 offsets, 8 colours) is 16^2 at Nt = 32 and 64^2 at Nt = 128:
+    the default FP64 coarse kernel (cooperative grid sweep) at 32 and 512 sites
+    per colour."""
     Nx = Nt
     U, D, hier, levels = make(Nt, Nx, [2, 2], m0=0.1, seed=8)
     rng = np.random.Generator(np.random.PCG64(9))
@@ -189,6 +190,73 @@ def test_smoothers_fp64(sweeps, Nt):
         for _ in range(sweeps):
             want = amg.gs_sweep(L.A, L.dinv, L.colour, want, W.to_flat(r[0]))
         assert relerr(host(e)[0], lattice_vec(want, L.Nt, L.Nx)) <= 1e-12
+
+
+def quantised_operator(L):
+    """Level operator as the FP32 Gauss-Seidel kernels hold it: off-diagonal
+    blocks in FP16 + per-block scale (oracle.mixed), diagonal blocks exact."""
+    import scipy.sparse as sp
+    from oracle import mixed
+    Bq = mixed.quantise_blocks(amg.block_stencil(L.A, L.offsets, L.Nt, L.Nx))
+    Bq[0] = amg.block_stencil(L.A, L.offsets, L.Nt, L.Nx)[0]
+    n = L.Nt * L.Nx
+    rows, cols, vals = [], [], []
+    for k, (dt, dx) in enumerate(L.offsets):
+        for v in range(n):
+            tv, xv = divmod(v, L.Nx)
+            w = ((tv + dt) % L.Nt) * L.Nx + (xv + dx) % L.Nx
+            for al in range(2):
+                for be in range(2):
+                    rows.append(2 * v + al); cols.append(2 * w + be); vals.append(Bq[k, v, al, be])
+    return sp.csr_matrix((vals, (rows, cols)), shape=(2 * n, 2 * n))
+
+
+def test_coarse_gs_kernels_agree_with_oracle(monkeypatch):
+    """Every coarse Gauss-Seidel kernel (one launch per colour, L2 cluster,
+    distributed-shared-memory cluster, cooperative grid) on a 32^2 level with 21
+    offsets (8 colours) and a 16^2 level with 25 offsets (16 colours), two
+    right-hand sides, FP64 and FP32 (FP16 + scale blocks)."""
+    from oracle import mixed
+    Nt = Nx = 64
+    aggs = [2, 2, 2]
+    U = random_links(Nt, Nx, 31)
+    levels = amg.build_hierarchy(W.dirac_matrix(U, 0.1), Nt, Nx, aggs)
+    assert levels[1].colour.max() + 1 == 8 and levels[2].colour.max() + 1 == 16
+    rng = np.random.Generator(np.random.PCG64(32))
+    R = 2
+    inputs = {}
+    for l in (1, 2):
+        L = levels[l]
+        shape = (R, 2, L.Nt, L.Nx)
+        inputs[l] = [mixed.round32(rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) for _ in range(2)]
+    got64 = {}
+    for kind in ("colour", "cluster", "dsmem", "grid"):
+        monkeypatch.setenv("AMAMG_COARSE_GS", kind)
+        hier = A.setup(dev(U), 0.1, A.make_params(aggs))
+        for l in (1, 2):
+            L = levels[l]
+            r, e0 = inputs[l]
+            e = dev(e0)
+            A.smooth(hier, l, dev(r), e, 2)
+            g = host(e)
+            Aq = quantised_operator(L)
+            dinv32 = mixed.round32(L.dinv)
+            e32 = dev(e0, torch.complex64)
+            A.smooth(hier, l, dev(r, torch.complex64), e32, 2)
+            g32 = host(e32)
+            for q in range(R):
+                want = W.to_flat(e0[q])
+                want32 = W.to_flat(e0[q])
+                for _ in range(2):
+                    want = amg.gs_sweep(L.A, L.dinv, L.colour, want, W.to_flat(r[q]))
+                    want32 = amg.gs_sweep(Aq, dinv32, L.colour, want32, W.to_flat(r[q]))
+                assert relerr(g[q], lattice_vec(want, L.Nt, L.Nx)) <= 1e-12, (kind, l, q)
+                assert relerr(g32[q], lattice_vec(want32, L.Nt, L.Nx)) <= 1e-5, (kind, l, q)
+            got64.setdefault(l, []).append(g)
+        hier.destroy()
+    for l in (1, 2):
+        for g in got64[l][1:]:
+            assert relerr(g, got64[l][0]) <= 1e-14
 
 
 def test_coarsest_solve_and_vcycle_fp64():
@@ -311,8 +379,8 @@ def test_invalid_arguments_rejected():
 def test_fp32_transfers_coarse_and_smoothers_match_emulated_storage(Nt):
     """FP32 kernels against FP64 arithmetic on the emulated FP16+scale operators
     and complex64-rounded inputs (oracle.mixed): FP32 rounding only.  The
-    coarse level is 8^2 (L2-based sweep) at Nt = 32 and 16^2 (cluster sweep
-    with the level in distributed shared memory) at Nt = 64."""
+    coarse level (8 colours) is 8^2 at Nt = 32 (L2 cluster sweep) and 16^2 at
+    Nt = 64 (cluster sweep with the level in distributed shared memory)."""
     from oracle import mixed
     Nx = Nt
     aggs = [4, 2]
@@ -375,7 +443,7 @@ def test_fp32_transfers_coarse_and_smoothers_match_emulated_storage(Nt):
     for _ in range(2):
         want = amg.gs_sweep(D32, L0.dinv, L0.colour, want, W.to_flat(r0[0]))
     assert relerr(host(e)[0], lattice_vec(want, Nt, Nx)) <= 1e-5
-    # coarse 16-colour sweep: FP16 off-diagonal blocks, FP32-rounded diagonal inverses
+    # coarse multicolour sweep: FP16 off-diagonal blocks, FP32-rounded diagonal inverses
     L1 = levels[1]
     Bq = mixed.quantise_blocks(amg.block_stencil(L1.A, L1.offsets, L1.Nt, L1.Nx))
     Bex = amg.block_stencil(L1.A, L1.offsets, L1.Nt, L1.Nx)

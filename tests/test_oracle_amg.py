@@ -191,20 +191,37 @@ def test_red_black_sweep_equals_sequential_gs():
     assert np.max(np.abs(amg.gs_sweep(D, dinv, colour, e0, r) - sequential_gs(D, e0, r, order))) < 1e-13
 
 
-def test_sixteen_colour_sweep_equals_sequential_gs():
-    Nt = Nx = 16
+@pytest.mark.parametrize("Nt,ncol", [(16, 8), (24, 16)])
+def test_coarse_colour_sweep_equals_sequential_gs(Nt, ncol):
+    """Level 1 of a [2, 2] hierarchy: 8 x 8 takes the 8-colour ordering
+    (t + 3x) mod 8, 12 x 12 (not a multiple of 8) the 16-colour one; either
+    way one sweep equals point-block GS visiting the sites in colour order."""
+    Nx = Nt
     U = random_links(Nt, Nx, 16)
     D = W.dirac_matrix(U, 0.2)
     levels = amg.build_hierarchy(D, Nt, Nx, [2, 2])
-    L1 = levels[1]                                   # 8 x 8 coarse level, 16 colours
+    L1 = levels[1]
+    assert int(L1.colour.max()) + 1 == ncol
     rng = np.random.Generator(np.random.PCG64(17))
     n = 2 * L1.Nt * L1.Nx
     r = rng.standard_normal(n) + 1j * rng.standard_normal(n)
     e0 = rng.standard_normal(n) + 1j * rng.standard_normal(n)
     col = L1.colour.reshape(-1)
-    order = [s for c in range(16) for s in range(L1.Nt * L1.Nx) if col[s] == c]
+    order = [s for c in range(ncol) for s in range(L1.Nt * L1.Nx) if col[s] == c]
     got = amg.gs_sweep(L1.A, L1.dinv, L1.colour, e0, r)
     assert np.max(np.abs(got - sequential_gs(L1.A, e0, r, order))) < 1e-12 * np.max(np.abs(got))
+
+
+def test_eight_colouring_separates_level1_couplings():
+    """(t + 3x) mod 8 separates the 21 level-1 offsets (|dp|, |dq| <= 2 without
+    the corners) but not the full 5 x 5 block of offsets."""
+    offs21 = [(dp, dq) for dp in range(-2, 3) for dq in range(-2, 3) if not (abs(dp) == 2 and abs(dq) == 2)]
+    offs25 = [(dp, dq) for dp in range(-2, 3) for dq in range(-2, 3)]
+    assert amg.eight_colour_valid(16, 16, amg.canonical_offsets(offs21, 16, 16))
+    assert not amg.eight_colour_valid(16, 16, amg.canonical_offsets(offs25, 16, 16))
+    assert not amg.eight_colour_valid(12, 12, amg.canonical_offsets(offs21, 12, 12))
+    col = amg.colouring(16, 16, fine=False, offsets=amg.canonical_offsets(offs21, 16, 16))
+    amg.check_colouring(col, amg.canonical_offsets(offs21, 16, 16))
 
 
 def test_gauss_seidel_converges_when_diagonally_dominant():
