@@ -1,6 +1,7 @@
 // Host engine and C ABI: hierarchy setup (Sec. 2, Sec. 4.1), the V-cycle of
 // Algorithm 1 used as preconditioner, the FP64 flexible GMRES outer solver, and
 // the apply/export entry points declared in include/amamg.h.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -163,20 +164,25 @@ int gs_colours(const Level& L) {
 }
 
 // Coarse Gauss-Seidel kernel of a smoothed coarse level, per precision.
-// Default: FP64 on the whole GPU (grid barrier), since one cluster has the FP64
-// throughput of only 16 SMs; FP32 on one 16-block cluster with the level in
-// distributed shared memory where it fits, else the L2 cluster sweep, else one
-// launch per colour.  AMAMG_COARSE_GS = colour | cluster | dsmem | grid forces a
-// kernel where it is available (for measurement); results are the same.
+// FP64: the owner sweep (all SMs, neighbour waits only), else the grid sweep,
+// since one 16-block cluster has the FP64 throughput of only 16 SMs.  FP32: one
+// 16-block cluster with the level in distributed shared memory where it fits,
+// else the owner sweep, else the grid sweep, else the L2 cluster sweep, else
+// one launch per colour.  AMAMG_COARSE_GS = colour | cluster | dsmem | grid |
+// owner forces a kernel where it is available (for measurement); results are
+// the same.
 void choose_gs_kernels(Level& C) {
+  OwnerConfig rc;
+  const bool owner64 = owner_sweep_config<double, double2>(C.Nt, C.Nx, C.off.K, C.ncol, C.off, 1, &rc);
+  const bool owner32 = owner_sweep_config<float, __half2>(C.Nt, C.Nx, C.off.K, C.ncol, C.off, 1, &rc);
   const bool grid64 = grid_sweep_blocks<double, double2>(C.n, C.ncol, 1) > 0;
   const bool grid32 = grid_sweep_blocks<float, __half2>(C.n, C.ncol, 1) > 0;
   const bool dsm64 = dsmem_sweeps_possible<double, double2>(C.n, C.off.K, C.ncol, false);
   const bool dsm32 = dsmem_sweeps_possible<float, __half2>(C.n, C.off.K, C.ncol,
                                                             dsmem_blocks_in_smem<float>(C.n, C.off.K));
   const bool clu32 = use_cluster_sweeps<float>(C.n, C.ncol);
-  C.gs64 = grid64 ? GS_GRID : dsm64 ? GS_DSMEM : GS_COLOUR;
-  C.gs32 = dsm32 ? GS_DSMEM : clu32 ? GS_CLUSTER : grid32 ? GS_GRID : GS_COLOUR;
+  C.gs64 = owner64 ? GS_OWNER : grid64 ? GS_GRID : dsm64 ? GS_DSMEM : GS_COLOUR;
+  C.gs32 = dsm32 ? GS_DSMEM : owner32 ? GS_OWNER : grid32 ? GS_GRID : clu32 ? GS_CLUSTER : GS_COLOUR;
   const char* env = getenv("AMAMG_COARSE_GS");
   if (!env) return;
   const std::string want(env);
@@ -184,6 +190,7 @@ void choose_gs_kernels(Level& C) {
   else if (want == "cluster") { C.gs32 = clu32 ? GS_CLUSTER : C.gs32; }
   else if (want == "dsmem") { C.gs64 = dsm64 ? GS_DSMEM : C.gs64; C.gs32 = dsm32 ? GS_DSMEM : C.gs32; }
   else if (want == "grid") { C.gs64 = grid64 ? GS_GRID : C.gs64; C.gs32 = grid32 ? GS_GRID : C.gs32; }
+  else if (want == "owner") { C.gs64 = owner64 ? GS_OWNER : C.gs64; C.gs32 = owner32 ? GS_OWNER : C.gs32; }
 }
 
 // ----------------------------------------------------------------- workspace
@@ -304,7 +311,7 @@ int smooth_impl(amamg_ctx* h, int l, typename cplx<T>::type* e, const typename c
   const int nc = L.ncol;
   const double bytes = (double)L.n / nc * ((L.off.K - 1) * blk + 4 * cb + R * 2 * 3 * cb);
   const double flops = (double)L.n / nc * R * ((L.off.K - 1) * 32.0 + 36.0);   // one colour
-  const int kind = f64 ? L.gs64 : L.gs32;
+  const int kind = gs_kind_for<T>(L, R);
   if (sweeps > 0 && kind == GS_DSMEM) {
     // every colour of every sweep on one 16-block cluster, level in shared memory
     const bool bsm = dsmem_blocks_in_smem<T>(L.n, L.off.K);
@@ -317,6 +324,19 @@ int smooth_impl(amamg_ctx* h, int l, typename cplx<T>::type* e, const typename c
       return launch(h, "coarse_smooth_f32", bytes * nc * sweeps, st, [&] {
         return launch_coarse_sweeps_dsmem<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, nc, sweeps,
                                                           R, bsm, st);
+      }, flops * nc * sweeps);
+  }
+  if (sweeps > 0 && kind == GS_OWNER) {
+    // every colour of every sweep in one cooperative launch, neighbour waits only
+    if constexpr (f64)
+      return launch(h, "coarse_smooth_f64", bytes * nc * sweeps, st, [&] {
+        return launch_coarse_sweeps_owner<double, double2>(e, r, L.Bc64, nullptr, L.Dc64, L.off, L.Nt, L.Nx, nc,
+                                                          sweeps, R, h->d_owner_flags, h->d_sync, st);
+      }, flops * nc * sweeps);
+    else
+      return launch(h, "coarse_smooth_f32", bytes * nc * sweeps, st, [&] {
+        return launch_coarse_sweeps_owner<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, nc, sweeps,
+                                                         R, h->d_owner_flags, h->d_sync, st);
       }, flops * nc * sweeps);
   }
   if (sweeps > 0 && kind == GS_GRID) {
@@ -699,16 +719,17 @@ int set_masses(amamg_ctx* h, const double* m0, int R, cudaStream_t st) {
   return AMAMG_OK;
 }
 
-// A grid Gauss-Seidel sweep whose barrier timed out left its flag set: report
-// it and re-arm the barrier (cooperative launches keep all blocks resident, so
+// A grid or owner Gauss-Seidel sweep whose wait timed out left its flag set:
+// report it and re-arm the counters (cooperative launches keep all blocks resident, so
 // this does not happen in a correct run).
 int check_grid_sync(amamg_ctx* h, cudaStream_t st) {
   unsigned flag[3] = {0, 0, 0};
   CK(cudaMemcpyAsync(flag, h->d_sync, sizeof(flag), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (!flag[2]) return AMAMG_OK;
-  CK(cudaMemsetAsync(h->d_sync, 0, sizeof(flag), st));
-  h->err = "coarse Gauss-Seidel grid barrier timed out";
+  CK(cudaMemsetAsync(h->d_sync, 0, 8 * sizeof(unsigned), st));
+  CK(cudaMemsetAsync(h->d_owner_flags, 0, OWNER_MAX_BLOCKS * sizeof(unsigned), st));
+  h->err = "coarse Gauss-Seidel synchronisation timed out";
   return AMAMG_ERR_TIMEOUT;
 }
 
@@ -796,7 +817,7 @@ void free_all(amamg_ctx* h) {
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
   h->ws = nullptr; h->ev_in = h->ev_out = nullptr;
-  dfree(h->U64); dfree(h->U32); dfree(h->Ainv); dfree(h->Ainv32); dfree(h->d_err); dfree(h->d_sync);
+  dfree(h->U64); dfree(h->U32); dfree(h->Ainv); dfree(h->Ainv32); dfree(h->d_err); dfree(h->d_sync); dfree(h->d_owner_flags);
   dfree(h->V); dfree(h->Z64); dfree(h->Z32); dfree(h->v32); dfree(h->w); dfree(h->res);
   dfree(h->partial); dfree(h->d_h); dfree(h->d_inv); dfree(h->d_flag); dfree(h->d_y); dfree(h->d_tickets); dfree(h->d_npart);
   dfree(h->d_diag64); dfree(h->d_inv64); dfree(h->d_inv32);
@@ -822,8 +843,10 @@ int do_setup(amamg_ctx* h, const void* Uin, cudaStream_t st) {
   CKS(dalloc(h, &h->U32, nl));
   CKS(dalloc(h, &h->d_err, 1));
   CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
-  CKS(dalloc(h, &h->d_sync, 3));
-  CK(cudaMemsetAsync(h->d_sync, 0, 3 * sizeof(unsigned), st));
+  CKS(dalloc(h, &h->d_sync, 8));
+  CK(cudaMemsetAsync(h->d_sync, 0, 8 * sizeof(unsigned), st));
+  CKS(dalloc(h, &h->d_owner_flags, OWNER_MAX_BLOCKS));
+  CK(cudaMemsetAsync(h->d_owner_flags, 0, OWNER_MAX_BLOCKS * sizeof(unsigned), st));
   CK(cudaMemcpyAsync(h->U64, Uin, nl * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   CKS(launch(h, "setup_cast_links", nl * 24.0, st,
              [&] { return launch_cast<double2, float2>(h->U64, h->U32, (long)nl, st); }));

@@ -9,6 +9,12 @@
 // block ([K][n]).
 #include <cooperative_groups.h>
 
+#include <algorithm>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <vector>
+
 #include "kernels.h"
 
 namespace cg = cooperative_groups;
@@ -225,6 +231,9 @@ k_coarse_sweeps_cluster(typename cplx<T>::type* __restrict__ e, const typename c
 // block's global stores before its arrival and the other blocks' stores before
 // its reads (which go through L2).
 constexpr unsigned GRID_SPIN_LIMIT = 1u << 23;
+#ifndef AMAMG_GRID_SLEEP_NS
+#define AMAMG_GRID_SLEEP_NS 64     // back-off between polls of the generation word
+#endif
 __device__ __forceinline__ bool grid_barrier(unsigned* sync, unsigned nblocks) {
   __shared__ int ok;
   __syncthreads();
@@ -245,7 +254,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* sync, unsigned nblocks) {
           ok = 0;
           break;
         }
-        __nanosleep(64);
+        if (AMAMG_GRID_SLEEP_NS > 0) __nanosleep(AMAMG_GRID_SLEEP_NS);
       }
     }
     __threadfence();
@@ -260,13 +269,19 @@ __device__ __forceinline__ bool grid_barrier(unsigned* sync, unsigned nblocks) {
 // grid_barrier.  Same arithmetic per site as k_coarse_colour.  For FP64, whose
 // pipe is narrow on this GPU, this spreads a colour over every SM instead of
 // the 16 SMs of one cluster.
+#ifndef AMAMG_GRID_LPS64
+#define AMAMG_GRID_LPS64 8         // lanes per site of the FP64 grid sweep
+#endif
+template <typename T> struct GridLanes { static constexpr int value = 32; };
+template <> struct GridLanes<double> { static constexpr int value = AMAMG_GRID_LPS64; };
+
 template <typename T, typename BT>
 __global__ void __launch_bounds__(256)
 k_coarse_sweeps_grid(typename cplx<T>::type* __restrict__ e, const typename cplx<T>::type* __restrict__ r,
                      const BT* __restrict__ B, const float* __restrict__ Bs,
                      const typename cplx<T>::type* __restrict__ Dinv, Offsets off, int Nt, int Nx, int ncol,
                      int sweeps, int R, unsigned* sync) {
-  constexpr int LPS = GsLanes<T>::value;
+  constexpr int LPS = GridLanes<T>::value;
   const int n = Nt * Nx;
   const int per_colour = n / ncol;
   const long units = (long)R * per_colour;
@@ -285,6 +300,241 @@ k_coarse_sweeps_grid(typename cplx<T>::type* __restrict__ e, const typename cplx
         gs_site<T, BT, LPS, false>(e + roff, r + roff, B, Bs, Dinv, off, Nt, Nx, ncol, colour, idx, g, valid);
       }
       if (!grid_barrier(sync, gridDim.x)) return;
+    }
+  }
+}
+
+// All colours of `sweeps` sweeps in one cooperative launch in which block b of
+// a right-hand side owns the sites j in [b cnt, (b+1) cnt) of every colour
+// (colour-major numbering of colour_site: for 8 colours a segment of 8 cnt
+// sites of one row, for 16 colours a strip of a 4-row band; the same ownership
+// as k_coarse_sweeps_dsmem with more, smaller owners).  The block keeps its
+// sites' r, diagonal inverses and (BSMEM) off-diagonal blocks in shared
+// memory; e lives in global memory.  At start every block lists the other
+// blocks that own a neighbour of one of its sites (the operator's offsets are
+// symmetric, so these are also the blocks that read its sites).  Instead of a
+// barrier over the whole grid, a block starts colour phase p once every
+// listed block has published phase p - 1: no neighbour value it reads is
+// stale, and no neighbour still reads a value it is about to overwrite.
+// Phase counters are flags[block] = base + phases done, base = sync[3]
+// (advanced by the last block to finish through the ticket sync[4]), so they
+// need no reset between launches.  Polls are bounded (OWNER_SPIN_LIMIT); a
+// block that times out sets sync[2] and stops waiting, so the launch always
+// ends.
+constexpr unsigned OWNER_SPIN_LIMIT = 1u << 22;
+// lanes per site: FP64 32 (one offset per lane: the shortest chain of
+// dependent FP64 instructions, which bounds a colour phase on this GPU's
+// narrow FP64 pipe), FP32 8
+#ifndef AMAMG_OWNER_LPS64
+#define AMAMG_OWNER_LPS64 32
+#endif
+#ifndef AMAMG_OWNER_LPS32
+#define AMAMG_OWNER_LPS32 8
+#endif
+template <typename T> struct OwnerLanes { static constexpr int value = AMAMG_OWNER_LPS32; };
+template <> struct OwnerLanes<double> { static constexpr int value = AMAMG_OWNER_LPS64; };
+
+template <typename T, typename BT, bool BSMEM>
+__global__ void __launch_bounds__(256, 1)
+k_coarse_sweeps_owner(typename cplx<T>::type* __restrict__ e, const typename cplx<T>::type* __restrict__ r,
+                      const BT* __restrict__ Bc, const float* __restrict__ Sc,
+                      const typename cplx<T>::type* __restrict__ Dc, Offsets off, int Nt, int Nx, int ncol,
+                      int sweeps, int cnt, unsigned* __restrict__ flags, unsigned* __restrict__ sync) {
+  using C = typename cplx<T>::type;
+  constexpr int LPS = OwnerLanes<T>::value;
+  static_assert(LPS >= 4 && LPS <= 32 && (LPS & (LPS - 1)) == 0, "lanes per site: a power of two, 4..32");
+  constexpr int IT = (GS_MAX_OFFDIAG + LPS - 1) / LPS;
+  const int n = Nt * Nx, m = n / ncol, K1 = off.K - 1;
+  const int nbpr = m / cnt;                                  // owner blocks per right-hand side
+  const int rhs = blockIdx.x / nbpr, b = blockIdx.x - rhs * nbpr;
+  const int j0 = b * cnt;
+  const int own = ncol * cnt;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* rs = reinterpret_cast<C*>(smem_raw);                    // [ncol][cnt][2]
+  C* ds = rs + 2 * own;                                      // [ncol][cnt][4]
+  BT* bs = reinterpret_cast<BT*>(ds + 4 * own);              // [ncol][K1][cnt][4]   (BSMEM)
+  float* ss = reinterpret_cast<float*>(bs + (BSMEM ? 4 * K1 * own : 0));   // [ncol][K1][cnt] (BSMEM, FP16)
+  __shared__ unsigned bm[OWNER_MAX_BLOCKS / 32];             // blocks owning a neighbour
+  __shared__ short wl[OWNER_MAX_WAIT];                       // ... as a list
+  __shared__ int nwait, alive;
+  const size_t roff = (size_t)rhs * 2 * n;
+  C* e0 = e + roff;
+  const C* r0 = r + roff;
+  const int words = (nbpr + 31) / 32;
+  for (int i = threadIdx.x; i < words; i += blockDim.x) bm[i] = 0u;
+  for (int i = threadIdx.x; i < own; i += blockDim.x) {
+    const int c = i / cnt, j = j0 + (i - c * cnt);
+    int t, x;
+    colour_site(ncol, c, j, Nx, t, x);
+    const int v = t * Nx + x;
+    rs[2 * i] = r0[v]; rs[2 * i + 1] = r0[n + v];
+#pragma unroll
+    for (int d = 0; d < 4; ++d) ds[4 * i + d] = Dc[((size_t)c * m + j) * 4 + d];
+  }
+  if constexpr (BSMEM) {
+    for (int i = threadIdx.x; i < K1 * own; i += blockDim.x) {
+      const int ck = i / cnt, jj = i - ck * cnt;                // ck = c K1 + (k - 1)
+      const size_t src = (size_t)ck * m + j0 + jj;
+#pragma unroll
+      for (int d = 0; d < 4; ++d) bs[4 * i + d] = Bc[src * 4 + d];
+      if (Sc) ss[i] = Sc[src];
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < K1 * own; i += blockDim.x) {
+    const int site = i / K1, k = 1 + (i - site * K1);
+    const int c = site / cnt, j = j0 + (site - c * cnt);
+    int t, x;
+    colour_site(ncol, c, j, Nx, t, x);
+    int tw = t + off.dt[k]; tw -= (tw >= Nt) ? Nt : 0;
+    int xw = x + off.dx[k]; xw -= (xw >= Nx) ? Nx : 0;
+    int cw, jw;
+    site_colour(ncol, tw, xw, Nx, cw, jw);
+    const int ob = jw / cnt;
+    if (ob != b) atomicOr(&bm[ob >> 5], 1u << (ob & 31));
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    // compact the bitmap into wl (warp 0, word order, so the list is sorted)
+    int total = 0;
+    for (int w0 = 0; w0 < words; w0 += 32) {
+      const unsigned word = (w0 + (int)threadIdx.x < words) ? bm[w0 + threadIdx.x] : 0u;
+      int cnt_w = __popc(word), incl = cnt_w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)threadIdx.x >= o) incl += y;
+      }
+      int pos = total + incl - cnt_w;
+      unsigned bits = word;
+      while (bits) {
+        const int bit = __ffs(bits) - 1;
+        bits &= bits - 1;
+        if (pos < OWNER_MAX_WAIT) wl[pos] = (short)((w0 + threadIdx.x) * 32 + bit);
+        ++pos;
+      }
+      total += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (threadIdx.x == 0) {
+      nwait = total < OWNER_MAX_WAIT ? total : OWNER_MAX_WAIT;
+      alive = 1;
+      if (total > OWNER_MAX_WAIT) { atomicExch(sync + 2, 1u); alive = 0; }
+    }
+  }
+  const unsigned base = *reinterpret_cast<volatile unsigned*>(sync + 3);
+  __syncthreads();
+  const int g = threadIdx.x & (LPS - 1);
+  const int groups = blockDim.x / LPS;
+  int p = 0;
+  for (int sw = 0; sw < sweeps; ++sw) {
+    for (int colour = 0; colour < ncol; ++colour, ++p) {
+      if (p > 0 && alive && threadIdx.x < nwait) {
+        const unsigned want = base + (unsigned)p;
+        for (int q = threadIdx.x; q < nwait; q += blockDim.x) {
+          const volatile unsigned* f = flags + rhs * nbpr + wl[q];
+          unsigned it = 0;
+          while ((int)(*f - want) < 0) {
+            if (++it == OWNER_SPIN_LIMIT) {
+              atomicExch(sync + 2, 1u);
+              alive = 0;
+              break;
+            }
+          }
+        }
+        __threadfence();
+      }
+      __syncthreads();
+      for (int base_i = 0; base_i < cnt; base_i += groups) {
+        const int jj = base_i + threadIdx.x / LPS;
+        const bool valid = jj < cnt;
+        const int j = j0 + (valid ? jj : 0);
+        int t, x;
+        colour_site(ncol, colour, j, Nx, t, x);
+        C xv[IT][2], bb[IT][4];
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+          const int k = 1 + g + it * LPS;
+          if (valid && k < off.K) {
+            int tw = t + off.dt[k]; tw -= (tw >= Nt) ? Nt : 0;
+            int xw = x + off.dx[k]; xw -= (xw >= Nx) ? Nx : 0;
+            const int w = tw * Nx + xw;
+            xv[it][0] = __ldcg(e0 + w);
+            xv[it][1] = __ldcg(e0 + n + w);
+            if constexpr (BSMEM) {
+              const int li = (colour * K1 + (k - 1)) * cnt + jj;
+              if constexpr (sizeof(T) == 4) {
+#pragma unroll
+                for (int d = 0; d < 4; ++d) bb[it][d] = h2c<float>(bs[4 * li + d], ss[li]);
+              } else {
+#pragma unroll
+                for (int d = 0; d < 4; ++d) bb[it][d] = to_c(bs[4 * li + d], T());
+              }
+            } else {
+              cm_block<T, BT>(Bc, Sc, ((size_t)colour * K1 + (k - 1)) * m + j, bb[it]);
+            }
+          } else {
+            xv[it][0] = xv[it][1] = czero<C>();
+            bb[it][0] = bb[it][1] = bb[it][2] = bb[it][3] = czero<C>();
+          }
+        }
+        C s0 = czero<C>(), s1 = czero<C>();
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+          cmac(s0, bb[it][0], xv[it][0]);
+          cmac(s0, bb[it][1], xv[it][1]);
+          cmac(s1, bb[it][2], xv[it][0]);
+          cmac(s1, bb[it][3], xv[it][1]);
+        }
+        // Reduce-scatter of (s0.x, s0.y, s1.x, s1.y) over the group's lanes:
+        // after it, lane g holds the full sum of component q = 2 h1 + h2
+        // (h1 = bit o1 of g, h2 = bit o2), with log2(LPS) + 1 dependent adds
+        // instead of 4 log2(LPS).
+        constexpr int o1 = LPS / 2, o2 = LPS / 4;
+        const bool h1 = (g & o1) != 0, h2 = (g & o2) != 0;
+        T ka = h1 ? s1.x : s0.x, kb = h1 ? s1.y : s0.y;
+        ka += __shfl_xor_sync(0xffffffffu, h1 ? s0.x : s1.x, o1);
+        kb += __shfl_xor_sync(0xffffffffu, h1 ? s0.y : s1.y, o1);
+        T sq = h2 ? kb : ka;
+        sq += __shfl_xor_sync(0xffffffffu, h2 ? ka : kb, o2);
+#pragma unroll
+        for (int o = o2 / 2; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        // a = r - s, component q here; every lane gathers all four, and the
+        // four lanes (h1, h2) each form one real component of
+        // e = [d0 d1; d2 d3] a  (e_0 = d0 a_0 + d1 a_1, e_1 = d2 a_0 + d3 a_1)
+        const int i = colour * cnt + jj;
+        const int q = 2 * h1 + h2;
+        const T aq = reinterpret_cast<const T*>(rs)[4 * i + q] - sq;
+        const int gb = (threadIdx.x & 31) & ~(LPS - 1);
+        const T A0 = __shfl_sync(0xffffffffu, aq, gb);
+        const T A1 = __shfl_sync(0xffffffffu, aq, gb + o2);
+        const T A2 = __shfl_sync(0xffffffffu, aq, gb + o1);
+        const T A3 = __shfl_sync(0xffffffffu, aq, gb + o1 + o2);
+        if (valid && (g & ~(o1 | o2)) == 0) {
+          const C dA = ds[4 * i + (h1 ? 2 : 0)], dB = ds[4 * i + (h1 ? 3 : 1)];
+          // real part (h2 = 0): dA.x A0 - dA.y A1 + dB.x A2 - dB.y A3;
+          // imaginary part (h2 = 1): dA.x A1 + dA.y A0 + dB.x A3 + dB.y A2
+          const T p0 = h2 ? A1 : A0, p1 = h2 ? A0 : A1, q0 = h2 ? A3 : A2, q1 = h2 ? A2 : A3;
+          T out = dA.x * p0;
+          out = fma(h2 ? dA.y : -dA.y, p1, out);
+          out = fma(dB.x, q0, out);
+          out = fma(h2 ? dB.y : -dB.y, q1, out);
+          const int v = t * Nx + x;
+          __stcg(reinterpret_cast<T*>(e0) + 2 * (v + (h1 ? n : 0)) + h2, out);
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicExch(flags + blockIdx.x, base + (unsigned)p + 1u);
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(sync + 4, 1u) == gridDim.x - 1) {
+      sync[4] = 0;
+      __threadfence();
+      atomicExch(sync + 3, base + (unsigned)p);
     }
   }
 }
@@ -559,10 +809,13 @@ size_t dsmem_sweep_bytes(int n, int K, size_t cbytes, bool bsmem, size_t bt_byte
   return b;
 }
 
-// Grid sweep: 64 threads per block (8 FP64 sites or 2 FP32 sites per block and
-// pass), as many blocks as the widest colour needs, at most the blocks that
+// Grid sweep: GRID_SWEEP_THREADS threads per block (GRID_SWEEP_THREADS / LPS
+// sites per block and pass), as many blocks as the widest colour needs, at most the blocks that
 // can be co-resident (cooperative launch).
-constexpr int GRID_SWEEP_THREADS = 64;
+#ifndef AMAMG_GRID_THREADS
+#define AMAMG_GRID_THREADS 64
+#endif
+constexpr int GRID_SWEEP_THREADS = AMAMG_GRID_THREADS;
 template <typename T, typename BT>
 int grid_sweep_blocks(int n, int ncol, int R) {
   static int cap[2] = {-1, -1};                       // per element type, first device queried
@@ -582,7 +835,7 @@ int grid_sweep_blocks(int n, int ncol, int R) {
   }
   if (c <= 0) return 0;
   const long groups = (long)R * (n / ncol);
-  const long want = (groups * GsLanes<T>::value + GRID_SWEEP_THREADS - 1) / GRID_SWEEP_THREADS;
+  const long want = (groups * GridLanes<T>::value + GRID_SWEEP_THREADS - 1) / GRID_SWEEP_THREADS;
   return (int)(want < c ? want : c);
 }
 
@@ -603,6 +856,126 @@ cudaError_t launch_coarse_sweeps_grid(typename cplx<T>::type* e, const typename 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_coarse_sweeps_grid<T, BT>, e, r, B, Bs, Dinv, off, Nt, Nx, ncol, sweeps, R, sync);
+}
+
+// Owner sweep configuration for a level: the fewest sites per block and colour
+// (cnt, a divisor of m = n / ncol, at least OWNER_MIN_CNT) whose R m / cnt
+// blocks can all be resident (cooperative launch) and whose neighbour-owner
+// lists fit OWNER_MAX_WAIT; threads = LPS cnt (at most 256, more sites take
+// several passes); blocks in shared memory when that stays within 100 KB.
+#ifndef AMAMG_OWNER_MIN_CNT
+#define AMAMG_OWNER_MIN_CNT 4
+#endif
+static size_t owner_smem(int own, int K1, size_t cb, bool bsmem, size_t btb) {
+  size_t s = (size_t)own * 6 * cb;
+  if (bsmem) s += (size_t)own * K1 * (4 * btb + 4);
+  return s;
+}
+
+// largest number of other blocks owning a neighbour of one block's sites
+static int owner_max_wait(int Nt, int Nx, int ncol, const Offsets& off, int cnt) {
+  const int m = Nt * Nx / ncol, nbpr = m / cnt;
+  int worst = 0;
+  std::vector<int> seen(nbpr, -1);
+  for (int b = 0; b < nbpr; ++b) {
+    int count = 0;
+    for (int c = 0; c < ncol; ++c)
+      for (int jj = 0; jj < cnt; ++jj) {
+        int t, x;
+        colour_site(ncol, c, b * cnt + jj, Nx, t, x);
+        for (int k = 1; k < off.K; ++k) {
+          int cw, jw;
+          site_colour(ncol, (t + off.dt[k]) % Nt, (x + off.dx[k]) % Nx, Nx, cw, jw);
+          const int ob = jw / cnt;
+          if (ob != b && seen[ob] != b) { seen[ob] = b; ++count; }
+        }
+      }
+    worst = std::max(worst, count);
+  }
+  return worst;
+}
+
+template <typename T, typename BT>
+static bool owner_sweep_search(int Nt, int Nx, int K, int ncol, const Offsets& off, int R, OwnerConfig* cfg) {
+  int dev = 0, sms = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) || !coop) {
+    cudaGetLastError();
+    return false;
+  }
+  const int m = Nt * Nx / ncol;
+  const size_t cb = sizeof(typename cplx<T>::type);
+  for (int cnt = std::min(AMAMG_OWNER_MIN_CNT, m); cnt <= m; ++cnt) {
+    if (m % cnt) continue;
+    const int nbpr = m / cnt;
+    const long blocks = (long)R * nbpr;
+    if (nbpr > OWNER_MAX_BLOCKS || blocks > OWNER_MAX_BLOCKS) continue;
+    const int own = ncol * cnt;
+    int threads = cnt * OwnerLanes<T>::value;
+    threads = threads > 256 ? 256 : ((threads + 31) / 32) * 32;
+    const bool bsmem = owner_smem(own, K - 1, cb, true, sizeof(BT)) <= 100 * 1024;
+    const size_t smem = owner_smem(own, K - 1, cb, bsmem, sizeof(BT));
+    auto kern = bsmem ? k_coarse_sweeps_owner<T, BT, true> : k_coarse_sweeps_owner<T, BT, false>;
+    int occ = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (blocks > (long)occ * sms) continue;
+    if (owner_max_wait(Nt, Nx, ncol, off, cnt) > OWNER_MAX_WAIT) continue;
+    cfg->cnt = cnt;
+    cfg->threads = threads;
+    cfg->smem = smem;
+    cfg->bsmem = bsmem;
+    cfg->blocks = (int)blocks;
+    return true;
+  }
+  return false;
+}
+
+// Cached per (element type, device, level shape, offsets, R).
+template <typename T, typename BT>
+bool owner_sweep_config(int Nt, int Nx, int K, int ncol, const Offsets& off, int R, OwnerConfig* cfg) {
+  static std::mutex mu;
+  static std::map<std::vector<int>, std::pair<bool, OwnerConfig>> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return false; }
+  std::vector<int> key = {dev, Nt, Nx, K, ncol, R};
+  for (int k = 0; k < off.K; ++k) { key.push_back(off.dt[k]); key.push_back(off.dx[k]); }
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(key);
+  if (it == cache.end()) {
+    OwnerConfig oc;
+    const bool ok = owner_sweep_search<T, BT>(Nt, Nx, K, ncol, off, R, &oc);
+    it = cache.emplace(key, std::make_pair(ok, oc)).first;
+  }
+  *cfg = it->second.second;
+  return it->second.first;
+}
+
+template <typename T, typename BT>
+cudaError_t launch_coarse_sweeps_owner(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* Bc,
+                                       const float* Sc, const typename cplx<T>::type* Dc, const Offsets& off,
+                                       int Nt, int Nx, int ncol, int sweeps, int R, unsigned* flags, unsigned* sync,
+                                       cudaStream_t st) {
+  OwnerConfig oc;
+  if (!owner_sweep_config<T, BT>(Nt, Nx, off.K, ncol, off, R, &oc)) return cudaErrorNotSupported;
+  auto kern = oc.bsmem ? k_coarse_sweeps_owner<T, BT, true> : k_coarse_sweeps_owner<T, BT, false>;
+  // the attribute is per kernel, and another level may have set a smaller one
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oc.smem);
+  if (err != cudaSuccess) return err;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(oc.blocks);
+  cfg.blockDim = dim3(oc.threads);
+  cfg.dynamicSmemBytes = oc.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, e, r, Bc, Sc, Dc, off, Nt, Nx, ncol, sweeps, oc.cnt, flags, sync);
 }
 
 // the distributed-shared-memory sweep needs per = n / (16 ncol) whole sites per
@@ -724,6 +1097,14 @@ template cudaError_t launch_coarse_colour<float, __half2>(float2*, const float2*
 template cudaError_t launch_coarse_sweeps_cluster<float, __half2>(float2*, const float2*, const __half2*, const float*,
                                                                   const float2*, const Offsets&, int, int, int, int,
                                                                   int, cudaStream_t);
+template bool owner_sweep_config<double, double2>(int, int, int, int, const Offsets&, int, OwnerConfig*);
+template bool owner_sweep_config<float, __half2>(int, int, int, int, const Offsets&, int, OwnerConfig*);
+template cudaError_t launch_coarse_sweeps_owner<double, double2>(double2*, const double2*, const double2*,
+                                                                const float*, const double2*, const Offsets&, int, int,
+                                                                int, int, int, unsigned*, unsigned*, cudaStream_t);
+template cudaError_t launch_coarse_sweeps_owner<float, __half2>(float2*, const float2*, const __half2*, const float*,
+                                                               const float2*, const Offsets&, int, int, int, int, int,
+                                                               unsigned*, unsigned*, cudaStream_t);
 template int grid_sweep_blocks<double, double2>(int, int, int);
 template int grid_sweep_blocks<float, __half2>(int, int, int);
 template cudaError_t launch_coarse_sweeps_grid<double, double2>(double2*, const double2*, const double2*, const float*,

@@ -86,8 +86,24 @@ struct OuterState {
 // Coarse Gauss-Seidel kernels (identical arithmetic per site): one launch per
 // colour; all phases on an 8-block cluster with e in L2; all phases on a
 // 16-block cluster with the level in distributed shared memory; all phases in
-// one cooperative launch over the whole GPU with a software grid barrier.
-enum GsKernel : int { GS_COLOUR = 0, GS_CLUSTER = 1, GS_DSMEM = 2, GS_GRID = 3 };
+// one cooperative launch over the whole GPU with a software grid barrier; all
+// phases in one cooperative launch of site-owning blocks that wait only for
+// the owners of their sites' neighbours.
+enum GsKernel : int { GS_COLOUR = 0, GS_CLUSTER = 1, GS_DSMEM = 2, GS_GRID = 3, GS_OWNER = 4 };
+
+// The kernel a smoothing launch of R right-hand sides uses on level L: the one
+// chosen in setup (for R = 1), or the whole-GPU grid sweep when the owner sweep
+// has no resident shape for this R.
+template <typename T>
+inline int gs_kind_for(const Level& L, int R) {
+  constexpr bool f64 = sizeof(T) == 8;
+  const int kind = f64 ? L.gs64 : L.gs32;
+  if (kind != GS_OWNER || R == 1) return kind;
+  OwnerConfig rc;
+  const bool ok = f64 ? owner_sweep_config<double, double2>(L.Nt, L.Nx, L.off.K, L.ncol, L.off, R, &rc)
+                      : owner_sweep_config<float, __half2>(L.Nt, L.Nx, L.off.K, L.ncol, L.off, R, &rc);
+  return ok ? GS_OWNER : GS_GRID;
+}
 
 struct amamg_ctx {
   amamg_params prm{};
@@ -100,7 +116,10 @@ struct amamg_ctx {
   float2* Ainv32 = nullptr;  // its FP32 rounding, applied by the mixed-precision V-cycle
   int nd = 0;
   int* d_err = nullptr;
-  unsigned* d_sync = nullptr;   // grid barrier of the grid Gauss-Seidel sweep: count, generation, time-out flag
+  // coarse Gauss-Seidel synchronisation: [0] grid-barrier count, [1] its
+  // generation, [2] time-out flag, [3] owner-sweep epoch base, [4] its end ticket
+  unsigned* d_sync = nullptr;
+  unsigned* d_owner_flags = nullptr;   // [OWNER_MAX_BLOCKS] owner-sweep phase counters
 
   // solver workspace
   int Rcap = 0;              // V-cycle work vectors

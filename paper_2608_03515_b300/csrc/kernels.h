@@ -61,6 +61,25 @@ template <typename T, typename BT>
 cudaError_t launch_coarse_sweeps_grid(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* B,
                                       const float* Bs, const typename cplx<T>::type* Dinv, const Offsets& off,
                                       int Nt, int Nx, int ncol, int sweeps, int R, unsigned* sync, cudaStream_t st);
+// all colours of `sweeps` sweeps in one cooperative launch, each block owning
+// cnt sites of every colour and waiting only for the blocks that own its
+// sites' neighbours (per-block phase flags, no grid barrier); flags:
+// OWNER_MAX_BLOCKS counters, sync[3] epoch base, sync[4] end ticket, sync[2]
+// time-out flag
+constexpr int OWNER_MAX_BLOCKS = 4096;
+constexpr int OWNER_MAX_WAIT = 256;
+struct OwnerConfig {
+  int cnt = 0, threads = 0, blocks = 0;
+  size_t smem = 0;
+  bool bsmem = false;
+};
+template <typename T, typename BT>
+bool owner_sweep_config(int Nt, int Nx, int K, int ncol, const Offsets& off, int R, OwnerConfig* cfg);
+template <typename T, typename BT>
+cudaError_t launch_coarse_sweeps_owner(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* Bc,
+                                       const float* Sc, const typename cplx<T>::type* Dc, const Offsets& off,
+                                       int Nt, int Nx, int ncol, int sweeps, int R, unsigned* flags, unsigned* sync,
+                                       cudaStream_t st);
 // Coarse Gauss-Seidel kernel choice.  Levels with n = 16 ncol per sites (per <= 64)
 // run all colours on one 16-block cluster with the level in distributed shared
 // memory; in FP32 also the off-diagonal blocks live in shared memory when they

@@ -97,7 +97,7 @@ cudaError_t vcycle_level(amamg_ctx* h, int l, const typename cplx<T>::type* r, t
       }
     return cudaSuccess;
   }
-  const int kind = f64 ? L.gs64 : L.gs32;
+  const int kind = gs_kind_for<T>(L, R);
   if (sweeps > 0 && kind == GS_DSMEM) {
     const bool bsm = dsmem_blocks_in_smem<T>(L.n, L.off.K);
     if constexpr (f64)
@@ -106,6 +106,16 @@ cudaError_t vcycle_level(amamg_ctx* h, int l, const typename cplx<T>::type* r, t
     else
       err = launch_coarse_sweeps_dsmem<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, L.ncol, sweeps,
                                                        R, bsm, st);
+    h->launches++;
+    return err;
+  }
+  if (sweeps > 0 && kind == GS_OWNER) {
+    if constexpr (f64)
+      err = launch_coarse_sweeps_owner<double, double2>(e, r, L.Bc64, nullptr, L.Dc64, L.off, L.Nt, L.Nx, L.ncol,
+                                                       sweeps, R, h->d_owner_flags, h->d_sync, st);
+    else
+      err = launch_coarse_sweeps_owner<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, L.ncol, sweeps,
+                                                      R, h->d_owner_flags, h->d_sync, st);
     h->launches++;
     return err;
   }

@@ -213,7 +213,8 @@ def quantised_operator(L):
 
 def test_coarse_gs_kernels_agree_with_oracle(monkeypatch):
     """Every coarse Gauss-Seidel kernel (one launch per colour, L2 cluster,
-    distributed-shared-memory cluster, cooperative grid) on a 32^2 level with 21
+    distributed-shared-memory cluster, cooperative grid, site-owning blocks with
+    neighbour waits) on a 32^2 level with 21
     offsets (8 colours) and a 16^2 level with 25 offsets (16 colours), two
     right-hand sides, FP64 and FP32 (FP16 + scale blocks)."""
     from oracle import mixed
@@ -230,7 +231,7 @@ def test_coarse_gs_kernels_agree_with_oracle(monkeypatch):
         shape = (R, 2, L.Nt, L.Nx)
         inputs[l] = [mixed.round32(rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) for _ in range(2)]
     got64 = {}
-    for kind in ("colour", "cluster", "dsmem", "grid"):
+    for kind in ("colour", "cluster", "dsmem", "grid", "owner"):
         monkeypatch.setenv("AMAMG_COARSE_GS", kind)
         hier = A.setup(dev(U), 0.1, A.make_params(aggs))
         for l in (1, 2):
@@ -379,8 +380,8 @@ def test_invalid_arguments_rejected():
 def test_fp32_transfers_coarse_and_smoothers_match_emulated_storage(Nt):
     """FP32 kernels against FP64 arithmetic on the emulated FP16+scale operators
     and complex64-rounded inputs (oracle.mixed): FP32 rounding only.  The
-    coarse level (8 colours) is 8^2 at Nt = 32 (L2 cluster sweep) and 16^2 at
-    Nt = 64 (cluster sweep with the level in distributed shared memory)."""
+    coarse level (8 colours) is 8^2 at Nt = 32 (cooperative grid sweep) and
+    16^2 at Nt = 64 (cluster sweep with the level in distributed shared memory)."""
     from oracle import mixed
     Nx = Nt
     aggs = [4, 2]
