@@ -270,7 +270,7 @@ int op_dslash<double>(amamg_ctx* h, const double2* in, double2* out, const doubl
   const Level& L = h->lv[0];
   const double bytes = (double)L.n * (R * (32.0 + 32.0 + (b ? 32.0 : 0.0)) + 32.0);
   return launch(h, b ? "dslash_residual_f64" : "dslash_f64", bytes, st, [&] {
-    return launch_dslash<double2, double2, double>(in, out, b, h->U64, h->m0 + 2.0, L.Nt, L.Nx, R, st, h->cur_diag64);
+    return launch_dslash<double2, double2, double>(in, out, b, h->U64s, h->m0 + 2.0, L.Nt, L.Nx, R, st, h->cur_diag64);
   }, (double)L.n * R * (b ? 60.0 : 56.0));
 }
 
@@ -297,7 +297,7 @@ int smooth_impl(amamg_ctx* h, int l, typename cplx<T>::type* e, const typename c
     const T inv = (T)(1.0 / (h->m0 + 2.0));
     const typename cplx<T>::type* U;
     const T* inv_r;
-    if constexpr (f64) { U = h->U64; inv_r = h->cur_inv64; } else { U = h->U32; inv_r = h->cur_inv32; }
+    if constexpr (f64) { U = h->U64s; inv_r = h->cur_inv64; } else { U = h->U32; inv_r = h->cur_inv32; }
     // half sweep: read r, read + write e on half the sites, links once
     const double bytes = (double)L.n / 2 * (R * 2 * 3 * cb) + (double)L.n * 2 * cb / 2;
     for (int s = 0; s < sweeps; ++s)
@@ -499,14 +499,18 @@ int arnoldi_step(amamg_ctx* h, int j, int R, cudaStream_t st) {
   const int ldh = 3 * (m + 2);
   double2* d_h1 = h->d_h;
   const double2* vj = h->V + (size_t)j * vi;
-  if (h->prm.precision == AMAMG_SOLVE_MIXED) {
+  const bool mixed = h->prm.precision == AMAMG_SOLVE_MIXED;
+  if (mixed) {
     float2* zj = h->Z32 + (size_t)j * vi;
-    CKS(launch(h, "cast_f64_f32", (double)R * len * 24.0, st,
-               [&] { return launch_cast<double2, float2>(vj, h->v32, (long)R * len, st); }));
+    // v_j in FP32: cast here for j = 0; for j >= 1 the previous step's
+    // normalisation wrote it
+    if (j == 0)
+      CKS(launch(h, "cast_f64_f32", (double)R * len * 24.0, st,
+                 [&] { return launch_cast<double2, float2>(vj, h->v32, (long)R * len, st); }));
     CKS(vcycle_from<float>(h, 0, h->v32, zj, R, st));
     const Level& L = h->lv[0];
     CKS(launch(h, "dslash_mixed", (double)L.n * (R * (16.0 + 32.0) + 32.0), st, [&] {
-      return launch_dslash<float2, double2, double>(zj, h->w, nullptr, h->U64, h->m0 + 2.0, L.Nt, L.Nx, R, st,
+      return launch_dslash<float2, double2, double>(zj, h->w, nullptr, h->U64s, h->m0 + 2.0, L.Nt, L.Nx, R, st,
                                                     h->cur_diag64);
     }));
   } else {
@@ -540,9 +544,14 @@ int arnoldi_step(amamg_ctx* h, int j, int R, cudaStream_t st) {
     return launch_axpy_norm(h->w, vr, h->V, vi, vr, d_h1 + (m + 2), ldh, J, len, R, h->d_flag, h->d_npart, tk_norm,
                             d_h1, ldh, nrm_off, h->d_inv, nullptr, 0, 0.0, 1, st);
   }, (double)R * len * 8.0 * (J + 1)));
-  CKS(launch(h, "scale_copy", (double)R * len * 32.0, st, [&] {
-    return launch_scale_copy<double2>(h->V + (size_t)(j + 1) * vi, vr, h->w, vr, h->d_inv, len, R, st);
-  }));
+  if (mixed)
+    CKS(launch(h, "scale_copy", (double)R * len * 40.0, st, [&] {
+      return launch_scale_copy_dual(h->V + (size_t)(j + 1) * vi, h->v32, vr, h->w, vr, h->d_inv, len, R, st);
+    }));
+  else
+    CKS(launch(h, "scale_copy", (double)R * len * 32.0, st, [&] {
+      return launch_scale_copy<double2>(h->V + (size_t)(j + 1) * vi, vr, h->w, vr, h->d_inv, len, R, st);
+    }));
   CK(cudaMemcpyAsync(h->h_h, h->d_h, sizeof(double2) * R * ldh, cudaMemcpyDeviceToHost, st));
   return AMAMG_OK;
 }
@@ -817,7 +826,7 @@ void free_all(amamg_ctx* h) {
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
   h->ws = nullptr; h->ev_in = h->ev_out = nullptr;
-  dfree(h->U64); dfree(h->U32); dfree(h->Ainv); dfree(h->Ainv32); dfree(h->d_err); dfree(h->d_sync); dfree(h->d_owner_flags);
+  dfree(h->U64); dfree(h->U64s); dfree(h->U32); dfree(h->Ainv); dfree(h->Ainv32); dfree(h->d_err); dfree(h->d_sync); dfree(h->d_owner_flags);
   dfree(h->V); dfree(h->Z64); dfree(h->Z32); dfree(h->v32); dfree(h->w); dfree(h->res);
   dfree(h->partial); dfree(h->d_h); dfree(h->d_inv); dfree(h->d_flag); dfree(h->d_y); dfree(h->d_tickets); dfree(h->d_npart);
   dfree(h->d_diag64); dfree(h->d_inv64); dfree(h->d_inv32);
@@ -840,6 +849,7 @@ int do_setup(amamg_ctx* h, const void* Uin, cudaStream_t st) {
   CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
   CKS(dalloc(h, &h->U64, nl));
+  CKS(dalloc(h, &h->U64s, nl));
   CKS(dalloc(h, &h->U32, nl));
   CKS(dalloc(h, &h->d_err, 1));
   CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
@@ -848,8 +858,11 @@ int do_setup(amamg_ctx* h, const void* Uin, cudaStream_t st) {
   CKS(dalloc(h, &h->d_owner_flags, OWNER_MAX_BLOCKS));
   CK(cudaMemsetAsync(h->d_owner_flags, 0, OWNER_MAX_BLOCKS * sizeof(unsigned), st));
   CK(cudaMemcpyAsync(h->U64, Uin, nl * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-  CKS(launch(h, "setup_cast_links", nl * 24.0, st,
-             [&] { return launch_cast<double2, float2>(h->U64, h->U32, (long)nl, st); }));
+  CK(cudaMemcpyAsync(h->U64s, Uin, nl * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  CKS(launch(h, "setup_cast_links", nl * 24.0, st, [&] {
+    const cudaError_t e = launch_fold_boundary_sign(h->U64s, h->Nt, h->Nx, st);
+    return e != cudaSuccess ? e : launch_cast<double2, float2>(h->U64s, h->U32, (long)nl, st);
+  }));
   Offsets fine_off = wilson_offsets(h->Nt, h->Nx);
   for (int l = 0; l + 1 < L; ++l) {
     Level& F = h->lv[l];
@@ -973,7 +986,7 @@ int amamg_query_bytes(const amamg_params* p, int Nt, int Nx, int max_rhs, size_t
   int rc = check_params(p, Nt, Nx, &why);
   if (rc != AMAMG_OK) return rc;
   if (max_rhs < 1) return AMAMG_ERR_INVALID_ARG;
-  size_t sb = 2 * (size_t)Nt * Nx * (16 + 8);   // links FP64 + FP32
+  size_t sb = 2 * (size_t)Nt * Nx * (16 + 16 + 8);   // links FP64 (as given, sign-folded) + FP32
   size_t vb = 0;                                 // V-cycle vectors per RHS
   int nt = Nt, nx = Nx;
   Offsets off = wilson_offsets(Nt, Nx);

@@ -112,6 +112,19 @@ k_scale_copy(Cd* __restrict__ dst, size_t dr, const double2* __restrict__ src, s
     dst[r * dr + k] = to_c(s * src[r * sr + k], typename real_of<Cd>::type());
 }
 
+// dst_r = src_r * scale[r], and its FP32 rounding in dst32_r
+__global__ void __launch_bounds__(256)
+k_scale_copy_dual(double2* __restrict__ dst, float2* __restrict__ dst32, size_t dr, const double2* __restrict__ src,
+                  size_t sr, const double* __restrict__ scale, long len) {
+  const int r = blockIdx.y;
+  const double s = scale[r];
+  for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < len; k += (long)gridDim.x * blockDim.x) {
+    const double2 v = s * src[r * sr + k];
+    dst[r * dr + k] = v;
+    dst32[r * dr + k] = to_c(v, float());
+  }
+}
+
 template <typename Cs, typename Cd>
 __global__ void __launch_bounds__(256) k_cast(const Cs* __restrict__ src, Cd* __restrict__ dst, long len) {
   for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < len; k += (long)gridDim.x * blockDim.x)
@@ -284,6 +297,13 @@ cudaError_t launch_scale_copy(Cd* dst, size_t dr, const double2* src, size_t sr,
                               cudaStream_t st) {
   dim3 grid(grid_for(len), R);
   k_scale_copy<Cd><<<grid, 256, 0, st>>>(dst, dr, src, sr, scale, len);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_copy_dual(double2* dst, float2* dst32, size_t dr, const double2* src, size_t sr,
+                                   const double* scale, long len, int R, cudaStream_t st) {
+  dim3 grid(grid_for(len), R);
+  k_scale_copy_dual<<<grid, 256, 0, st>>>(dst, dst32, dr, src, sr, scale, len);
   return cudaGetLastError();
 }
 

@@ -110,8 +110,9 @@ struct amamg_ctx {
   int Nt = 0, Nx = 0;
   double m0 = 0.0;
   std::vector<Level> lv;
-  double2* U64 = nullptr;
-  float2* U32 = nullptr;
+  double2* U64 = nullptr;    // links as given (setup's local operators)
+  double2* U64s = nullptr;   // with the t-boundary sign folded in (stencil kernels)
+  float2* U32 = nullptr;     // FP32 rounding of U64s
   double2* Ainv = nullptr;   // coarsest inverse, nd x nd row-major
   float2* Ainv32 = nullptr;  // its FP32 rounding, applied by the mixed-precision V-cycle
   int nd = 0;

@@ -3,6 +3,10 @@
 //
 // Layout: vectors [R][spin][Nt][Nx] complex, links [mu][Nt][Nx] complex,
 // mu = 0 the (antiperiodic) t direction, mu = 1 the periodic x direction.
+// The stencil kernels take links with the Eq. (7) boundary sign folded in:
+// both hops across the t boundary (forward from t = Nt-1, backward from t = 0)
+// use the link U_0(Nt-1, x) and carry the factor -1, so storing -U_0(Nt-1, x)
+// gives exactly the same products without a per-site sign.
 // One thread per site and right-hand side; neighbours are re-read through L1/L2
 // (each input element is needed by 5 threads of adjacent rows/columns).
 #include "kernels.h"
@@ -10,7 +14,7 @@
 namespace {
 
 // h = sum_mu [ (1 - sigma_mu) U_mu(n) psi(n+mu) + (1 + sigma_mu) U_mu(n-mu)^* psi(n-mu) ]
-// with the Eq. (7) sign on hops across the t boundary, so that
+// (boundary sign folded into U, see above), so that
 // (D psi)(n) = (m0 + 2) psi(n) - h / 2.  Spin projection: every (1 -/+ sigma)
 // has rank one, so each hop needs one complex multiplication by its link.
 template <typename T, typename Cin>
@@ -24,18 +28,16 @@ __device__ __forceinline__ void hop_sum(const Cin* __restrict__ p0, const Cin* _
   const int tb = (t == 0) ? Nt - 1 : t - 1;
   const int xf = (x + 1 == Nx) ? 0 : x + 1;
   const int xb = (x == 0) ? Nx - 1 : x - 1;
-  const T sf = (t + 1 == Nt) ? T(-1) : T(1);
-  const T sb = (t == 0) ? T(-1) : T(1);
   const int s_tf = tf * Nx + x, s_tb = tb * Nx + x, s_xf = t * Nx + xf, s_xb = t * Nx + xb;
 
   // t forward: (1 - sigma_0) psi = (g, -g), g = psi_0 - psi_1
   C g = to_c(p0[s_tf], T()) - to_c(p1[s_tf], T());
-  g = sf * cmul(U[s], g);
+  g = cmul(U[s], g);
   h0 = g;
   h1 = -g;
   // t backward: (1 + sigma_0) psi = (g, g), g = psi_0 + psi_1, link U_0(n - t)^*
   g = to_c(p0[s_tb], T()) + to_c(p1[s_tb], T());
-  g = sb * cmulc(U[s_tb], g);
+  g = cmulc(U[s_tb], g);
   h0 += g;
   h1 += g;
   // x forward: (1 - sigma_1) psi = (g, -i g), g = psi_0 + i psi_1
@@ -104,7 +106,20 @@ k_rb_half(typename cplx<T>::type* __restrict__ e, const typename cplx<T>::type* 
   e0[s + n] = inv_diag * (rr[s + n] + T(0.5) * h1);
 }
 
+// U_0(Nt-1, x) <- -U_0(Nt-1, x) for every x (the boundary sign of Eq. (7))
+__global__ void k_fold_boundary_sign(double2* __restrict__ U, int Nt, int Nx) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= Nx) return;
+  double2& u = U[(size_t)(Nt - 1) * Nx + x];
+  u = make_double2(-u.x, -u.y);
+}
+
 }  // namespace
+
+cudaError_t launch_fold_boundary_sign(double2* U, int Nt, int Nx, cudaStream_t st) {
+  k_fold_boundary_sign<<<(Nx + 255) / 256, 256, 0, st>>>(U, Nt, Nx);
+  return cudaGetLastError();
+}
 
 template <typename Cin, typename Cout, typename T>
 cudaError_t launch_dslash(const Cin* in, Cout* out, const Cout* b, const typename cplx<T>::type* U,

@@ -34,6 +34,10 @@ template <typename T, typename PT>
 cudaError_t launch_restrict(const typename cplx<T>::type* ef, typename cplx<T>::type* ec, const PT* P,
                             const float* Pscale, int Nxf, int a, int Np, int Nq, int R, cudaStream_t st);
 
+// links with the t-boundary sign folded into U_0(Nt-1, x) (what the stencil
+// kernels take)
+cudaError_t launch_fold_boundary_sign(double2* U, int Nt, int Nx, cudaStream_t st);
+
 // coarse.cu
 template <typename T, typename BT>
 cudaError_t launch_coarse_apply(const typename cplx<T>::type* in, typename cplx<T>::type* out,
@@ -128,6 +132,9 @@ cudaError_t launch_multi_axpy(double2* y, size_t yr, const Cx* X, size_t xi, siz
 template <typename Cd>
 cudaError_t launch_scale_copy(Cd* dst, size_t dr, const double2* src, size_t sr, const double* scale, long len, int R,
                               cudaStream_t st);
+// dst_r = scale[r] src_r and dst32_r = its FP32 rounding (same strides)
+cudaError_t launch_scale_copy_dual(double2* dst, float2* dst32, size_t dr, const double2* src, size_t sr,
+                                   const double* scale, long len, int R, cudaStream_t st);
 template <typename Cs, typename Cd>
 cudaError_t launch_cast(const Cs* src, Cd* dst, long len, cudaStream_t st);
 

@@ -88,7 +88,7 @@ cudaError_t vcycle_level(amamg_ctx* h, int l, const typename cplx<T>::type* r, t
   if (l == 0) {
     const T inv = (T)(1.0 / (h->m0 + 2.0));
     const typename cplx<T>::type* U;
-    if constexpr (f64) U = h->U64; else U = h->U32;
+    if constexpr (f64) U = h->U64s; else U = h->U32;
     for (int s = 0; s < sweeps; ++s)
       for (int c = 0; c < 2; ++c) {
         err = launch_rb_half<T>(e, r, U, inv, L.Nt, L.Nx, c, R, st);

@@ -63,7 +63,10 @@ k_prolong(const typename cplx<T>::type* __restrict__ ec, typename cplx<T>::type*
 // e_coarse = P^H e_fine.  One warp per coarse vertex v = (p, q): it gathers the
 // rows of the four tiles that have v as a corner (tile (p-di, q-dj) sees v as
 // its corner c = 2 di + dj) plus v's own fine site (identity row), so every
-// coarse value is written once and no atomics are needed.
+// coarse value is written once and no atomics are needed.  The 4 nrows
+// (corner, row) pairs are dealt round-robin to the lanes; the lanes' partial
+// sums (two complex values) are combined by a reduce-scatter, after which lane
+// 8 h2 + 16 h1 holds real component q = 2 h1 + h2 of (e_c0, e_c1) and stores it.
 template <typename T, typename PT>
 __global__ void __launch_bounds__(256)
 k_restrict(const typename cplx<T>::type* __restrict__ ef, typename cplx<T>::type* __restrict__ ec,
@@ -74,37 +77,36 @@ k_restrict(const typename cplx<T>::type* __restrict__ ef, typename cplx<T>::type
   const int nf = nc * a * a;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (warp >= nc) return;
+  if (warp >= nc) return;                      // whole warps leave together
   const int p = warp / Nq, q = warp - (warp / Nq) * Nq;
   const C* f0 = ef + (size_t)blockIdx.y * 2 * nf;
   C acc0 = czero<C>(), acc1 = czero<C>();
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
+  for (int idx = lane; idx < 4 * nrows; idx += 32) {
+    const int c = idx / nrows, lr = idx - c * nrows;
     const int di = c >> 1, dj = c & 1;
     const int pT = (p - di < 0) ? Np - 1 : p - di;
     const int qT = (q - dj < 0) ? Nq - 1 : q - dj;
     const int tile = pT * Nq + qT;
     const size_t base = (size_t)tile * 8 * nrows + (size_t)(2 * c) * nrows;
-    for (int lr = lane; lr < nrows; lr += 32) {
-      const int l = (lr >> 1) + 1, alpha = lr & 1;
-      const int i = l / a, j = l - (l / a) * a;
-      const C f = f0[(size_t)alpha * nf + (pT * a + i) * Nxf + qT * a + j];
-      cmacc(acc0, p_load<T, PT>(P, Pscale, base + lr, tile), f);
-      cmacc(acc1, p_load<T, PT>(P, Pscale, base + nrows + lr, tile), f);
-    }
+    const int l = (lr >> 1) + 1, alpha = lr & 1;
+    const int i = l / a, j = l - (l / a) * a;
+    const C f = f0[(size_t)alpha * nf + (pT * a + i) * Nxf + qT * a + j];
+    cmacc(acc0, p_load<T, PT>(P, Pscale, base + lr, tile), f);
+    cmacc(acc1, p_load<T, PT>(P, Pscale, base + nrows + lr, tile), f);
   }
+  const bool h1 = (lane & 16) != 0, h2 = (lane & 8) != 0;
+  T ka = h1 ? acc1.x : acc0.x, kb = h1 ? acc1.y : acc0.y;
+  ka += __shfl_xor_sync(0xffffffffu, h1 ? acc0.x : acc1.x, 16);
+  kb += __shfl_xor_sync(0xffffffffu, h1 ? acc0.y : acc1.y, 16);
+  T sq = h2 ? kb : ka;
+  sq += __shfl_xor_sync(0xffffffffu, h2 ? ka : kb, 8);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    acc0.x += __shfl_xor_sync(0xffffffffu, acc0.x, o);
-    acc0.y += __shfl_xor_sync(0xffffffffu, acc0.y, o);
-    acc1.x += __shfl_xor_sync(0xffffffffu, acc1.x, o);
-    acc1.y += __shfl_xor_sync(0xffffffffu, acc1.y, o);
-  }
-  if (lane == 0) {
+  for (int o = 4; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if ((lane & 7) == 0) {
     const int sv = (p * a) * Nxf + q * a;
-    C* e0 = ec + (size_t)blockIdx.y * 2 * nc;
-    e0[warp] = acc0 + f0[sv];
-    e0[nc + warp] = acc1 + f0[nf + sv];
+    const T* fv = reinterpret_cast<const T*>(f0 + (h1 ? nf : 0) + sv);
+    T* e0 = reinterpret_cast<T*>(ec + (size_t)blockIdx.y * 2 * nc + (h1 ? nc : 0) + warp);
+    e0[h2] = sq + fv[h2];
   }
 }
 
