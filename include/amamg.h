@@ -197,6 +197,19 @@ int amamg_vcycle(amamg_handle h, const void* r, void* e, int R, int precision, v
  *     streams, other handles) race on it: serialise them. */
 int amamg_vcycle_noalloc(amamg_handle h, const void* r, void* e, int R, int precision, void* stream);
 
+/* Self-test of the bounded waits of the coarse Gauss-Seidel owner sweep (the
+ * kernel that runs coarse smoothing on most levels; its blocks wait only for
+ * the blocks owning their sites' neighbours, each wait limited to about half a
+ * second of polling).  Runs one two-sweep smoothing of coarse level l
+ * (1 <= l < nlevels - 1) in `precision` on the handle's own zero work vectors
+ * with one block that never publishes its phase counter, so its neighbours'
+ * waits run out.  Synchronises the stream.  Returns AMAMG_ERR_TIMEOUT when the
+ * time-out was recorded and reported (the expected outcome; the counters are
+ * re-armed and the handle stays usable), AMAMG_OK if no wait ran out, or
+ * AMAMG_ERR_INVALID_ARG when level l has no owner sweep with two or more
+ * blocks.  Nothing else in the library uses this path. */
+int amamg_selftest_sync_timeout(amamg_handle h, int level, int precision, void* stream);
+
 /* Integer structure of level l (host arrays; bit-exact tests):
  * role[Nt_l*Nx_l] (0 vertex, 1 edge, 2 interior), owner_tile[Nt_l*Nx_l]
  * (index p*(Nx_l/a)+q of the basket a site takes its formula from),

@@ -32,7 +32,7 @@ MAX_LEVELS = 4
 EXPORTED = [
     "amamg_default_params", "amamg_query_bytes", "amamg_setup", "amamg_solve", "amamg_apply_D",
     "amamg_apply_P", "amamg_apply_PH", "amamg_apply_coarse", "amamg_smooth", "amamg_coarsest_solve",
-    "amamg_vcycle", "amamg_vcycle_noalloc", "amamg_export_structure", "amamg_level_info", "amamg_export_P", "amamg_export_coarse",
+    "amamg_vcycle", "amamg_vcycle_noalloc", "amamg_selftest_sync_timeout", "amamg_export_structure", "amamg_level_info", "amamg_export_P", "amamg_export_coarse",
     "amamg_profile_enable", "amamg_profile_reset", "amamg_profile_get", "amamg_launch_count",
     "amamg_setup_seconds", "amamg_destroy", "amamg_status_string", "amamg_last_error",
     "amamg_batch_create", "amamg_batch_admit", "amamg_batch_cycle", "amamg_batch_retire", "amamg_batch_destroy",
@@ -79,6 +79,7 @@ def _load() -> ctypes.CDLL:
         "amamg_coarsest_solve": ([vp, vp, vp, ci, vp], ci),
         "amamg_vcycle": ([vp, vp, vp, ci, ci, vp], ci),
         "amamg_vcycle_noalloc": ([vp, vp, vp, ci, ci, vp], ci),
+        "amamg_selftest_sync_timeout": ([vp, ci, ci, vp], ci),
         "amamg_export_structure": ([vp, ci, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                     ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], ci),
         "amamg_level_info": ([vp, ci, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(ci)], ci),
@@ -283,6 +284,13 @@ def vcycle_noalloc(hier: Hierarchy, r, e, stream=None):
     R = int(r.shape[0])
     hier._check(_lib.amamg_vcycle_noalloc(hier.h, _ptr(r), _ptr(e), R, _prec(r), _stream(stream)),
                 "amamg_vcycle_noalloc")
+
+
+def selftest_sync_timeout(hier: Hierarchy, level: int, precision: int = None, stream=None) -> int:
+    """amamg_selftest_sync_timeout: one coarse smoothing in which one owner block
+    withholds its phase counter; returns the raw status (TIMEOUT expected)."""
+    prec = F64 if precision is None else precision
+    return int(_lib.amamg_selftest_sync_timeout(hier.h, level, prec, _stream(stream)))
 
 
 def export_structure(hier: Hierarchy, level: int):

@@ -395,6 +395,40 @@ int op_prolong(amamg_ctx* h, int l, const typename cplx<T>::type* ec, typename c
     }, (double)L.nT * L.nrows * 64.0 * R);
 }
 
+// The fine-level end of a V-cycle (prolongation from level 1, then the
+// post-smoothing red-black sweeps) as one launch when a resident shape exists.
+template <typename T>
+bool fine_post_possible(const amamg_ctx* h, int R) {
+  if (!h->fine_fused) return false;
+  const Level& L = h->lv[0];
+  if constexpr (sizeof(T) == 8) return fine_post_rows<double, double2>(L.Nt, L.Nx, L.a, R) > 0;
+  else return fine_post_rows<float, __half2>(L.Nt, L.Nx, L.a, R) > 0;
+}
+
+template <typename T>
+int op_fine_post(amamg_ctx* h, const typename cplx<T>::type* ec, typename cplx<T>::type* e,
+                 const typename cplx<T>::type* r, int R, cudaStream_t st) {
+  const Level& L = h->lv[0];
+  constexpr bool f64 = sizeof(T) == 8;
+  const double cb = f64 ? 16.0 : 8.0;
+  const int sweeps = h->prm.post_smooth;
+  const double pbytes = (double)L.nT * 8 * L.nrows * (f64 ? 16.0 : 4.0) + (f64 ? 0.0 : 4.0 * L.nT);
+  const double bytes = pbytes + (double)R * 2 * (L.n + h->lv[1].n) * cb +
+                       2.0 * sweeps * ((double)L.n / 2 * (R * 2 * 3 * cb) + (double)L.n * 2 * cb / 2);
+  const double flops = (double)L.nT * L.nrows * 64.0 * R + 2.0 * sweeps * (double)L.n / 2 * R * 56.0;
+  const T inv = (T)(1.0 / (h->m0 + 2.0));
+  if constexpr (f64)
+    return launch(h, "fine_post_f64", bytes, st, [&] {
+      return launch_fine_post<double, double2>(ec, e, r, L.P64, nullptr, h->U64s, inv, h->cur_inv64, L.Nt, L.Nx,
+                                               L.a, sweeps, R, h->d_owner_flags, h->d_sync, st);
+    }, flops);
+  else
+    return launch(h, "fine_post_f32", bytes, st, [&] {
+      return launch_fine_post<float, __half2>(ec, e, r, L.P16, L.Ps, h->U32, inv, h->cur_inv32, L.Nt, L.Nx, L.a,
+                                              sweeps, R, h->d_owner_flags, h->d_sync, st);
+    }, flops);
+}
+
 template <typename T>
 int op_restrict(amamg_ctx* h, int l, const typename cplx<T>::type* ef, typename cplx<T>::type* ec, int R,
                 cudaStream_t st) {
@@ -463,6 +497,8 @@ int vcycle_from(amamg_ctx* h, int l, const typename cplx<T>::type* r, typename c
   if constexpr (sizeof(T) == 8) { rc = C.r64; ec = C.e64; } else { rc = C.r32; ec = C.e32; }
   CKS(op_restrict<T>(h, l, r, rc, R, st));
   CKS(vcycle_from<T>(h, l + 1, rc, ec, R, st));
+  if (l == 0 && h->prm.post_smooth > 0 && fine_post_possible<T>(h, R))
+    return op_fine_post<T>(h, ec, e, r, R, st);
   CKS(op_prolong<T>(h, l, ec, e, R, st));
   return smooth_impl<T>(h, l, e, r, R, h->prm.post_smooth, st);
 }
@@ -1025,6 +1061,10 @@ int amamg_setup(const amamg_params* p, const void* U, int Nt, int Nx, double m0,
   // AMAMG_GRAPHS=0 runs the Arnoldi steps as plain launches instead of CUDA
   // graphs (same kernels; for profilers that handle graph nodes slowly)
   if (const char* g = std::getenv("AMAMG_GRAPHS")) h->use_graphs = std::strcmp(g, "0") != 0;
+  // AMAMG_FINE_FUSED=1 runs the fine-level prolongation and red-black sweeps as
+  // one cooperative launch (same arithmetic; measured no faster than the
+  // separate launches on the 256^2 workload, so off by default)
+  if (const char* g = std::getenv("AMAMG_FINE_FUSED")) h->fine_fused = std::atoi(g) != 0;
   h->Nt = Nt; h->Nx = Nx; h->m0 = m0;
   cudaStream_t st = S(stream);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1189,6 +1229,37 @@ int amamg_smooth(amamg_handle h, int level, const void* r, void* e, int R, int s
   if (precision == AMAMG_F64) return smooth_impl<double>(h, level, (double2*)e, (const double2*)r, R, sweeps, S(stream));
   if (precision == AMAMG_F32) return smooth_impl<float>(h, level, (float2*)e, (const float2*)r, R, sweeps, S(stream));
   return AMAMG_ERR_INVALID_ARG;
+}
+
+int amamg_selftest_sync_timeout(amamg_handle h, int level, int precision, void* stream) {
+  if (!h || level < 1 || level + 1 >= (int)h->lv.size()) return AMAMG_ERR_INVALID_ARG;
+  if (precision != AMAMG_F64 && precision != AMAMG_F32) return AMAMG_ERR_INVALID_ARG;
+  cudaStream_t st = S(stream);
+  CKS(ensure_vcycle_ws(h, 1));
+  Level& L = h->lv[level];
+  OwnerConfig oc;
+  const bool f64 = precision == AMAMG_F64;
+  const bool ok = f64 ? owner_sweep_config<double, double2>(L.Nt, L.Nx, L.off.K, L.ncol, L.off, 1, &oc)
+                      : owner_sweep_config<float, __half2>(L.Nt, L.Nx, L.off.K, L.ncol, L.off, 1, &oc);
+  if (!ok || oc.blocks < 2) {
+    h->err = "level has no owner sweep with two or more blocks";
+    return AMAMG_ERR_INVALID_ARG;
+  }
+  cudaError_t e;
+  if (f64) {
+    CK(cudaMemsetAsync(L.r64, 0, sizeof(double2) * 2 * L.n, st));
+    CK(cudaMemsetAsync(L.e64, 0, sizeof(double2) * 2 * L.n, st));
+    e = launch_coarse_sweeps_owner<double, double2>(L.e64, L.r64, L.Bc64, nullptr, L.Dc64, L.off, L.Nt, L.Nx, L.ncol,
+                                                    2, 1, h->d_owner_flags, h->d_sync, st, 0);
+  } else {
+    CK(cudaMemsetAsync(L.r32, 0, sizeof(float2) * 2 * L.n, st));
+    CK(cudaMemsetAsync(L.e32, 0, sizeof(float2) * 2 * L.n, st));
+    e = launch_coarse_sweeps_owner<float, __half2>(L.e32, L.r32, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, L.ncol,
+                                                   2, 1, h->d_owner_flags, h->d_sync, st, 0);
+  }
+  CK(e);
+  h->launches++;
+  return check_grid_sync(h, st);
 }
 
 int amamg_coarsest_solve(amamg_handle h, const void* r, void* e, int R, void* stream) {

@@ -318,10 +318,11 @@ k_coarse_sweeps_grid(typename cplx<T>::type* __restrict__ e, const typename cplx
 // stale, and no neighbour still reads a value it is about to overwrite.
 // Phase counters are flags[block] = base + phases done, base = sync[3]
 // (advanced by the last block to finish through the ticket sync[4]), so they
-// need no reset between launches.  Polls are bounded (OWNER_SPIN_LIMIT); a
-// block that times out sets sync[2] and stops waiting, so the launch always
-// ends.
-constexpr unsigned OWNER_SPIN_LIMIT = 1u << 22;
+// need no reset between launches.  Polls are bounded (OWNER_SPIN_LIMIT, about
+// half a second); a block that times out sets sync[2] and stops waiting, so
+// the launch always ends.  withhold >= 0 names a block that never publishes
+// (self-test of that time-out path; -1 in every normal launch).
+constexpr unsigned OWNER_SPIN_LIMIT = 1u << 20;
 // lanes per site: FP64 32 (one offset per lane: the shortest chain of
 // dependent FP64 instructions, which bounds a colour phase on this GPU's
 // narrow FP64 pipe), FP32 8
@@ -339,7 +340,8 @@ __global__ void __launch_bounds__(256, 1)
 k_coarse_sweeps_owner(typename cplx<T>::type* __restrict__ e, const typename cplx<T>::type* __restrict__ r,
                       const BT* __restrict__ Bc, const float* __restrict__ Sc,
                       const typename cplx<T>::type* __restrict__ Dc, Offsets off, int Nt, int Nx, int ncol,
-                      int sweeps, int cnt, unsigned* __restrict__ flags, unsigned* __restrict__ sync) {
+                      int sweeps, int cnt, unsigned* __restrict__ flags, unsigned* __restrict__ sync,
+                      int withhold) {
   using C = typename cplx<T>::type;
   constexpr int LPS = OwnerLanes<T>::value;
   static_assert(LPS >= 4 && LPS <= 32 && (LPS & (LPS - 1)) == 0, "lanes per site: a power of two, 4..32");
@@ -523,7 +525,7 @@ k_coarse_sweeps_owner(typename cplx<T>::type* __restrict__ e, const typename cpl
         }
       }
       __syncthreads();
-      if (threadIdx.x == 0) {
+      if (threadIdx.x == 0 && (int)blockIdx.x != withhold) {
         __threadfence();
         atomicExch(flags + blockIdx.x, base + (unsigned)p + 1u);
       }
@@ -958,7 +960,7 @@ template <typename T, typename BT>
 cudaError_t launch_coarse_sweeps_owner(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* Bc,
                                        const float* Sc, const typename cplx<T>::type* Dc, const Offsets& off,
                                        int Nt, int Nx, int ncol, int sweeps, int R, unsigned* flags, unsigned* sync,
-                                       cudaStream_t st) {
+                                       cudaStream_t st, int withhold) {
   OwnerConfig oc;
   if (!owner_sweep_config<T, BT>(Nt, Nx, off.K, ncol, off, R, &oc)) return cudaErrorNotSupported;
   auto kern = oc.bsmem ? k_coarse_sweeps_owner<T, BT, true> : k_coarse_sweeps_owner<T, BT, false>;
@@ -975,7 +977,8 @@ cudaError_t launch_coarse_sweeps_owner(typename cplx<T>::type* e, const typename
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, e, r, Bc, Sc, Dc, off, Nt, Nx, ncol, sweeps, oc.cnt, flags, sync);
+  return cudaLaunchKernelEx(&cfg, kern, e, r, Bc, Sc, Dc, off, Nt, Nx, ncol, sweeps, oc.cnt, flags, sync,
+                            withhold);
 }
 
 // the distributed-shared-memory sweep needs per = n / (16 ncol) whole sites per
@@ -1101,10 +1104,10 @@ template bool owner_sweep_config<double, double2>(int, int, int, int, const Offs
 template bool owner_sweep_config<float, __half2>(int, int, int, int, const Offsets&, int, OwnerConfig*);
 template cudaError_t launch_coarse_sweeps_owner<double, double2>(double2*, const double2*, const double2*,
                                                                 const float*, const double2*, const Offsets&, int, int,
-                                                                int, int, int, unsigned*, unsigned*, cudaStream_t);
+                                                                int, int, int, unsigned*, unsigned*, cudaStream_t, int);
 template cudaError_t launch_coarse_sweeps_owner<float, __half2>(float2*, const float2*, const __half2*, const float*,
                                                                const float2*, const Offsets&, int, int, int, int, int,
-                                                               unsigned*, unsigned*, cudaStream_t);
+                                                               unsigned*, unsigned*, cudaStream_t, int);
 template int grid_sweep_blocks<double, double2>(int, int, int);
 template int grid_sweep_blocks<float, __half2>(int, int, int);
 template cudaError_t launch_coarse_sweeps_grid<double, double2>(double2*, const double2*, const double2*, const float*,

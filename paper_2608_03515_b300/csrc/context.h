@@ -159,6 +159,7 @@ struct amamg_ctx {
   std::vector<long long> step_graph_kernels;
   int graph_R = 0;
   bool use_graphs = true;
+  bool fine_fused = false;   // fine-level prolongation + red-black sweeps in one launch (AMAMG_FINE_FUSED=1: on)
 
   std::string err;
   long long launches = 0;

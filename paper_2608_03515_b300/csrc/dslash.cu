@@ -9,6 +9,8 @@
 // gives exactly the same products without a per-site sign.
 // One thread per site and right-hand side; neighbours are re-read through L1/L2
 // (each input element is needed by 5 threads of adjacent rows/columns).
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace {
@@ -17,7 +19,15 @@ namespace {
 // (boundary sign folded into U, see above), so that
 // (D psi)(n) = (m0 + 2) psi(n) - h / 2.  Spin projection: every (1 -/+ sigma)
 // has rank one, so each hop needs one complex multiplication by its link.
-template <typename T, typename Cin>
+// loads of the vector hop_sum reads: plain, or through L2 (ld.global.cg) when
+// other blocks of the same launch wrote it
+template <bool CG, typename Cin>
+__device__ __forceinline__ Cin hop_ld(const Cin* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
+template <typename T, typename Cin, bool CG = false>
 __device__ __forceinline__ void hop_sum(const Cin* __restrict__ p0, const Cin* __restrict__ p1,
                                         const typename cplx<T>::type* __restrict__ U,
                                         int t, int x, int Nt, int Nx, int n,
@@ -31,22 +41,22 @@ __device__ __forceinline__ void hop_sum(const Cin* __restrict__ p0, const Cin* _
   const int s_tf = tf * Nx + x, s_tb = tb * Nx + x, s_xf = t * Nx + xf, s_xb = t * Nx + xb;
 
   // t forward: (1 - sigma_0) psi = (g, -g), g = psi_0 - psi_1
-  C g = to_c(p0[s_tf], T()) - to_c(p1[s_tf], T());
+  C g = to_c(hop_ld<CG>(p0 + s_tf), T()) - to_c(hop_ld<CG>(p1 + s_tf), T());
   g = cmul(U[s], g);
   h0 = g;
   h1 = -g;
   // t backward: (1 + sigma_0) psi = (g, g), g = psi_0 + psi_1, link U_0(n - t)^*
-  g = to_c(p0[s_tb], T()) + to_c(p1[s_tb], T());
+  g = to_c(hop_ld<CG>(p0 + s_tb), T()) + to_c(hop_ld<CG>(p1 + s_tb), T());
   g = cmulc(U[s_tb], g);
   h0 += g;
   h1 += g;
   // x forward: (1 - sigma_1) psi = (g, -i g), g = psi_0 + i psi_1
-  g = to_c(p0[s_xf], T()) + ci(to_c(p1[s_xf], T()));
+  g = to_c(hop_ld<CG>(p0 + s_xf), T()) + ci(to_c(hop_ld<CG>(p1 + s_xf), T()));
   g = cmul(U[n + s], g);
   h0 += g;
   h1 -= ci(g);
   // x backward: (1 + sigma_1) psi = (g, i g), g = psi_0 - i psi_1, link U_1(n - x)^*
-  g = to_c(p0[s_xb], T()) - ci(to_c(p1[s_xb], T()));
+  g = to_c(hop_ld<CG>(p0 + s_xb), T()) - ci(to_c(hop_ld<CG>(p1 + s_xb), T()));
   g = cmulc(U[n + s_xb], g);
   h0 += g;
   h1 += ci(g);
@@ -106,6 +116,124 @@ k_rb_half(typename cplx<T>::type* __restrict__ e, const typename cplx<T>::type* 
   e0[s + n] = inv_diag * (rr[s + n] + T(0.5) * h1);
 }
 
+// P entry of the fused kernel (same layout and rounding as the transfer kernels)
+template <typename T, typename PT>
+__device__ __forceinline__ typename cplx<T>::type fp_load(const PT* P, const float* scale, size_t idx, int tile);
+template <>
+__device__ __forceinline__ double2 fp_load<double, double2>(const double2* P, const float*, size_t idx, int) {
+  return P[idx];
+}
+template <>
+__device__ __forceinline__ float2 fp_load<float, __half2>(const __half2* P, const float* scale, size_t idx, int tile) {
+  return h2c<float>(P[idx], scale[tile]);
+}
+
+// Fine-level end of the V-cycle in one cooperative launch: e = P e_c (phase
+// 0), then `sweeps` red-black sweeps on D e = r (phases 1, 2, ...: colour 0,
+// colour 1, ...).  Block b owns rows [b rows, (b+1) rows) of one right-hand
+// side.  A red-black update reads e one
+// row up and down, so before phase p a block waits only until the two
+// neighbouring row blocks have published phase p - 1 (the owner-sweep scheme:
+// flags[block] = base + phases done, base = sync[3], end ticket sync[4],
+// bounded polls, time-out flag sync[2]).  Per site the arithmetic is that of
+// k_prolong and k_rb_half (same order), so the result equals that of the
+// separate launches; e is read through L2 because other blocks wrote it.
+constexpr unsigned FINE_SPIN_LIMIT = 1u << 20;
+
+template <typename T, typename PT>
+__global__ void __launch_bounds__(256)
+k_fine_post(const typename cplx<T>::type* __restrict__ ec, typename cplx<T>::type* __restrict__ e,
+            const typename cplx<T>::type* __restrict__ r, const PT* __restrict__ P, const float* __restrict__ Pscale,
+            const typename cplx<T>::type* __restrict__ U, T inv_diag_s, const T* __restrict__ inv_diag_r,
+            int Nt, int Nx, int a, int sweeps, int rows, unsigned* __restrict__ flags, unsigned* __restrict__ sync) {
+  using C = typename cplx<T>::type;
+  __shared__ int alive;
+  const int nrb = Nt / rows;
+  const int rhs = blockIdx.x / nrb, b = blockIdx.x - rhs * nrb;
+  const int n = Nt * Nx, Np = Nt / a, Nq = Nx / a, nc = Np * Nq, nrows = 2 * (a * a - 1);
+  const T inv_diag = inv_diag_r ? inv_diag_r[rhs] : inv_diag_s;
+  C* e0 = e + (size_t)rhs * 2 * n;
+  const C* r0 = r + (size_t)rhs * 2 * n;
+  const C* c0 = ec + (size_t)rhs * 2 * nc;
+  const int t0 = b * rows;
+  const unsigned base = *reinterpret_cast<volatile unsigned*>(sync + 3);
+  if (threadIdx.x == 0) alive = 1;
+  // phase 0: prolongation of the owned rows (both spins of a site per thread)
+  for (int idx = threadIdx.x; idx < rows * Nx; idx += blockDim.x) {
+    const int t = t0 + idx / Nx, x = idx - (idx / Nx) * Nx;
+    const int p = t / a, i = t - p * a, q = x / a, j = x - q * a;
+    const int tile = p * Nq + q, l = i * a + j, v = t * Nx + x;
+    if (l == 0) {
+      __stcg(e0 + v, c0[tile]);
+      __stcg(e0 + n + v, c0[nc + tile]);
+      continue;
+    }
+    const int p1 = (p + 1 == Np) ? 0 : p + 1, q1 = (q + 1 == Nq) ? 0 : q + 1;
+    const int vtx[4] = {p * Nq + q, p * Nq + q1, p1 * Nq + q, p1 * Nq + q1};
+#pragma unroll
+    for (int alpha = 0; alpha < 2; ++alpha) {
+      const int lr = 2 * (l - 1) + alpha;
+      const size_t pb = (size_t)tile * 8 * nrows + lr;
+      C acc = czero<C>();
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        cmac(acc, fp_load<T, PT>(P, Pscale, pb + (size_t)(2 * c) * nrows, tile), c0[vtx[c]]);
+        cmac(acc, fp_load<T, PT>(P, Pscale, pb + (size_t)(2 * c + 1) * nrows, tile), c0[nc + vtx[c]]);
+      }
+      __stcg(e0 + (size_t)alpha * n + v, acc);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicExch(flags + blockIdx.x, base + 1u);
+  }
+  int p = 1;
+  const int hx = Nx >> 1;
+  for (int sw = 0; sw < sweeps; ++sw) {
+    for (int colour = 0; colour < 2; ++colour, ++p) {
+      if (threadIdx.x < 2 && nrb > 1 && alive) {
+        int nb = b + (threadIdx.x == 0 ? -1 : 1);
+        nb += nb < 0 ? nrb : (nb >= nrb ? -nrb : 0);
+        const volatile unsigned* f = flags + rhs * nrb + nb;
+        const unsigned want = base + (unsigned)p;
+        unsigned it = 0;
+        while ((int)(*f - want) < 0) {
+          if (++it == FINE_SPIN_LIMIT) {
+            atomicExch(sync + 2, 1u);
+            alive = 0;
+            break;
+          }
+        }
+        __threadfence();
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < rows * hx; idx += blockDim.x) {
+        const int t = t0 + idx / hx;
+        const int x = 2 * (idx - (idx / hx) * hx) + ((t + colour) & 1);
+        const int s = t * Nx + x;
+        C h0, h1;
+        hop_sum<T, C, true>(e0, e0 + n, U, t, x, Nt, Nx, n, h0, h1);
+        __stcg(e0 + s, inv_diag * (r0[s] + T(0.5) * h0));
+        __stcg(e0 + s + n, inv_diag * (r0[s + n] + T(0.5) * h1));
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicExch(flags + blockIdx.x, base + (unsigned)p + 1u);
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(sync + 4, 1u) == gridDim.x - 1) {
+      sync[4] = 0;
+      __threadfence();
+      atomicExch(sync + 3, base + (unsigned)p);
+    }
+  }
+}
+
 // U_0(Nt-1, x) <- -U_0(Nt-1, x) for every x (the boundary sign of Eq. (7))
 __global__ void k_fold_boundary_sign(double2* __restrict__ U, int Nt, int Nx) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -139,6 +267,63 @@ cudaError_t launch_rb_half(typename cplx<T>::type* e, const typename cplx<T>::ty
   k_rb_half<T><<<grid, 256, 0, st>>>(e, r, U, inv_diag, inv_diag_r, Nt, Nx, colour);
   return cudaGetLastError();
 }
+
+// rows per block of the fused fine post-smoother for R right-hand sides: the
+// fewest (a divisor of Nt) whose R Nt / rows blocks of 256 threads are at most
+// two per SM and can all be resident; 0 when none (then the separate kernels
+// run).  Prolongation is per site, so a block's rows need not be whole tiles.
+template <typename T, typename PT>
+int fine_post_rows(int Nt, int Nx, int a, int R) {
+  static int cap = -1, sms = 0;          // co-resident blocks of 256 threads, SMs; first device queried
+  if (cap < 0) {
+    int dev = 0, occ = 0, coop = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fine_post<T, PT>, 256, 0) != cudaSuccess) {
+      cudaGetLastError();
+      cap = 0;
+    } else {
+      cap = coop ? sms * occ : 0;
+    }
+  }
+  if (cap <= 0 || (Nx & 1) || Nt % a || Nx % a) return 0;
+  const long limit = std::min<long>(std::min<long>(cap, 2L * sms), FINE_MAX_BLOCKS);
+  for (int rows = 1; rows <= Nt; ++rows) {
+    if (Nt % rows) continue;
+    if ((long)R * (Nt / rows) <= limit) return rows;
+  }
+  return 0;
+}
+
+template <typename T, typename PT>
+cudaError_t launch_fine_post(const typename cplx<T>::type* ec, typename cplx<T>::type* e,
+                             const typename cplx<T>::type* r, const PT* P, const float* Pscale,
+                             const typename cplx<T>::type* U, T inv_diag, const T* inv_diag_r, int Nt, int Nx, int a,
+                             int sweeps, int R, unsigned* flags, unsigned* sync, cudaStream_t st) {
+  const int rows = fine_post_rows<T, PT>(Nt, Nx, a, R);
+  if (rows <= 0) return cudaErrorNotSupported;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(R * (Nt / rows));
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_fine_post<T, PT>, ec, e, r, P, Pscale, U, inv_diag, inv_diag_r, Nt, Nx, a,
+                            sweeps, rows, flags, sync);
+}
+
+template int fine_post_rows<double, double2>(int, int, int, int);
+template int fine_post_rows<float, __half2>(int, int, int, int);
+template cudaError_t launch_fine_post<double, double2>(const double2*, double2*, const double2*, const double2*,
+                                                       const float*, const double2*, double, const double*, int, int,
+                                                       int, int, int, unsigned*, unsigned*, cudaStream_t);
+template cudaError_t launch_fine_post<float, __half2>(const float2*, float2*, const float2*, const __half2*,
+                                                      const float*, const float2*, float, const float*, int, int, int,
+                                                      int, int, unsigned*, unsigned*, cudaStream_t);
 
 template cudaError_t launch_dslash<double2, double2, double>(const double2*, double2*, const double2*,
                                                              const double2*, double, int, int, int, cudaStream_t,

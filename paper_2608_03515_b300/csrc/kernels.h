@@ -38,6 +38,20 @@ cudaError_t launch_restrict(const typename cplx<T>::type* ef, typename cplx<T>::
 // kernels take)
 cudaError_t launch_fold_boundary_sign(double2* U, int Nt, int Nx, cudaStream_t st);
 
+// Fine-level end of the V-cycle (e = P e_c, then `sweeps` red-black sweeps on
+// D e = r) in one cooperative launch of row-owning blocks with neighbour waits
+// (flags / sync as the owner sweep); the same arithmetic per site as
+// launch_prolong followed by the launch_rb_half sequence.  fine_post_rows = 0:
+// no resident shape for R (the separate kernels run).
+constexpr int FINE_MAX_BLOCKS = 4096;
+template <typename T, typename PT>
+int fine_post_rows(int Nt, int Nx, int a, int R);
+template <typename T, typename PT>
+cudaError_t launch_fine_post(const typename cplx<T>::type* ec, typename cplx<T>::type* e,
+                             const typename cplx<T>::type* r, const PT* P, const float* Pscale,
+                             const typename cplx<T>::type* U, T inv_diag, const T* inv_diag_r, int Nt, int Nx, int a,
+                             int sweeps, int R, unsigned* flags, unsigned* sync, cudaStream_t st);
+
 // coarse.cu
 template <typename T, typename BT>
 cudaError_t launch_coarse_apply(const typename cplx<T>::type* in, typename cplx<T>::type* out,
@@ -83,7 +97,7 @@ template <typename T, typename BT>
 cudaError_t launch_coarse_sweeps_owner(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* Bc,
                                        const float* Sc, const typename cplx<T>::type* Dc, const Offsets& off,
                                        int Nt, int Nx, int ncol, int sweeps, int R, unsigned* flags, unsigned* sync,
-                                       cudaStream_t st);
+                                       cudaStream_t st, int withhold = -1);
 // Coarse Gauss-Seidel kernel choice.  Levels with n = 16 ncol per sites (per <= 64)
 // run all colours on one 16-block cluster with the level in distributed shared
 // memory; in FP32 also the off-diagonal blocks live in shared memory when they

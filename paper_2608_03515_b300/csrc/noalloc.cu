@@ -80,11 +80,29 @@ cudaError_t vcycle_level(amamg_ctx* h, int l, const typename cplx<T>::type* r, t
   h->launches++;
   err = vcycle_level<T>(h, l + 1, w.r[l + 1], w.e[l + 1], w, R, st);
   if (err != cudaSuccess) return err;
+  const int sweeps = h->prm.post_smooth;
+  if (l == 0 && sweeps > 0 && h->fine_fused) {
+    // the same choice as the allocating V-cycle: prolongation and red-black
+    // sweeps in one launch when a resident shape exists
+    const T inv = (T)(1.0 / (h->m0 + 2.0));
+    bool fused;
+    if constexpr (f64) fused = fine_post_rows<double, double2>(L.Nt, L.Nx, L.a, R) > 0;
+    else fused = fine_post_rows<float, __half2>(L.Nt, L.Nx, L.a, R) > 0;
+    if (fused) {
+      if constexpr (f64)
+        err = launch_fine_post<double, double2>(w.e[l + 1], e, r, L.P64, nullptr, h->U64s, inv, nullptr, L.Nt, L.Nx,
+                                                L.a, sweeps, R, h->d_owner_flags, h->d_sync, st);
+      else
+        err = launch_fine_post<float, __half2>(w.e[l + 1], e, r, L.P16, L.Ps, h->U32, inv, nullptr, L.Nt, L.Nx, L.a,
+                                               sweeps, R, h->d_owner_flags, h->d_sync, st);
+      h->launches++;
+      return err;
+    }
+  }
   if constexpr (f64) err = launch_prolong<double, double2>(w.e[l + 1], e, L.P64, nullptr, L.Nx, L.a, L.Np, L.Nq, R, st);
   else err = launch_prolong<float, __half2>(w.e[l + 1], e, L.P16, L.Ps, L.Nx, L.a, L.Np, L.Nq, R, st);
   if (err != cudaSuccess) return err;
   h->launches++;
-  const int sweeps = h->prm.post_smooth;
   if (l == 0) {
     const T inv = (T)(1.0 / (h->m0 + 2.0));
     const typename cplx<T>::type* U;

@@ -260,6 +260,58 @@ def test_coarse_gs_kernels_agree_with_oracle(monkeypatch):
             assert relerr(g, got64[l][0]) <= 1e-14
 
 
+@pytest.mark.parametrize("R", [1, 3])
+def test_fused_fine_post_smoother_equals_separate_launches(monkeypatch, R):
+    """The fine-level end of the V-cycle (prolongation + two red-black sweeps)
+    as one cooperative launch gives the result of the separate kernels (same
+    arithmetic per site), in FP64 and FP32, and the FP64 V-cycle matches the
+    oracle's."""
+    Nt, Nx = 64, 32
+    aggs = [4, 2]
+    U = random_links(Nt, Nx, 41)
+    levels = amg.build_hierarchy(W.dirac_matrix(U, 0.1), Nt, Nx, aggs)
+    psi = fx.gaussian_rhs(R, Nt, Nx, 42)
+    out = {}
+    for fused in ("1", "0"):
+        monkeypatch.setenv("AMAMG_FINE_FUSED", fused)
+        hier = A.setup(dev(U), 0.1, A.make_params(aggs))
+        e64 = torch.empty(psi.shape, dtype=torch.complex128, device=DEV)
+        e32 = torch.empty(psi.shape, dtype=torch.complex64, device=DEV)
+        A.vcycle(hier, dev(psi), e64)
+        A.vcycle(hier, dev(psi, torch.complex64), e32)
+        out[fused] = (host(e64), host(e32))
+        hier.destroy()
+    assert relerr(out["1"][0], out["0"][0]) <= 1e-15
+    assert relerr(out["1"][1], out["0"][1]) <= 1e-6
+    for r in range(R):
+        want = lattice_vec(amg.vcycle(levels, W.to_flat(psi[r])), Nt, Nx)
+        assert relerr(out["1"][0][r], want) <= 1e-11
+
+
+def test_owner_sweep_wait_time_out_is_reported_and_handle_recovers():
+    """A block of the owner sweep that never publishes makes its neighbours'
+    bounded waits run out: the library reports AMAMG_ERR_TIMEOUT (no fault, no
+    hang), re-arms its counters, and the next smoothing is correct again."""
+    import time
+    Nt = Nx = 64
+    aggs = [2, 2, 2]
+    U, D, hier, levels = make(Nt, Nx, aggs, m0=0.1, seed=33)
+    L = levels[1]
+    rng = np.random.Generator(np.random.PCG64(34))
+    for prec in (A.F64, A.F32):
+        t0 = time.time()
+        assert A.selftest_sync_timeout(hier, 1, prec) == A.ERR_TIMEOUT
+        assert time.time() - t0 < 60.0
+        r = rng.standard_normal((1, 2, L.Nt, L.Nx)) + 1j * rng.standard_normal((1, 2, L.Nt, L.Nx))
+        e0 = rng.standard_normal((1, 2, L.Nt, L.Nx)) + 1j * rng.standard_normal((1, 2, L.Nt, L.Nx))
+        e = dev(e0)
+        A.smooth(hier, 1, dev(r), e, 2)
+        want = W.to_flat(e0[0])
+        for _ in range(2):
+            want = amg.gs_sweep(L.A, L.dinv, L.colour, want, W.to_flat(r[0]))
+        assert relerr(host(e)[0], lattice_vec(want, L.Nt, L.Nx)) <= 1e-12
+
+
 def test_coarsest_solve_and_vcycle_fp64():
     Nt = Nx = 32
     U, D, hier, levels = make(Nt, Nx, [4, 2], m0=0.05, seed=10)
