@@ -208,6 +208,38 @@ def run_probe(args):
                       "ms_per_rep": ev[0].elapsed_time(ev[1]) / max(args.reps, 1)}))
 
 
+# ----------------------------------------------------------------------------- wirebasket-size spread
+
+SPREAD_AGGS = ([4, 2], [2, 2, 2], [4, 4], [2, 4])
+
+
+def run_spread(dev, U, masses, psi):
+    """The benchmark field and masses solved (FP64) with several tile-side
+    hierarchies: iterations, solve and setup time per hierarchy (the paper's
+    claim that iteration counts depend little on the wirebasket size)."""
+    import torch
+    from paper_2608_03515_b300 import amamg as A
+    out = []
+    x = torch.empty_like(psi)
+    for aggs in SPREAD_AGGS:
+        row = {"tiles": aggs, "iterations": [], "solve_ms": [], "setup_ms": []}
+        for m0 in masses:
+            h = A.setup(U, m0, A.make_params(aggs, precision=A.SOLVE_FP64, restart=RESTART, tol=TOL))
+            row["setup_ms"].append(round(1e3 * A.setup_seconds(h), 1))
+            A.solve(h, psi, x)                                   # warm-up (graphs)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(torch.cuda.current_stream())
+            info = A.solve(h, psi, x)
+            ev[1].record(torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            assert info[0].status == A.OK and info[0].true_relres <= TOL, info
+            row["iterations"].append(info[0].iterations)
+            row["solve_ms"].append(round(ev[0].elapsed_time(ev[1]), 2))
+            A.destroy(h)
+        out.append(row)
+    return out
+
+
 # ----------------------------------------------------------------------------- serving stream
 
 SERVING_SIZES = (64, 128, 256, 512, 1024)
@@ -268,6 +300,8 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--serving", type=int, default=0,
                     help="also run a serving stream of this many requests (continuous batching, mixed precision)")
+    ap.add_argument("--spread", action="store_true",
+                    help="also solve the workload with several tile-side hierarchies (iterations vs wirebasket size)")
     ap.add_argument("--serving-rate", type=float, default=0.0,
                     help="Poisson arrival rate in requests/s (0: 0.8 x the calibrated saturated rate)")
     args = ap.parse_args()
@@ -501,6 +535,8 @@ def main():
         del xin, yout
     del hd
 
+    spread_out = run_spread(dev, U, masses, psis[0]) if args.spread else None
+
     serving_out = None
     if args.serving > 0:
         free, total = torch.cuda.mem_get_info()
@@ -548,6 +584,8 @@ def main():
         }
         if serving_out is not None:
             out["serving"] = serving_out
+        if spread_out is not None:
+            out["spread"] = spread_out
         print(json.dumps(out))
     if world > 1:
         dist.barrier()

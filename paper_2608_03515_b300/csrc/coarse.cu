@@ -711,7 +711,11 @@ k_dense_gemv(const double2* __restrict__ A, const Cv* __restrict__ x, Cv* __rest
 }
 
 // Mixed-precision V-cycle: y_r = Ainv32 x_r with the FP32 rounding of the FP64
-// inverse (the factorisation itself is FP64); FP32 arithmetic.
+// inverse (the factorisation itself is FP64); FP32 arithmetic.  One warp per
+// row; a lane reads two complex entries per 16-byte load and keeps eight such
+// loads in flight (the 2048 x 2048 matrix of the 256^2 hierarchy is 33.5 MB,
+// read once per V-cycle: the kernel is bound by bytes in flight, not FLOPs).
+// nd is even (two spins per site) and rows start 16-byte aligned.
 template <int RR>
 __global__ void __launch_bounds__(256)
 k_dense_gemv32(const float2* __restrict__ A, const float2* __restrict__ x, float2* __restrict__ y, int nd) {
@@ -721,21 +725,30 @@ k_dense_gemv32(const float2* __restrict__ A, const float2* __restrict__ x, float
   float2 acc[RR];
 #pragma unroll
   for (int r = 0; r < RR; ++r) acc[r] = make_float2(0.f, 0.f);
-  const float2* a = A + (size_t)row * nd;
-  int j = lane;
-  for (; j + 96 < nd; j += 128) {
-    float2 aj[4];
+  const float4* a4 = reinterpret_cast<const float4*>(A + (size_t)row * nd);
+  const int nq = nd >> 1;                       // 16-byte pairs per row
+  int q = lane;
+  for (; q + 32 * 7 < nq; q += 32 * 8) {
+    float4 aq[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) aj[u] = __ldcs(a + j + 32 * u);
+    for (int u = 0; u < 8; ++u) aq[u] = __ldg(a4 + q + 32 * u);
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < 8; ++u)
 #pragma unroll
-      for (int r = 0; r < RR; ++r) cmac(acc[r], aj[u], x[(size_t)r * nd + j + 32 * u]);
+      for (int r = 0; r < RR; ++r) {
+        const float4 xq = __ldg(reinterpret_cast<const float4*>(x + (size_t)r * nd) + q + 32 * u);
+        cmac(acc[r], make_float2(aq[u].x, aq[u].y), make_float2(xq.x, xq.y));
+        cmac(acc[r], make_float2(aq[u].z, aq[u].w), make_float2(xq.z, xq.w));
+      }
   }
-  for (; j < nd; j += 32) {
-    const float2 aj = a[j];
+  for (; q < nq; q += 32) {
+    const float4 aq = __ldg(a4 + q);
 #pragma unroll
-    for (int r = 0; r < RR; ++r) cmac(acc[r], aj, x[(size_t)r * nd + j]);
+    for (int r = 0; r < RR; ++r) {
+      const float4 xq = __ldg(reinterpret_cast<const float4*>(x + (size_t)r * nd) + q);
+      cmac(acc[r], make_float2(aq.x, aq.y), make_float2(xq.x, xq.y));
+      cmac(acc[r], make_float2(aq.z, aq.w), make_float2(xq.z, xq.w));
+    }
   }
 #pragma unroll
   for (int r = 0; r < RR; ++r) {

@@ -11,6 +11,8 @@
 
 namespace {
 
+constexpr int RESTRICT_UNROLL = 4;
+
 template <typename T, typename PT>
 __device__ __forceinline__ typename cplx<T>::type p_load(const PT* P, const float* scale, size_t idx, int tile);
 
@@ -81,7 +83,35 @@ k_restrict(const typename cplx<T>::type* __restrict__ ef, typename cplx<T>::type
   const int p = warp / Nq, q = warp - (warp / Nq) * Nq;
   const C* f0 = ef + (size_t)blockIdx.y * 2 * nf;
   C acc0 = czero<C>(), acc1 = czero<C>();
-  for (int idx = lane; idx < 4 * nrows; idx += 32) {
+  // the lane's first RESTRICT_UNROLL pairs: all loads issued, then the
+  // arithmetic (a <= 4 needs at most 4 pairs per lane); further pairs (larger
+  // tiles) one at a time, in the same order
+  C fv[RESTRICT_UNROLL], pa[RESTRICT_UNROLL], pb[RESTRICT_UNROLL];
+#pragma unroll
+  for (int u = 0; u < RESTRICT_UNROLL; ++u) {
+    const int idx = lane + 32 * u;
+    if (idx < 4 * nrows) {
+      const int c = idx / nrows, lr = idx - c * nrows;
+      const int di = c >> 1, dj = c & 1;
+      const int pT = (p - di < 0) ? Np - 1 : p - di;
+      const int qT = (q - dj < 0) ? Nq - 1 : q - dj;
+      const int tile = pT * Nq + qT;
+      const size_t base = (size_t)tile * 8 * nrows + (size_t)(2 * c) * nrows;
+      const int l = (lr >> 1) + 1, alpha = lr & 1;
+      const int i = l / a, j = l - (l / a) * a;
+      fv[u] = f0[(size_t)alpha * nf + (pT * a + i) * Nxf + qT * a + j];
+      pa[u] = p_load<T, PT>(P, Pscale, base + lr, tile);
+      pb[u] = p_load<T, PT>(P, Pscale, base + nrows + lr, tile);
+    } else {
+      fv[u] = pa[u] = pb[u] = czero<C>();
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < RESTRICT_UNROLL; ++u) {
+    cmacc(acc0, pa[u], fv[u]);
+    cmacc(acc1, pb[u], fv[u]);
+  }
+  for (int idx = lane + 32 * RESTRICT_UNROLL; idx < 4 * nrows; idx += 32) {
     const int c = idx / nrows, lr = idx - c * nrows;
     const int di = c >> 1, dj = c & 1;
     const int pT = (p - di < 0) ? Np - 1 : p - di;
