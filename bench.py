@@ -43,6 +43,13 @@ WORKLOAD = ("256x256 Wilson-Dirac (periodic x, antiperiodic t), quenched U(1) be
             "m0 = m_crit + {0.1, 0.02, 0.005}, 3-level SM-AMG (tiles 4, 2), FGMRES(30) to 1e-10, 1 RHS per mass")
 
 
+def arm_config(world):
+    """The workload description both arms print."""
+    return {"workload": WORKLOAD, "lattice": f"{L}x{L}", "levels": 3, "tiles": AGGS, "restart": RESTART,
+            "tol": TOL, "rhs_per_mass": 1, "masses": len(MASS_OFFSETS), "parallelism": f"replicas x{world}",
+            "l2": "flushed (256 MB write) between steps"}
+
+
 def load_mcrit():
     path = os.path.join(ROOT, "tests", "golden", "mcrit.json")
     table = json.load(open(path))
@@ -155,7 +162,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(timed)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": "m_crit+0.1 mass only"},
+        "config": arm_config(args.gpus),
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -556,9 +563,7 @@ def main():
             "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "lattice": f"{L}x{L}", "levels": 3, "tiles": AGGS,
-                       "restart": RESTART, "tol": TOL, "rhs_per_mass": 1, "masses": len(masses),
-                       "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) between steps"},
+            "config": arm_config(world),
             "e2e": {"value": round(e2e_value, 3), "unit": "solves/s", "h2d_bytes_per_step": nbytes * len(masses),
                     "d2h_bytes_per_step": nbytes * len(masses)},
             "gpu_launches": int(launches),
