@@ -39,6 +39,11 @@ RESTART = 30
 TOL = 1e-10
 RHS_SEED0 = 1000
 FP64_PEAK_GFLOPS = 1250.0      # nominal B300 FP64 rate
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# FP64 level-1 coarse Gauss-Seidel (k_coarse_sweeps_owner<double>) on this
+# workload, from one ncu capture of this benchmark (profiles/coarse_gs_owner_64x64.md);
+# set to None when that kernel changes
+COARSE_SMOOTH_F64_DRAM_BYTES = 5798315
 WORKLOAD = ("256x256 Wilson-Dirac (periodic x, antiperiodic t), quenched U(1) beta=6 seed 2, "
             "m0 = m_crit + {0.1, 0.02, 0.005}, 3-level SM-AMG (tiles 4, 2), FGMRES(30) to 1e-10, 1 RHS per mass")
 
@@ -510,6 +515,9 @@ def main():
                          "frac": round(gflops / FP64_PEAK_GFLOPS, 4),
                          "peak_source": "nominal B300 FP64 rate (no measured FP64 figure)",
                          "hbm_GB/s": round(gbs, 1), "hbm_frac": round(gbs / peak, 4)})
+        if dname == "coarse_smooth_f64" and COARSE_SMOOTH_F64_DRAM_BYTES is not None:
+            roof["traffic"] = COARSE_SMOOTH_F64_DRAM_BYTES
+            roof["traffic_source"] = "ncu dram bytes per launch, profiles/coarse_gs_owner_64x64.md"
         return roof, share
 
     roofline, kernel_share = profile(hs64)
