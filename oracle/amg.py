@@ -14,15 +14,18 @@ periodic lattice and with tile side a (a | Nt, a | Nx, Nt/a >= 2, Nx/a >= 2):
   * ownership: a non-vertex site (t, x) takes its interpolation formula from the
     single basket W(t // a, x // a) ("the first aggregate it was assigned to"
     read as the basket of the tile that contains it; each basket owns its
-    lower and left borders).
+    lower and left borders).  The alternative reading, the basket of smallest
+    index among those containing the site ("first_lex"), is available for
+    comparison.
 
 Local interpolation (Eqs. (14)-(16)): with A_W = A[W, W] (couplings inside the
 basket only) and F = W minus its four corner vertices, the ideal-smoothing system
 of Eq. (15) gives u_F = -A_FF^{-1} A_FV u_V.  Route A solves that system as one
 block; route B applies the two Schur-complement formulas printed after Eq. (15)
 (interior and edge rows separately).  Both routes must agree.  The normalisation
-N of Eq. (16) is read as the identity (exact ideal interpolation); see the
-readings list of the design notes.
+N of Eq. (16) is read as the identity (exact ideal interpolation); a row-sum
+normalisation (each non-vertex row divided by its complex row sum) is available
+for comparison.
 
 Global interpolator (Sec. 4.1, last paragraph): rows of owned non-vertex sites
 come from their basket's local formula, vertex rows are the identity onto their
@@ -72,13 +75,43 @@ def site_roles(Nt: int, Nx: int, a: int) -> np.ndarray:
     return role
 
 
-def owner_tiles(Nt: int, Nx: int, a: int) -> np.ndarray:
-    """owner[t, x] = index p * (Nx/a) + q of the basket whose formula the site uses
-    (for a vertex: the tile whose corner (0, 0) it is)."""
+OWNERSHIP_RULES = ("tile", "first_lex")
+
+
+def owner_basket(t: int, x: int, Nt: int, Nx: int, a: int, rule: str = "tile") -> int:
+    """Index p * (Nx/a) + q of the basket whose formula site (t, x) uses.
+
+    "tile" (the method's reading): the basket of the tile that contains the
+    site, W(t // a, x // a).  "first_lex" (the alternative reading of "the first
+    aggregate it was assigned to", Sec. 4.1): among the baskets that contain the
+    site, the one with the smallest index p * (Nx/a) + q.  An interior site lies
+    in one basket only, so the rules differ on edge sites; a vertex gets the tile
+    whose corner (0, 0) it is under both."""
+    Np, Nq = Nt // a, Nx // a
+    p, q = t // a, x // a
+    if rule == "tile" or (t % a == 0 and x % a == 0):
+        return p * Nq + q
+    if rule != "first_lex":
+        raise ValueError(f"unknown ownership rule {rule!r}")
+    if t % a == 0:                       # bottom border of W(p, q), top border of W(p-1, q)
+        return min(p * Nq + q, ((p - 1) % Np) * Nq + q)
+    if x % a == 0:                       # left border of W(p, q), right border of W(p, q-1)
+        return min(p * Nq + q, p * Nq + (q - 1) % Nq)
+    return p * Nq + q
+
+
+def owner_tiles(Nt: int, Nx: int, a: int, rule: str = "tile") -> np.ndarray:
+    """owner[t, x] = owner_basket(t, x) for every site."""
     check_tiling(Nt, Nx, a)
-    p = (np.arange(Nt) // a)[:, None]
-    q = (np.arange(Nx) // a)[None, :]
-    return (p * (Nx // a) + q).astype(np.int32)
+    if rule == "tile":
+        p = (np.arange(Nt) // a)[:, None]
+        q = (np.arange(Nx) // a)[None, :]
+        return (p * (Nx // a) + q).astype(np.int32)
+    out = np.empty((Nt, Nx), dtype=np.int32)
+    for t in range(Nt):
+        for x in range(Nx):
+            out[t, x] = owner_basket(t, x, Nt, Nx, a, rule)
+    return out
 
 
 def basket_sites(Nt: int, Nx: int, a: int, p: int, q: int):
@@ -147,19 +180,31 @@ def local_interpolation(A: sp.csr_matrix, Nt: int, Nx: int, a: int, p: int, q: i
     return F_sites, P_F
 
 
-def build_interpolator(A: sp.csr_matrix, Nt: int, Nx: int, a: int, route: str = "A"):
+NORMALIZATIONS = ("none", "rowsum")
+ROWSUM_FLOOR = 1e-12
+
+
+def build_interpolator(A: sp.csr_matrix, Nt: int, Nx: int, a: int, route: str = "A",
+                       ownership: str = "tile", normalization: str = "none", stats: dict = None):
     """Global interpolator P (2 Nt Nx) x (2 Nt Nx / a^2) and its structural pattern.
 
     Every owned row stores all 8 corner weights, so the structural pattern does
-    not depend on numeric zeros."""
+    not depend on numeric zeros.  ownership picks the basket whose formula a
+    border site takes (owner_basket).  normalization "none" keeps the exact
+    ideal interpolation (the method's reading of N in Eq. (16)); "rowsum"
+    divides every non-vertex scalar row by its complex row sum, leaving rows
+    whose |sum| is below ROWSUM_FLOOR times the largest |sum| unnormalised
+    (their number goes to stats["rowsum_skipped"] when stats is given)."""
     check_tiling(Nt, Nx, a)
+    if normalization not in NORMALIZATIONS:
+        raise ValueError(f"unknown normalisation {normalization!r}")
     Np, Nq = Nt // a, Nx // a
     rows, cols, vals = [], [], []
     for p in range(Np):
         for q in range(Nq):
             F_sites, P_F = local_interpolation(A, Nt, Nx, a, p, q, route)
             for k, (t, x, i, j) in enumerate(F_sites):
-                if i >= a or j >= a:        # border owned by another basket
+                if owner_basket(t, x, Nt, Nx, a, ownership) != p * Nq + q:   # another basket's row
                     continue
                 for alpha in range(2):
                     r = 2 * (t * Nx + x) + alpha
@@ -179,6 +224,17 @@ def build_interpolator(A: sp.csr_matrix, Nt: int, Nx: int, a: int, route: str = 
     shape = (2 * Nt * Nx, 2 * Np * Nq)
     P = sp.csr_matrix((vals, (rows, cols)), shape=shape)
     pattern = sp.csr_matrix((np.ones(len(rows), dtype=np.int64), (rows, cols)), shape=shape)
+    if normalization == "rowsum":
+        role = site_roles(Nt, Nx, a).reshape(-1)
+        sums = np.asarray(P.sum(axis=1)).reshape(-1)
+        vertex_row = np.repeat(role == ROLE_VERTEX, 2)
+        floor = ROWSUM_FLOOR * np.max(np.abs(sums[~vertex_row]))
+        ok = (~vertex_row) & (np.abs(sums) >= floor)
+        scale = np.ones(P.shape[0], dtype=complex)
+        scale[ok] = 1.0 / sums[ok]
+        P = (sp.diags(scale) @ P).tocsr()
+        if stats is not None:
+            stats["rowsum_skipped"] = int(np.sum((~vertex_row) & ~ok))
     return P, pattern
 
 
@@ -334,15 +390,17 @@ class Level:
 
 
 def build_hierarchy(D: sp.csr_matrix, Nt: int, Nx: int, aggs: List[int], route: str = "A",
-                    smooth: bool = True) -> List[Level]:
+                    smooth: bool = True, ownership: str = "tile", normalization: str = "none") -> List[Level]:
     """Setup phase (Sec. 2): coarsening, interpolation, Galerkin, recursively;
-    the last level is factorised for the exact coarsest solve."""
+    the last level is factorised for the exact coarsest solve.  ownership and
+    normalization select the readings of build_interpolator (defaults: the
+    method's)."""
     levels = [Level(Nt, Nx, D.tocsr(), canonical_offsets(WILSON_OFFSETS_RAW, Nt, Nx))]
     A_pat = pattern_from_offsets(levels[0].offsets, Nt, Nx)
     for li, a in enumerate(aggs):
         L = levels[-1]
         L.a = a
-        L.P, L.P_pattern = build_interpolator(L.A, L.Nt, L.Nx, a, route)
+        L.P, L.P_pattern = build_interpolator(L.A, L.Nt, L.Nx, a, route, ownership, normalization)
         offs = coarse_offsets(L.P_pattern, A_pat, L.Nt, L.Nx, a)
         Ac = galerkin(L.P, L.A)
         nxt = Level(L.Nt // a, L.Nx // a, Ac, offs)

@@ -35,8 +35,11 @@ def site_index(t, x, Nx):
     return t * Nx + x
 
 
-def dirac_matrix(U: np.ndarray, m0: float) -> sp.csr_matrix:
-    """Assemble D of Eq. (3) as a sparse (2 V) x (2 V) complex matrix, one entry at a time."""
+def dirac_matrix(U: np.ndarray, m0: float, t_sign: float = -1.0) -> sp.csr_matrix:
+    """Assemble D of Eq. (3) as a sparse (2 V) x (2 V) complex matrix, one entry at a time.
+
+    t_sign is the factor on hops across the t boundary: -1 (antiperiodic, Eq. (7);
+    the method's case) or +1 (periodic, used only by the normalisation pin)."""
     _, Nt, Nx = U.shape
     V = Nt * Nx
     rows, cols, vals = [], [], []
@@ -57,9 +60,9 @@ def dirac_matrix(U: np.ndarray, m0: float) -> sp.csr_matrix:
                 # forward neighbour n + mu_hat, with the Eq. (7) sign when it wraps in t
                 if mu == 0:
                     tf, xf = (t + 1) % Nt, x
-                    sign_f = -1.0 if t == Nt - 1 else 1.0
+                    sign_f = t_sign if t == Nt - 1 else 1.0
                     tb, xb = (t - 1) % Nt, x
-                    sign_b = -1.0 if t == 0 else 1.0
+                    sign_b = t_sign if t == 0 else 1.0
                 else:
                     tf, xf = t, (x + 1) % Nx
                     sign_f = 1.0

@@ -282,3 +282,123 @@ def test_stationary_vcycle_reduces_residual_c1_field():
         now = np.linalg.norm(b - D @ x)
         assert now < prev
         prev = now
+
+
+# ------------------------------------------------------------------ alternative readings (comparison only)
+
+@pytest.mark.parametrize("Nt,Nx,a", [(8, 8, 2), (8, 12, 4), (12, 8, 2)])
+def test_first_lex_ownership_by_enumeration(Nt, Nx, a):
+    """The first_lex owner of every non-vertex site is the smallest-index basket
+    among all baskets listing it (brute force over basket_sites); the tile rule
+    is the basket of the containing tile; the two agree off the borders."""
+    Np, Nq = Nt // a, Nx // a
+    containing = {}
+    for p in range(Np):
+        for q in range(Nq):
+            for (t, x, _, _) in amg.basket_sites(Nt, Nx, a, p, q):
+                containing.setdefault((t, x), []).append(p * Nq + q)
+    lex = amg.owner_tiles(Nt, Nx, a, "first_lex")
+    tile = amg.owner_tiles(Nt, Nx, a, "tile")
+    role = amg.site_roles(Nt, Nx, a)
+    for (t, x), bs in containing.items():
+        if role[t, x] == amg.ROLE_VERTEX:
+            continue
+        assert lex[t, x] == min(bs)
+        assert tile[t, x] == (t // a) * Nq + x // a and tile[t, x] in bs
+        if role[t, x] == amg.ROLE_INTERIOR:
+            assert len(bs) == 1 and lex[t, x] == tile[t, x]
+        else:
+            assert len(bs) == 2
+    # the interpolator takes each non-vertex row from its owner's corners
+    P, _ = amg.build_interpolator(W.dirac_matrix(random_links(Nt, Nx, 5), 0.2), Nt, Nx, a, ownership="first_lex")
+    Pc = P.tocsr()
+    for t in range(Nt):
+        for x in range(Nx):
+            if role[t, x] == amg.ROLE_VERTEX:
+                continue
+            ob = lex[t, x]
+            corners = {amg.corner_vertex(Nt, Nx, a, ob // Nq, ob % Nq, c) for c in range(4)}
+            for alpha in range(2):
+                r = 2 * (t * Nx + x) + alpha
+                cols = Pc.indices[Pc.indptr[r]:Pc.indptr[r + 1]]
+                assert len(cols) == 8 and {c // 2 for c in cols} == corners
+
+
+def test_first_lex_ownership_is_not_translation_invariant_but_still_solves():
+    """Under first_lex a border site goes to the neighbouring basket except on
+    the first tile row / column, where the periodic wrap makes its own basket
+    the smaller index: the ownership map does not commute with a one-tile shift
+    (the tile rule's does; the per-tile interpolator storage of the CUDA path
+    relies on that).  The coarse neighbour pattern is still the 21 offsets, and
+    the hierarchy gives a convergent preconditioner."""
+    from oracle import krylov
+    Nt = Nx = 16
+    a = 2
+    Np, Nq = Nt // a, Nx // a
+
+    def shifted_by_one_tile(own):
+        # owner map of the lattice shifted by one tile in t, as basket indices shifted back
+        sh = np.roll(own, -a, axis=0)
+        p, q = sh // Nq, sh % Nq
+        return ((p - 1) % Np) * Nq + q
+
+    tile = amg.owner_tiles(Nt, Nx, a, "tile")
+    lex = amg.owner_tiles(Nt, Nx, a, "first_lex")
+    assert np.array_equal(shifted_by_one_tile(tile), tile)
+    assert not np.array_equal(shifted_by_one_tile(lex), lex)
+    U = fx.links_from_angles(fx.metropolis_u1(Nt, Nx, 3.0, 100, 7))
+    D = W.dirac_matrix(U, 0.05)
+    levels = amg.build_hierarchy(D, Nt, Nx, [2, 2], ownership="first_lex")
+    assert len(levels[1].offsets) == 21
+    b = W.to_flat(fx.gaussian_rhs(1, Nt, Nx, 8)[0])
+    res = krylov.fgmres(lambda v: D @ v, lambda r: amg.vcycle(levels, r), b, 30, 1e-10, 2000)
+    x = np.linalg.solve(D.toarray(), b)
+    assert np.linalg.norm(b - D @ res.x) / np.linalg.norm(b) <= 1e-10
+    assert np.linalg.norm(res.x - x) / np.linalg.norm(x) <= 1e-7
+
+
+@pytest.mark.parametrize("a", [2, 4])
+def test_rowsum_normalisation_maps_constants_to_constants(a):
+    """Row-sum normalisation: on the free field with periodic boundaries at
+    m0 = 0 (where constants solve D u = 0) P 1 = 1, vertex rows stay the
+    identity, no row is left unnormalised; the exact (none) interpolation does
+    not map constants to constants there, because a basket drops its couplings
+    to outside sites."""
+    Nt = Nx = 8
+    U = np.ones((2, Nt, Nx), dtype=complex)
+    D = W.dirac_matrix(U, 0.0, t_sign=1.0)
+    assert np.max(np.abs(D @ np.ones(2 * Nt * Nx))) < 1e-14
+    stats = {}
+    P, _ = amg.build_interpolator(D, Nt, Nx, a, normalization="rowsum", stats=stats)
+    P0, _ = amg.build_interpolator(D, Nt, Nx, a)
+    ones_c = np.ones(P.shape[1])
+    assert stats["rowsum_skipped"] == 0
+    assert np.max(np.abs(P @ ones_c - 1.0)) < 1e-12
+    assert np.max(np.abs(P0 @ ones_c - 1.0)) > 1e-3
+    role = amg.site_roles(Nt, Nx, a).reshape(-1)
+    vrows = np.repeat(role == amg.ROLE_VERTEX, 2)
+    assert np.array_equal(P.toarray()[vrows], P0.toarray()[vrows])
+
+
+def test_rowsum_normalisation_is_not_gauge_covariant_and_still_solves():
+    """With U(1) phases the row sum changes under a gauge transformation, so the
+    row-sum normalised P is not covariant (the reason the method keeps the exact
+    interpolation, whose covariance is pinned above); the preconditioner built
+    from it still converges."""
+    from oracle import krylov
+    Nt = Nx = 8
+    a = 2
+    U = random_links(Nt, Nx, 21)
+    rng = np.random.Generator(np.random.PCG64(22))
+    omega = np.exp(1j * rng.uniform(-np.pi, np.pi, size=(Nt, Nx)))
+    D1, D2 = W.dirac_matrix(U, 0.3), W.dirac_matrix(W.gauge_transform_links(U, omega), 0.3)
+    P1, _ = amg.build_interpolator(D1, Nt, Nx, a, normalization="rowsum")
+    P2, _ = amg.build_interpolator(D2, Nt, Nx, a, normalization="rowsum")
+    Om = np.diag(np.repeat(omega.reshape(-1), 2))
+    OmV = np.diag(np.repeat(omega[::a, ::a].reshape(-1), 2))
+    assert np.max(np.abs(P2.toarray() - Om @ P1.toarray() @ OmV.conj().T)) > 1e-3
+    levels = amg.build_hierarchy(D1, Nt, Nx, [2], normalization="rowsum")
+    b = W.to_flat(fx.gaussian_rhs(1, Nt, Nx, 23)[0])
+    res = krylov.fgmres(lambda v: D1 @ v, lambda r: amg.vcycle(levels, r), b, 30, 1e-10, 2000)
+    x = np.linalg.solve(D1.toarray(), b)
+    assert np.linalg.norm(res.x - x) / np.linalg.norm(x) <= 1e-7
