@@ -416,13 +416,31 @@ def build_hierarchy(D: sp.csr_matrix, Nt: int, Nx: int, aggs: List[int], route: 
     return levels
 
 
-def vcycle(levels: List[Level], r: np.ndarray, level: int = 0, post_smooth: int = 2) -> np.ndarray:
-    """Preconditioner M(r) of Algorithm 1 with start vector 0 and no pre-smoothing."""
+COARSEST_SOLVERS = ("lu", "gmres")
+
+
+def coarsest_gmres(L: "Level", r: np.ndarray, tol: float = 0.1, restart: int = 30) -> np.ndarray:
+    """The paper's coarsest-level solver (Sec. 5): unpreconditioned GMRES from a
+    zero start to a relative residual of tol (the oracle's FGMRES with the
+    identity as preconditioner, which is plain restarted GMRES)."""
+    from . import krylov
+    return krylov.fgmres(lambda v: L.A @ v, lambda v: v, r, restart, tol, 100000).x
+
+
+def vcycle(levels: List[Level], r: np.ndarray, level: int = 0, post_smooth: int = 2,
+           coarsest: str = "lu") -> np.ndarray:
+    """Preconditioner M(r) of Algorithm 1 with start vector 0 and no pre-smoothing.
+    coarsest: "lu" (the method's reading: exact solve) or "gmres" (the paper's
+    setting: GMRES to 0.1, for comparison)."""
     L = levels[level]
     if level == len(levels) - 1:
+        if coarsest == "gmres":
+            return coarsest_gmres(L, r)
+        if coarsest != "lu":
+            raise ValueError(f"unknown coarsest solver {coarsest!r}")
         return sla.lu_solve(L.lu, r)
     rc = L.P.conj().T @ r                       # restrict: d^H = I_h^H d^h
-    ec = vcycle(levels, rc, level + 1, post_smooth)
+    ec = vcycle(levels, rc, level + 1, post_smooth, coarsest)
     e = L.P @ ec                                # interpolate the coarse correction
     for _ in range(post_smooth):
         e = gs_sweep(L.A, L.dinv, L.colour, e, r)

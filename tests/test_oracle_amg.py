@@ -402,3 +402,34 @@ def test_rowsum_normalisation_is_not_gauge_covariant_and_still_solves():
     res = krylov.fgmres(lambda v: D1 @ v, lambda r: amg.vcycle(levels, r), b, 30, 1e-10, 2000)
     x = np.linalg.solve(D1.toarray(), b)
     assert np.linalg.norm(res.x - x) / np.linalg.norm(x) <= 1e-7
+
+
+def test_coarsest_gmres_setting_meets_its_tolerance_and_the_solve_converges():
+    """The paper's coarsest solver (unpreconditioned GMRES to a relative residual
+    of 0.1) as an oracle option: each coarse solve meets its tolerance, a tight
+    tolerance reproduces the LU solve, and the flexible outer solve still
+    reaches 1e-10 and the dense solution on the 32^2 beta = 3 field."""
+    import json
+    import os
+    from oracle import krylov
+    Nt = Nx = 32
+    U = fx.links_from_angles(fx.metropolis_u1(Nt, Nx, 3.0, 500, 0))
+    here = os.path.dirname(os.path.abspath(__file__))
+    mc = json.load(open(os.path.join(here, "golden", "mcrit.json")))["L32_b3_s0"]["m_crit"]
+    D = W.dirac_matrix(U, mc + 0.05)
+    levels = amg.build_hierarchy(D, Nt, Nx, [4, 2])
+    C = levels[-1]
+    rng = np.random.Generator(np.random.PCG64(31))
+    rc = rng.standard_normal(C.A.shape[0]) + 1j * rng.standard_normal(C.A.shape[0])
+    e = amg.coarsest_gmres(C, rc)
+    assert np.linalg.norm(rc - C.A @ e) <= 0.1 * np.linalg.norm(rc)
+    e_tight = amg.coarsest_gmres(C, rc, tol=1e-13)
+    e_lu = amg.sla.lu_solve(C.lu, rc)
+    assert np.linalg.norm(e_tight - e_lu) <= 1e-10 * np.linalg.norm(e_lu)
+    b = W.to_flat(fx.gaussian_rhs(1, Nt, Nx, 1)[0])
+    res = krylov.fgmres(lambda v: D @ v, lambda r: amg.vcycle(levels, r, coarsest="gmres"), b, 30, 1e-10, 5000)
+    ref = krylov.fgmres(lambda v: D @ v, lambda r: amg.vcycle(levels, r), b, 30, 1e-10, 5000)
+    x = np.linalg.solve(D.toarray(), b)
+    assert np.linalg.norm(b - D @ res.x) / np.linalg.norm(b) <= 1e-10
+    assert np.linalg.norm(res.x - x) / np.linalg.norm(x) <= 1e-7
+    assert res.iterations <= 1.5 * ref.iterations
