@@ -53,7 +53,8 @@ typedef struct amamg_ctx* amamg_handle;
 #define AMAMG_ERR_CUDA          -3
 #define AMAMG_ERR_SINGULAR      -4   /* a local or coarsest pivot vanished in setup */
 #define AMAMG_ERR_NONFINITE     -5   /* NaN/Inf in a right-hand side or a residual */
-#define AMAMG_ERR_TIMEOUT       -6
+#define AMAMG_ERR_TIMEOUT       -6   /* a bounded device wait of a coarse smoother ran out (reported by
+                                        amamg_solve / amamg_batch_cycle; the handle stays usable) */
 
 /* vector precision of apply-style calls */
 #define AMAMG_F64 0                  /* complex128 vectors, FP64 operators */
