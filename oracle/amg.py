@@ -24,8 +24,9 @@ of Eq. (15) gives u_F = -A_FF^{-1} A_FV u_V.  Route A solves that system as one
 block; route B applies the two Schur-complement formulas printed after Eq. (15)
 (interior and edge rows separately).  Both routes must agree.  The normalisation
 N of Eq. (16) is read as the identity (exact ideal interpolation); a row-sum
-normalisation (each non-vertex row divided by its complex row sum) is available
-for comparison.
+normalisation (each non-vertex row divided by its complex row sum) and a
+spin-split interpolation (spin-diagonal weights only) are available for
+comparison.
 
 Global interpolator (Sec. 4.1, last paragraph): rows of owned non-vertex sites
 come from their basket's local formula, vertex rows are the identity onto their
@@ -185,7 +186,8 @@ ROWSUM_FLOOR = 1e-12
 
 
 def build_interpolator(A: sp.csr_matrix, Nt: int, Nx: int, a: int, route: str = "A",
-                       ownership: str = "tile", normalization: str = "none", stats: dict = None):
+                       ownership: str = "tile", normalization: str = "none", stats: dict = None,
+                       spin_split: bool = False):
     """Global interpolator P (2 Nt Nx) x (2 Nt Nx / a^2) and its structural pattern.
 
     Every owned row stores all 8 corner weights, so the structural pattern does
@@ -194,7 +196,11 @@ def build_interpolator(A: sp.csr_matrix, Nt: int, Nx: int, a: int, route: str = 
     ideal interpolation (the method's reading of N in Eq. (16)); "rowsum"
     divides every non-vertex scalar row by its complex row sum, leaving rows
     whose |sum| is below ROWSUM_FLOOR times the largest |sum| unnormalised
-    (their number goes to stats["rowsum_skipped"] when stats is given)."""
+    (their number goes to stats["rowsum_skipped"] when stats is given).
+    spin_split keeps only the spin-diagonal weights, P -> (P + s3 P s3) / 2 with
+    s3 = sigma_3 on every site (fine and coarse): P then commutes with sigma_3
+    and the Galerkin operator inherits sigma_3-hermiticity (the direction the
+    paper proposes for future work, Sec. 6; comparison only)."""
     check_tiling(Nt, Nx, a)
     if normalization not in NORMALIZATIONS:
         raise ValueError(f"unknown normalisation {normalization!r}")
@@ -235,6 +241,11 @@ def build_interpolator(A: sp.csr_matrix, Nt: int, Nx: int, a: int, route: str = 
         P = (sp.diags(scale) @ P).tocsr()
         if stats is not None:
             stats["rowsum_skipped"] = int(np.sum((~vertex_row) & ~ok))
+    if spin_split:
+        s3f = sp.diags(np.tile([1.0, -1.0], Nt * Nx))
+        s3c = sp.diags(np.tile([1.0, -1.0], Np * Nq))
+        P = (0.5 * (P + s3f @ P @ s3c)).tocsr()
+        P.eliminate_zeros()
     return P, pattern
 
 
@@ -390,7 +401,8 @@ class Level:
 
 
 def build_hierarchy(D: sp.csr_matrix, Nt: int, Nx: int, aggs: List[int], route: str = "A",
-                    smooth: bool = True, ownership: str = "tile", normalization: str = "none") -> List[Level]:
+                    smooth: bool = True, ownership: str = "tile", normalization: str = "none",
+                    spin_split: bool = False) -> List[Level]:
     """Setup phase (Sec. 2): coarsening, interpolation, Galerkin, recursively;
     the last level is factorised for the exact coarsest solve.  ownership and
     normalization select the readings of build_interpolator (defaults: the
@@ -400,7 +412,8 @@ def build_hierarchy(D: sp.csr_matrix, Nt: int, Nx: int, aggs: List[int], route: 
     for li, a in enumerate(aggs):
         L = levels[-1]
         L.a = a
-        L.P, L.P_pattern = build_interpolator(L.A, L.Nt, L.Nx, a, route, ownership, normalization)
+        L.P, L.P_pattern = build_interpolator(L.A, L.Nt, L.Nx, a, route, ownership, normalization,
+                                              spin_split=spin_split)
         offs = coarse_offsets(L.P_pattern, A_pat, L.Nt, L.Nx, a)
         Ac = galerkin(L.P, L.A)
         nxt = Level(L.Nt // a, L.Nx // a, Ac, offs)

@@ -433,3 +433,34 @@ def test_coarsest_gmres_setting_meets_its_tolerance_and_the_solve_converges():
     assert np.linalg.norm(b - D @ res.x) / np.linalg.norm(b) <= 1e-10
     assert np.linalg.norm(res.x - x) / np.linalg.norm(x) <= 1e-7
     assert res.iterations <= 1.5 * ref.iterations
+
+
+def test_spin_split_interpolation_restores_sigma3_hermiticity():
+    """Spin-split interpolation (spin-diagonal weights only): P commutes with
+    sigma_3, so P^H D P inherits sigma_3 D sigma_3 = D^H (Eq. (5)); the full
+    interpolation of reading 3 mixes spins and its coarse operator lacks the
+    property.  The spin-split hierarchy still solves to the dense solution."""
+    from oracle import krylov
+    Nt = Nx = 16
+    U = fx.links_from_angles(fx.metropolis_u1(Nt, Nx, 3.0, 100, 9))
+    D = W.dirac_matrix(U, 0.1)
+    a = 2
+    s3f = sp.diags(np.tile([1.0, -1.0], Nt * Nx))
+    s3c = sp.diags(np.tile([1.0, -1.0], (Nt // a) * (Nx // a)))
+    P, _ = amg.build_interpolator(D, Nt, Nx, a, spin_split=True)
+    Pf, _ = amg.build_interpolator(D, Nt, Nx, a)
+    assert abs(s3f @ P @ s3c - P).max() < 1e-15
+    Dc = amg.galerkin(P, D).toarray()
+    Dcf = amg.galerkin(Pf, D).toarray()
+    S = s3c.toarray()
+    assert np.max(np.abs(S @ Dc @ S - Dc.conj().T)) < 1e-12 * np.max(np.abs(Dc))
+    assert np.max(np.abs(S @ Dcf @ S - Dcf.conj().T)) > 1e-3 * np.max(np.abs(Dcf))
+    # vertex rows stay the identity; a site's weights keep its spin
+    role = amg.site_roles(Nt, Nx, a).reshape(-1)
+    vrows = np.repeat(role == amg.ROLE_VERTEX, 2)
+    assert np.array_equal(P.toarray()[vrows], Pf.toarray()[vrows])
+    levels = amg.build_hierarchy(D, Nt, Nx, [2, 2], spin_split=True)
+    b = W.to_flat(fx.gaussian_rhs(1, Nt, Nx, 10)[0])
+    res = krylov.fgmres(lambda v: D @ v, lambda r: amg.vcycle(levels, r), b, 30, 1e-10, 2000)
+    x = np.linalg.solve(D.toarray(), b)
+    assert np.linalg.norm(res.x - x) / np.linalg.norm(x) <= 1e-7
