@@ -461,6 +461,19 @@ def main():
                              "max_iterations": its}
         del psib, xb
 
+    # the opt-in spin-split hierarchy (spin-diagonal interpolation weights; a
+    # comparison beside the method as read): one warm-up and one timed step
+    hs_ss = []
+    for m0 in masses:
+        hs_ss.append(A.setup(U, m0, A.make_params(AGGS, precision=A.SOLVE_FP64, restart=RESTART, tol=TOL,
+                                                 spin_split=True)))
+    run(hs_ss, nst=1)
+    st_ss, _, it_ss, _ = run(hs_ss, nst=2, skip=1)
+    spin_split = {"fp64_solves_per_s": round(len(masses) / (st_ss[0] * 1e-3), 3),
+                  "iterations": it_ss[-len(masses):]}
+    for h in hs_ss:
+        A.destroy(h)
+
     # end to end through the public API with host buffers
     psi_h = [p.cpu().pin_memory() for p in psis]
     x_h = torch.empty(psis[0].shape, dtype=torch.complex128).pin_memory()
@@ -589,6 +602,7 @@ def main():
             "latency_ms": {"p50": round(float(np.percentile(solve_ms, 50)), 3),
                            "p99": round(float(np.percentile(solve_ms, 99)), 3)},
             "batched_mixed": batched,
+            "spin_split": spin_split,
             "iterations": iters64[-len(masses):],
             "true_relres_max": max(relres64),
             "setup_ms": [round(s, 2) for s in setup64],

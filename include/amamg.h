@@ -74,6 +74,10 @@ typedef struct {
     int    max_iter;                 /* total Arnoldi steps before AMAMG_NOT_CONVERGED */
     int    post_smooth;              /* post-smoothing sweeps per level (paper: 2); no pre-smoothing */
     double tol;                      /* relative residual ||psi - D x|| / ||psi|| */
+    int    spin_split;               /* 0 (default): the ideal interpolation of Eq. (16), spins mixed;
+                                        1: only its spin-diagonal weights, (P + s3 P s3) / 2, so the
+                                        coarse operators keep sigma_3-hermiticity (the direction
+                                        Sec. 6 proposes; a comparison hierarchy, not the method as read) */
 } amamg_params;
 
 typedef struct {

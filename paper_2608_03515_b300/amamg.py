@@ -48,6 +48,7 @@ class Params(ctypes.Structure):
         ("max_iter", ctypes.c_int),
         ("post_smooth", ctypes.c_int),
         ("tol", ctypes.c_double),
+        ("spin_split", ctypes.c_int),
     ]
 
 
@@ -153,7 +154,7 @@ def default_params() -> Params:
 
 
 def make_params(aggs: Sequence[int], precision: int = SOLVE_FP64, restart: int = 30, max_iter: int = 3000,
-                post_smooth: int = 2, tol: float = 1e-10) -> Params:
+                post_smooth: int = 2, tol: float = 1e-10, spin_split: bool = False) -> Params:
     p = default_params()
     p.nlevels = len(aggs) + 1
     for i, a in enumerate(aggs):
@@ -163,6 +164,7 @@ def make_params(aggs: Sequence[int], precision: int = SOLVE_FP64, restart: int =
     p.max_iter = max_iter
     p.post_smooth = post_smooth
     p.tol = tol
+    p.spin_split = 1 if spin_split else 0
     return p
 
 

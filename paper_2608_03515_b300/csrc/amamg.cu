@@ -836,6 +836,7 @@ int check_params(const amamg_params* p, int Nt, int Nx, std::string* why) {
   if (p->precision != AMAMG_SOLVE_FP64 && p->precision != AMAMG_SOLVE_MIXED) { *why = "bad precision"; return AMAMG_ERR_INVALID_ARG; }
   if (p->restart < 1 || p->restart > 64) { *why = "restart must be 1..64"; return AMAMG_ERR_INVALID_ARG; }
   if (p->max_iter < 1 || p->post_smooth < 0 || !(p->tol > 0.0)) { *why = "bad max_iter/post_smooth/tol"; return AMAMG_ERR_INVALID_ARG; }
+  if (p->spin_split != 0 && p->spin_split != 1) { *why = "spin_split must be 0 or 1"; return AMAMG_ERR_INVALID_ARG; }
   if (Nt < 4 || Nx < 4 || (Nt & 1) || (Nx & 1)) { *why = "Nt, Nx must be even and >= 4"; return AMAMG_ERR_INVALID_ARG; }
   int nt = Nt, nx = Nx;
   for (int l = 0; l + 1 < p->nlevels; ++l) {
@@ -918,10 +919,14 @@ int do_setup(amamg_ctx* h, const void* Uin, cudaStream_t st) {
     if (l == 0) {
       WilsonOp op{h->U64, h->m0 + 2.0, F.Nt, F.Nx};
       CKS(launch(h, "setup_local_solve", 0.0, st, [&] { return launch_local_solve(op, F.a, F.Np, F.Nq, F.P64, h->d_err, st); }));
+      if (h->prm.spin_split)
+        CKS(launch(h, "setup_spin_split", 0.0, st, [&] { return launch_spin_split_P(F.P64, F.nrows, F.nT, st); }));
       CKS(launch(h, "setup_galerkin", 0.0, st, [&] { return launch_galerkin(op, F.P64, F.a, F.Np, F.Nq, C.off, C.B64, st); }));
     } else {
       StencilOp op{F.B64, F.off, F.Nt, F.Nx};
       CKS(launch(h, "setup_local_solve", 0.0, st, [&] { return launch_local_solve(op, F.a, F.Np, F.Nq, F.P64, h->d_err, st); }));
+      if (h->prm.spin_split)
+        CKS(launch(h, "setup_spin_split", 0.0, st, [&] { return launch_spin_split_P(F.P64, F.nrows, F.nT, st); }));
       CKS(launch(h, "setup_galerkin", 0.0, st, [&] { return launch_galerkin(op, F.P64, F.a, F.Np, F.Nq, C.off, C.B64, st); }));
     }
     CKS(launch(h, "setup_pack", 0.0, st, [&] { return launch_pack_P16(F.P64, 8 * F.nrows, F.nT, F.P16, F.Ps, st); }));

@@ -165,6 +165,8 @@ cudaError_t launch_gj_step(double2* A, int nd, int k, double2* colk, int* perm, 
                            cudaStream_t st);
 cudaError_t launch_gather_cols(const double2* X, double2* Y, const int* cols, int nd, cudaStream_t st);
 cudaError_t launch_pack_P16(const double2* P, int per_tile, int ntiles, __half2* P16, float* scale, cudaStream_t st);
+// zero the cross-spin weights of every P tile ([ntiles][8][nrows])
+cudaError_t launch_spin_split_P(double2* P, int nrows, int ntiles, cudaStream_t st);
 cudaError_t launch_pack_B16(const double2* B, int K, int n, __half2* B16, float* scale, cudaStream_t st);
 cudaError_t launch_pack_colour_major(const double2* B64, const __half2* B16, const float* Bs, const double2* D64,
                                      const float2* D32, int K, int Nt, int Nx, int ncol, double2* Bc64, __half2* Bc16,

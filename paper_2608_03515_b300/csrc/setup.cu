@@ -532,6 +532,24 @@ cudaError_t launch_gather_cols(const double2* X, double2* Y, const int* cols, in
   return cudaGetLastError();
 }
 
+namespace {
+// Spin-split interpolation: zero the weights that couple different spins
+// (column 2c + beta, row 2(l-1) + alpha with alpha != beta) of every tile.
+__global__ void k_spin_split_P(double2* __restrict__ P, int nrows, long total) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int lr = (int)(idx % nrows);
+  const int col = (int)((idx / nrows) % 8);
+  if ((col & 1) != (lr & 1)) P[idx] = make_double2(0.0, 0.0);
+}
+}  // namespace
+
+cudaError_t launch_spin_split_P(double2* P, int nrows, int ntiles, cudaStream_t st) {
+  const long total = (long)ntiles * 8 * nrows;
+  k_spin_split_P<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(P, nrows, total);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pack_P16(const double2* P, int per_tile, int ntiles, __half2* P16, float* scale,
                             cudaStream_t st) {
   k_pack_P16<<<(ntiles * 32 + 255) / 256, 256, 0, st>>>(P, per_tile, ntiles, P16, scale);

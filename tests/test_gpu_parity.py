@@ -144,6 +144,43 @@ def test_interpolator_and_galerkin_fp64(Nt, Nx, aggs):
         assert relerr(host(Bg), Bw) <= 1e-12
 
 
+def test_spin_split_hierarchy_matches_oracle():
+    """The opt-in spin-split hierarchy (spin-diagonal interpolation weights,
+    amamg_params.spin_split = 1) against the oracle's: interpolator tiles and
+    coarse blocks to 1e-12, and the FP64 solve on the 32^2 beta = 3 field to
+    1e-10 with an iteration count within 10 % of the oracle's."""
+    import json
+    import os
+    Nt = Nx = 32
+    aggs = [4, 2]
+    U = fx.links_from_angles(fx.metropolis_u1(Nt, Nx, 3.0, 500, 0))
+    here = os.path.dirname(os.path.abspath(__file__))
+    m0 = json.load(open(os.path.join(here, "golden", "mcrit.json")))["L32_b3_s0"]["m_crit"] + 0.05
+    D = W.dirac_matrix(U, m0)
+    levels = amg.build_hierarchy(D, Nt, Nx, aggs, spin_split=True)
+    hier = A.setup(dev(U), m0, A.make_params(aggs, spin_split=True))
+    for l, a in enumerate(aggs):
+        L = levels[l]
+        want = oracle_P_tiles(L.P, L.Nt, L.Nx, a)
+        got = torch.empty(want.shape, dtype=torch.complex128, device=DEV)
+        A.export_P(hier, l, got)
+        assert relerr(host(got), want) <= 1e-12
+        C = levels[l + 1]
+        Bw = amg.block_stencil(C.A, C.offsets, C.Nt, C.Nx)
+        Bw = np.transpose(Bw.reshape(len(C.offsets), C.Nt * C.Nx, 4), (0, 2, 1))
+        Bg = torch.empty(Bw.shape, dtype=torch.complex128, device=DEV)
+        A.export_coarse(hier, l + 1, Bg)
+        assert relerr(host(Bg), Bw) <= 1e-12
+    psi = fx.gaussian_rhs(1, Nt, Nx, 1)
+    x = torch.empty(psi.shape, dtype=torch.complex128, device=DEV)
+    info = A.solve(hier, dev(psi), x)
+    ref = krylov.fgmres(lambda v: D @ v, lambda r: amg.vcycle(levels, r), W.to_flat(psi[0]), 30, 1e-10, 5000)
+    b = W.to_flat(psi[0])
+    res = np.linalg.norm(b - D @ W.to_flat(host(x)[0])) / np.linalg.norm(b)
+    assert info[0].status == A.OK and res <= 1e-10
+    assert abs(info[0].iterations - ref.iterations) <= max(1, 0.1 * ref.iterations)
+
+
 # ------------------------------------------------------------------ transfers, coarse operator
 
 @pytest.mark.parametrize("Nt,Nx,aggs,R", [(16, 16, [4], 2), (32, 32, [4, 2], 1), (16, 24, [2, 2], 3)])
