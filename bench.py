@@ -40,9 +40,9 @@ TOL = 1e-10
 RHS_SEED0 = 1000
 FP64_PEAK_GFLOPS = 1250.0      # nominal B300 FP64 rate
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# FP64 level-1 coarse Gauss-Seidel (k_coarse_sweeps_owner<double>) on this
-# workload, from one ncu capture of this benchmark (profiles/coarse_gs_owner_64x64.md);
-# set to None when that kernel changes
+# FP64 level-1 coarse Gauss-Seidel (k_coarse_sweeps_owner<double>, two sweeps of
+# the 64x64 level of this workload), from one ncu capture of that kernel; set to
+# None when that kernel changes
 COARSE_SMOOTH_F64_DRAM_BYTES = 5798315
 WORKLOAD = ("256x256 Wilson-Dirac (periodic x, antiperiodic t), quenched U(1) beta=6 seed 2, "
             "m0 = m_crit + {0.1, 0.02, 0.005}, 3-level SM-AMG (tiles 4, 2), FGMRES(30) to 1e-10, 1 RHS per mass")
@@ -130,48 +130,67 @@ def cpu_cores():
 
 # ----------------------------------------------------------------------------- reference arm (oracle)
 
-def oracle_solve_time(theta, m0, psi_flat, reps):
-    from oracle import amg, krylov
+def oracle_hierarchy(theta, m0):
+    from oracle import amg
     from oracle import wilson as W
     from paper_2608_03515_b300 import fixtures as fx
-    U = fx.links_from_angles(theta)
-    D = W.dirac_matrix(U, m0)
+    D = W.dirac_matrix(fx.links_from_angles(theta), m0)
     t0 = time.perf_counter()
     levels = amg.build_hierarchy(D, L, L, AGGS)
-    setup_s = time.perf_counter() - t0
-    times, iters = [], []
-    for i in range(reps):
-        t0 = time.perf_counter()
-        res = krylov.fgmres(lambda v: D @ v, lambda r: amg.vcycle(levels, r), psi_flat[i], RESTART, TOL, 3000)
-        times.append(time.perf_counter() - t0)
-        iters.append(res.iterations)
-    return setup_s, times, iters
+    return D, levels, time.perf_counter() - t0
+
+
+def oracle_solve(D, levels, psi_flat):
+    from oracle import amg, krylov
+    t0 = time.perf_counter()
+    res = krylov.fgmres(lambda v: D @ v, lambda r: amg.vcycle(levels, r), psi_flat, RESTART, TOL, 3000)
+    return time.perf_counter() - t0, res
 
 
 def run_reference(args):
+    """The oracle on this arm's workload: the three masses' hierarchies, and
+    per timed step one solve, step i on mass i mod 3 with its own right-hand
+    side; the solves/s of the 1:1:1 mix (the work of one GPU step per three
+    solves) is 3 / sum over masses of the mean solve time."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from oracle import wilson as W
     from paper_2608_03515_b300 import fixtures as fx
     theta = fx.metropolis_u1(L, L, BETA, SWEEPS, FIELD_SEED)
-    m0 = load_mcrit() + MASS_OFFSETS[0]
-    n = args.warmup + args.steps
-    psi = [W.to_flat(fx.gaussian_rhs(1, L, L, RHS_SEED0 + i)[0]) for i in range(n)]
-    setup_s, times, iters = oracle_solve_time(theta, m0, psi, n)
-    timed = times[args.warmup:]
-    value = len(timed) / sum(timed)
-    sample = (f"oracle (FP64 NumPy/SciPy) solves of the m_crit+0.1 mass only, 1 RHS each, "
-              f"{len(timed)} timed after {args.warmup} warm-up; setup {setup_s:.1f} s excluded")
+    mcrit = load_mcrit()
+    hiers, setup_s = [], 0.0
+    for d in MASS_OFFSETS:
+        D, levels, s_ = oracle_hierarchy(theta, mcrit + d)
+        hiers.append((D, levels))
+        setup_s += s_
+    nm = len(MASS_OFFSETS)
+    timed_n = max(args.steps, nm)
+    for i in range(args.warmup):           # warm-up: the cheapest mass
+        oracle_solve(*hiers[0], W.to_flat(fx.gaussian_rhs(1, L, L, RHS_SEED0 + i)[0]))
+    per_mass = [[] for _ in range(nm)]
+    iters = []
+    for i in range(timed_n):
+        k = i % nm
+        psi = W.to_flat(fx.gaussian_rhs(1, L, L, RHS_SEED0 + args.warmup + i)[0])
+        dt, res = oracle_solve(*hiers[k], psi)
+        per_mass[k].append(dt)
+        iters.append(res.iterations)
+    step_s = sum(float(np.mean(t)) for t in per_mass)     # one solve of every mass
+    value = nm / step_s
+    sample = (f"oracle (FP64 NumPy/SciPy, sparse kernels single-threaded) solves of all {nm} masses, "
+              f"{timed_n} timed solves (solve i on mass i mod {nm}) after {args.warmup} warm-up solves; "
+              f"value = {nm} / sum of the per-mass mean solve times; setup {setup_s:.1f} s excluded")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(timed)),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": arm_config(args.gpus),
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "iterations": iters[args.warmup:],
+        "iterations": iters,
+        "mean_solve_s_per_mass": [round(float(np.mean(t)), 3) for t in per_mass],
     }))
 
 
@@ -437,6 +456,14 @@ def main():
         assert r <= TOL
     mixed_value = len(sv32) / (np.sum(st32) * 1e-3) * world
 
+    # the first timed right-hand side on the m_crit + 0.1 hierarchy, FP64 and
+    # mixed, kept for the comparison with the oracle's solution
+    A.solve(hs64[0], psis[args.warmup], x)
+    x_check64 = x.cpu().numpy()[0].copy()
+    A.solve(hs32[0], psis[args.warmup], x)
+    x_check32 = x.cpu().numpy()[0].copy()
+    errs_vs_oracle = {}
+
     # multi-RHS batches: R right-hand sides per solve call (mixed precision), all
     # three masses; solves/s counts right-hand sides
     batched = {}
@@ -530,7 +557,7 @@ def main():
                          "hbm_GB/s": round(gbs, 1), "hbm_frac": round(gbs / peak, 4)})
         if dname == "coarse_smooth_f64" and COARSE_SMOOTH_F64_DRAM_BYTES is not None:
             roof["traffic"] = COARSE_SMOOTH_F64_DRAM_BYTES
-            roof["traffic_source"] = "ncu dram bytes per launch, profiles/coarse_gs_owner_64x64.md"
+            roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch (64x64 owner sweep)"
         return roof, share
 
     roofline, kernel_share = profile(hs64)
@@ -575,11 +602,16 @@ def main():
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             from oracle import wilson as W
-            psi_flat = [W.to_flat(psis[args.warmup].cpu().numpy()[0])]
-            setup_s, ot, oit = oracle_solve_time(theta, masses[0], psi_flat, 1)
-            cpu = {"value": 1.0 / ot[0], "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
-                   "sample": f"1 oracle solve (m_crit+0.1 mass, {oit[0]} iterations, FP64 NumPy/SciPy, sparse "
-                             f"kernels single-threaded); oracle setup {setup_s:.1f} s excluded"}
+            D0, lv0, setup_s = oracle_hierarchy(theta, masses[0])
+            ot, ores = oracle_solve(D0, lv0, W.to_flat(psis[args.warmup].cpu().numpy()[0]))
+            cpu = {"value": 1.0 / ot, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+                   "sample": f"1 oracle solve (m_crit+0.1 mass, {ores.iterations} iterations, FP64 NumPy/SciPy, "
+                             f"sparse kernels single-threaded); oracle setup {setup_s:.1f} s excluded"}
+            # error of the GPU solutions of that right-hand side against the oracle's
+            xo = ores.x
+            for key, xg in (("fp64", x_check64), ("mixed", x_check32)):
+                xf = W.to_flat(xg)
+                errs_vs_oracle[key] = float(np.linalg.norm(xf - xo) / np.linalg.norm(xo))
         out = {
             "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
@@ -594,7 +626,10 @@ def main():
             "kernel_share_mixed": kernel_share_mixed,
             "cpu_baseline": cpu,
             "clocks": clk,
+            "error_vs_oracle": ({"x": "||x_gpu - x_oracle|| / ||x_oracle||, m_crit+0.1 mass, first timed RHS",
+                                 **errs_vs_oracle} if errs_vs_oracle else None),
             "mixed": {"value": round(mixed_value, 3), "unit": "solves/s", "speedup_vs_fp64": round(mixed_value / value, 3),
+                      "error_vs_oracle": errs_vs_oracle.get("mixed"),
                       "iterations": it32[-len(masses):], "true_relres_max": max(rr32),
                       "latency_ms": {"p50": round(float(np.percentile(sv32, 50)), 3),
                                      "p99": round(float(np.percentile(sv32, 99)), 3)},

@@ -54,7 +54,8 @@ typedef struct amamg_ctx* amamg_handle;
 #define AMAMG_ERR_SINGULAR      -4   /* a local or coarsest pivot vanished in setup */
 #define AMAMG_ERR_NONFINITE     -5   /* NaN/Inf in a right-hand side or a residual */
 #define AMAMG_ERR_TIMEOUT       -6   /* a bounded device wait of a coarse smoother ran out (reported by
-                                        amamg_solve / amamg_batch_cycle; the handle stays usable) */
+                                        amamg_solve, amamg_batch_cycle and amamg_sync_status; the
+                                        handle stays usable) */
 
 /* vector precision of apply-style calls */
 #define AMAMG_F64 0                  /* complex128 vectors, FP64 operators */
@@ -65,6 +66,17 @@ typedef struct amamg_ctx* amamg_handle;
 #define AMAMG_SOLVE_MIXED 1          /* FP64 outer FGMRES, FP32 V-cycle, FP64 coarsest solve */
 
 #define AMAMG_MAX_LEVELS 4
+
+/* normalisation N of the local interpolation, Eq. (16) */
+#define AMAMG_NORM_NONE   0          /* N = identity: the exact ideal interpolation (default) */
+#define AMAMG_NORM_ROWSUM 1          /* every non-vertex scalar row of P divided by its complex row sum;
+                                        rows whose |sum| is below 1e-12 x the level's largest |sum| stay */
+
+/* which basket a border site takes its formula from ("the first aggregate it
+ * was assigned to", Sec. 4.1) */
+#define AMAMG_OWNER_TILE      0      /* the basket of the tile containing the site, W(t/a, x/a) (default) */
+#define AMAMG_OWNER_FIRST_LEX 1      /* of the baskets containing the site, the one of smallest index
+                                        p (Nx/a) + q */
 
 typedef struct {
     int    nlevels;                  /* 2..4 levels including the fine one */
@@ -78,6 +90,8 @@ typedef struct {
                                         1: only its spin-diagonal weights, (P + s3 P s3) / 2, so the
                                         coarse operators keep sigma_3-hermiticity (the direction
                                         Sec. 6 proposes; a comparison hierarchy, not the method as read) */
+    int    normalization;            /* AMAMG_NORM_NONE (default) or AMAMG_NORM_ROWSUM, every level */
+    int    edge_owner;               /* AMAMG_OWNER_TILE (default) or AMAMG_OWNER_FIRST_LEX, every level */
 } amamg_params;
 
 typedef struct {
@@ -165,6 +179,14 @@ int amamg_apply_PH(amamg_handle h, int level, const void* fine_in, void* coarse_
 int amamg_apply_coarse(amamg_handle h, int level, const void* in, void* out,
                        int R, int precision, void* stream);
 
+/* Time-outs of apply-style calls.  The coarse smoothers of amamg_smooth,
+ * amamg_vcycle and amamg_vcycle_noalloc wait on other thread blocks with
+ * bounded polls; these calls only enqueue work and do not report a wait that
+ * ran out (their e is then not the smoothed result).  Such a time-out stays
+ * recorded on the handle until amamg_sync_status (or the next amamg_solve /
+ * amamg_batch_cycle, which check at their end) reports it and re-arms the
+ * counters. */
+
 /* sweeps block Gauss-Seidel sweeps on A_l e = r, starting from the e passed in
  * (red-black on the fine level; on coarse levels 8 colours (t + 3x) mod 8
  * when both extents are multiples of 8 and no coupling (dt, dx) of the level
@@ -190,9 +212,13 @@ int amamg_vcycle(amamg_handle h, const void* r, void* e, int R, int precision, v
  * the same result as amamg_vcycle; the coarse-level work vectors live in one
  * file-scope __device__ array of AMAMG_NOALLOC_SCRATCH_BYTES that every GPU
  * loading the library holds until the process exits.
- *   - Needs 2 * R * 2 * (n_1 + ... + n_L) complex elements (each level's
+ *   - Needs 2 * R * 2 * (n_1 + ... + n_L) complex elements (r and e of every
+ *     coarse level l >= 1, two spins per site, R right-hand sides; each level's
  *     vectors rounded up to 256 bytes); larger requests return
  *     AMAMG_ERR_INVALID_ARG with the sizes in amamg_last_error.
+ *   - Like amamg_vcycle it does not report a time-out of a coarse smoother's
+ *     bounded wait: follow it with amamg_sync_status where that matters (that
+ *     call synchronises the stream and allocates nothing).
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress, with that device current); make that first call
  *     before any stream capture.
@@ -202,22 +228,31 @@ int amamg_vcycle(amamg_handle h, const void* r, void* e, int R, int precision, v
  *     streams, other handles) race on it: serialise them. */
 int amamg_vcycle_noalloc(amamg_handle h, const void* r, void* e, int R, int precision, void* stream);
 
+/* Reports (and clears) a time-out of a coarse smoother's bounded wait left by
+ * any earlier call on this handle: synchronises the stream, reads the
+ * handle's time-out flag, and when it is set re-arms the synchronisation
+ * counters and returns AMAMG_ERR_TIMEOUT; else AMAMG_OK.  Allocates nothing. */
+int amamg_sync_status(amamg_handle h, void* stream);
+
 /* Self-test of the bounded waits of the coarse Gauss-Seidel owner sweep (the
  * kernel that runs coarse smoothing on most levels; its blocks wait only for
  * the blocks owning their sites' neighbours, each wait limited to about half a
- * second of polling).  Runs one two-sweep smoothing of coarse level l
+ * second of polling).  Enqueues one two-sweep smoothing of coarse level l
  * (1 <= l < nlevels - 1) in `precision` on the handle's own zero work vectors
  * with one block that never publishes its phase counter, so its neighbours'
- * waits run out.  Synchronises the stream.  Returns AMAMG_ERR_TIMEOUT when the
- * time-out was recorded and reported (the expected outcome; the counters are
- * re-armed and the handle stays usable), AMAMG_OK if no wait ran out, or
- * AMAMG_ERR_INVALID_ARG when level l has no owner sweep with two or more
- * blocks.  Nothing else in the library uses this path. */
+ * waits run out; like the other apply-style calls it does not report the
+ * time-out itself: amamg_sync_status then returns AMAMG_ERR_TIMEOUT (the
+ * expected outcome; the counters are re-armed and the handle stays usable).
+ * Returns AMAMG_OK once enqueued, or AMAMG_ERR_INVALID_ARG when level l has no
+ * owner sweep with two or more blocks.  Nothing else in the library uses this
+ * path. */
 int amamg_selftest_sync_timeout(amamg_handle h, int level, int precision, void* stream);
 
 /* Integer structure of level l (host arrays; bit-exact tests):
  * role[Nt_l*Nx_l] (0 vertex, 1 edge, 2 interior), owner_tile[Nt_l*Nx_l]
- * (index p*(Nx_l/a)+q of the basket a site takes its formula from),
+ * (index p*(Nx_l/a)+q of the basket a site takes its formula from under the
+ * handle's edge_owner rule; both computed on the device by the rule the
+ * transfer kernels index with),
  * nbr_offsets[2*K] canonical (dt mod Nt_{l+1}, dx mod Nx_{l+1}) block offsets of
  * the level-(l+1) operator, lexicographically sorted, *nbr_count = K.
  * Arrays may be NULL to skip them; nbr_offsets must hold 2*32 ints. */

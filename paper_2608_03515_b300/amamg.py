@@ -28,11 +28,15 @@ F32 = 1
 SOLVE_FP64 = 0
 SOLVE_MIXED = 1
 MAX_LEVELS = 4
+NORM_NONE = 0
+NORM_ROWSUM = 1
+OWNER_TILE = 0
+OWNER_FIRST_LEX = 1
 
 EXPORTED = [
     "amamg_default_params", "amamg_query_bytes", "amamg_setup", "amamg_solve", "amamg_apply_D",
     "amamg_apply_P", "amamg_apply_PH", "amamg_apply_coarse", "amamg_smooth", "amamg_coarsest_solve",
-    "amamg_vcycle", "amamg_vcycle_noalloc", "amamg_selftest_sync_timeout", "amamg_export_structure", "amamg_level_info", "amamg_export_P", "amamg_export_coarse",
+    "amamg_vcycle", "amamg_vcycle_noalloc", "amamg_selftest_sync_timeout", "amamg_sync_status", "amamg_export_structure", "amamg_level_info", "amamg_export_P", "amamg_export_coarse",
     "amamg_profile_enable", "amamg_profile_reset", "amamg_profile_get", "amamg_launch_count",
     "amamg_setup_seconds", "amamg_destroy", "amamg_status_string", "amamg_last_error",
     "amamg_batch_create", "amamg_batch_admit", "amamg_batch_cycle", "amamg_batch_retire", "amamg_batch_destroy",
@@ -49,6 +53,8 @@ class Params(ctypes.Structure):
         ("post_smooth", ctypes.c_int),
         ("tol", ctypes.c_double),
         ("spin_split", ctypes.c_int),
+        ("normalization", ctypes.c_int),
+        ("edge_owner", ctypes.c_int),
     ]
 
 
@@ -81,6 +87,7 @@ def _load() -> ctypes.CDLL:
         "amamg_vcycle": ([vp, vp, vp, ci, ci, vp], ci),
         "amamg_vcycle_noalloc": ([vp, vp, vp, ci, ci, vp], ci),
         "amamg_selftest_sync_timeout": ([vp, ci, ci, vp], ci),
+        "amamg_sync_status": ([vp, vp], ci),
         "amamg_export_structure": ([vp, ci, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                     ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], ci),
         "amamg_level_info": ([vp, ci, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(ci)], ci),
@@ -154,7 +161,10 @@ def default_params() -> Params:
 
 
 def make_params(aggs: Sequence[int], precision: int = SOLVE_FP64, restart: int = 30, max_iter: int = 3000,
-                post_smooth: int = 2, tol: float = 1e-10, spin_split: bool = False) -> Params:
+                post_smooth: int = 2, tol: float = 1e-10, spin_split: bool = False,
+                normalization: str = "none", ownership: str = "tile") -> Params:
+    """Parameters of amamg_setup; normalization "none" | "rowsum" and ownership
+    "tile" | "first_lex" name the readings the oracle's build_hierarchy takes."""
     p = default_params()
     p.nlevels = len(aggs) + 1
     for i, a in enumerate(aggs):
@@ -165,6 +175,8 @@ def make_params(aggs: Sequence[int], precision: int = SOLVE_FP64, restart: int =
     p.post_smooth = post_smooth
     p.tol = tol
     p.spin_split = 1 if spin_split else 0
+    p.normalization = {"none": NORM_NONE, "rowsum": NORM_ROWSUM}[normalization]
+    p.edge_owner = {"tile": OWNER_TILE, "first_lex": OWNER_FIRST_LEX}[ownership]
     return p
 
 
@@ -289,10 +301,17 @@ def vcycle_noalloc(hier: Hierarchy, r, e, stream=None):
 
 
 def selftest_sync_timeout(hier: Hierarchy, level: int, precision: int = None, stream=None) -> int:
-    """amamg_selftest_sync_timeout: one coarse smoothing in which one owner block
-    withholds its phase counter; returns the raw status (TIMEOUT expected)."""
+    """amamg_selftest_sync_timeout: enqueues one coarse smoothing in which one
+    owner block withholds its phase counter; returns the raw status (OK once
+    enqueued; sync_status then reports the time-out)."""
     prec = F64 if precision is None else precision
     return int(_lib.amamg_selftest_sync_timeout(hier.h, level, prec, _stream(stream)))
+
+
+def sync_status(hier: Hierarchy, stream=None) -> int:
+    """amamg_sync_status: the raw status of the bounded-wait check (OK or
+    ERR_TIMEOUT), re-arming the counters after a time-out."""
+    return int(_lib.amamg_sync_status(hier.h, _stream(stream)))
 
 
 def export_structure(hier: Hierarchy, level: int):

@@ -119,7 +119,10 @@ Offsets wilson_offsets(int Nt, int Nx) {
 // support of coarse column 0 is its own vertex site plus the owned sites of the
 // four tiles that have it as a corner; A widens it by its offsets; each reached
 // site contributes its vertex (vertex row) or its tile's four corners.
-int coarse_offsets(const Offsets& fine, int Nt, int Nx, int a, Offsets* out) {
+int coarse_offsets_owned(const Offsets& fine, int Nt, int Nx, int a, int own, Offsets* out);
+
+int coarse_offsets(const Offsets& fine, int Nt, int Nx, int a, int own, Offsets* out) {
+  if (own != OWN_TILE) return coarse_offsets_owned(fine, Nt, Nx, a, own, out);
   const int Np = Nt / a, Nq = Nx / a;
   std::set<std::pair<int, int>> W;
   std::vector<std::pair<int, int>> supp;
@@ -145,6 +148,62 @@ int coarse_offsets(const Offsets& fine, int Nt, int Nx, int a, Offsets* out) {
   Offsets o{};
   o.K = 0;
   for (auto& p : W) { o.dt[o.K] = p.first; o.dx[o.K] = p.second; ++o.K; }
+  *out = o;
+  return AMAMG_OK;
+}
+
+// The same for an ownership rule that is not translation invariant (first-lex:
+// the rows of the first tile row and column come from other baskets than
+// elsewhere): the column pattern of every coarse column v, i.e. the rows
+// (vertices w) reached from v's support (its vertex site and the F sites its
+// four corner baskets own) through A, collected as offsets w - v over all v.
+int coarse_offsets_owned(const Offsets& fine, int Nt, int Nx, int a, int own, Offsets* out) {
+  const int Np = Nt / a, Nq = Nx / a;
+  std::vector<char> hit((size_t)Np * Nq, 0);
+  std::vector<std::pair<int, int>> supp;
+  for (int pv = 0; pv < Np; ++pv)
+    for (int qv = 0; qv < Nq; ++qv) {
+      supp.clear();
+      supp.push_back({pv * a, qv * a});
+      for (int c = 0; c < 4; ++c) {
+        const int pB = wrap(pv - (c >> 1), Np), qB = wrap(qv - (c & 1), Nq);
+        for (int i = 0; i <= a; ++i)
+          for (int j = 0; j <= a; ++j) {
+            if ((i == 0 || i == a) && (j == 0 || j == a)) continue;
+            const int it = (i == a) ? 0 : i, jt = (j == a) ? 0 : j;
+            const int pT = (i == a) ? wrap(pB + 1, Np) : pB, qT = (j == a) ? wrap(qB + 1, Nq) : qB;
+            int dp, dq;
+            row_basket(own, pT, qT, it, jt, dp, dq);
+            if (wrap(pT + dp, Np) == pB && wrap(qT + dq, Nq) == qB) supp.push_back({pT * a + it, qT * a + jt});
+          }
+      }
+      for (auto& sv : supp)
+        for (int k = 0; k < fine.K; ++k) {
+          const int t = wrap(sv.first + fine.dt[k], Nt), x = wrap(sv.second + fine.dx[k], Nx);
+          const int pt = t / a, qt = x / a, it = t % a, jt = x % a;
+          if (it == 0 && jt == 0) {
+            hit[(size_t)wrap(pt - pv, Np) * Nq + wrap(qt - qv, Nq)] = 1;
+          } else {
+            int dp, dq;
+            row_basket(own, pt, qt, it, jt, dp, dq);
+            for (int c = 0; c < 4; ++c)
+              hit[(size_t)wrap(pt + dp + (c >> 1) - pv, Np) * Nq + wrap(qt + dq + (c & 1) - qv, Nq)] = 1;
+          }
+        }
+    }
+  // row v couples to column v + o for every pair found as (w - v) with w the
+  // row: the pattern is symmetric (A's is), so both signs are marked
+  for (int dt = 0; dt < Np; ++dt)
+    for (int dx = 0; dx < Nq; ++dx)
+      if (hit[(size_t)dt * Nq + dx]) hit[(size_t)wrap(-dt, Np) * Nq + wrap(-dx, Nq)] = 2;
+  Offsets o{};
+  o.K = 0;
+  for (int dt = 0; dt < Np; ++dt)
+    for (int dx = 0; dx < Nq; ++dx) {
+      if (!hit[(size_t)dt * Nq + dx]) continue;
+      if (o.K == AMAMG_MAX_OFFSETS) return AMAMG_ERR_INVALID_ARG;
+      o.dt[o.K] = dt; o.dx[o.K] = dx; ++o.K;
+    }
   *out = o;
   return AMAMG_OK;
 }
@@ -387,11 +446,12 @@ int op_prolong(amamg_ctx* h, int l, const typename cplx<T>::type* ec, typename c
   const double bytes = pbytes + (double)R * 2 * (L.n + h->lv[l + 1].n) * cb;
   if constexpr (f64)
     return launch(h, "prolong_f64", bytes, st, [&] {
-      return launch_prolong<double, double2>(ec, ef, L.P64, nullptr, L.Nx, L.a, L.Np, L.Nq, R, st);
+      return launch_prolong<double, double2>(ec, ef, L.P64, nullptr, L.Nx, L.a, L.Np, L.Nq, R, st,
+                                             h->prm.edge_owner);
     }, (double)L.nT * L.nrows * 64.0 * R);
   else
     return launch(h, "prolong_f32", bytes, st, [&] {
-      return launch_prolong<float, __half2>(ec, ef, L.P16, L.Ps, L.Nx, L.a, L.Np, L.Nq, R, st);
+      return launch_prolong<float, __half2>(ec, ef, L.P16, L.Ps, L.Nx, L.a, L.Np, L.Nq, R, st, h->prm.edge_owner);
     }, (double)L.nT * L.nrows * 64.0 * R);
 }
 
@@ -399,7 +459,7 @@ int op_prolong(amamg_ctx* h, int l, const typename cplx<T>::type* ec, typename c
 // post-smoothing red-black sweeps) as one launch when a resident shape exists.
 template <typename T>
 bool fine_post_possible(const amamg_ctx* h, int R) {
-  if (!h->fine_fused) return false;
+  if (!h->fine_fused || h->prm.edge_owner != AMAMG_OWNER_TILE) return false;   // the fused kernel reads tile corners
   const Level& L = h->lv[0];
   if constexpr (sizeof(T) == 8) return fine_post_rows<double, double2>(L.Nt, L.Nx, L.a, R) > 0;
   else return fine_post_rows<float, __half2>(L.Nt, L.Nx, L.a, R) > 0;
@@ -439,11 +499,12 @@ int op_restrict(amamg_ctx* h, int l, const typename cplx<T>::type* ef, typename 
   const double bytes = pbytes + (double)R * 2 * (L.n + h->lv[l + 1].n) * cb;
   if constexpr (f64)
     return launch(h, "restrict_f64", bytes, st, [&] {
-      return launch_restrict<double, double2>(ef, ec, L.P64, nullptr, L.Nx, L.a, L.Np, L.Nq, R, st);
+      return launch_restrict<double, double2>(ef, ec, L.P64, nullptr, L.Nx, L.a, L.Np, L.Nq, R, st,
+                                              h->prm.edge_owner);
     }, (double)L.nT * L.nrows * 64.0 * R);
   else
     return launch(h, "restrict_f32", bytes, st, [&] {
-      return launch_restrict<float, __half2>(ef, ec, L.P16, L.Ps, L.Nx, L.a, L.Np, L.Nq, R, st);
+      return launch_restrict<float, __half2>(ef, ec, L.P16, L.Ps, L.Nx, L.a, L.Np, L.Nq, R, st, h->prm.edge_owner);
     }, (double)L.nT * L.nrows * 64.0 * R);
 }
 
@@ -486,21 +547,32 @@ int vcycle_coarsest(amamg_ctx* h, const float2* r, float2* e, int R, cudaStream_
 }
 
 // V-cycle of Algorithm 1 (start vector 0, no pre-smoothing) from level l:
-// e = P M_{l+1}(P^H r), then post-smoothing sweeps on A_l e = r.
+// e = P M_{l+1}(P^H r), then post-smoothing sweeps on A_l e = r.  The coarse
+// levels' r and e come from w (the handle's own vectors, or caller scratch).
 template <typename T>
-int vcycle_from(amamg_ctx* h, int l, const typename cplx<T>::type* r, typename cplx<T>::type* e, int R,
-                cudaStream_t st) {
+int vcycle_from(amamg_ctx* h, int l, const typename cplx<T>::type* r, typename cplx<T>::type* e,
+                const VcycleVecs<T>& w, int R, cudaStream_t st) {
   const int Lc = (int)h->lv.size() - 1;
   if (l == Lc) return vcycle_coarsest(h, r, e, R, st);
-  Level& C = h->lv[l + 1];
-  typename cplx<T>::type *rc, *ec;
-  if constexpr (sizeof(T) == 8) { rc = C.r64; ec = C.e64; } else { rc = C.r32; ec = C.e32; }
+  typename cplx<T>::type* rc = w.r[l + 1];
+  typename cplx<T>::type* ec = w.e[l + 1];
   CKS(op_restrict<T>(h, l, r, rc, R, st));
-  CKS(vcycle_from<T>(h, l + 1, rc, ec, R, st));
+  CKS(vcycle_from<T>(h, l + 1, rc, ec, w, R, st));
   if (l == 0 && h->prm.post_smooth > 0 && fine_post_possible<T>(h, R))
     return op_fine_post<T>(h, ec, e, r, R, st);
   CKS(op_prolong<T>(h, l, ec, e, R, st));
   return smooth_impl<T>(h, l, e, r, R, h->prm.post_smooth, st);
+}
+
+// the handle's own coarse work vectors (ensure_vcycle_ws sizes them)
+template <typename T>
+VcycleVecs<T> handle_vecs(const amamg_ctx* h) {
+  VcycleVecs<T> w;
+  for (size_t l = 1; l < h->lv.size(); ++l) {
+    if constexpr (sizeof(T) == 8) { w.r[l] = h->lv[l].r64; w.e[l] = h->lv[l].e64; }
+    else { w.r[l] = h->lv[l].r32; w.e[l] = h->lv[l].e32; }
+  }
+  return w;
 }
 
 // ----------------------------------------------------------------- FGMRES
@@ -543,7 +615,7 @@ int arnoldi_step(amamg_ctx* h, int j, int R, cudaStream_t st) {
     if (j == 0)
       CKS(launch(h, "cast_f64_f32", (double)R * len * 24.0, st,
                  [&] { return launch_cast<double2, float2>(vj, h->v32, (long)R * len, st); }));
-    CKS(vcycle_from<float>(h, 0, h->v32, zj, R, st));
+    CKS(vcycle_from<float>(h, 0, h->v32, zj, handle_vecs<float>(h), R, st));
     const Level& L = h->lv[0];
     CKS(launch(h, "dslash_mixed", (double)L.n * (R * (16.0 + 32.0) + 32.0), st, [&] {
       return launch_dslash<float2, double2, double>(zj, h->w, nullptr, h->U64s, h->m0 + 2.0, L.Nt, L.Nx, R, st,
@@ -551,7 +623,7 @@ int arnoldi_step(amamg_ctx* h, int j, int R, cudaStream_t st) {
     }));
   } else {
     double2* zj = h->Z64 + (size_t)j * vi;
-    CKS(vcycle_from<double>(h, 0, vj, zj, R, st));
+    CKS(vcycle_from<double>(h, 0, vj, zj, handle_vecs<double>(h), R, st));
     CKS(op_dslash<double>(h, zj, h->w, nullptr, R, st));
   }
   // Classical Gram-Schmidt with the DGKS criterion: one pass, and a second
@@ -837,6 +909,14 @@ int check_params(const amamg_params* p, int Nt, int Nx, std::string* why) {
   if (p->restart < 1 || p->restart > 64) { *why = "restart must be 1..64"; return AMAMG_ERR_INVALID_ARG; }
   if (p->max_iter < 1 || p->post_smooth < 0 || !(p->tol > 0.0)) { *why = "bad max_iter/post_smooth/tol"; return AMAMG_ERR_INVALID_ARG; }
   if (p->spin_split != 0 && p->spin_split != 1) { *why = "spin_split must be 0 or 1"; return AMAMG_ERR_INVALID_ARG; }
+  if (p->normalization != AMAMG_NORM_NONE && p->normalization != AMAMG_NORM_ROWSUM) {
+    *why = "normalization must be AMAMG_NORM_NONE or AMAMG_NORM_ROWSUM";
+    return AMAMG_ERR_INVALID_ARG;
+  }
+  if (p->edge_owner != AMAMG_OWNER_TILE && p->edge_owner != AMAMG_OWNER_FIRST_LEX) {
+    *why = "edge_owner must be AMAMG_OWNER_TILE or AMAMG_OWNER_FIRST_LEX";
+    return AMAMG_ERR_INVALID_ARG;
+  }
   if (Nt < 4 || Nx < 4 || (Nt & 1) || (Nx & 1)) { *why = "Nt, Nx must be even and >= 4"; return AMAMG_ERR_INVALID_ARG; }
   int nt = Nt, nx = Nx;
   for (int l = 0; l + 1 < p->nlevels; ++l) {
@@ -864,6 +944,7 @@ void free_all(amamg_ctx* h) {
   if (h->ev_out) cudaEventDestroy(h->ev_out);
   h->ws = nullptr; h->ev_in = h->ev_out = nullptr;
   dfree(h->U64); dfree(h->U64s); dfree(h->U32); dfree(h->Ainv); dfree(h->Ainv32); dfree(h->d_err); dfree(h->d_sync); dfree(h->d_owner_flags);
+  dfree(h->d_smax); dfree(h->d_rowsum_skipped);
   dfree(h->V); dfree(h->Z64); dfree(h->Z32); dfree(h->v32); dfree(h->w); dfree(h->res);
   dfree(h->partial); dfree(h->d_h); dfree(h->d_inv); dfree(h->d_flag); dfree(h->d_y); dfree(h->d_tickets); dfree(h->d_npart);
   dfree(h->d_diag64); dfree(h->d_inv64); dfree(h->d_inv32);
@@ -894,6 +975,9 @@ int do_setup(amamg_ctx* h, const void* Uin, cudaStream_t st) {
   CK(cudaMemsetAsync(h->d_sync, 0, 8 * sizeof(unsigned), st));
   CKS(dalloc(h, &h->d_owner_flags, OWNER_MAX_BLOCKS));
   CK(cudaMemsetAsync(h->d_owner_flags, 0, OWNER_MAX_BLOCKS * sizeof(unsigned), st));
+  CKS(dalloc(h, &h->d_smax, 1));
+  CKS(dalloc(h, &h->d_rowsum_skipped, AMAMG_MAX_LEVELS));
+  CK(cudaMemsetAsync(h->d_rowsum_skipped, 0, AMAMG_MAX_LEVELS * sizeof(unsigned), st));
   CK(cudaMemcpyAsync(h->U64, Uin, nl * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(h->U64s, Uin, nl * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   CKS(launch(h, "setup_cast_links", nl * 24.0, st, [&] {
@@ -911,24 +995,29 @@ int do_setup(amamg_ctx* h, const void* Uin, cudaStream_t st) {
     CKS(dalloc(h, &F.P16, (size_t)F.nT * 8 * F.nrows));
     CKS(dalloc(h, &F.Ps, (size_t)F.nT));
     const Offsets& fo = (l == 0) ? fine_off : F.off;
-    if (coarse_offsets(fo, F.Nt, F.Nx, F.a, &C.off) != AMAMG_OK || C.off.K - 1 > GS_MAX_OFFDIAG) {
+    if (coarse_offsets(fo, F.Nt, F.Nx, F.a, h->prm.edge_owner, &C.off) != AMAMG_OK ||
+        C.off.K - 1 > GS_MAX_OFFDIAG) {
       h->err = "coarse operator has more block offsets than the smoother supports (25)";
       return AMAMG_ERR_INVALID_ARG;
     }
     CKS(dalloc(h, &C.B64, (size_t)C.off.K * 4 * C.n));
-    if (l == 0) {
-      WilsonOp op{h->U64, h->m0 + 2.0, F.Nt, F.Nx};
-      CKS(launch(h, "setup_local_solve", 0.0, st, [&] { return launch_local_solve(op, F.a, F.Np, F.Nq, F.P64, h->d_err, st); }));
+    const int own = h->prm.edge_owner;
+    // local interpolation, then Eq. (16)'s normalisation (row sums) and the
+    // optional spin split, then the Galerkin product with the final P
+    auto build_level = [&](const auto& op) -> int {
+      CKS(launch(h, "setup_local_solve", 0.0, st,
+                 [&] { return launch_local_solve(op, F.a, F.Np, F.Nq, F.P64, h->d_err, own, st); }));
+      if (h->prm.normalization == AMAMG_NORM_ROWSUM)
+        CKS(launch(h, "setup_rowsum", 0.0, st, [&] {
+          return launch_rowsum_normalize(F.P64, F.nrows, F.nT, h->d_smax, h->d_rowsum_skipped + l, st);
+        }));
       if (h->prm.spin_split)
         CKS(launch(h, "setup_spin_split", 0.0, st, [&] { return launch_spin_split_P(F.P64, F.nrows, F.nT, st); }));
-      CKS(launch(h, "setup_galerkin", 0.0, st, [&] { return launch_galerkin(op, F.P64, F.a, F.Np, F.Nq, C.off, C.B64, st); }));
-    } else {
-      StencilOp op{F.B64, F.off, F.Nt, F.Nx};
-      CKS(launch(h, "setup_local_solve", 0.0, st, [&] { return launch_local_solve(op, F.a, F.Np, F.Nq, F.P64, h->d_err, st); }));
-      if (h->prm.spin_split)
-        CKS(launch(h, "setup_spin_split", 0.0, st, [&] { return launch_spin_split_P(F.P64, F.nrows, F.nT, st); }));
-      CKS(launch(h, "setup_galerkin", 0.0, st, [&] { return launch_galerkin(op, F.P64, F.a, F.Np, F.Nq, C.off, C.B64, st); }));
-    }
+      return launch(h, "setup_galerkin", 0.0, st,
+                    [&] { return launch_galerkin(op, F.P64, F.a, F.Np, F.Nq, C.off, C.B64, own, st); });
+    };
+    if (l == 0) CKS(build_level(WilsonOp{h->U64, h->m0 + 2.0, F.Nt, F.Nx}));
+    else CKS(build_level(StencilOp{F.B64, F.off, F.Nt, F.Nx}));
     CKS(launch(h, "setup_pack", 0.0, st, [&] { return launch_pack_P16(F.P64, 8 * F.nrows, F.nT, F.P16, F.Ps, st); }));
   }
   for (int l = 1; l < L; ++l) {
@@ -1006,6 +1095,14 @@ bool valid_level(amamg_ctx* h, int level, bool need_next) {
 
 }  // namespace
 
+template <typename T>
+int engine_vcycle(amamg_ctx* h, const typename cplx<T>::type* r, typename cplx<T>::type* e, const VcycleVecs<T>& w,
+                  int R, cudaStream_t st) {
+  return vcycle_from<T>(h, 0, r, e, w, R, st);
+}
+template int engine_vcycle<double>(amamg_ctx*, const double2*, double2*, const VcycleVecs<double>&, int, cudaStream_t);
+template int engine_vcycle<float>(amamg_ctx*, const float2*, float2*, const VcycleVecs<float>&, int, cudaStream_t);
+
 // =================================================================== C ABI
 extern "C" {
 
@@ -1036,7 +1133,7 @@ int amamg_query_bytes(const amamg_params* p, int Nt, int Nx, int max_rhs, size_t
     const size_t nT = (size_t)(nt / a) * (nx / a), nrows = 2 * (a * a - 1);
     sb += nT * 8 * nrows * (16 + 4) + nT * 4;
     Offsets c;
-    if (coarse_offsets(off, nt, nx, a, &c) != AMAMG_OK) return AMAMG_ERR_INVALID_ARG;
+    if (coarse_offsets(off, nt, nx, a, p->edge_owner, &c) != AMAMG_OK) return AMAMG_ERR_INVALID_ARG;
     nt /= a; nx /= a;
     const size_t n = (size_t)nt * nx;
     sb += (size_t)c.K * n * (4 * 16 + 4 * 4 + 4) + 4 * n * (16 + 8);
@@ -1264,7 +1361,12 @@ int amamg_selftest_sync_timeout(amamg_handle h, int level, int precision, void* 
   }
   CK(e);
   h->launches++;
-  return check_grid_sync(h, st);
+  return AMAMG_OK;
+}
+
+int amamg_sync_status(amamg_handle h, void* stream) {
+  if (!h) return AMAMG_ERR_INVALID_ARG;
+  return check_grid_sync(h, S(stream));
 }
 
 int amamg_coarsest_solve(amamg_handle h, const void* r, void* e, int R, void* stream) {
@@ -1276,8 +1378,10 @@ int amamg_vcycle(amamg_handle h, const void* r, void* e, int R, int precision, v
   if (!h || !r || !e || R < 1) return AMAMG_ERR_INVALID_ARG;
   int rc = ensure_vcycle_ws(h, R);
   if (rc != AMAMG_OK) return rc;
-  if (precision == AMAMG_F64) return vcycle_from<double>(h, 0, (const double2*)r, (double2*)e, R, S(stream));
-  if (precision == AMAMG_F32) return vcycle_from<float>(h, 0, (const float2*)r, (float2*)e, R, S(stream));
+  if (precision == AMAMG_F64)
+    return vcycle_from<double>(h, 0, (const double2*)r, (double2*)e, handle_vecs<double>(h), R, S(stream));
+  if (precision == AMAMG_F32)
+    return vcycle_from<float>(h, 0, (const float2*)r, (float2*)e, handle_vecs<float>(h), R, S(stream));
   return AMAMG_ERR_INVALID_ARG;
 }
 
@@ -1286,13 +1390,20 @@ int amamg_export_structure(amamg_handle h, int level, int32_t* role, int32_t* ow
   if (!h || !valid_level(h, level, true)) return AMAMG_ERR_INVALID_ARG;
   const Level& L = h->lv[level];
   const Level& C = h->lv[level + 1];
-  for (int t = 0; t < L.Nt; ++t)
-    for (int x = 0; x < L.Nx; ++x) {
-      const int s = t * L.Nx + x;
-      const bool t0 = t % L.a == 0, x0 = x % L.a == 0;
-      if (role) role[s] = (t0 && x0) ? 0 : (t0 != x0 ? 1 : 2);
-      if (owner_tile) owner_tile[s] = (t / L.a) * L.Nq + x / L.a;
+  if (role || owner_tile) {
+    // computed on the device by the ownership rule the transfer kernels use
+    int* d = nullptr;
+    CKS(dalloc(h, &d, 2 * (size_t)L.n));
+    cudaError_t e = launch_structure(L.Nt, L.Nx, L.a, h->prm.edge_owner, d, d + L.n, 0);
+    std::vector<int> tmp(2 * (size_t)L.n);
+    if (e == cudaSuccess) e = cudaMemcpy(tmp.data(), d, sizeof(int) * 2 * L.n, cudaMemcpyDeviceToHost);
+    dfree(d);
+    CK(e);
+    for (int s = 0; s < L.n; ++s) {
+      if (role) role[s] = tmp[s];
+      if (owner_tile) owner_tile[s] = tmp[L.n + s];
     }
+  }
   if (nbr_offsets)
     for (int k = 0; k < C.off.K; ++k) { nbr_offsets[2 * k] = C.off.dt[k]; nbr_offsets[2 * k + 1] = C.off.dx[k]; }
   if (nbr_count) *nbr_count = C.off.K;

@@ -110,3 +110,26 @@ __host__ __device__ __forceinline__ void site_colour(int ncol, int t, int x, int
     j = t * (Nx >> 3) + (x >> 3);
   }
 }
+
+// Edge ownership (Sec. 4.1: a border site takes its interpolation formula from
+// "the first aggregate it was assigned to").  Row of the non-vertex site at
+// in-tile position (i, j) of tile (p, q): its formula comes from basket
+// W(p + dp, q + dq) (indices mod the tile counts), where it sits at in-basket
+// position (i - a dp, j - a dq), and its stored columns 2c + beta are corner c
+// of that basket.
+//   OWN_TILE:      the tile's own basket (dp = dq = 0).
+//   OWN_FIRST_LEX: of the baskets containing the site, the one of smallest
+//                  index p Nq + q: a bottom-border site (i = 0) of a tile with
+//                  p >= 1 lies on the top border of W(p-1, q), a left-border
+//                  site (j = 0) of a tile with q >= 1 on the right border of
+//                  W(p, q-1); on the first tile row / column the periodic
+//                  neighbour has the larger index, so the tile's own basket keeps it.
+enum OwnerRule : int { OWN_TILE = 0, OWN_FIRST_LEX = 1 };
+__host__ __device__ __forceinline__ void row_basket(int own, int p, int q, int i, int j, int& dp, int& dq) {
+  dp = 0;
+  dq = 0;
+  if (own == OWN_FIRST_LEX) {
+    if (i == 0 && p >= 1) dp = -1;
+    else if (j == 0 && q >= 1) dq = -1;
+  }
+}

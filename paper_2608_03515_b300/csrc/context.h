@@ -105,6 +105,14 @@ inline int gs_kind_for(const Level& L, int R) {
   return ok ? GS_OWNER : GS_GRID;
 }
 
+// Coarse-level work vectors of one V-cycle: r_l and e_l of level l >= 1
+// (entry 0 unused), R right-hand sides each, [R][2][n_l] complex.
+template <typename T>
+struct VcycleVecs {
+  typename cplx<T>::type* r[AMAMG_MAX_LEVELS] = {};
+  typename cplx<T>::type* e[AMAMG_MAX_LEVELS] = {};
+};
+
 struct amamg_ctx {
   amamg_params prm{};
   int Nt = 0, Nx = 0;
@@ -121,6 +129,8 @@ struct amamg_ctx {
   // generation, [2] time-out flag, [3] owner-sweep epoch base, [4] its end ticket
   unsigned* d_sync = nullptr;
   unsigned* d_owner_flags = nullptr;   // [OWNER_MAX_BLOCKS] owner-sweep phase counters
+  unsigned long long* d_smax = nullptr;     // row-sum normalisation: largest |row sum| of a level (setup)
+  unsigned* d_rowsum_skipped = nullptr;     // [AMAMG_MAX_LEVELS] rows left unnormalised per level
 
   // solver workspace
   int Rcap = 0;              // V-cycle work vectors
@@ -180,3 +190,10 @@ struct amamg_batch {
   std::vector<SlotState> sl;
   std::vector<double> mass;
 };
+
+// One V-cycle of Algorithm 1 on the fine level (start vector 0, no
+// pre-smoothing, post_smooth sweeps per level) with the coarse work vectors w:
+// the kernels and kernel choice of amamg_vcycle (amamg.cu).
+template <typename T>
+int engine_vcycle(amamg_ctx* h, const typename cplx<T>::type* r, typename cplx<T>::type* e, const VcycleVecs<T>& w,
+                  int R, cudaStream_t st);

@@ -10,6 +10,9 @@
 // One thread per site and right-hand side; neighbours are re-read through L1/L2
 // (each input element is needed by 5 threads of adjacent rows/columns).
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "kernels.h"
 
@@ -274,17 +277,33 @@ cudaError_t launch_rb_half(typename cplx<T>::type* e, const typename cplx<T>::ty
 // run).  Prolongation is per site, so a block's rows need not be whole tiles.
 template <typename T, typename PT>
 int fine_post_rows(int Nt, int Nx, int a, int R) {
-  static int cap = -1, sms = 0;          // co-resident blocks of 256 threads, SMs; first device queried
-  if (cap < 0) {
-    int dev = 0, occ = 0, coop = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fine_post<T, PT>, 256, 0) != cudaSuccess) {
-      cudaGetLastError();
-      cap = 0;
-    } else {
-      cap = coop ? sms * occ : 0;
+  // co-resident blocks of 256 threads and SM count, per device (several host
+  // threads may ask at once, for GPUs of different kinds)
+  static std::mutex mu;
+  static std::map<int, std::pair<int, int>> per_device;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int cap = 0, sms = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = per_device.find(dev);
+    if (it == per_device.end()) {
+      int occ = 0, coop = 0;
+      if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fine_post<T, PT>, 256, 0) != cudaSuccess) {
+        cudaGetLastError();
+        cap = 0;
+      } else {
+        cap = coop ? sms * occ : 0;
+      }
+      it = per_device.emplace(dev, std::make_pair(cap, sms)).first;
     }
+    cap = it->second.first;
+    sms = it->second.second;
   }
   if (cap <= 0 || (Nx & 1) || Nt % a || Nx % a) return 0;
   const long limit = std::min<long>(std::min<long>(cap, 2L * sms), FINE_MAX_BLOCKS);

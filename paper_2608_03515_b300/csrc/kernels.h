@@ -26,13 +26,19 @@ cudaError_t launch_rb_half(typename cplx<T>::type* e, const typename cplx<T>::ty
                            T inv_diag, int Nt, int Nx, int colour, int R, cudaStream_t st,
                            const T* inv_diag_r = nullptr);
 
-// transfer.cu
+// transfer.cu (own: edge-ownership rule, OwnerRule)
 template <typename T, typename PT>
 cudaError_t launch_prolong(const typename cplx<T>::type* ec, typename cplx<T>::type* ef, const PT* P,
-                           const float* Pscale, int Nxf, int a, int Np, int Nq, int R, cudaStream_t st);
+                           const float* Pscale, int Nxf, int a, int Np, int Nq, int R, cudaStream_t st,
+                           int own = OWN_TILE);
 template <typename T, typename PT>
 cudaError_t launch_restrict(const typename cplx<T>::type* ef, typename cplx<T>::type* ec, const PT* P,
-                            const float* Pscale, int Nxf, int a, int Np, int Nq, int R, cudaStream_t st);
+                            const float* Pscale, int Nxf, int a, int Np, int Nq, int R, cudaStream_t st,
+                            int own = OWN_TILE);
+
+// role (0 vertex, 1 edge, 2 interior) and owner basket of every site of a
+// level, as the transfer kernels index them (device int arrays of Nt Nx)
+cudaError_t launch_structure(int Nt, int Nx, int a, int own, int* role, int* owner, cudaStream_t st);
 
 // links with the t-boundary sign folded into U_0(Nt-1, x) (what the stencil
 // kernels take)
@@ -153,11 +159,17 @@ template <typename Cs, typename Cd>
 cudaError_t launch_cast(const Cs* src, Cd* dst, long len, cudaStream_t st);
 
 // setup.cu
+// own: edge-ownership rule (OwnerRule, row_basket)
 template <typename Op>
-cudaError_t launch_local_solve(const Op& op, int a, int Np, int Nq, double2* P, int* err, cudaStream_t st);
+cudaError_t launch_local_solve(const Op& op, int a, int Np, int Nq, double2* P, int* err, int own, cudaStream_t st);
 template <typename Op>
 cudaError_t launch_galerkin(const Op& op, const double2* P, int a, int Np, int Nq, const Offsets& offc, double2* Bc,
-                            cudaStream_t st);
+                            int own, cudaStream_t st);
+// Eq. (16) with N = diag(1 / row sum): every stored row divided by the sum of
+// its 8 weights, except rows whose |sum| is below 1e-12 x the level's largest
+// (their number is added to *skipped); smax: one device word of scratch
+cudaError_t launch_rowsum_normalize(double2* P, int nrows, int ntiles, unsigned long long* smax, unsigned* skipped,
+                                    cudaStream_t st);
 cudaError_t launch_diag_inv(const double2* B, int n, double2* D64, float2* D32, int* err, cudaStream_t st);
 cudaError_t launch_dense_from_blocks(const double2* B, const Offsets& off, int Nt, int Nx, double2* Ad,
                                      cudaStream_t st);

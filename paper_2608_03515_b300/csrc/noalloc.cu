@@ -45,12 +45,6 @@ cudaError_t scratch_address(void** out) {
 
 inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-template <typename T>
-struct LevelVecs {
-  typename cplx<T>::type* r[AMAMG_MAX_LEVELS] = {};
-  typename cplx<T>::type* e[AMAMG_MAX_LEVELS] = {};
-};
-
 // Bytes of scratch one V-cycle with R right-hand sides of element size cb needs.
 size_t scratch_bytes(const amamg_ctx* h, int R, size_t cb) {
   size_t b = 0;
@@ -58,115 +52,9 @@ size_t scratch_bytes(const amamg_ctx* h, int R, size_t cb) {
   return b;
 }
 
-// The same kernels, in the same order and with the same arguments, as the
-// V-cycle behind amamg_vcycle (Algorithm 1, start vector 0, no pre-smoothing,
-// post_smooth sweeps), with the coarse vectors taken from the scratch array.
-template <typename T>
-cudaError_t vcycle_level(amamg_ctx* h, int l, const typename cplx<T>::type* r, typename cplx<T>::type* e,
-                         const LevelVecs<T>& w, int R, cudaStream_t st) {
-  constexpr bool f64 = sizeof(T) == 8;
-  const int Lc = (int)h->lv.size() - 1;
-  cudaError_t err;
-  if (l == Lc) {
-    if constexpr (f64) err = launch_dense_gemv<double2>(h->Ainv, r, e, h->nd, R, st);
-    else err = launch_dense_gemv32(h->Ainv32, r, e, h->nd, R, st);
-    h->launches++;
-    return err;
-  }
-  const Level& L = h->lv[l];
-  if constexpr (f64) err = launch_restrict<double, double2>(r, w.r[l + 1], L.P64, nullptr, L.Nx, L.a, L.Np, L.Nq, R, st);
-  else err = launch_restrict<float, __half2>(r, w.r[l + 1], L.P16, L.Ps, L.Nx, L.a, L.Np, L.Nq, R, st);
-  if (err != cudaSuccess) return err;
-  h->launches++;
-  err = vcycle_level<T>(h, l + 1, w.r[l + 1], w.e[l + 1], w, R, st);
-  if (err != cudaSuccess) return err;
-  const int sweeps = h->prm.post_smooth;
-  if (l == 0 && sweeps > 0 && h->fine_fused) {
-    // the same choice as the allocating V-cycle: prolongation and red-black
-    // sweeps in one launch when a resident shape exists
-    const T inv = (T)(1.0 / (h->m0 + 2.0));
-    bool fused;
-    if constexpr (f64) fused = fine_post_rows<double, double2>(L.Nt, L.Nx, L.a, R) > 0;
-    else fused = fine_post_rows<float, __half2>(L.Nt, L.Nx, L.a, R) > 0;
-    if (fused) {
-      if constexpr (f64)
-        err = launch_fine_post<double, double2>(w.e[l + 1], e, r, L.P64, nullptr, h->U64s, inv, nullptr, L.Nt, L.Nx,
-                                                L.a, sweeps, R, h->d_owner_flags, h->d_sync, st);
-      else
-        err = launch_fine_post<float, __half2>(w.e[l + 1], e, r, L.P16, L.Ps, h->U32, inv, nullptr, L.Nt, L.Nx, L.a,
-                                               sweeps, R, h->d_owner_flags, h->d_sync, st);
-      h->launches++;
-      return err;
-    }
-  }
-  if constexpr (f64) err = launch_prolong<double, double2>(w.e[l + 1], e, L.P64, nullptr, L.Nx, L.a, L.Np, L.Nq, R, st);
-  else err = launch_prolong<float, __half2>(w.e[l + 1], e, L.P16, L.Ps, L.Nx, L.a, L.Np, L.Nq, R, st);
-  if (err != cudaSuccess) return err;
-  h->launches++;
-  if (l == 0) {
-    const T inv = (T)(1.0 / (h->m0 + 2.0));
-    const typename cplx<T>::type* U;
-    if constexpr (f64) U = h->U64s; else U = h->U32;
-    for (int s = 0; s < sweeps; ++s)
-      for (int c = 0; c < 2; ++c) {
-        err = launch_rb_half<T>(e, r, U, inv, L.Nt, L.Nx, c, R, st);
-        if (err != cudaSuccess) return err;
-        h->launches++;
-      }
-    return cudaSuccess;
-  }
-  const int kind = gs_kind_for<T>(L, R);
-  if (sweeps > 0 && kind == GS_DSMEM) {
-    const bool bsm = dsmem_blocks_in_smem<T>(L.n, L.off.K);
-    if constexpr (f64)
-      err = launch_coarse_sweeps_dsmem<double, double2>(e, r, L.Bc64, nullptr, L.Dc64, L.off, L.Nt, L.Nx, L.ncol,
-                                                        sweeps, R, bsm, st);
-    else
-      err = launch_coarse_sweeps_dsmem<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, L.ncol, sweeps,
-                                                       R, bsm, st);
-    h->launches++;
-    return err;
-  }
-  if (sweeps > 0 && kind == GS_OWNER) {
-    if constexpr (f64)
-      err = launch_coarse_sweeps_owner<double, double2>(e, r, L.Bc64, nullptr, L.Dc64, L.off, L.Nt, L.Nx, L.ncol,
-                                                       sweeps, R, h->d_owner_flags, h->d_sync, st);
-    else
-      err = launch_coarse_sweeps_owner<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, L.ncol, sweeps,
-                                                      R, h->d_owner_flags, h->d_sync, st);
-    h->launches++;
-    return err;
-  }
-  if (sweeps > 0 && kind == GS_GRID) {
-    if constexpr (f64)
-      err = launch_coarse_sweeps_grid<double, double2>(e, r, L.Bc64, nullptr, L.Dc64, L.off, L.Nt, L.Nx, L.ncol,
-                                                       sweeps, R, h->d_sync, st);
-    else
-      err = launch_coarse_sweeps_grid<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, L.ncol, sweeps,
-                                                      R, h->d_sync, st);
-    h->launches++;
-    return err;
-  }
-  if constexpr (!f64) {
-    if (sweeps > 0 && kind == GS_CLUSTER && use_cluster_sweeps<T>(L.n, L.ncol)) {
-      err = launch_coarse_sweeps_cluster<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, L.ncol, sweeps,
-                                                         R, st);
-      h->launches++;
-      return err;
-    }
-  }
-  for (int s = 0; s < sweeps; ++s)
-    for (int c = 0; c < L.ncol; ++c) {
-      if constexpr (f64)
-        err = launch_coarse_colour<double, double2>(e, r, L.Bc64, nullptr, L.Dc64, L.off, L.Nt, L.Nx, L.ncol, c, R, st);
-      else
-        err = launch_coarse_colour<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, L.ncol, c, R, st);
-      if (err != cudaSuccess) return err;
-      h->launches++;
-    }
-  return cudaSuccess;
-}
-
+// The V-cycle behind amamg_vcycle (the engine's own code path: same kernels,
+// same order, same arguments) with the coarse vectors carved out of the
+// scratch array instead of the handle's allocations.
 template <typename T>
 int vcycle_noalloc(amamg_ctx* h, const void* r, void* e, int R, cudaStream_t st) {
   const size_t cb = sizeof(typename cplx<T>::type);
@@ -183,7 +71,7 @@ int vcycle_noalloc(amamg_ctx* h, const void* r, void* e, int R, cudaStream_t st)
     h->err = std::string("amamg_vcycle_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(err);
     return AMAMG_ERR_CUDA;
   }
-  LevelVecs<T> w;
+  VcycleVecs<T> w;
   unsigned char* p = static_cast<unsigned char*>(base);
   for (size_t l = 1; l < h->lv.size(); ++l) {
     const size_t b = align256((size_t)R * 2 * h->lv[l].n * cb);
@@ -192,13 +80,8 @@ int vcycle_noalloc(amamg_ctx* h, const void* r, void* e, int R, cudaStream_t st)
     w.e[l] = reinterpret_cast<typename cplx<T>::type*>(p);
     p += b;
   }
-  err = vcycle_level<T>(h, 0, static_cast<const typename cplx<T>::type*>(r), static_cast<typename cplx<T>::type*>(e),
-                        w, R, st);
-  if (err != cudaSuccess) {
-    h->err = std::string("amamg_vcycle_noalloc: ") + cudaGetErrorString(err);
-    return AMAMG_ERR_CUDA;
-  }
-  return AMAMG_OK;
+  return engine_vcycle<T>(h, static_cast<const typename cplx<T>::type*>(r), static_cast<typename cplx<T>::type*>(e),
+                          w, R, st);
 }
 
 }  // namespace

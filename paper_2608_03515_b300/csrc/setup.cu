@@ -108,7 +108,7 @@ __device__ __forceinline__ double2 crecip(double2 a) {
 // M = [A_FF | A_FV] (NF x (NF + 8)), eliminated in place; X = A_FF^{-1} A_FV.
 template <int A, typename Op>
 __global__ void __launch_bounds__(128)
-k_local_solve(Op op, int Np, int Nq, double2* __restrict__ P, int* __restrict__ err, double rel_tol) {
+k_local_solve(Op op, int Np, int Nq, double2* __restrict__ P, int* __restrict__ err, double rel_tol, int own) {
   constexpr int NB = (A + 1) * (A + 1);
   constexpr int NFS = NB - 4;
   constexpr int NF = 2 * NFS;
@@ -208,21 +208,29 @@ k_local_solve(Op op, int Np, int Nq, double2* __restrict__ P, int* __restrict__ 
     }
     __syncthreads();
   }
-  // owned rows (i < A, j < A, not the vertex): P = -X
+  // the rows this basket owns (row_basket): F site (i, j) lies in tile
+  // (p + i / A, q + j / A) at in-tile (i mod A, j mod A) and is stored there;
+  // P = -X.  Under the tile rule these are the sites with i, j < A.
   for (int e = threadIdx.x; e < NFS * 2 * 8; e += blockDim.x) {
     const int f = e >> 4, rem = e & 15, alpha = rem >> 3, c8 = rem & 7;
     const int i = fi[f], j = fj[f];
-    if (i >= A || j >= A) continue;
-    const int l = i * A + j;
+    const int it = (i == A) ? 0 : i, jt = (j == A) ? 0 : j;
+    const int pT = (i == A) ? ((p + 1 == Np) ? 0 : p + 1) : p;
+    const int qT = (j == A) ? ((q + 1 == Nq) ? 0 : q + 1) : q;
+    int dp, dq;
+    row_basket(own, pT, qT, it, jt, dp, dq);
+    if (wrap(pT + dp, Np) != p || wrap(qT + dq, Nq) != q) continue;
+    const int l = it * A + jt;
     const int lr = 2 * (l - 1) + alpha;
-    P[((size_t)tile * 8 + c8) * NR + lr] = -M[2 * f + alpha][NF + c8];
+    P[((size_t)(pT * Nq + qT) * 8 + c8) * NR + lr] = -M[2 * f + alpha][NF + c8];
   }
 }
 
 // ------------------------------------------------------------------ Galerkin
 // Interpolation weight P[(site (t,x), spin tau), (vertex (pw,qw), spin beta)].
+// The row's stored columns are the corners of its basket (row_basket).
 __device__ __forceinline__ double2 p_weight(const double2* __restrict__ P, int t, int x, int tau, int pw, int qw,
-                                            int beta, int a, int Np, int Nq, int nrows) {
+                                            int beta, int a, int Np, int Nq, int nrows, int own) {
   const int it = t % a, ix = x % a;
   const int pt = t / a, qt = x / a;
   if (it == 0 && ix == 0) {
@@ -231,9 +239,11 @@ __device__ __forceinline__ double2 p_weight(const double2* __restrict__ P, int t
   const int l = it * a + ix;
   const int lr = 2 * (l - 1) + tau;
   const int tile = pt * Nq + qt;
+  int dp, dq;
+  row_basket(own, pt, qt, it, ix, dp, dq);
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    const int pc = wrap(pt + (c >> 1), Np), qc = wrap(qt + (c & 1), Nq);
+    const int pc = wrap(pt + dp + (c >> 1), Np), qc = wrap(qt + dq + (c & 1), Nq);
     if (pc == pw && qc == qw) return P[((size_t)tile * 8 + 2 * c + beta) * nrows + lr];
   }
   return make_double2(0.0, 0.0);
@@ -241,7 +251,7 @@ __device__ __forceinline__ double2 p_weight(const double2* __restrict__ P, int t
 
 template <typename Op>
 __device__ double2 ap_entry(const Op& op, const double2* __restrict__ P, int t, int x, int sigma, int pw, int qw,
-                            int beta, int a, int Np, int Nq, int nrows) {
+                            int beta, int a, int Np, int Nq, int nrows, int own) {
   // (A P)[(s, sigma), (w, beta)] = sum_nb sum_tau A[(s,sigma),(s',tau)] P[(s',tau),(w,beta)]
   double2 acc = make_double2(0.0, 0.0);
   const int nn = op_count(op);
@@ -251,7 +261,7 @@ __device__ double2 ap_entry(const Op& op, const double2* __restrict__ P, int t, 
     op_nb(op, t, x, k, tn, xn, blk);
 #pragma unroll
     for (int tau = 0; tau < 2; ++tau) {
-      const double2 pwv = p_weight(P, tn, xn, tau, pw, qw, beta, a, Np, Nq, nrows);
+      const double2 pwv = p_weight(P, tn, xn, tau, pw, qw, beta, a, Np, Nq, nrows, own);
       if (pwv.x != 0.0 || pwv.y != 0.0) acc += cmul(blk[2 * sigma + tau], pwv);
     }
   }
@@ -261,7 +271,8 @@ __device__ double2 ap_entry(const Op& op, const double2* __restrict__ P, int t, 
 // one CTA per coarse site v, thread = (k, alpha, beta): Bc[k][2 alpha + beta][v]
 template <typename Op>
 __global__ void __launch_bounds__(128)
-k_galerkin(Op op, const double2* __restrict__ P, int a, int Np, int Nq, Offsets offc, double2* __restrict__ Bc) {
+k_galerkin(Op op, const double2* __restrict__ P, int a, int Np, int Nq, Offsets offc, double2* __restrict__ Bc,
+           int own) {
   const int v = blockIdx.x;
   const int th = threadIdx.x;
   if (th >= offc.K * 4) return;
@@ -272,19 +283,68 @@ k_galerkin(Op op, const double2* __restrict__ P, int a, int Np, int Nq, Offsets 
   const int nrows = 2 * (a * a - 1);
   double2 acc = make_double2(0.0, 0.0);
   // v's own fine site: P row is the identity on spin alpha
-  acc += ap_entry(op, P, p * a, q * a, alpha, pw, qw, beta, a, Np, Nq, nrows);
-  // the four tiles that have v as corner c
+  acc += ap_entry(op, P, p * a, q * a, alpha, pw, qw, beta, a, Np, Nq, nrows, own);
+  // the rows whose basket has v as corner c: the F sites that basket
+  // W(p - di, q - dj) owns (under the tile rule: every row of tile (p-di, q-dj))
   for (int c = 0; c < 4; ++c) {
-    const int pT = wrap(p - (c >> 1), Np), qT = wrap(q - (c & 1), Nq);
-    const int tile = pT * Nq + qT;
-    for (int lr = 0; lr < nrows; ++lr) {
-      const double2 pv = P[((size_t)tile * 8 + 2 * c + alpha) * nrows + lr];
-      const int l = (lr >> 1) + 1, sigma = lr & 1;
-      const int t = pT * a + l / a, x = qT * a + l % a;
-      acc += cmulc(pv, ap_entry(op, P, t, x, sigma, pw, qw, beta, a, Np, Nq, nrows));
-    }
+    const int pB = wrap(p - (c >> 1), Np), qB = wrap(q - (c & 1), Nq);
+    for (int i = 0; i <= a; ++i)
+      for (int j = 0; j <= a; ++j) {
+        if ((i == 0 || i == a) && (j == 0 || j == a)) continue;      // corners
+        const int it = (i == a) ? 0 : i, jt = (j == a) ? 0 : j;
+        const int pT = (i == a) ? wrap(pB + 1, Np) : pB, qT = (j == a) ? wrap(qB + 1, Nq) : qB;
+        int dp, dq;
+        row_basket(own, pT, qT, it, jt, dp, dq);
+        if (wrap(pT + dp, Np) != pB || wrap(qT + dq, Nq) != qB) continue;
+        const int l = it * a + jt;
+        const int tile = pT * Nq + qT;
+        for (int sigma = 0; sigma < 2; ++sigma) {
+          const double2 pv = P[((size_t)tile * 8 + 2 * c + alpha) * nrows + 2 * (l - 1) + sigma];
+          acc += cmulc(pv, ap_entry(op, P, pT * a + it, qT * a + jt, sigma, pw, qw, beta, a, Np, Nq, nrows, own));
+        }
+      }
   }
   Bc[((size_t)k * 4 + 2 * alpha + beta) * nc + v] = acc;
+}
+
+// Row-sum normalisation of Eq. (16) (N = diag(1 / row sum)): the complex sum
+// s of every stored row's 8 weights; the largest |s| of the level goes to
+// *smax as the bits of a non-negative double (ordered like unsigned integers).
+__global__ void k_rowsum_max(const double2* __restrict__ P, int nrows, int ntiles,
+                             unsigned long long* __restrict__ smax) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  double m = 0.0;
+  if (g < ntiles * nrows) {
+    const int tile = g / nrows, lr = g - (g / nrows) * nrows;
+    double2 s = make_double2(0.0, 0.0);
+    for (int c8 = 0; c8 < 8; ++c8) s += P[((size_t)tile * 8 + c8) * nrows + lr];
+    m = sqrt(cabs2(s));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(smax, (unsigned long long)__double_as_longlong(m));
+}
+
+// rows with |s| >= rel_floor * max |s| are divided by s; the others stay and
+// are counted
+__global__ void k_rowsum_scale(double2* __restrict__ P, int nrows, int ntiles,
+                               const unsigned long long* __restrict__ smax, double rel_floor,
+                               unsigned* __restrict__ skipped) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ntiles * nrows) return;
+  const int tile = g / nrows, lr = g - (g / nrows) * nrows;
+  double2 s = make_double2(0.0, 0.0);
+  for (int c8 = 0; c8 < 8; ++c8) s += P[((size_t)tile * 8 + c8) * nrows + lr];
+  const double floor_ = rel_floor * __longlong_as_double((long long)*smax);
+  if (!(sqrt(cabs2(s)) >= floor_)) {
+    atomicAdd(skipped, 1u);
+    return;
+  }
+  const double2 inv = crecip(s);
+  for (int c8 = 0; c8 < 8; ++c8) {
+    double2& w = P[((size_t)tile * 8 + c8) * nrows + lr];
+    w = cmul(w, inv);
+  }
 }
 
 // ------------------------------------------------------------------ small kernels
@@ -487,18 +547,30 @@ cudaError_t launch_pack_colour_major(const double2* B64, const __half2* B16, con
 }
 
 template <typename Op>
-cudaError_t launch_local_solve(const Op& op, int a, int Np, int Nq, double2* P, int* err, cudaStream_t st) {
+cudaError_t launch_local_solve(const Op& op, int a, int Np, int Nq, double2* P, int* err, int own, cudaStream_t st) {
   const double rel_tol = 1e-13;
-  if (a == 4) k_local_solve<4, Op><<<Np * Nq, 128, 0, st>>>(op, Np, Nq, P, err, rel_tol);
-  else if (a == 2) k_local_solve<2, Op><<<Np * Nq, 128, 0, st>>>(op, Np, Nq, P, err, rel_tol);
+  if (a == 4) k_local_solve<4, Op><<<Np * Nq, 128, 0, st>>>(op, Np, Nq, P, err, rel_tol, own);
+  else if (a == 2) k_local_solve<2, Op><<<Np * Nq, 128, 0, st>>>(op, Np, Nq, P, err, rel_tol, own);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
 template <typename Op>
 cudaError_t launch_galerkin(const Op& op, const double2* P, int a, int Np, int Nq, const Offsets& offc, double2* Bc,
-                            cudaStream_t st) {
-  k_galerkin<Op><<<Np * Nq, 128, 0, st>>>(op, P, a, Np, Nq, offc, Bc);
+                            int own, cudaStream_t st) {
+  k_galerkin<Op><<<Np * Nq, 128, 0, st>>>(op, P, a, Np, Nq, offc, Bc, own);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rowsum_normalize(double2* P, int nrows, int ntiles, unsigned long long* smax, unsigned* skipped,
+                                    cudaStream_t st) {
+  const int total = ntiles * nrows;
+  cudaError_t e = cudaMemsetAsync(smax, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  k_rowsum_max<<<(total + 255) / 256, 256, 0, st>>>(P, nrows, ntiles, smax);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_rowsum_scale<<<(total + 255) / 256, 256, 0, st>>>(P, nrows, ntiles, smax, 1e-12, skipped);
   return cudaGetLastError();
 }
 
@@ -561,9 +633,11 @@ cudaError_t launch_pack_B16(const double2* B, int K, int n, __half2* B16, float*
   return cudaGetLastError();
 }
 
-template cudaError_t launch_local_solve<WilsonOp>(const WilsonOp&, int, int, int, double2*, int*, cudaStream_t);
-template cudaError_t launch_local_solve<StencilOp>(const StencilOp&, int, int, int, double2*, int*, cudaStream_t);
+template cudaError_t launch_local_solve<WilsonOp>(const WilsonOp&, int, int, int, double2*, int*, int,
+                                                  cudaStream_t);
+template cudaError_t launch_local_solve<StencilOp>(const StencilOp&, int, int, int, double2*, int*, int,
+                                                   cudaStream_t);
 template cudaError_t launch_galerkin<WilsonOp>(const WilsonOp&, const double2*, int, int, int, const Offsets&,
-                                               double2*, cudaStream_t);
+                                               double2*, int, cudaStream_t);
 template cudaError_t launch_galerkin<StencilOp>(const StencilOp&, const double2*, int, int, int, const Offsets&,
-                                                double2*, cudaStream_t);
+                                                double2*, int, cudaStream_t);

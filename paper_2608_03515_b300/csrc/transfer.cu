@@ -26,12 +26,13 @@ __device__ __forceinline__ float2 p_load<float, __half2>(const __half2* P, const
 }
 
 // e_fine = P e_coarse.  One thread per (tile, row); rows nrows, nrows+1 are the
-// vertex's two spins (identity).
+// vertex's two spins (identity).  A row's columns are the corners of its
+// basket (row_basket: the tile's own under the tile rule).
 template <typename T, typename PT>
 __global__ void __launch_bounds__(256)
 k_prolong(const typename cplx<T>::type* __restrict__ ec, typename cplx<T>::type* __restrict__ ef,
           const PT* __restrict__ P, const float* __restrict__ Pscale,
-          int Nxf, int a, int nrows, int Np, int Nq) {
+          int Nxf, int a, int nrows, int Np, int Nq, int own) {
   using C = typename cplx<T>::type;
   const int rows_tot = nrows + 2;
   const int nc = Np * Nq;
@@ -50,8 +51,11 @@ k_prolong(const typename cplx<T>::type* __restrict__ ec, typename cplx<T>::type*
   }
   const int l = (lr >> 1) + 1, alpha = lr & 1;
   const int i = l / a, j = l - (l / a) * a;
-  const int p1 = (p + 1 == Np) ? 0 : p + 1, q1 = (q + 1 == Nq) ? 0 : q + 1;
-  const int vtx[4] = {p * Nq + q, p * Nq + q1, p1 * Nq + q, p1 * Nq + q1};
+  int dp, dq;
+  row_basket(own, p, q, i, j, dp, dq);
+  const int pb = (p + dp < 0) ? Np - 1 : p + dp, qb = (q + dq < 0) ? Nq - 1 : q + dq;
+  const int p1 = (pb + 1 == Np) ? 0 : pb + 1, q1 = (qb + 1 == Nq) ? 0 : qb + 1;
+  const int vtx[4] = {pb * Nq + qb, pb * Nq + q1, p1 * Nq + qb, p1 * Nq + q1};
   C acc = czero<C>();
   const size_t base = (size_t)tile * 8 * nrows + lr;
 #pragma unroll
@@ -140,33 +144,114 @@ k_restrict(const typename cplx<T>::type* __restrict__ ef, typename cplx<T>::type
   }
 }
 
+// e_coarse = P^H e_fine for any ownership rule: one warp per coarse vertex
+// v = (p, q) walks the F sites of the four baskets that have v as a corner c
+// (W(p - di, q - dj)) and takes the rows each basket owns (row_basket), plus
+// v's own fine site (identity row).  Used for the first-lex rule, whose rows of
+// a tile come from up to three baskets (k_restrict covers the tile rule).
+template <typename T, typename PT>
+__global__ void __launch_bounds__(256)
+k_restrict_owned(const typename cplx<T>::type* __restrict__ ef, typename cplx<T>::type* __restrict__ ec,
+                 const PT* __restrict__ P, const float* __restrict__ Pscale,
+                 int Nxf, int a, int nrows, int Np, int Nq, int own) {
+  using C = typename cplx<T>::type;
+  const int nc = Np * Nq;
+  const int nf = nc * a * a;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= nc) return;                      // whole warps leave together
+  const int p = warp / Nq, q = warp - (warp / Nq) * Nq;
+  const C* f0 = ef + (size_t)blockIdx.y * 2 * nf;
+  const int nb = (a + 1) * (a + 1);
+  C acc0 = czero<C>(), acc1 = czero<C>();
+  for (int idx = lane; idx < 4 * nb; idx += 32) {
+    const int c = idx / nb, s = idx - c * nb;
+    const int i = s / (a + 1), j = s - (s / (a + 1)) * (a + 1);
+    if ((i == 0 || i == a) && (j == 0 || j == a)) continue;          // corners
+    const int pB = (p - (c >> 1) < 0) ? Np - 1 : p - (c >> 1);
+    const int qB = (q - (c & 1) < 0) ? Nq - 1 : q - (c & 1);
+    const int it = (i == a) ? 0 : i, jt = (j == a) ? 0 : j;
+    const int pT = (i == a) ? ((pB + 1 == Np) ? 0 : pB + 1) : pB;
+    const int qT = (j == a) ? ((qB + 1 == Nq) ? 0 : qB + 1) : qB;
+    int dp, dq;
+    row_basket(own, pT, qT, it, jt, dp, dq);
+    const int po = (pT + dp < 0) ? Np - 1 : pT + dp, qo = (qT + dq < 0) ? Nq - 1 : qT + dq;
+    if (po != pB || qo != qB) continue;                              // another basket's row
+    const int tile = pT * Nq + qT, l = it * a + jt;
+    const size_t base = (size_t)tile * 8 * nrows + (size_t)(2 * c) * nrows + 2 * (l - 1);
+    const int site = (pT * a + it) * Nxf + qT * a + jt;
+#pragma unroll
+    for (int sigma = 0; sigma < 2; ++sigma) {
+      const C f = f0[(size_t)sigma * nf + site];
+      cmacc(acc0, p_load<T, PT>(P, Pscale, base + sigma, tile), f);
+      cmacc(acc1, p_load<T, PT>(P, Pscale, base + nrows + sigma, tile), f);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    acc0.x += __shfl_xor_sync(0xffffffffu, acc0.x, o);
+    acc0.y += __shfl_xor_sync(0xffffffffu, acc0.y, o);
+    acc1.x += __shfl_xor_sync(0xffffffffu, acc1.x, o);
+    acc1.y += __shfl_xor_sync(0xffffffffu, acc1.y, o);
+  }
+  if (lane == 0) {
+    const int sv = (p * a) * Nxf + q * a;
+    C* e0 = ec + (size_t)blockIdx.y * 2 * nc;
+    e0[warp] = acc0 + f0[sv];
+    e0[nc + warp] = acc1 + f0[nf + sv];
+  }
+}
+
+// Level structure as the transfer kernels index it: role of every site (0
+// vertex, 1 edge, 2 interior) and the basket p Nq + q whose formula its row
+// takes (row_basket; a vertex: its own tile's basket).
+__global__ void k_structure(int Nt, int Nx, int a, int own, int* __restrict__ role, int* __restrict__ owner) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= Nt * Nx) return;
+  const int t = s / Nx, x = s - (s / Nx) * Nx;
+  const int Np = Nt / a, Nq = Nx / a;
+  const int p = t / a, q = x / a, i = t - p * a, j = x - q * a;
+  const bool ti = i == 0, xj = j == 0;
+  role[s] = (ti && xj) ? 0 : (ti != xj ? 1 : 2);
+  int dp = 0, dq = 0;
+  if (!(ti && xj)) row_basket(own, p, q, i, j, dp, dq);
+  const int pb = (p + dp < 0) ? Np - 1 : p + dp, qb = (q + dq < 0) ? Nq - 1 : q + dq;
+  owner[s] = pb * Nq + qb;
+}
+
 }  // namespace
+
+cudaError_t launch_structure(int Nt, int Nx, int a, int own, int* role, int* owner, cudaStream_t st) {
+  k_structure<<<(Nt * Nx + 255) / 256, 256, 0, st>>>(Nt, Nx, a, own, role, owner);
+  return cudaGetLastError();
+}
 
 template <typename T, typename PT>
 cudaError_t launch_prolong(const typename cplx<T>::type* ec, typename cplx<T>::type* ef, const PT* P,
-                           const float* Pscale, int Nxf, int a, int Np, int Nq, int R, cudaStream_t st) {
+                           const float* Pscale, int Nxf, int a, int Np, int Nq, int R, cudaStream_t st, int own) {
   const int nrows = 2 * (a * a - 1);
   const int total = Np * Nq * (nrows + 2);
   dim3 grid((total + 255) / 256, R);
-  k_prolong<T, PT><<<grid, 256, 0, st>>>(ec, ef, P, Pscale, Nxf, a, nrows, Np, Nq);
+  k_prolong<T, PT><<<grid, 256, 0, st>>>(ec, ef, P, Pscale, Nxf, a, nrows, Np, Nq, own);
   return cudaGetLastError();
 }
 
 template <typename T, typename PT>
 cudaError_t launch_restrict(const typename cplx<T>::type* ef, typename cplx<T>::type* ec, const PT* P,
-                            const float* Pscale, int Nxf, int a, int Np, int Nq, int R, cudaStream_t st) {
+                            const float* Pscale, int Nxf, int a, int Np, int Nq, int R, cudaStream_t st, int own) {
   const int nrows = 2 * (a * a - 1);
   const int nc = Np * Nq;
   dim3 grid((nc * 32 + 255) / 256, R);
-  k_restrict<T, PT><<<grid, 256, 0, st>>>(ef, ec, P, Pscale, Nxf, a, nrows, Np, Nq);
+  if (own == OWN_TILE) k_restrict<T, PT><<<grid, 256, 0, st>>>(ef, ec, P, Pscale, Nxf, a, nrows, Np, Nq);
+  else k_restrict_owned<T, PT><<<grid, 256, 0, st>>>(ef, ec, P, Pscale, Nxf, a, nrows, Np, Nq, own);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_prolong<double, double2>(const double2*, double2*, const double2*, const float*, int,
-                                                     int, int, int, int, cudaStream_t);
+                                                     int, int, int, int, cudaStream_t, int);
 template cudaError_t launch_prolong<float, __half2>(const float2*, float2*, const __half2*, const float*, int, int,
-                                                    int, int, int, cudaStream_t);
+                                                    int, int, int, cudaStream_t, int);
 template cudaError_t launch_restrict<double, double2>(const double2*, double2*, const double2*, const float*, int,
-                                                      int, int, int, int, cudaStream_t);
+                                                      int, int, int, int, cudaStream_t, int);
 template cudaError_t launch_restrict<float, __half2>(const float2*, float2*, const __half2*, const float*, int,
-                                                     int, int, int, int, cudaStream_t);
+                                                     int, int, int, int, cudaStream_t, int);

@@ -337,8 +337,10 @@ def test_owner_sweep_wait_time_out_is_reported_and_handle_recovers():
     rng = np.random.Generator(np.random.PCG64(34))
     for prec in (A.F64, A.F32):
         t0 = time.time()
-        assert A.selftest_sync_timeout(hier, 1, prec) == A.ERR_TIMEOUT
+        assert A.selftest_sync_timeout(hier, 1, prec) == A.OK      # enqueued; not reported by itself
+        assert A.sync_status(hier) == A.ERR_TIMEOUT
         assert time.time() - t0 < 60.0
+        assert A.sync_status(hier) == A.OK                          # re-armed
         r = rng.standard_normal((1, 2, L.Nt, L.Nx)) + 1j * rng.standard_normal((1, 2, L.Nt, L.Nx))
         e0 = rng.standard_normal((1, 2, L.Nt, L.Nx)) + 1j * rng.standard_normal((1, 2, L.Nt, L.Nx))
         e = dev(e0)
