@@ -166,6 +166,24 @@ int amamg_batch_destroy(amamg_batch_handle b);
 /* out = D in on the fine lattice, Eq. (3).  precision AMAMG_F64 or AMAMG_F32. */
 int amamg_apply_D(amamg_handle h, const void* in, void* out, int R, int precision, void* stream);
 
+/* out = D^H in = sigma_3 D sigma_3 in (sigma_3-hermiticity, Eq. (6)) on the
+ * fine lattice at the setup mass; in, out: device complex128 [R][2][Nt][Nx]. */
+int amamg_apply_Ddag(amamg_handle h, const void* in, void* out, int R, void* stream);
+
+/* The paper's unpreconditioned comparison solver (Sec. 5): conjugate
+ * gradients on the normal equations D^H D x = D^H psi (CGNR, x0 = 0) with
+ * D^H = sigma_3 D sigma_3 (Eq. (6)), in FP64 on the device, at the setup mass.
+ * psi, x: device complex128 [R][2][Nt][Nx] (x overwritten).  One iteration
+ * applies D and D^H once; iterations stop for a right-hand side when the
+ * recursive ||psi - D x|| / ||psi|| reaches tol, and the solve ends when the
+ * true residual is below tol for every right-hand side (the recurrence restarts
+ * from the true residual where it is not) or max_iter iterations are spent.
+ * info: host array of R records (iterations, status, true relative residual).
+ * Returns AMAMG_OK, AMAMG_NOT_CONVERGED (x holds the last iterate),
+ * AMAMG_ERR_NONFINITE or an error; allocates its work vectors (4 R vectors). */
+int amamg_cgnr(amamg_handle h, const void* psi, void* x, int R, int max_iter, double tol, void* stream,
+               amamg_solve_info* info);
+
 /* fine_out = P_l coarse_in: interpolation from level l+1 to level l
  * (Eq. (16) rows for owned edge/interior sites, identity on vertices). */
 int amamg_apply_P(amamg_handle h, int level, const void* coarse_in, void* fine_out,
@@ -255,7 +273,7 @@ int amamg_selftest_sync_timeout(amamg_handle h, int level, int precision, void* 
  * transfer kernels index with),
  * nbr_offsets[2*K] canonical (dt mod Nt_{l+1}, dx mod Nx_{l+1}) block offsets of
  * the level-(l+1) operator, lexicographically sorted, *nbr_count = K.
- * Arrays may be NULL to skip them; nbr_offsets must hold 2*32 ints. */
+ * Arrays may be NULL to skip them; nbr_offsets must hold 2*48 ints. */
 int amamg_export_structure(amamg_handle h, int level, int32_t* role, int32_t* owner_tile,
                            int32_t* nbr_offsets, int32_t* nbr_count);
 

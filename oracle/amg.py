@@ -263,25 +263,32 @@ def site_pattern(pattern_dof: sp.spmatrix) -> sp.csr_matrix:
     return sp.csr_matrix((np.ones_like(P.row), (P.row // 2, P.col // 2)), shape=(n_r, n_c))
 
 
-def coarse_offsets(P_pattern: sp.spmatrix, A_pattern: sp.spmatrix, Nt: int, Nx: int, a: int):
+def coarse_offsets(P_pattern: sp.spmatrix, A_pattern: sp.spmatrix, Nt: int, Nx: int, a: int,
+                   union: bool = False):
     """Block-neighbour offsets of P^H A P from the boolean product of structural patterns.
 
     Returns the canonical offset list shared by every coarse site, after checking
-    that the pattern is the same for all sites (translation invariance)."""
+    that the pattern is the same for all sites (translation invariance).  The
+    first-lex ownership reading of Sec. 4.1 gives the first tile row and column
+    other baskets than the rest, so its pattern can differ between coarse sites:
+    with union=True the list is the union over all sites (a site's blocks at
+    offsets it does not couple through are zero)."""
     Ps = site_pattern(P_pattern)
     As = site_pattern(A_pattern)
     C = (Ps.T @ As @ Ps).tocsr()
     Np, Nq = Nt // a, Nx // a
     ref = None
+    seen = set()
     for v in range(Np * Nq):
         pv, qv = divmod(v, Nq)
         nbrs = C.indices[C.indptr[v]:C.indptr[v + 1]]
         offs = canonical_offsets([((w // Nq) - pv, (w % Nq) - qv) for w in nbrs], Np, Nq)
+        seen.update(offs)
         if ref is None:
             ref = offs
-        elif offs != ref:
+        elif offs != ref and not union:
             raise AssertionError("coarse sparsity is not translation invariant")
-    return ref
+    return sorted(seen) if union else ref
 
 
 def galerkin(P: sp.csr_matrix, A: sp.csr_matrix) -> sp.csr_matrix:
@@ -414,7 +421,7 @@ def build_hierarchy(D: sp.csr_matrix, Nt: int, Nx: int, aggs: List[int], route: 
         L.a = a
         L.P, L.P_pattern = build_interpolator(L.A, L.Nt, L.Nx, a, route, ownership, normalization,
                                               spin_split=spin_split)
-        offs = coarse_offsets(L.P_pattern, A_pat, L.Nt, L.Nx, a)
+        offs = coarse_offsets(L.P_pattern, A_pat, L.Nt, L.Nx, a, union=(ownership != "tile"))
         Ac = galerkin(L.P, L.A)
         nxt = Level(L.Nt // a, L.Nx // a, Ac, offs)
         A_pat = pattern_from_offsets(offs, nxt.Nt, nxt.Nx)

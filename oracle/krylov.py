@@ -102,3 +102,60 @@ def fgmres(apply_A: Callable[[np.ndarray], np.ndarray],
             y[i] = (g[i] - H[i, i + 1:k] @ y[i + 1:k]) / H[i, i]
         x = x + Z[:k].T @ y
         restarts += 1
+
+
+@dataclass
+class CgnrResult:
+    x: np.ndarray
+    iterations: int
+    true_relres: float
+    converged: bool
+
+
+def cgnr(apply_A: Callable[[np.ndarray], np.ndarray],
+         apply_AH: Callable[[np.ndarray], np.ndarray],
+         b: np.ndarray, tol: float, max_iter: int) -> CgnrResult:
+    """Conjugate gradients on the normal equations A^H A x = A^H b (CGNR, Saad's
+    "Iterative Methods for Sparse Linear Systems", Sec. 8.3), the paper's
+    unpreconditioned comparison solver (Sec. 5), with A^H = sigma_3 A sigma_3 for
+    the Wilson operator (Eq. (6)).
+
+    x0 = 0; r = b - A x is the residual of the original system, carried by the
+    recurrence; z = A^H r is the normal-equation residual.  One iteration:
+        w = A p,  alpha = ||z||^2 / ||w||^2,  x += alpha p,  r -= alpha w,
+        z' = A^H r,  beta = ||z'||^2 / ||z||^2,  p = z' + beta p.
+    The iteration count is the number of such steps; a step whose recursive
+    ||r|| / ||b|| reaches tol ends the loop, and the solve stops only when the
+    true residual ||b - A x|| / ||b|| is below tol (else it restarts the
+    recurrence from the true residual)."""
+    n = b.shape[0]
+    x = np.zeros(n, dtype=np.complex128)
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0:
+        return CgnrResult(x, 0, 0.0, True)
+    iters = 0
+    while True:
+        r = b - apply_A(x)
+        rel = np.linalg.norm(r) / bnorm
+        if rel <= tol:
+            return CgnrResult(x, iters, rel, True)
+        if iters >= max_iter:
+            return CgnrResult(x, iters, rel, False)
+        z = apply_AH(r)
+        p = z.copy()
+        zz = np.vdot(z, z).real
+        while iters < max_iter:
+            w = apply_A(p)
+            ww = np.vdot(w, w).real
+            if ww == 0.0:
+                break
+            alpha = zz / ww
+            x = x + alpha * p
+            r = r - alpha * w
+            iters += 1
+            if np.linalg.norm(r) <= tol * bnorm:
+                break
+            z = apply_AH(r)
+            zz_new = np.vdot(z, z).real
+            p = z + (zz_new / zz) * p
+            zz = zz_new

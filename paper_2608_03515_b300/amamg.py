@@ -35,6 +35,7 @@ OWNER_FIRST_LEX = 1
 
 EXPORTED = [
     "amamg_default_params", "amamg_query_bytes", "amamg_setup", "amamg_solve", "amamg_apply_D",
+    "amamg_apply_Ddag", "amamg_cgnr",
     "amamg_apply_P", "amamg_apply_PH", "amamg_apply_coarse", "amamg_smooth", "amamg_coarsest_solve",
     "amamg_vcycle", "amamg_vcycle_noalloc", "amamg_selftest_sync_timeout", "amamg_sync_status", "amamg_export_structure", "amamg_level_info", "amamg_export_P", "amamg_export_coarse",
     "amamg_profile_enable", "amamg_profile_reset", "amamg_profile_get", "amamg_launch_count",
@@ -79,6 +80,8 @@ def _load() -> ctypes.CDLL:
         "amamg_setup": ([ctypes.POINTER(Params), vp, ci, ci, cd, vp, ctypes.POINTER(vp)], ci),
         "amamg_solve": ([vp, vp, vp, ci, vp, ctypes.POINTER(SolveInfo)], ci),
         "amamg_apply_D": ([vp, vp, vp, ci, ci, vp], ci),
+        "amamg_apply_Ddag": ([vp, vp, vp, ci, vp], ci),
+        "amamg_cgnr": ([vp, vp, vp, ci, ci, cd, vp, ctypes.POINTER(SolveInfo)], ci),
         "amamg_apply_P": ([vp, ci, vp, vp, ci, ci, vp], ci),
         "amamg_apply_PH": ([vp, ci, vp, vp, ci, ci, vp], ci),
         "amamg_apply_coarse": ([vp, ci, vp, vp, ci, ci, vp], ci),
@@ -245,6 +248,21 @@ def setup(U, m0: float, params: Params, stream=None) -> Hierarchy:
     return Hierarchy(h, params, Nt, Nx, float(m0))
 
 
+def apply_Ddag(hier: Hierarchy, inp, out, stream=None):
+    """amamg_apply_Ddag: out = sigma_3 D sigma_3 in (complex128)."""
+    hier._check(_lib.amamg_apply_Ddag(hier.h, _ptr(inp), _ptr(out), int(inp.shape[0]), _stream(stream)),
+                "amamg_apply_Ddag")
+
+
+def cgnr(hier: Hierarchy, psi, x, max_iter: int = 100000, tol: float = 1e-10, stream=None) -> List["Info"]:
+    """amamg_cgnr: CG on the normal equations; psi, x complex128 [R, 2, Nt, Nx]."""
+    R = int(psi.shape[0])
+    info = (SolveInfo * R)()
+    st = _lib.amamg_cgnr(hier.h, _ptr(psi), _ptr(x), R, int(max_iter), float(tol), _stream(stream), info)
+    hier._check(st, "amamg_cgnr")
+    return [Info(i.iterations, i.status, i.true_relres) for i in info]
+
+
 def solve(hier: Hierarchy, psi, x, stream=None) -> List[Info]:
     """amamg_solve: psi, x complex128 [R, 2, Nt, Nx]; returns per-RHS info."""
     R = int(psi.shape[0])
@@ -319,7 +337,7 @@ def export_structure(hier: Hierarchy, level: int):
     nt, nx, _ = hier.level_info(level)
     role = np.zeros(nt * nx, dtype=np.int32)
     owner = np.zeros(nt * nx, dtype=np.int32)
-    offs = np.zeros(64, dtype=np.int32)
+    offs = np.zeros(96, dtype=np.int32)
     cnt = ctypes.c_int32()
     P = ctypes.POINTER(ctypes.c_int32)
     hier._check(_lib.amamg_export_structure(hier.h, level, role.ctypes.data_as(P), owner.ctypes.data_as(P),

@@ -90,6 +90,14 @@ template <typename P>
 int dalloc(amamg_ctx* h, P** p, size_t count) {
   *p = nullptr;
   if (count == 0) return AMAMG_OK;
+  // failure injection on the host (AMAMG_FAIL_ALLOC_AFTER=n, read by
+  // amamg_setup): the handle's allocation number n + 1 and later report
+  // out-of-memory without calling cudaMalloc, so the error paths can be tested
+  // without exhausting the device
+  if (h->fail_alloc_after >= 0 && h->allocs++ >= h->fail_alloc_after) {
+    h->err = "cudaMalloc: out of memory (injected by AMAMG_FAIL_ALLOC_AFTER)";
+    return AMAMG_ERR_OOM;
+  }
   cudaError_t e = cudaMalloc((void**)p, count * sizeof(P));
   if (e != cudaSuccess) {
     h->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
@@ -995,9 +1003,12 @@ int do_setup(amamg_ctx* h, const void* Uin, cudaStream_t st) {
     CKS(dalloc(h, &F.P16, (size_t)F.nT * 8 * F.nrows));
     CKS(dalloc(h, &F.Ps, (size_t)F.nT));
     const Offsets& fo = (l == 0) ? fine_off : F.off;
-    if (coarse_offsets(fo, F.Nt, F.Nx, F.a, h->prm.edge_owner, &C.off) != AMAMG_OK ||
-        C.off.K - 1 > GS_MAX_OFFDIAG) {
-      h->err = "coarse operator has more block offsets than the smoother supports (25)";
+    if (coarse_offsets(fo, F.Nt, F.Nx, F.a, h->prm.edge_owner, &C.off) != AMAMG_OK) {
+      h->err = "coarse operator has more block offsets than the library stores (48)";
+      return AMAMG_ERR_INVALID_ARG;
+    }
+    if (l + 2 < L && C.off.K - 1 > GS_MAX_OFFDIAG) {   // a smoothed coarse level
+      h->err = "smoothed coarse level has more block offsets than the Gauss-Seidel kernels support (25)";
       return AMAMG_ERR_INVALID_ARG;
     }
     CKS(dalloc(h, &C.B64, (size_t)C.off.K * 4 * C.n));
@@ -1167,6 +1178,7 @@ int amamg_setup(const amamg_params* p, const void* U, int Nt, int Nx, double m0,
   // one cooperative launch (same arithmetic; measured no faster than the
   // separate launches on the 256^2 workload, so off by default)
   if (const char* g = std::getenv("AMAMG_FINE_FUSED")) h->fine_fused = std::atoi(g) != 0;
+  if (const char* g = std::getenv("AMAMG_FAIL_ALLOC_AFTER")) h->fail_alloc_after = std::atoi(g);
   h->Nt = Nt; h->Nx = Nx; h->m0 = m0;
   cudaStream_t st = S(stream);
   cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -73,7 +73,7 @@ __device__ __forceinline__ typename cplx<T>::type h2c(__half2 h, float s) {
 }
 
 // canonical (mod N) block offsets of a level operator, passed by value to kernels
-#define AMAMG_MAX_OFFSETS 32
+#define AMAMG_MAX_OFFSETS 48
 // off-diagonal block offsets a smoothed coarse level may have (K - 1); setup
 // rejects hierarchies beyond it
 #define GS_MAX_OFFDIAG 24

@@ -173,6 +173,8 @@ struct amamg_ctx {
 
   std::string err;
   long long launches = 0;
+  int fail_alloc_after = -1;   // allocation-failure injection (AMAMG_FAIL_ALLOC_AFTER); -1: off
+  int allocs = 0;              // device allocations made through dalloc
   bool prof = false;
   std::vector<ProfCat> cats;
   std::vector<ProfRec> recs;

@@ -30,7 +30,9 @@ __device__ __forceinline__ Cin hop_ld(const Cin* p) {
   else return *p;
 }
 
-template <typename T, typename Cin, bool CG = false>
+// NEG1: the lower spin component is read negated, i.e. the hops act on
+// sigma_3 psi (the conjugated operator sigma_3 D sigma_3 of Eq. (6))
+template <typename T, typename Cin, bool CG = false, bool NEG1 = false>
 __device__ __forceinline__ void hop_sum(const Cin* __restrict__ p0, const Cin* __restrict__ p1,
                                         const typename cplx<T>::type* __restrict__ U,
                                         int t, int x, int Nt, int Nx, int n,
@@ -44,22 +46,23 @@ __device__ __forceinline__ void hop_sum(const Cin* __restrict__ p0, const Cin* _
   const int s_tf = tf * Nx + x, s_tb = tb * Nx + x, s_xf = t * Nx + xf, s_xb = t * Nx + xb;
 
   // t forward: (1 - sigma_0) psi = (g, -g), g = psi_0 - psi_1
-  C g = to_c(hop_ld<CG>(p0 + s_tf), T()) - to_c(hop_ld<CG>(p1 + s_tf), T());
+  const T s1 = NEG1 ? T(-1) : T(1);
+  C g = to_c(hop_ld<CG>(p0 + s_tf), T()) - s1 * to_c(hop_ld<CG>(p1 + s_tf), T());
   g = cmul(U[s], g);
   h0 = g;
   h1 = -g;
   // t backward: (1 + sigma_0) psi = (g, g), g = psi_0 + psi_1, link U_0(n - t)^*
-  g = to_c(hop_ld<CG>(p0 + s_tb), T()) + to_c(hop_ld<CG>(p1 + s_tb), T());
+  g = to_c(hop_ld<CG>(p0 + s_tb), T()) + s1 * to_c(hop_ld<CG>(p1 + s_tb), T());
   g = cmulc(U[s_tb], g);
   h0 += g;
   h1 += g;
   // x forward: (1 - sigma_1) psi = (g, -i g), g = psi_0 + i psi_1
-  g = to_c(hop_ld<CG>(p0 + s_xf), T()) + ci(to_c(hop_ld<CG>(p1 + s_xf), T()));
+  g = to_c(hop_ld<CG>(p0 + s_xf), T()) + s1 * ci(to_c(hop_ld<CG>(p1 + s_xf), T()));
   g = cmul(U[n + s], g);
   h0 += g;
   h1 -= ci(g);
   // x backward: (1 + sigma_1) psi = (g, i g), g = psi_0 - i psi_1, link U_1(n - x)^*
-  g = to_c(hop_ld<CG>(p0 + s_xb), T()) - ci(to_c(hop_ld<CG>(p1 + s_xb), T()));
+  g = to_c(hop_ld<CG>(p0 + s_xb), T()) - s1 * ci(to_c(hop_ld<CG>(p1 + s_xb), T()));
   g = cmulc(U[n + s_xb], g);
   h0 += g;
   h1 += ci(g);
@@ -91,6 +94,25 @@ k_dslash(const Cin* __restrict__ in, Cout* __restrict__ out, const Cout* __restr
   }
   o[s] = to_c(y0, typename real_of<Cout>::type());
   o[s + n] = to_c(y1, typename real_of<Cout>::type());
+}
+
+// out = sigma_3 D sigma_3 in = D^H in (Eq. (6): sigma_3-hermiticity), FP64:
+// with phi = sigma_3 in = (in_0, -in_1), (D phi)_0 = diag in_0 - h_0(phi) / 2
+// and -(D phi)_1 = diag in_1 + h_1(phi) / 2.
+__global__ void __launch_bounds__(256)
+k_dslash_dag(const double2* __restrict__ in, double2* __restrict__ out, const double2* __restrict__ U, double diag,
+             int Nt, int Nx) {
+  const int n = Nt * Nx;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const size_t roff = (size_t)blockIdx.y * 2 * n;
+  const double2* p0 = in + roff;
+  const double2* p1 = p0 + n;
+  const int t = s / Nx, x = s - (s / Nx) * Nx;
+  double2 h0, h1;
+  hop_sum<double, double2, false, true>(p0, p1, U, t, x, Nt, Nx, n, h0, h1);
+  out[roff + s] = diag * p0[s] - 0.5 * h0;
+  out[roff + n + s] = diag * p1[s] + 0.5 * h1;
 }
 
 // Red-black half sweep of colour c on D e = r: for every site n with
@@ -249,6 +271,14 @@ __global__ void k_fold_boundary_sign(double2* __restrict__ U, int Nt, int Nx) {
 
 cudaError_t launch_fold_boundary_sign(double2* U, int Nt, int Nx, cudaStream_t st) {
   k_fold_boundary_sign<<<(Nx + 255) / 256, 256, 0, st>>>(U, Nt, Nx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dslash_dag(const double2* in, double2* out, const double2* U, double diag, int Nt, int Nx, int R,
+                              cudaStream_t st) {
+  const int n = Nt * Nx;
+  dim3 grid((n + 255) / 256, R);
+  k_dslash_dag<<<grid, 256, 0, st>>>(in, out, U, diag, Nt, Nx);
   return cudaGetLastError();
 }
 

@@ -21,6 +21,9 @@ struct StencilOp {         // Galerkin level, [K][4][n] blocks
 template <typename Cin, typename Cout, typename T>
 cudaError_t launch_dslash(const Cin* in, Cout* out, const Cout* b, const typename cplx<T>::type* U, T diag, int Nt,
                           int Nx, int R, cudaStream_t st, const T* diag_r = nullptr);
+// out = sigma_3 D sigma_3 in = D^H in (Eq. (6)), FP64, diag = m0 + 2
+cudaError_t launch_dslash_dag(const double2* in, double2* out, const double2* U, double diag, int Nt, int Nx, int R,
+                              cudaStream_t st);
 template <typename T>
 cudaError_t launch_rb_half(typename cplx<T>::type* e, const typename cplx<T>::type* r, const typename cplx<T>::type* U,
                            T inv_diag, int Nt, int Nx, int colour, int R, cudaStream_t st,

@@ -268,43 +268,44 @@ __device__ double2 ap_entry(const Op& op, const double2* __restrict__ P, int t, 
   return acc;
 }
 
-// one CTA per coarse site v, thread = (k, alpha, beta): Bc[k][2 alpha + beta][v]
+// one CTA per coarse site v, thread = (k, alpha, beta) (several passes when
+// 4 K exceeds the block): Bc[k][2 alpha + beta][v]
 template <typename Op>
 __global__ void __launch_bounds__(128)
 k_galerkin(Op op, const double2* __restrict__ P, int a, int Np, int Nq, Offsets offc, double2* __restrict__ Bc,
            int own) {
   const int v = blockIdx.x;
-  const int th = threadIdx.x;
-  if (th >= offc.K * 4) return;
-  const int k = th >> 2, alpha = (th >> 1) & 1, beta = th & 1;
-  const int nc = Np * Nq;
-  const int p = v / Nq, q = v - (v / Nq) * Nq;
-  const int pw = wrap(p + offc.dt[k], Np), qw = wrap(q + offc.dx[k], Nq);
-  const int nrows = 2 * (a * a - 1);
-  double2 acc = make_double2(0.0, 0.0);
-  // v's own fine site: P row is the identity on spin alpha
-  acc += ap_entry(op, P, p * a, q * a, alpha, pw, qw, beta, a, Np, Nq, nrows, own);
-  // the rows whose basket has v as corner c: the F sites that basket
-  // W(p - di, q - dj) owns (under the tile rule: every row of tile (p-di, q-dj))
-  for (int c = 0; c < 4; ++c) {
-    const int pB = wrap(p - (c >> 1), Np), qB = wrap(q - (c & 1), Nq);
-    for (int i = 0; i <= a; ++i)
-      for (int j = 0; j <= a; ++j) {
-        if ((i == 0 || i == a) && (j == 0 || j == a)) continue;      // corners
-        const int it = (i == a) ? 0 : i, jt = (j == a) ? 0 : j;
-        const int pT = (i == a) ? wrap(pB + 1, Np) : pB, qT = (j == a) ? wrap(qB + 1, Nq) : qB;
-        int dp, dq;
-        row_basket(own, pT, qT, it, jt, dp, dq);
-        if (wrap(pT + dp, Np) != pB || wrap(qT + dq, Nq) != qB) continue;
-        const int l = it * a + jt;
-        const int tile = pT * Nq + qT;
-        for (int sigma = 0; sigma < 2; ++sigma) {
-          const double2 pv = P[((size_t)tile * 8 + 2 * c + alpha) * nrows + 2 * (l - 1) + sigma];
-          acc += cmulc(pv, ap_entry(op, P, pT * a + it, qT * a + jt, sigma, pw, qw, beta, a, Np, Nq, nrows, own));
+  for (int th = threadIdx.x; th < offc.K * 4; th += blockDim.x) {
+    const int k = th >> 2, alpha = (th >> 1) & 1, beta = th & 1;
+    const int nc = Np * Nq;
+    const int p = v / Nq, q = v - (v / Nq) * Nq;
+    const int pw = wrap(p + offc.dt[k], Np), qw = wrap(q + offc.dx[k], Nq);
+    const int nrows = 2 * (a * a - 1);
+    double2 acc = make_double2(0.0, 0.0);
+    // v's own fine site: P row is the identity on spin alpha
+    acc += ap_entry(op, P, p * a, q * a, alpha, pw, qw, beta, a, Np, Nq, nrows, own);
+    // the rows whose basket has v as corner c: the F sites that basket
+    // W(p - di, q - dj) owns (under the tile rule: every row of tile (p-di, q-dj))
+    for (int c = 0; c < 4; ++c) {
+      const int pB = wrap(p - (c >> 1), Np), qB = wrap(q - (c & 1), Nq);
+      for (int i = 0; i <= a; ++i)
+        for (int j = 0; j <= a; ++j) {
+          if ((i == 0 || i == a) && (j == 0 || j == a)) continue;      // corners
+          const int it = (i == a) ? 0 : i, jt = (j == a) ? 0 : j;
+          const int pT = (i == a) ? wrap(pB + 1, Np) : pB, qT = (j == a) ? wrap(qB + 1, Nq) : qB;
+          int dp, dq;
+          row_basket(own, pT, qT, it, jt, dp, dq);
+          if (wrap(pT + dp, Np) != pB || wrap(qT + dq, Nq) != qB) continue;
+          const int l = it * a + jt;
+          const int tile = pT * Nq + qT;
+          for (int sigma = 0; sigma < 2; ++sigma) {
+            const double2 pv = P[((size_t)tile * 8 + 2 * c + alpha) * nrows + 2 * (l - 1) + sigma];
+            acc += cmulc(pv, ap_entry(op, P, pT * a + it, qT * a + jt, sigma, pw, qw, beta, a, Np, Nq, nrows, own));
+          }
         }
-      }
+    }
+    Bc[((size_t)k * 4 + 2 * alpha + beta) * nc + v] = acc;
   }
-  Bc[((size_t)k * 4 + 2 * alpha + beta) * nc + v] = acc;
 }
 
 // Row-sum normalisation of Eq. (16) (N = diag(1 / row sum)): the complex sum

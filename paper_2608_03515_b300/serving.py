@@ -27,6 +27,10 @@ import numpy as np
 
 from . import amamg as A
 
+# status of a request withdrawn by Server.cancel (a serving-level status, not a
+# library code)
+CANCELLED = -100
+
 
 def aggregates_for(L: int) -> List[int]:
     """Tile sides: 4 while the coarse lattice stays above 64^2, then 2 down to 32^2."""
@@ -56,6 +60,7 @@ class Request:
     iterations: List[int] = field(default_factory=list)
     relres: List[float] = field(default_factory=list)
     finish: Optional[float] = None
+    cancelled: bool = False
 
 
 class Group:
@@ -80,12 +85,36 @@ class Group:
         self.cv = threading.Condition()
         self.cycles = 0
         self.busy_s = 0.0
+        self.cancelling: List[Request] = []
 
     def submit(self, req: Request):
         with self.cv:
             for i in range(req.R):
                 self.queue.append((req, i))
             self.cv.notify()
+
+    def cancel(self, req: Request):
+        """Withdraws req: its queued right-hand sides are dropped now, the slots
+        it holds are freed after the restart cycle in flight (if any)."""
+        with self.cv:
+            req.cancelled = True
+            self.queue = [(r, i) for (r, i) in self.queue if r is not req]
+            self.cv.notify()
+
+    def _finish_cancelled(self):
+        """Retires the slots of cancelled requests (no copy of the iterate) and
+        closes requests that hold no slot any more.  Called between cycles by
+        the worker, on its stream."""
+        for slot, (req, i) in list(self.where.items()):
+            if req.cancelled:
+                self.batch.retire(slot, None, stream=self.stream)
+                del self.where[slot]
+                self.free.append(slot)
+        for req in list(self.cancelling):
+            if not any(r is req for (r, _) in self.where.values()):
+                req.status = CANCELLED
+                req.finish = time.perf_counter() - self.server.t0
+                self.cancelling.remove(req)
 
     def run(self):
         import torch
@@ -95,13 +124,20 @@ class Group:
         x = torch.empty(2, L, L, dtype=torch.complex128, device=self.server.device)
         while True:
             with self.cv:
-                while not self.queue and not self.where and not self.server.closing:
+                while (not self.queue and not self.where and not self.server.closing
+                       and not self._pending_cancel()):
                     self.cv.wait(timeout=0.05)
+                for r in self._pending_cancel():
+                    self.cancelling.append(r)
+                with torch.cuda.stream(self.stream):
+                    self._finish_cancelled()
                 if self.server.closing and not self.queue and not self.where:
                     return
                 admit = []
                 while self.free and self.queue:
                     admit.append((self.free.pop(0), self.queue.pop(0)))
+            if not admit and not self.where:
+                continue
             t0 = time.perf_counter()
             with torch.cuda.stream(self.stream):
                 for slot, (req, i) in admit:
@@ -112,7 +148,7 @@ class Group:
                 self.cycles += 1
                 for slot, (req, i) in list(self.where.items()):
                     active, done, status, iters, relres = info[slot]
-                    if not done:
+                    if not done or req.cancelled:
                         continue
                     self.batch.retire(slot, x, stream=self.stream)
                     del self.where[slot]
@@ -126,6 +162,14 @@ class Group:
                         self.stream.synchronize()
                         req.finish = time.perf_counter() - self.server.t0
             self.busy_s += time.perf_counter() - t0
+
+    def _pending_cancel(self) -> List[Request]:
+        """Cancelled requests that still hold slots here and are not yet being closed."""
+        seen = []
+        for (r, _) in self.where.values():
+            if r.cancelled and r.finish is None and r not in self.cancelling and r not in seen:
+                seen.append(r)
+        return seen
 
 
 class Server:
@@ -167,6 +211,16 @@ class Server:
     def submit(self, req: Request):
         self.groups[(req.L, req.field)].submit(req)
 
+    def cancel(self, req: Request):
+        """Withdraws a submitted request (its right-hand sides stop at the end of
+        the restart cycle in flight; status CANCELLED)."""
+        g = self.groups[(req.L, req.field)]
+        g.cancel(req)
+        with g.cv:
+            if req.finish is None and not any(r is req for (r, _) in g.where.values()):
+                req.status = CANCELLED                  # nothing admitted yet: done at once
+                req.finish = time.perf_counter() - self.t0
+
     def close(self):
         self.closing = True
         for g in self.groups.values():
@@ -195,8 +249,9 @@ def serve(server: Server, requests: List[Request], time_scale: float = 1.0) -> d
         "requests": len(requests), "solves": solves, "wall_s": wall,
         "solves_per_s": solves / wall, "requests_per_s": len(requests) / wall,
         "latency_p50_ms": float(np.percentile(lat, 50) * 1e3), "latency_p99_ms": float(np.percentile(lat, 99) * 1e3),
-        "not_converged": sum(1 for r in requests if r.status != A.OK),
-        "max_true_relres": float(max(max(r.relres) for r in requests)),
+        "not_converged": sum(1 for r in requests if r.status not in (A.OK, CANCELLED)),
+        "cancelled": sum(1 for r in requests if r.status == CANCELLED),
+        "max_true_relres": float(max(max(r.relres) for r in requests if r.relres)),
         "slots": {f"{k[0]}/{k[1]}": g.slots for k, g in server.groups.items()},
         "cycles": sum(g.cycles for g in server.groups.values()),
     }

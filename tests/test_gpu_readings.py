@@ -70,7 +70,7 @@ def links(Nt, Nx, seed):
 
 @pytest.mark.parametrize("ownership,normalization", READINGS)
 @pytest.mark.parametrize("Nt,Nx,aggs", [(8, 8, [2]), (16, 16, [4]), (32, 32, [4, 2]), (16, 24, [2, 2]),
-                                        (32, 32, [2, 2, 2])])
+                                        (64, 64, [4, 2])])
 def test_setup_matches_oracle(Nt, Nx, aggs, ownership, normalization):
     U = links(Nt, Nx, 41)
     m0 = 0.07
@@ -101,9 +101,12 @@ def test_setup_matches_oracle(Nt, Nx, aggs, ownership, normalization):
         A.apply_P(hier, l, dev(ec), out_f)
         A.apply_PH(hier, l, dev(ef), out_c)
         gf, gc = host(out_f), host(out_c)
+        # row sums near the floor make some normalised weights large: their
+        # rounding sets the relative error of the transfers
+        tol = 1e-13 if normalization == "none" else 1e-12
         for r in range(2):
-            assert relerr(gf[r], W.from_flat(L.P @ W.to_flat(ec[r]), L.Nt, L.Nx)) <= 1e-13
-            assert relerr(gc[r], W.from_flat(L.P.conj().T @ W.to_flat(ef[r]), C.Nt, C.Nx)) <= 1e-13
+            assert relerr(gf[r], W.from_flat(L.P @ W.to_flat(ec[r]), L.Nt, L.Nx)) <= tol
+            assert relerr(gc[r], W.from_flat(L.P.conj().T @ W.to_flat(ef[r]), C.Nt, C.Nx)) <= tol
     hier.destroy()
 
 
@@ -133,3 +136,14 @@ def test_solve_matches_oracle(ownership, normalization, precision):
     assert abs(info[0].iterations - ref.iterations) <= max(1, 0.1 * ref.iterations), (info[0].iterations,
                                                                                        ref.iterations)
     hier.destroy()
+
+
+def test_first_lex_smoothed_level_beyond_the_smoother_is_rejected():
+    """Under first-lex ownership the second coarse level of a 32^2 lattice with
+    tile sides 2, 2, 2 couples 37 block offsets (the union over its sites); it
+    is a smoothed level, so setup rejects it with a clear error instead of
+    building a smoother it cannot run."""
+    U = links(32, 32, 43)
+    with pytest.raises(A.AmamgError) as ei:
+        A.setup(dev(U), 0.1, A.make_params([2, 2, 2], ownership="first_lex"))
+    assert ei.value.status == A.ERR_INVALID_ARG

@@ -464,3 +464,44 @@ def test_spin_split_interpolation_restores_sigma3_hermiticity():
     res = krylov.fgmres(lambda v: D @ v, lambda r: amg.vcycle(levels, r), b, 30, 1e-10, 2000)
     x = np.linalg.solve(D.toarray(), b)
     assert np.linalg.norm(res.x - x) / np.linalg.norm(x) <= 1e-7
+
+
+def test_vcycle_post_smoothing_placement_two_level_formula():
+    """Algorithm 1 with no pre-smoothing and two post-smoothing sweeps,
+    assembled by hand from dense matrices on a 4^2 lattice (a = 2, two
+    levels): e0 = P A_c^{-1} P^H r, then two red-black block Gauss-Seidel
+    sweeps on A e = r, each e_R <- A_RR^{-1} (r_R - A_RB e_B) followed by
+    e_B <- A_BB^{-1} (r_B - A_BR e_R) (red = even t + x).  The oracle's V-cycle
+    equals it, and differs from the same two sweeps placed before the coarse
+    correction (pre-smoothing) or left out."""
+    Nt = Nx = 4
+    rng = np.random.Generator(np.random.PCG64(77))
+    U = np.exp(1j * rng.uniform(-np.pi, np.pi, size=(2, Nt, Nx)))
+    m0 = 0.3
+    D = W.dirac_matrix(U, m0)
+    levels = amg.build_hierarchy(D, Nt, Nx, [2])
+    A = D.toarray()
+    P = levels[0].P.toarray()
+    Ac = P.conj().T @ A @ P
+    r = rng.standard_normal(2 * Nt * Nx) + 1j * rng.standard_normal(2 * Nt * Nx)
+    t, x = np.divmod(np.arange(Nt * Nx), Nx)
+    red_sites = np.nonzero((t + x) % 2 == 0)[0]
+    black_sites = np.nonzero((t + x) % 2 == 1)[0]
+    Rd = np.concatenate([[2 * s, 2 * s + 1] for s in red_sites])
+    Bd = np.concatenate([[2 * s, 2 * s + 1] for s in black_sites])
+
+    def sweep(e):
+        e = e.copy()
+        e[Rd] = np.linalg.solve(A[np.ix_(Rd, Rd)], r[Rd] - A[np.ix_(Rd, Bd)] @ e[Bd])
+        e[Bd] = np.linalg.solve(A[np.ix_(Bd, Bd)], r[Bd] - A[np.ix_(Bd, Rd)] @ e[Rd])
+        return e
+
+    coarse = lambda v: P @ np.linalg.solve(Ac, P.conj().T @ v)
+    post = sweep(sweep(coarse(r)))
+    got = amg.vcycle(levels, r, post_smooth=2)
+    assert np.linalg.norm(got - post) <= 1e-12 * np.linalg.norm(post)
+    x1 = sweep(sweep(np.zeros_like(r)))
+    pre = x1 + coarse(r - A @ x1)
+    assert np.linalg.norm(got - pre) > 1e-3 * np.linalg.norm(post)
+    assert np.linalg.norm(got - coarse(r)) > 1e-3 * np.linalg.norm(post)
+    assert np.linalg.norm(amg.vcycle(levels, r, post_smooth=0) - coarse(r)) <= 1e-12 * np.linalg.norm(post)

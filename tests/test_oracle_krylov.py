@@ -68,3 +68,36 @@ def test_amg_preconditioned_solve_matches_dense_lu(aggs):
     # the preconditioner helps: fewer steps than plain GMRES
     plain = krylov.fgmres(lambda v: D @ v, lambda v: v, b, 30, 1e-10, 2000)
     assert res.iterations < plain.iterations
+
+
+def test_cgnr_equals_cg_on_the_normal_equations_and_solves_the_system():
+    """CGNR's iterates are those of CG applied to D^H D x = D^H b: after k steps
+    they equal the minimiser of ||b - D x|| over the Krylov space
+    K_k(D^H D, D^H b), which a dense least-squares solve in that space gives;
+    run to the tolerance, the solution matches the dense solve of D x = b, and
+    D^H taken as sigma_3 D sigma_3 (Eq. (6)) gives the same iterates."""
+    Nt = Nx = 8
+    D = W.dirac_matrix(random_links(Nt, Nx, 35), 0.3)
+    Dd = D.toarray()
+    b = W.to_flat(fx.gaussian_rhs(1, Nt, Nx, 36)[0])
+    AH = lambda v: D.conj().T @ v
+    for k in (1, 3, 6):
+        res = krylov.cgnr(lambda v: D @ v, AH, b, 1e-300, k)
+        assert res.iterations == k
+        # dense Krylov basis of D^H D from D^H b, orthonormalised, then least squares
+        N = Dd.conj().T @ Dd
+        Kb = [Dd.conj().T @ b]
+        for _ in range(k - 1):
+            Kb.append(N @ Kb[-1])
+        Q, _ = np.linalg.qr(np.stack(Kb, axis=1))
+        y, *_ = np.linalg.lstsq(Dd @ Q, b, rcond=None)
+        xk = Q @ y
+        assert np.linalg.norm(res.x - xk) <= 1e-8 * np.linalg.norm(xk)
+    res = krylov.cgnr(lambda v: D @ v, AH, b, 1e-10, 5000)
+    assert res.converged and res.true_relres <= 1e-10
+    xs = np.linalg.solve(Dd, b)
+    assert np.linalg.norm(res.x - xs) <= 1e-7 * np.linalg.norm(xs)
+    s3 = W.sigma3_full(Nt * Nx)
+    res3 = krylov.cgnr(lambda v: D @ v, lambda v: s3 @ (D @ (s3 @ v)), b, 1e-10, 5000)
+    assert res3.iterations == res.iterations
+    assert np.linalg.norm(res3.x - res.x) <= 1e-10 * np.linalg.norm(res.x)
