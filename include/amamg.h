@@ -72,6 +72,11 @@ typedef struct amamg_ctx* amamg_handle;
 #define AMAMG_NORM_ROWSUM 1          /* every non-vertex scalar row of P divided by its complex row sum;
                                         rows whose |sum| is below 1e-12 x the level's largest |sum| stay */
 
+/* coarsest-level solver inside the V-cycle */
+#define AMAMG_COARSEST_DIRECT 0      /* exact: the FP64 inverse from setup (default) */
+#define AMAMG_COARSEST_GMRES  1      /* the paper's setting (Sec. 5): unpreconditioned GMRES(30) from a
+                                        zero start to relative residual 0.1, on the device */
+
 /* which basket a border site takes its formula from ("the first aggregate it
  * was assigned to", Sec. 4.1) */
 #define AMAMG_OWNER_TILE      0      /* the basket of the tile containing the site, W(t/a, x/a) (default) */
@@ -92,6 +97,10 @@ typedef struct {
                                         Sec. 6 proposes; a comparison hierarchy, not the method as read) */
     int    normalization;            /* AMAMG_NORM_NONE (default) or AMAMG_NORM_ROWSUM, every level */
     int    edge_owner;               /* AMAMG_OWNER_TILE (default) or AMAMG_OWNER_FIRST_LEX, every level */
+    int    coarsest;                 /* AMAMG_COARSEST_DIRECT (default) or AMAMG_COARSEST_GMRES; with
+                                        GMRES no dense inverse is formed (no size limit on the coarsest
+                                        level) and the V-cycle is no longer a fixed linear map (the
+                                        outer FGMRES is flexible) */
 } amamg_params;
 
 typedef struct {
@@ -213,7 +222,8 @@ int amamg_apply_coarse(amamg_handle h, int level, const void* in, void* out,
 int amamg_smooth(amamg_handle h, int level, const void* r, void* e, int R,
                  int sweeps, int precision, void* stream);
 
-/* e = A_L^{-1} r on the coarsest level, in FP64 (complex128 vectors). */
+/* e = A_L^{-1} r on the coarsest level, in FP64 (complex128 vectors): the dense
+ * inverse, or with AMAMG_COARSEST_GMRES the GMRES solve to relative residual 0.1. */
 int amamg_coarsest_solve(amamg_handle h, const void* r, void* e, int R, void* stream);
 
 /* e = M(r): one V-cycle of Algorithm 1 on the fine level with start vector 0,

@@ -32,6 +32,8 @@ NORM_NONE = 0
 NORM_ROWSUM = 1
 OWNER_TILE = 0
 OWNER_FIRST_LEX = 1
+COARSEST_DIRECT = 0
+COARSEST_GMRES = 1
 
 EXPORTED = [
     "amamg_default_params", "amamg_query_bytes", "amamg_setup", "amamg_solve", "amamg_apply_D",
@@ -56,6 +58,7 @@ class Params(ctypes.Structure):
         ("spin_split", ctypes.c_int),
         ("normalization", ctypes.c_int),
         ("edge_owner", ctypes.c_int),
+        ("coarsest", ctypes.c_int),
     ]
 
 
@@ -165,9 +168,11 @@ def default_params() -> Params:
 
 def make_params(aggs: Sequence[int], precision: int = SOLVE_FP64, restart: int = 30, max_iter: int = 3000,
                 post_smooth: int = 2, tol: float = 1e-10, spin_split: bool = False,
-                normalization: str = "none", ownership: str = "tile") -> Params:
+                normalization: str = "none", ownership: str = "tile", coarsest: str = "direct") -> Params:
     """Parameters of amamg_setup; normalization "none" | "rowsum" and ownership
-    "tile" | "first_lex" name the readings the oracle's build_hierarchy takes."""
+    "tile" | "first_lex" name the readings the oracle's build_hierarchy takes;
+    coarsest "direct" | "gmres" the coarsest solver (the oracle's vcycle
+    coarsest="lu" | "gmres")."""
     p = default_params()
     p.nlevels = len(aggs) + 1
     for i, a in enumerate(aggs):
@@ -180,6 +185,7 @@ def make_params(aggs: Sequence[int], precision: int = SOLVE_FP64, restart: int =
     p.spin_split = 1 if spin_split else 0
     p.normalization = {"none": NORM_NONE, "rowsum": NORM_ROWSUM}[normalization]
     p.edge_owner = {"tile": OWNER_TILE, "first_lex": OWNER_FIRST_LEX}[ownership]
+    p.coarsest = {"direct": COARSEST_DIRECT, "gmres": COARSEST_GMRES}[coarsest]
     return p
 
 

@@ -534,6 +534,40 @@ int op_coarse(amamg_ctx* h, int l, const typename cplx<T>::type* in, typename cp
     }, (double)L.n * R * L.off.K * 32.0);
 }
 
+// The paper's coarsest solver (Sec. 5): GMRES(GMRES_RESTART) to relative
+// residual GMRES_TOL from a zero start, at most GMRES_MAX_R right-hand sides per
+// launch.  Bytes and FLOPs are not counted (the iteration count is data dependent).
+constexpr int GMRES_RESTART = 30;
+constexpr double GMRES_TOL = 0.1;
+constexpr int GMRES_MAX_CYCLES = 200;
+
+template <typename T>
+int op_coarsest_gmres(amamg_ctx* h, const typename cplx<T>::type* r, typename cplx<T>::type* e, int R,
+                      cudaStream_t st) {
+  using C = typename cplx<T>::type;
+  const Level& L = h->lv.back();
+  const size_t len = 2 * (size_t)L.n;
+  for (int r0 = 0; r0 < R; r0 += GMRES_MAX_R) {
+    const int Rc = std::min(GMRES_MAX_R, R - r0);
+    const C* rr = r + r0 * len;
+    C* ee = e + r0 * len;
+    C* V = reinterpret_cast<C*>(h->gm_V);
+    if constexpr (sizeof(T) == 8)
+      CKS(launch(h, "coarsest_gmres_f64", 0.0, st, [&] {
+        return launch_coarsest_gmres<double, double2>(rr, ee, L.B64, nullptr, L.off, L.Nt, L.Nx, Rc, GMRES_RESTART,
+                                                      GMRES_TOL, GMRES_MAX_CYCLES, V, h->gm_part, h->gm_st,
+                                                      h->d_sync, h->gm_done, h->gm_blocks64, st);
+      }));
+    else
+      CKS(launch(h, "coarsest_gmres_f32", 0.0, st, [&] {
+        return launch_coarsest_gmres<float, __half2>(rr, ee, L.B16, L.Bs, L.off, L.Nt, L.Nx, Rc, GMRES_RESTART,
+                                                     GMRES_TOL, GMRES_MAX_CYCLES, V, h->gm_part, h->gm_st,
+                                                     h->d_sync, h->gm_done, h->gm_blocks32, st);
+      }));
+  }
+  return AMAMG_OK;
+}
+
 template <typename Cv>
 int op_coarsest(amamg_ctx* h, const Cv* r, Cv* e, int R, cudaStream_t st) {
   const double bytes = (double)h->nd * h->nd * 16.0 + (double)R * 2 * h->nd * sizeof(Cv);
@@ -543,11 +577,14 @@ int op_coarsest(amamg_ctx* h, const Cv* r, Cv* e, int R, cudaStream_t st) {
 }
 
 // coarsest level inside a V-cycle: FP64 inverse for FP64 vectors, its FP32
-// rounding for the FP32 (mixed-precision) V-cycle
+// rounding for the FP32 (mixed-precision) V-cycle; or GMRES in the vectors'
+// precision (FP16 + scale blocks for FP32)
 int vcycle_coarsest(amamg_ctx* h, const double2* r, double2* e, int R, cudaStream_t st) {
+  if (h->prm.coarsest == AMAMG_COARSEST_GMRES) return op_coarsest_gmres<double>(h, r, e, R, st);
   return op_coarsest<double2>(h, r, e, R, st);
 }
 int vcycle_coarsest(amamg_ctx* h, const float2* r, float2* e, int R, cudaStream_t st) {
+  if (h->prm.coarsest == AMAMG_COARSEST_GMRES) return op_coarsest_gmres<float>(h, r, e, R, st);
   const double bytes = (double)h->nd * h->nd * 8.0 + (double)R * 2 * h->nd * 8.0;
   return launch(h, "coarsest_gemv_f32", bytes, st,
                 [&] { return launch_dense_gemv32(h->Ainv32, r, e, h->nd, R, st); },
@@ -934,8 +971,15 @@ int check_params(const amamg_params* p, int Nt, int Nx, std::string* why) {
     if (l >= 1 && (nt % 4 || nx % 4)) { *why = "smoothed coarse levels need extents divisible by 4"; return AMAMG_ERR_INVALID_ARG; }
     nt /= a; nx /= a;
   }
+  if (p->coarsest != AMAMG_COARSEST_DIRECT && p->coarsest != AMAMG_COARSEST_GMRES) {
+    *why = "coarsest must be AMAMG_COARSEST_DIRECT or AMAMG_COARSEST_GMRES";
+    return AMAMG_ERR_INVALID_ARG;
+  }
   const double nd = 2.0 * nt * nx;
-  if (nd > 16384) { *why = "coarsest level too large for the dense inverse (2 Nt_L Nx_L > 16384)"; return AMAMG_ERR_INVALID_ARG; }
+  if (p->coarsest == AMAMG_COARSEST_DIRECT && nd > 16384) {
+    *why = "coarsest level too large for the dense inverse (2 Nt_L Nx_L > 16384)";
+    return AMAMG_ERR_INVALID_ARG;
+  }
   return AMAMG_OK;
 }
 
@@ -953,6 +997,7 @@ void free_all(amamg_ctx* h) {
   h->ws = nullptr; h->ev_in = h->ev_out = nullptr;
   dfree(h->U64); dfree(h->U64s); dfree(h->U32); dfree(h->Ainv); dfree(h->Ainv32); dfree(h->d_err); dfree(h->d_sync); dfree(h->d_owner_flags);
   dfree(h->d_smax); dfree(h->d_rowsum_skipped);
+  dfree(h->gm_V); dfree(h->gm_part); dfree(h->gm_st); dfree(h->gm_done);
   dfree(h->V); dfree(h->Z64); dfree(h->Z32); dfree(h->v32); dfree(h->w); dfree(h->res);
   dfree(h->partial); dfree(h->d_h); dfree(h->d_inv); dfree(h->d_flag); dfree(h->d_y); dfree(h->d_tickets); dfree(h->d_npart);
   dfree(h->d_diag64); dfree(h->d_inv64); dfree(h->d_inv32);
@@ -1054,10 +1099,31 @@ int do_setup(amamg_ctx* h, const void* Uin, cudaStream_t st) {
       choose_gs_kernels(C);
     }
   }
-  // coarsest: dense matrix and its Gauss-Jordan inverse
+  // coarsest: GMRES workspace, or the dense matrix and its Gauss-Jordan inverse
   Level& Cl = h->lv[L - 1];
   h->nd = 2 * Cl.n;
   const size_t nd = (size_t)h->nd;
+  if (h->prm.coarsest == AMAMG_COARSEST_GMRES) {
+    h->gm_blocks64 = coarsest_gmres_blocks<double, double2>(GMRES_RESTART);
+    h->gm_blocks32 = coarsest_gmres_blocks<float, __half2>(GMRES_RESTART);
+    const int gb = std::max(h->gm_blocks64, h->gm_blocks32);
+    if (h->gm_blocks64 <= 0 || h->gm_blocks32 <= 0) {
+      h->err = "cooperative launches are unavailable for the coarsest GMRES";
+      return AMAMG_ERR_CUDA;
+    }
+    CKS(dalloc(h, &h->gm_V, (size_t)(GMRES_RESTART + 1) * GMRES_MAX_R * nd));
+    CKS(dalloc(h, &h->gm_part, (size_t)gb * GMRES_MAX_R * (GMRES_RESTART + 2)));
+    CKS(dalloc(h, &h->gm_st, (size_t)GMRES_MAX_R));
+    CKS(dalloc(h, &h->gm_done, 1));
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (herr) {
+      h->err = (herr & 1) ? "vanishing pivot in a local basket solve" : "singular 2x2 diagonal block on a coarse level";
+      return AMAMG_ERR_SINGULAR;
+    }
+    return AMAMG_OK;
+  }
   double2* X = nullptr;
   double2* colk = nullptr;
   int* perm = nullptr;
@@ -1152,7 +1218,10 @@ int amamg_query_bytes(const amamg_params* p, int Nt, int Nx, int max_rhs, size_t
     off = c;
   }
   const size_t nd = 2 * (size_t)nt * nx;
-  sb += 2 * nd * nd * 16;                        // inverse + its work copy during setup
+  if (p->coarsest == AMAMG_COARSEST_GMRES)
+    sb += (size_t)(30 + 1) * 32 * nd * 16 + 32 * sizeof(GmresRhs) + (size_t)2 * 148 * 32 * 32 * 16;
+  else
+    sb += 2 * nd * nd * 16 + nd * nd * 8;        // inverse, its work copy during setup, its FP32 rounding
   const size_t len = 2 * (size_t)Nt * Nx;
   const int m = p->restart;
   size_t rb = vb + (size_t)(m + 1) * len * 16 + 2 * len * 16 +
@@ -1383,7 +1452,7 @@ int amamg_sync_status(amamg_handle h, void* stream) {
 
 int amamg_coarsest_solve(amamg_handle h, const void* r, void* e, int R, void* stream) {
   if (!h || !r || !e || R < 1) return AMAMG_ERR_INVALID_ARG;
-  return op_coarsest<double2>(h, (const double2*)r, (double2*)e, R, S(stream));
+  return vcycle_coarsest(h, (const double2*)r, (double2*)e, R, S(stream));
 }
 
 int amamg_vcycle(amamg_handle h, const void* r, void* e, int R, int precision, void* stream) {

@@ -121,6 +121,14 @@ struct amamg_ctx {
   double2* U64 = nullptr;    // links as given (setup's local operators)
   double2* U64s = nullptr;   // with the t-boundary sign folded in (stencil kernels)
   float2* U32 = nullptr;     // FP32 rounding of U64s
+  // coarsest solve by GMRES (AMAMG_COARSEST_GMRES): basis, partial sums,
+  // per-RHS least-squares state, "all done" word (GMRES_MAX_R right-hand sides
+  // per launch)
+  double2* gm_V = nullptr;
+  double2* gm_part = nullptr;
+  GmresRhs* gm_st = nullptr;
+  int* gm_done = nullptr;
+  int gm_blocks64 = 0, gm_blocks32 = 0;   // co-resident blocks of the GMRES kernel per precision
   double2* Ainv = nullptr;   // coarsest inverse, nd x nd row-major
   float2* Ainv32 = nullptr;  // its FP32 rounding, applied by the mixed-precision V-cycle
   int nd = 0;

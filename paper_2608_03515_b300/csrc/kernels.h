@@ -186,3 +186,32 @@ cudaError_t launch_pack_B16(const double2* B, int K, int n, __half2* B16, float*
 cudaError_t launch_pack_colour_major(const double2* B64, const __half2* B16, const float* Bs, const double2* D64,
                                      const float2* D32, int K, int Nt, int Nx, int ncol, double2* Bc64, __half2* Bc16,
                                      float* Bcs, double2* Dc64, float2* Dc32, cudaStream_t st);
+
+// coarsest_gmres.cu: the coarsest level by unpreconditioned restarted GMRES to
+// relative residual tol from a zero start (Sec. 5), one cooperative launch per
+// at most GMRES_MAX_R right-hand sides; restart length m <= GMRES_MAX_M.
+constexpr int GMRES_MAX_M = 32;
+constexpr int GMRES_MAX_R = 32;
+struct GmresRhs {                    // the small least-squares problem of one right-hand side (FP64)
+  double2 H[(GMRES_MAX_M + 1) * GMRES_MAX_M];   // Hessenberg matrix, rotated in place, H[i * GMRES_MAX_M + j]
+  double2 H2[GMRES_MAX_M];           // second-pass Gram-Schmidt coefficients of the current column
+  double2 g[GMRES_MAX_M + 1];        // rotated right-hand side beta e_1
+  double2 sn[GMRES_MAX_M];
+  double2 y[GMRES_MAX_M];
+  double cs[GMRES_MAX_M];
+  double s[GMRES_MAX_M + 1];         // inverse norms of the stored (unnormalised) basis vectors
+  double bnorm;
+  int k, done, cdone, iters;         // steps this cycle, solved, cycle ended, total steps
+};
+size_t coarsest_gmres_smem(int R, int m);
+// co-resident blocks of the kernel (cap of max_blocks), 0 without cooperative launches
+template <typename T, typename BT>
+int coarsest_gmres_blocks(int m);
+// r, e: [R][2][Nt][Nx] (R <= GMRES_MAX_R); V: (m + 1) R 2 Nt Nx elements;
+// part: max_blocks R (m + 2) double2; st: R records; sync: grid-barrier words
+// {count (0 between launches), generation, time-out}
+template <typename T, typename BT>
+cudaError_t launch_coarsest_gmres(const typename cplx<T>::type* r, typename cplx<T>::type* e, const BT* B,
+                                  const float* Bs, const Offsets& off, int Nt, int Nx, int R, int m, double tol,
+                                  int max_cycles, typename cplx<T>::type* V, double2* part, GmresRhs* st,
+                                  unsigned* sync, int* all_done, int max_blocks, cudaStream_t s);
