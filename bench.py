@@ -207,7 +207,7 @@ def run_probe(args):
     Lp = args.lattice
     rng = np.random.Generator(np.random.PCG64(5))
     U = torch.from_numpy(np.exp(1j * rng.uniform(-np.pi, np.pi, size=(2, Lp, Lp)))).to(dev)
-    aggs = [4, 4, 2] if Lp >= 1024 else [4, 2]
+    aggs = [int(a) for a in args.tiles.split(",")] if args.tiles else ([4, 4, 2] if Lp >= 1024 else [4, 2])
     prec = A.SOLVE_MIXED if args.prec == "f32" else A.SOLVE_FP64
     h = A.setup(U, 0.1, A.make_params(aggs, precision=prec))
     dt = torch.complex64 if args.prec == "f32" else torch.complex128
@@ -227,10 +227,11 @@ def run_probe(args):
             A.vcycle(h, x, y)
         elif args.probe == "smooth1":
             A.smooth(h, 1, r1, e1, 2)
-        elif args.probe == "coarsest":
+        elif args.probe in ("coarsest", "coarsest_f32"):
             nt, nx, _ = h.level_info(len(aggs))
-            xc = torch.randn(args.rhs, 2, nt, nx, dtype=torch.complex128, device=dev)
-            A.coarsest_solve(h, xc, torch.empty_like(xc))
+            cdt = torch.complex64 if args.probe == "coarsest_f32" else torch.complex128
+            xc = torch.randn(args.rhs, 2, nt, nx, dtype=cdt, device=dev)
+            A.coarsest_apply(h, xc, torch.empty_like(xc))
         else:
             A.solve(h, x.to(torch.complex128), torch.empty(x.shape, dtype=torch.complex128, device=dev))
     ev[1].record(stream)
@@ -296,7 +297,15 @@ def serving_fields_available():
     return out
 
 
-def run_serving(n_requests, rate, dev, mem_budget):
+def field_angles(Lf, beta, seed):
+    """Quenched field of the fixtures (run in a worker process of the field pool)."""
+    from paper_2608_03515_b300 import fixtures as fx
+    return fx.metropolis_u1(Lf, Lf, beta, SWEEPS, seed)
+
+
+def run_serving(n_requests, rate, dev, mem_budget, thetas):
+    """The serving stream: n_requests Poisson arrivals over the resident fields
+    whose critical mass is tabulated (thetas[(L, k)]: futures of their angles)."""
     import torch
     from paper_2608_03515_b300 import fixtures as fx
     from paper_2608_03515_b300 import serving
@@ -304,7 +313,7 @@ def run_serving(n_requests, rate, dev, mem_budget):
     sizes = sorted({L for (L, _) in avail})
     fields, mcrit = {}, {}
     for (L, k), (beta, mc) in avail.items():
-        U = torch.from_numpy(fx.links_from_angles(fx.metropolis_u1(L, L, beta, SWEEPS, 10 + k))).to(dev)
+        U = torch.from_numpy(fx.links_from_angles(thetas[(L, k)].result())).to(dev)
         fields[(L, k)] = (U, mc + 0.005)            # hierarchy at the lowest serving mass
         mcrit[(L, k)] = mc
     if rate <= 0:
@@ -317,7 +326,88 @@ def run_serving(n_requests, rate, dev, mem_budget):
     reqs = serving.poisson_requests(n_requests, rate, list(avail), mcrit, seed=100)
     out = serving.serve(srv, reqs)
     out.update({"rate_req_per_s": rate, "sizes": sizes, "fields": len(fields),
-                "setup_s_total": sum(g.setup_s for g in srv.groups.values())})
+                "setup_s_total": sum(g.setup_s for g in srv.groups.values()),
+                "config": "Poisson arrivals at 0.8 x the calibrated saturated request rate; each request draws "
+                          "(L, field) uniformly from the resident fields, m0 = m_crit + U[0.005, 0.1], "
+                          "R ~ U{1..16}; mixed precision to 1e-10",
+                "sizes_missing": [Lm for Lm in SERVING_SIZES if Lm not in sizes]})
+    return out
+
+
+# ----------------------------------------------------------------------------- many right-hand sides
+
+C4_L, C4_BETA, C4_SEED, C4_DM, C4_AGGS, C4_R, C4_RHS_SEED = 1024, 12.0, 5, 0.005, [4, 4], 64, 6
+
+
+def c4_mcrit():
+    table = json.load(open(os.path.join(ROOT, "tests", "golden", "mcrit.json")))
+    e = table.get(f"L{C4_L}_b{C4_BETA:g}_s{C4_SEED}")
+    return None if e is None else e["m_crit"]
+
+
+def run_c4(dev, theta_future):
+    """64 right-hand sides on the 1024^2 beta = 12 field at m_crit + 0.005, 3
+    levels (tiles 4, 4; coarsest 64^2 = 8192 unknowns, FP64 inverse), mixed
+    precision, FGMRES(30) to 1e-10: one warm-up and one timed solve of all 64;
+    beside it the plain FP64 form on the first right-hand side alone; and the
+    oracle's iteration counts and sampled solution entries for the first four
+    (tests/golden/c4_oracle.json, when present)."""
+    import torch
+    from paper_2608_03515_b300 import amamg as A
+    from paper_2608_03515_b300 import fixtures as fx
+    mc = c4_mcrit()
+    if mc is None:
+        return {"skipped": "critical mass of the 1024^2 beta=12 field not tabulated"}
+    m0 = mc + C4_DM
+    U = torch.from_numpy(fx.links_from_angles(theta_future.result())).to(dev)
+    psi = torch.from_numpy(fx.gaussian_rhs(C4_R, C4_L, C4_L, C4_RHS_SEED)).to(dev)
+    x = torch.empty_like(psi)
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"{C4_L}x{C4_L} quenched U(1) beta={C4_BETA:g} seed {C4_SEED}, m0 = m_crit + {C4_DM}, "
+                       f"tiles {C4_AGGS} (coarsest 64^2, FP64 inverse), FGMRES(30) to 1e-10, {C4_R} RHS per call",
+           "m0": m0}
+    h = A.setup(U, m0, A.make_params(C4_AGGS, precision=A.SOLVE_MIXED, restart=RESTART, tol=TOL))
+    out["setup_ms"] = round(1e3 * A.setup_seconds(h), 1)
+    A.solve(h, psi, x)                                       # warm-up (captures the 64-wide graphs)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    info = A.solve(h, psi, x)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1])
+    its = [i.iterations for i in info]
+    out["mixed_batched"] = {"solves_per_s": round(C4_R / (ms * 1e-3), 3), "ms": round(ms, 1),
+                            "iterations": {"min": min(its), "max": max(its), "mean": round(float(np.mean(its)), 1)},
+                            "true_relres_max": max(i.true_relres for i in info),
+                            "all_converged": all(i.status == A.OK for i in info)}
+    xh = x[:4].cpu().numpy()
+    A.destroy(h)
+    del x
+    # the plain FP64 form, one right-hand side per call
+    h64 = A.setup(U, m0, A.make_params(C4_AGGS, precision=A.SOLVE_FP64, restart=RESTART, tol=TOL))
+    x1 = torch.empty_like(psi[:1])
+    A.solve(h64, psi[:1], x1)
+    ev[0].record(stream)
+    i64 = A.solve(h64, psi[:1], x1)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms64 = ev[0].elapsed_time(ev[1])
+    out["fp64_single"] = {"solves_per_s": round(1.0 / (ms64 * 1e-3), 3), "ms": round(ms64, 1),
+                          "iterations": i64[0].iterations, "true_relres": i64[0].true_relres}
+    out["speedup_mixed_batched_vs_fp64_single"] = round(out["mixed_batched"]["solves_per_s"] /
+                                                        out["fp64_single"]["solves_per_s"], 2)
+    A.destroy(h64)
+    gold = os.path.join(ROOT, "tests", "golden", "c4_oracle.json")
+    if os.path.exists(gold):
+        g = json.load(open(gold))
+        cmp = []
+        for row in g["solves"]:
+            r = row["rhs"]
+            xs = np.array([[complex(*v) for v in site] for site in row["x_at_sites"]])
+            xg = np.array([[xh[r][a, t, xx] for a in range(2)] for (t, xx) in g["sites"]])
+            cmp.append({"rhs": r, "iterations": its[r], "oracle_iterations": row["iterations"],
+                        "sampled_rel_err": float(np.max(np.abs(xg - xs)) / row["x_norm"])})
+        out["vs_oracle"] = cmp
     return out
 
 
@@ -330,14 +420,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--probe", default=None, choices=["apply_D", "vcycle", "smooth1", "solve", "coarsest"],
+    ap.add_argument("--probe", default=None,
+                    choices=["apply_D", "vcycle", "smooth1", "solve", "coarsest", "coarsest_f32"],
                     help="time one kernel family on a small random-phase case (for profiler captures)")
     ap.add_argument("--lattice", type=int, default=512)
+    ap.add_argument("--tiles", default="", help="probe: tile sides, e.g. 4,4")
     ap.add_argument("--rhs", type=int, default=1)
     ap.add_argument("--prec", default="f64", choices=["f64", "f32"])
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--serving", type=int, default=0,
-                    help="also run a serving stream of this many requests (continuous batching, mixed precision)")
+    ap.add_argument("--serving", type=int, default=2000,
+                    help="serving stream of this many requests (continuous batching, mixed precision; 0: skip)")
+    ap.add_argument("--no-c4", action="store_true",
+                    help="skip the 1024^2, 64-right-hand-side mixed-precision leg")
     ap.add_argument("--no-spread", action="store_true",
                     help="skip the parameter spread (tile sides, edge ownership, normalisation)")
     ap.add_argument("--serving-rate", type=float, default=0.0,
@@ -351,6 +445,20 @@ def main():
     if args.probe:
         run_probe(args)
         return
+
+    # host-side fixtures of the later legs, generated by a spawned process pool
+    # (started before the first CUDA call) while the GPU runs the earlier ones
+    import concurrent.futures
+    import multiprocessing
+    pool = concurrent.futures.ProcessPoolExecutor(max_workers=max(1, min(8, cpu_cores() - 2)),
+                                                  mp_context=multiprocessing.get_context("spawn"))
+    c4_theta = None
+    if not args.no_c4 and c4_mcrit() is not None:
+        c4_theta = pool.submit(field_angles, C4_L, C4_BETA, C4_SEED)
+    serving_thetas = {}
+    if args.serving > 0:
+        for (Ls, k), (beta, _) in serving_fields_available().items():
+            serving_thetas[(Ls, k)] = pool.submit(field_angles, Ls, beta, 10 + k)
 
     import torch
     import torch.distributed as dist
@@ -508,6 +616,37 @@ def main():
     for h in hs_ss:
         A.destroy(h)
 
+    # the paper's coarsest setting (GMRES(30) to 0.1 instead of the exact
+    # solve), FP64 and mixed: one warm-up and one timed step each
+    coarsest_gmres = {}
+    for name, prec in (("fp64", A.SOLVE_FP64), ("mixed", A.SOLVE_MIXED)):
+        hs_g = [A.setup(U, m0, A.make_params(AGGS, precision=prec, restart=RESTART, tol=TOL, coarsest="gmres"))
+                for m0 in masses]
+        run(hs_g, nst=1)
+        st_g, sv_g, it_g, rr_g = run(hs_g, nst=2, skip=1)
+        coarsest_gmres[name] = {"solves_per_s": round(len(masses) / (st_g[0] * 1e-3), 3),
+                                "iterations": it_g[-len(masses):], "solve_ms": [round(v, 2) for v in sv_g],
+                                "true_relres_max": max(rr_g[-len(masses):])}
+        for h in hs_g:
+            A.destroy(h)
+
+    # the paper's unpreconditioned comparison solver: CG on the normal
+    # equations (D^H = sigma_3 D sigma_3), FP64, same right-hand side per mass
+    cgnr = {"iterations": [], "solve_ms": [], "true_relres": []}
+    for h in hs64:
+        A.cgnr(h, psis[0], x, max_iter=200000, tol=TOL)           # warm-up
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        info = A.cgnr(h, psis[args.warmup], x, max_iter=200000, tol=TOL)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        cgnr["iterations"].append(info[0].iterations)
+        cgnr["solve_ms"].append(round(ev[0].elapsed_time(ev[1]), 2))
+        cgnr["true_relres"].append(info[0].true_relres)
+    cgnr["amg_iterations"] = iters64[-len(masses):]
+    amg_ms = [float(np.mean(solve_ms[k::len(masses)])) for k in range(len(masses))]   # per mass, timed steps
+    cgnr["time_ratio_vs_amg_fp64"] = [round(c / a, 2) for c, a in zip(cgnr["solve_ms"], amg_ms)]
+
     # end to end through the public API with host buffers
     psi_h = [p.cpu().pin_memory() for p in psis]
     x_h = torch.empty(psis[0].shape, dtype=torch.complex128).pin_memory()
@@ -599,10 +738,12 @@ def main():
 
     spread_out = None if args.no_spread else run_spread(dev, U, masses, psis[0])
 
+    c4_out = run_c4(dev, c4_theta) if not args.no_c4 else None
+
     serving_out = None
     if args.serving > 0:
         free, total = torch.cuda.mem_get_info()
-        serving_out = run_serving(args.serving, args.serving_rate, dev, int(0.7 * free))
+        serving_out = run_serving(args.serving, args.serving_rate, dev, int(0.7 * free), serving_thetas)
 
     out = None
     if rank == 0:
@@ -645,17 +786,22 @@ def main():
                            "p99": round(float(np.percentile(solve_ms, 99)), 3)},
             "batched_mixed": batched,
             "spin_split": spin_split,
+            "coarsest_gmres": coarsest_gmres,
+            "cgnr": cgnr,
             "iterations": iters64[-len(masses):],
             "true_relres_max": max(relres64),
             "setup_ms": [round(s, 2) for s in setup64],
             "d_apply": d_apply,
             "wall_s_timed_region": round(wall_s, 3),
         }
+        if c4_out is not None:
+            out["c4"] = c4_out
         if serving_out is not None:
             out["serving"] = serving_out
         if spread_out is not None:
             out["spread"] = spread_out
         print(json.dumps(out))
+    pool.shutdown(wait=False, cancel_futures=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()

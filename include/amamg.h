@@ -226,6 +226,13 @@ int amamg_smooth(amamg_handle h, int level, const void* r, void* e, int R,
  * inverse, or with AMAMG_COARSEST_GMRES the GMRES solve to relative residual 0.1. */
 int amamg_coarsest_solve(amamg_handle h, const void* r, void* e, int R, void* stream);
 
+/* The coarsest step of the V-cycle in the given precision: AMAMG_F64 as
+ * amamg_coarsest_solve; AMAMG_F32 (complex64 vectors) the FP32 rounding of the
+ * FP64 inverse, applied on the tensor cores (TF32 inputs, FP32 accumulation)
+ * when R >= 8 and 2 Nt_L Nx_L is a multiple of 128, or GMRES in FP32 with
+ * AMAMG_COARSEST_GMRES. */
+int amamg_coarsest_apply(amamg_handle h, const void* r, void* e, int R, int precision, void* stream);
+
 /* e = M(r): one V-cycle of Algorithm 1 on the fine level with start vector 0,
  * no pre-smoothing and post_smooth sweeps per level. */
 int amamg_vcycle(amamg_handle h, const void* r, void* e, int R, int precision, void* stream);

@@ -37,7 +37,7 @@ COARSEST_GMRES = 1
 
 EXPORTED = [
     "amamg_default_params", "amamg_query_bytes", "amamg_setup", "amamg_solve", "amamg_apply_D",
-    "amamg_apply_Ddag", "amamg_cgnr",
+    "amamg_apply_Ddag", "amamg_cgnr", "amamg_coarsest_apply",
     "amamg_apply_P", "amamg_apply_PH", "amamg_apply_coarse", "amamg_smooth", "amamg_coarsest_solve",
     "amamg_vcycle", "amamg_vcycle_noalloc", "amamg_selftest_sync_timeout", "amamg_sync_status", "amamg_export_structure", "amamg_level_info", "amamg_export_P", "amamg_export_coarse",
     "amamg_profile_enable", "amamg_profile_reset", "amamg_profile_get", "amamg_launch_count",
@@ -90,6 +90,7 @@ def _load() -> ctypes.CDLL:
         "amamg_apply_coarse": ([vp, ci, vp, vp, ci, ci, vp], ci),
         "amamg_smooth": ([vp, ci, vp, vp, ci, ci, ci, vp], ci),
         "amamg_coarsest_solve": ([vp, vp, vp, ci, vp], ci),
+        "amamg_coarsest_apply": ([vp, vp, vp, ci, ci, vp], ci),
         "amamg_vcycle": ([vp, vp, vp, ci, ci, vp], ci),
         "amamg_vcycle_noalloc": ([vp, vp, vp, ci, ci, vp], ci),
         "amamg_selftest_sync_timeout": ([vp, ci, ci, vp], ci),
@@ -310,6 +311,13 @@ def smooth(hier: Hierarchy, level: int, r, e, sweeps: int, stream=None):
 def coarsest_solve(hier: Hierarchy, r, e, stream=None):
     R = int(r.shape[0])
     hier._check(_lib.amamg_coarsest_solve(hier.h, _ptr(r), _ptr(e), R, _stream(stream)), "amamg_coarsest_solve")
+
+
+def coarsest_apply(hier: Hierarchy, r, e, stream=None):
+    """amamg_coarsest_apply in the precision of r (complex128 or complex64)."""
+    R = int(r.shape[0])
+    hier._check(_lib.amamg_coarsest_apply(hier.h, _ptr(r), _ptr(e), R, _prec(r), _stream(stream)),
+                "amamg_coarsest_apply")
 
 
 def vcycle(hier: Hierarchy, r, e, stream=None):

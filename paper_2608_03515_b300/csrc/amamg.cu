@@ -586,6 +586,11 @@ int vcycle_coarsest(amamg_ctx* h, const double2* r, double2* e, int R, cudaStrea
 int vcycle_coarsest(amamg_ctx* h, const float2* r, float2* e, int R, cudaStream_t st) {
   if (h->prm.coarsest == AMAMG_COARSEST_GMRES) return op_coarsest_gmres<float>(h, r, e, R, st);
   const double bytes = (double)h->nd * h->nd * 8.0 + (double)R * 2 * h->nd * 8.0;
+  if (h->tc_ok && coarsest_tc_possible(h->nd, R))
+    // many right-hand sides: a dense contraction, on the tensor cores (TF32 in, FP32 accumulate)
+    return launch(h, "coarsest_mma_tf32", bytes, st, [&] {
+      return launch_coarsest_tc(h->Ainv32, r, e, h->nd, R, h->tc_bop, reinterpret_cast<int*>(h->d_sync + 2), st);
+    }, (double)h->nd * h->nd * 8.0 * R);
   return launch(h, "coarsest_gemv_f32", bytes, st,
                 [&] { return launch_dense_gemv32(h->Ainv32, r, e, h->nd, R, st); },
                 (double)h->nd * h->nd * 8.0 * R);
@@ -997,7 +1002,7 @@ void free_all(amamg_ctx* h) {
   h->ws = nullptr; h->ev_in = h->ev_out = nullptr;
   dfree(h->U64); dfree(h->U64s); dfree(h->U32); dfree(h->Ainv); dfree(h->Ainv32); dfree(h->d_err); dfree(h->d_sync); dfree(h->d_owner_flags);
   dfree(h->d_smax); dfree(h->d_rowsum_skipped);
-  dfree(h->gm_V); dfree(h->gm_part); dfree(h->gm_st); dfree(h->gm_done);
+  dfree(h->gm_V); dfree(h->gm_part); dfree(h->gm_st); dfree(h->gm_done); dfree(h->tc_bop);
   dfree(h->V); dfree(h->Z64); dfree(h->Z32); dfree(h->v32); dfree(h->w); dfree(h->res);
   dfree(h->partial); dfree(h->d_h); dfree(h->d_inv); dfree(h->d_flag); dfree(h->d_y); dfree(h->d_tickets); dfree(h->d_npart);
   dfree(h->d_diag64); dfree(h->d_inv64); dfree(h->d_inv32);
@@ -1149,6 +1154,14 @@ int do_setup(amamg_ctx* h, const void* Uin, cudaStream_t st) {
   if (rc == AMAMG_OK) rc = dalloc(h, &h->Ainv32, nd * nd);
   if (rc == AMAMG_OK)
     rc = launch(h, "setup_cast", 0.0, st, [&] { return launch_cast<double2, float2>(h->Ainv, h->Ainv32, (long)(nd * nd), st); });
+  // tensor-core apply of Ainv32 to many right-hand sides (mixed V-cycle)
+  const char* tc_env = std::getenv("AMAMG_COARSEST_TC");
+  if (rc == AMAMG_OK && coarsest_tc_possible(h->nd, 8) && !(tc_env && std::strcmp(tc_env, "0") == 0) &&
+      coarsest_tc_init() == cudaSuccess) {
+    rc = dalloc(h, &h->tc_bop, coarsest_tc_bop_elems(h->nd));
+    h->tc_ok = rc == AMAMG_OK;
+  }
+  cudaGetLastError();
   int herr = 0;
   if (rc == AMAMG_OK && cudaMemcpyAsync(&herr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = AMAMG_ERR_CUDA;
   if (rc == AMAMG_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = AMAMG_ERR_CUDA;
@@ -1453,6 +1466,13 @@ int amamg_sync_status(amamg_handle h, void* stream) {
 int amamg_coarsest_solve(amamg_handle h, const void* r, void* e, int R, void* stream) {
   if (!h || !r || !e || R < 1) return AMAMG_ERR_INVALID_ARG;
   return vcycle_coarsest(h, (const double2*)r, (double2*)e, R, S(stream));
+}
+
+int amamg_coarsest_apply(amamg_handle h, const void* r, void* e, int R, int precision, void* stream) {
+  if (!h || !r || !e || R < 1) return AMAMG_ERR_INVALID_ARG;
+  if (precision == AMAMG_F64) return vcycle_coarsest(h, (const double2*)r, (double2*)e, R, S(stream));
+  if (precision == AMAMG_F32) return vcycle_coarsest(h, (const float2*)r, (float2*)e, R, S(stream));
+  return AMAMG_ERR_INVALID_ARG;
 }
 
 int amamg_vcycle(amamg_handle h, const void* r, void* e, int R, int precision, void* stream) {

@@ -131,6 +131,8 @@ struct amamg_ctx {
   int gm_blocks64 = 0, gm_blocks32 = 0;   // co-resident blocks of the GMRES kernel per precision
   double2* Ainv = nullptr;   // coarsest inverse, nd x nd row-major
   float2* Ainv32 = nullptr;  // its FP32 rounding, applied by the mixed-precision V-cycle
+  float* tc_bop = nullptr;   // tensor-core coarsest apply: its right-hand-side operand (scratch)
+  bool tc_ok = false;        // the tensor-core coarsest apply is available (AMAMG_COARSEST_TC=0: off)
   int nd = 0;
   int* d_err = nullptr;
   // coarse Gauss-Seidel synchronisation: [0] grid-barrier count, [1] its

@@ -11,6 +11,7 @@
 // (each input element is needed by 5 threads of adjacent rows/columns).
 #include <algorithm>
 #include <map>
+#include <type_traits>
 #include <mutex>
 #include <utility>
 
@@ -66,6 +67,84 @@ __device__ __forceinline__ void hop_sum(const Cin* __restrict__ p0, const Cin* _
   g = cmulc(U[n + s_xb], g);
   h0 += g;
   h1 += ci(g);
+}
+
+// The hop sum of one site from its neighbour values (the arithmetic of
+// hop_sum, same operations in the same order): f/b = forward/backward
+// neighbour, t/x = direction, 0/1 = spin; ut = U_0(n), utb = U_0(n - t),
+// ux = U_1(n), uxb = U_1(n - x).
+template <typename C>
+__device__ __forceinline__ void hop_vals(C ft0, C ft1, C bt0, C bt1, C fx0, C fx1, C bx0, C bx1, C ut, C utb, C ux,
+                                         C uxb, C& h0, C& h1) {
+  C g = cmul(ut, ft0 - ft1);
+  h0 = g;
+  h1 = -g;
+  g = cmulc(utb, bt0 + bt1);
+  h0 += g;
+  h1 += g;
+  g = cmul(ux, fx0 + ci(fx1));
+  h0 += g;
+  h1 -= ci(g);
+  g = cmulc(uxb, bx0 - ci(bx1));
+  h0 += g;
+  h1 += ci(g);
+}
+
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+
+// FP32 out = D in (or b - D in) with two x-adjacent sites (x even) per thread:
+// every pair of complex values a thread needs from its own row and the rows
+// t +- 1 comes in one 16-byte load, so a thread has twice the bytes in flight
+// of k_dslash with half the load instructions.  Per site the arithmetic of
+// k_dslash.  Nx must be even.
+__global__ void __launch_bounds__(256)
+k_dslash32x2(const float2* __restrict__ in, float2* __restrict__ out, const float2* __restrict__ b,
+             const float2* __restrict__ U, float diag_s, const float* __restrict__ diag_r, int Nt, int Nx) {
+  const float diag = diag_r ? diag_r[blockIdx.y] : diag_s;
+  const int n = Nt * Nx, hx = Nx >> 1;
+  const int pidx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pidx >= (n >> 1)) return;
+  const int t = pidx / hx, x = 2 * (pidx - t * hx);
+  const int s = t * Nx + x;
+  const int tf = (t + 1 == Nt) ? 0 : t + 1, tb = (t == 0) ? Nt - 1 : t - 1;
+  const int xf2 = (x + 2 == Nx) ? 0 : x + 2, xb = (x == 0) ? Nx - 1 : x - 1;
+  const size_t roff = (size_t)blockIdx.y * 2 * n;
+  const float2* p0 = in + roff;
+  const float2* p1 = p0 + n;
+  const float4 own0 = *reinterpret_cast<const float4*>(p0 + s), own1 = *reinterpret_cast<const float4*>(p1 + s);
+  const float4 ft0 = *reinterpret_cast<const float4*>(p0 + tf * Nx + x);
+  const float4 ft1 = *reinterpret_cast<const float4*>(p1 + tf * Nx + x);
+  const float4 bt0 = *reinterpret_cast<const float4*>(p0 + tb * Nx + x);
+  const float4 bt1 = *reinterpret_cast<const float4*>(p1 + tb * Nx + x);
+  const float2 fx0 = p0[t * Nx + xf2], fx1 = p1[t * Nx + xf2];
+  const float2 bx0 = p0[t * Nx + xb], bx1 = p1[t * Nx + xb];
+  const float4 ut = *reinterpret_cast<const float4*>(U + s);
+  const float4 utb = *reinterpret_cast<const float4*>(U + tb * Nx + x);
+  const float4 ux = *reinterpret_cast<const float4*>(U + n + s);
+  const float2 uxb = U[n + t * Nx + xb];
+  float2 h0, h1, y0, y1;
+  float4 o0, o1;
+  // site x: x-neighbours x + 1 (own pair, upper half) and x - 1
+  hop_vals(lo2(ft0), lo2(ft1), lo2(bt0), lo2(bt1), hi2(own0), hi2(own1), bx0, bx1, lo2(ut), lo2(utb), lo2(ux), uxb,
+           h0, h1);
+  y0 = diag * lo2(own0) - 0.5f * h0;
+  y1 = diag * lo2(own1) - 0.5f * h1;
+  o0.x = y0.x; o0.y = y0.y; o1.x = y1.x; o1.y = y1.y;
+  // site x + 1: x-neighbours x + 2 and x (own pair, lower half); backward link U_1(x)
+  hop_vals(hi2(ft0), hi2(ft1), hi2(bt0), hi2(bt1), fx0, fx1, lo2(own0), lo2(own1), hi2(ut), hi2(utb), hi2(ux),
+           lo2(ux), h0, h1);
+  y0 = diag * hi2(own0) - 0.5f * h0;
+  y1 = diag * hi2(own1) - 0.5f * h1;
+  o0.z = y0.x; o0.w = y0.y; o1.z = y1.x; o1.w = y1.y;
+  if (b) {
+    const float4 b0 = *reinterpret_cast<const float4*>(b + roff + s);
+    const float4 b1 = *reinterpret_cast<const float4*>(b + roff + n + s);
+    o0 = make_float4(b0.x - o0.x, b0.y - o0.y, b0.z - o0.z, b0.w - o0.w);
+    o1 = make_float4(b1.x - o1.x, b1.y - o1.y, b1.z - o1.z, b1.w - o1.w);
+  }
+  *reinterpret_cast<float4*>(out + roff + s) = o0;
+  *reinterpret_cast<float4*>(out + roff + n + s) = o1;
 }
 
 // out = D in   (b == nullptr)   or   out = b - D in   (residual form)
@@ -286,6 +365,13 @@ template <typename Cin, typename Cout, typename T>
 cudaError_t launch_dslash(const Cin* in, Cout* out, const Cout* b, const typename cplx<T>::type* U,
                           T diag, int Nt, int Nx, int R, cudaStream_t st, const T* diag_r) {
   const int n = Nt * Nx;
+  if constexpr (std::is_same<Cin, float2>::value && std::is_same<Cout, float2>::value) {
+    if ((Nx & 1) == 0) {
+      dim3 grid((n / 2 + 255) / 256, R);
+      k_dslash32x2<<<grid, 256, 0, st>>>(in, out, b, U, diag, diag_r, Nt, Nx);
+      return cudaGetLastError();
+    }
+  }
   dim3 grid((n + 255) / 256, R);
   k_dslash<Cin, Cout, T><<<grid, 256, 0, st>>>(in, out, b, U, diag, diag_r, Nt, Nx);
   return cudaGetLastError();

@@ -215,3 +215,14 @@ cudaError_t launch_coarsest_gmres(const typename cplx<T>::type* r, typename cplx
                                   const float* Bs, const Offsets& off, int Nt, int Nx, int R, int m, double tol,
                                   int max_cycles, typename cplx<T>::type* V, double2* part, GmresRhs* st,
                                   unsigned* sync, int* all_done, int max_blocks, cudaStream_t s);
+
+// coarsest_tc.cu: y_r = Ainv32 x_r for R >= 8 right-hand sides on the tensor
+// cores (tcgen05.mma kind::tf32, FP32 accumulation in tensor memory); nd a
+// multiple of 128.  bop: coarsest_tc_bop_elems(nd) floats of scratch; err: a
+// word set when a bounded wait ran out.  coarsest_tc_init: once per process
+// (opts the kernel in to its shared-memory size), outside stream capture.
+bool coarsest_tc_possible(int nd, int R);
+size_t coarsest_tc_bop_elems(int nd);
+cudaError_t coarsest_tc_init();
+cudaError_t launch_coarsest_tc(const float2* A, const float2* x, float2* y, int nd, int R, float* bop, int* err,
+                               cudaStream_t st);

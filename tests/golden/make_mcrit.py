@@ -3,9 +3,11 @@ field used by the tests and the benchmark, computed by the oracle's spectrum
 routine (m_crit = -min Re lambda(D at m0 = 0)) on the quenched Metropolis
 fields of the fixtures module (500 sweeps from a cold start).
 
-    python tests/golden/make_mcrit.py [--serving] [L ...]
+    python tests/golden/make_mcrit.py [--serving] [--tol T] [L ...]
         L ...      only these lattice sizes (default: all)
         --serving  also the eight serving fields per size
+        --tol T    ARPACK's relative tolerance (default 1e-6; the entries
+                   computed with another one record it)
 
 Only the oracle and the input fixtures are called.
 """
@@ -35,7 +37,7 @@ def key(L, beta, seed):
     return f"L{L}_b{beta:g}_s{seed}"
 
 
-def main(sizes=None, serving=False):
+def main(sizes=None, serving=False, tol=1e-6):
     table = json.load(open(OUT)) if os.path.exists(OUT) else {}
     for (L, beta, seed) in FIELDS + (SERVING if serving else []):
         if sizes and L not in sizes:
@@ -45,8 +47,10 @@ def main(sizes=None, serving=False):
             continue
         t0 = time.time()
         theta = fx.metropolis_u1(L, L, beta, SWEEPS, seed)
-        mc = spectrum.critical_mass(fx.links_from_angles(theta))
+        mc = spectrum.critical_mass(fx.links_from_angles(theta), tol=tol)
         entry = {"L": L, "beta": beta, "seed": seed, "sweeps": SWEEPS, "m_crit": mc}
+        if tol != 1e-6:
+            entry["arpack_tol"] = tol
         print(k, mc, f"{time.time() - t0:.1f}s", flush=True)
         # merge with what other runs wrote meanwhile
         table = json.load(open(OUT)) if os.path.exists(OUT) else {}
@@ -57,4 +61,5 @@ def main(sizes=None, serving=False):
 
 if __name__ == "__main__":
     args = sys.argv[1:]
-    main([int(a) for a in args if a.isdigit()] or None, serving="--serving" in args)
+    tol = float(args[args.index("--tol") + 1]) if "--tol" in args else 1e-6
+    main([int(a) for a in args if a.isdigit()] or None, serving="--serving" in args, tol=tol)
