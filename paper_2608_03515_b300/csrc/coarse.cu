@@ -66,6 +66,58 @@ k_coarse_apply(const typename cplx<T>::type* __restrict__ in, typename cplx<T>::
   o[n + v] = y1;
 }
 
+// The same for many right-hand sides: a thread keeps site v's blocks in
+// registers for RB right-hand sides at a time (blockIdx.y selects the group), so
+// each 2x2 block is loaded once per RB right-hand sides instead of once per
+// right-hand side.  Per right-hand side the arithmetic of k_coarse_apply.
+template <typename T, typename BT, int RB>
+__global__ void __launch_bounds__(256)
+k_coarse_apply_rb(const typename cplx<T>::type* __restrict__ in, typename cplx<T>::type* __restrict__ out,
+                  const typename cplx<T>::type* __restrict__ b, const BT* __restrict__ B,
+                  const float* __restrict__ Bs, Offsets off, int Nt, int Nx, int R) {
+  using C = typename cplx<T>::type;
+  const int n = Nt * Nx;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  const int r0 = blockIdx.y * RB;
+  const int nr = R - r0 < RB ? R - r0 : RB;
+  const int t = v / Nx, x = v - (v / Nx) * Nx;
+  C y0[RB], y1[RB];
+#pragma unroll
+  for (int j = 0; j < RB; ++j) y0[j] = y1[j] = czero<C>();
+  for (int k = 0; k < off.K; ++k) {
+    int tw = t + off.dt[k]; tw -= (tw >= Nt) ? Nt : 0;
+    int xw = x + off.dx[k]; xw -= (xw >= Nx) ? Nx : 0;
+    const int w = tw * Nx + xw;
+    const C b00 = b_load<T, BT>(B, Bs, k, 0, n, v), b01 = b_load<T, BT>(B, Bs, k, 1, n, v);
+    const C b10 = b_load<T, BT>(B, Bs, k, 2, n, v), b11 = b_load<T, BT>(B, Bs, k, 3, n, v);
+#pragma unroll
+    for (int j = 0; j < RB; ++j) {
+      if (j < nr) {
+        const C* i0 = in + (size_t)(r0 + j) * 2 * n;
+        const C x0 = i0[w], x1 = i0[n + w];
+        cmac(y0[j], b00, x0);
+        cmac(y0[j], b01, x1);
+        cmac(y1[j], b10, x0);
+        cmac(y1[j], b11, x1);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < RB; ++j) {
+    if (j < nr) {
+      const size_t roff = (size_t)(r0 + j) * 2 * n;
+      C a0 = y0[j], a1 = y1[j];
+      if (b) {
+        a0 = b[roff + v] - a0;
+        a1 = b[roff + n + v] - a1;
+      }
+      out[roff + v] = a0;
+      out[roff + n + v] = a1;
+    }
+  }
+}
+
 // Colour-major copies of a smoothed level's operator (built in setup): for
 // colour c, site j of the colour (colour_site / site_colour below, m = n / ncol
 // sites per colour) and off-diagonal offset k = 1..K-1:
@@ -769,6 +821,13 @@ cudaError_t launch_coarse_apply(const typename cplx<T>::type* in, typename cplx<
                                 const typename cplx<T>::type* b, const BT* B, const float* Bs,
                                 const Offsets& off, int Nt, int Nx, int R, cudaStream_t st) {
   const int n = Nt * Nx;
+  if (R >= 4) {
+    // blocks loaded once per group of right-hand sides
+    constexpr int RB = sizeof(T) == 8 ? 4 : 8;
+    dim3 grid((n + 255) / 256, (R + RB - 1) / RB);
+    k_coarse_apply_rb<T, BT, RB><<<grid, 256, 0, st>>>(in, out, b, B, Bs, off, Nt, Nx, R);
+    return cudaGetLastError();
+  }
   dim3 grid((n + 255) / 256, R);
   k_coarse_apply<T, BT><<<grid, 256, 0, st>>>(in, out, b, B, Bs, off, Nt, Nx);
   return cudaGetLastError();

@@ -17,9 +17,10 @@
 // (128 bytes of every row); each chunk of A (128 rows) and Bop (N rows) is
 // copied with cp.async into the canonical no-swizzle K-major layout (8-row x
 // 16-byte core matrices, 128 bytes each: core (r/8, c) at (r/8) SBO + c LBO,
-// LBO = 128 B, SBO = 1024 B), CM_STAGES chunks in flight.  Thread 0 issues the
-// four K = 8 MMAs of a chunk and commits them to the chunk's mbarrier, which the
-// threads wait on before refilling that stage.  All waits are bounded; on a
+// LBO = 128 B, SBO = 1024 B), up to CM_STAGES stages with S - 2 chunks in
+// flight ahead of the one being multiplied.  Thread 0 issues the four K = 8
+// MMAs of a chunk and commits them to the chunk's mbarrier, which the threads
+// wait on before refilling that stage two chunks later.  All waits are bounded; on a
 // time-out the kernel records it, lets its copies finish, frees its tensor
 // memory and returns.
 #include "context.h"
@@ -29,7 +30,8 @@ namespace {
 constexpr int CM_THREADS = 256;
 constexpr int CM_BM = 128;              // rows per CTA (MMA M)
 constexpr int CM_BK = 32;               // floats of K per stage
-constexpr int CM_STAGES = 4;
+constexpr int CM_STAGES = 6;            // at most; fewer when a stage is large (smem budget CM_SMEM)
+constexpr int CM_SMEM = 200 * 1024;
 constexpr unsigned CM_SPIN_LIMIT = 1u << 24;
 constexpr uint32_t CM_LBO = 128, CM_SBO = 1024;
 
@@ -60,6 +62,13 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// wait until at most n (0..3, clamped) of this thread's newest groups are pending
+__device__ __forceinline__ void cp_async_wait_n(int n) {
+  if (n >= 3) cp_async_wait<3>();
+  else if (n == 2) cp_async_wait<2>();
+  else if (n == 1) cp_async_wait<1>();
+  else cp_async_wait<0>();
+}
 
 __device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(addr), "r"(count) : "memory");
@@ -129,7 +138,7 @@ __global__ void k_coarsest_bop(const float2* __restrict__ x, float4* __restrict_
 
 __global__ void __launch_bounds__(CM_THREADS, 1)
 k_coarsest_tc(const float* __restrict__ A, const float* __restrict__ Bop, float2* __restrict__ y, int nd, int R,
-              int Rp, uint32_t tmem_cols, int* __restrict__ err) {
+              int Rp, uint32_t tmem_cols, int S, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint64_t mbar[CM_STAGES];
   __shared__ uint32_t tmem_base;
@@ -146,7 +155,7 @@ k_coarsest_tc(const float* __restrict__ A, const float* __restrict__ Bop, float2
 
   if (tid == 0) {
     failed = 0;
-    for (int s = 0; s < CM_STAGES; ++s) mbar_init(smem_u32(&mbar[s]), 1);
+    for (int s = 0; s < S; ++s) mbar_init(smem_u32(&mbar[s]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
@@ -175,17 +184,19 @@ k_coarsest_tc(const float* __restrict__ A, const float* __restrict__ Bop, float2
     }
   };
 
-#pragma unroll
-  for (int s = 0; s < CM_STAGES - 1; ++s) {
-    if (s < nk) load_stage(s, s);
+  // S stages, P = S - 2 chunks prefetched ahead: a refill goes to the stage
+  // whose MMAs were issued two chunks earlier, so it rarely waits for them
+  const int P = S - 2;
+  for (int c = 0; c < P; ++c) {
+    if (c < nk) load_stage(c, c);
     cp_async_commit();
   }
   const uint32_t idesc = idesc_tf32(CM_BM, N);
   for (int kt = 0; kt < nk; ++kt) {
-    const int s = kt % CM_STAGES;
-    cp_async_wait<CM_STAGES - 2>();                      // chunk kt has landed (this thread's copies)
+    const int s = kt % S;
+    cp_async_wait_n(P - 1);                              // at most P - 1 newer groups pending: chunk kt landed
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();                                     // ... and every thread's
+    __syncthreads();                                     // ... for every thread's copies
     if (tid == 0) {
       tc_fence_after();
       const uint32_t sa = sbase + s * stage_bytes, sb = sa + a_bytes;
@@ -195,11 +206,11 @@ k_coarsest_tc(const float* __restrict__ A, const float* __restrict__ Bop, float2
                     (kt > 0 || k8 > 0) ? 1u : 0u);
       tc_commit(smem_u32(&mbar[s]));
     }
-    // refill the stage read at kt - 1 with chunk kt + STAGES - 1 once its MMAs are done
-    const int next = kt + CM_STAGES - 1;
+    // chunk kt + P goes to the stage of chunk kt - 2 once that chunk's MMAs are done
+    const int next = kt + P;
     if (next < nk) {
-      const int sn = next % CM_STAGES;
-      if (kt >= 1 && !mbar_wait(smem_u32(&mbar[sn]), (uint32_t)(((kt - 1) / CM_STAGES) & 1))) failed = 1;
+      const int sn = next % S;
+      if (kt >= 2 && !mbar_wait(smem_u32(&mbar[sn]), (uint32_t)(((kt - 2) / S) & 1))) failed = 1;
       __syncthreads();
       if (failed) break;
       load_stage(next, sn);
@@ -207,8 +218,7 @@ k_coarsest_tc(const float* __restrict__ A, const float* __restrict__ Bop, float2
     cp_async_commit();
   }
   // the last chunk's MMAs (committed to its stage's barrier) end the accumulation
-  if (!failed && !mbar_wait(smem_u32(&mbar[(nk - 1) % CM_STAGES]), (uint32_t)(((nk - 1) / CM_STAGES) & 1)))
-    failed = 1;
+  if (!failed && !mbar_wait(smem_u32(&mbar[(nk - 1) % S]), (uint32_t)(((nk - 1) / S) & 1))) failed = 1;
   cp_async_wait_all();
   __syncthreads();
   tc_fence_after();
@@ -236,9 +246,15 @@ k_coarsest_tc(const float* __restrict__ A, const float* __restrict__ Bop, float2
 
 bool coarsest_tc_possible(int nd, int R) { return nd % CM_BM == 0 && nd >= CM_BM && R >= 8; }
 
+// stages for N columns of Bop: as many as fit CM_SMEM, at most CM_STAGES (at least 3)
+static int tc_stages(int N) {
+  const int stage = CM_BM * CM_BK * 4 + N * CM_BK * 4;
+  const int S = CM_SMEM / stage;
+  return S > CM_STAGES ? CM_STAGES : (S < 3 ? 3 : S);
+}
+
 cudaError_t coarsest_tc_init() {
-  const int smem = CM_STAGES * (CM_BM * CM_BK * 4 + 256 * CM_BK * 4);
-  return cudaFuncSetAttribute(k_coarsest_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return cudaFuncSetAttribute(k_coarsest_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, CM_SMEM);
 }
 
 size_t coarsest_tc_bop_elems(int nd) { return (size_t)2 * 128 * 2 * nd; }   // floats for up to 128 RHS per launch
@@ -261,9 +277,10 @@ cudaError_t launch_coarsest_tc(const float2* A, const float2* x, float2* y, int 
         x + (size_t)r0 * nd, reinterpret_cast<float4*>(bop), nd, Rc, Rp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t smem = (size_t)CM_STAGES * (CM_BM * CM_BK * 4 + (size_t)N * CM_BK * 4);
+    const int S = tc_stages(N);
+    const size_t smem = (size_t)S * (CM_BM * CM_BK * 4 + (size_t)N * CM_BK * 4);
     k_coarsest_tc<<<nd / CM_BM, CM_THREADS, smem, st>>>(reinterpret_cast<const float*>(A), bop, y + (size_t)r0 * nd,
-                                                       nd, Rc, Rp, cols, err);
+                                                       nd, Rc, Rp, cols, S, err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

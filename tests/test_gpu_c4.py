@@ -1,0 +1,67 @@
+"""The many-right-hand-side workload: 64 Gaussian right-hand sides on the
+1024^2 quenched U(1) field at beta = 12 (seed 5), m0 = m_crit + 0.005, three
+levels with tile sides 4 then 4 (coarsest 64^2, 8192 unknowns, FP64 inverse
+applied on the tensor cores in the mixed V-cycle), mixed precision, FGMRES(30)
+to 1e-10.  Every right-hand side reaches the tolerance; the first four are
+checked against the oracle's FP64 solves (tests/golden/c4_oracle.json):
+outer iteration counts within 10 % and the solution at the sampled sites
+within the conditioning bound of two 1e-10 solves."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import wilson as W
+from paper_2608_03515_b300 import fixtures as fx
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2608_03515_b300 import build  # noqa: E402
+
+build.build()
+from paper_2608_03515_b300 import amamg as A  # noqa: E402
+
+DEV = torch.device("cuda:0")
+HERE = os.path.dirname(os.path.abspath(__file__))
+KEY = "L1024_b12_s5"
+
+
+def test_c4_many_rhs_mixed():
+    table = json.load(open(os.path.join(HERE, "golden", "mcrit.json")))
+    if KEY not in table:
+        pytest.skip("critical mass of the 1024^2 beta = 12 field not tabulated")
+    L, R, dm = 1024, 64, 0.005
+    m0 = table[KEY]["m_crit"] + dm
+    Uh = fx.links_from_angles(fx.metropolis_u1(L, L, 12.0, 500, 5))
+    psi = fx.gaussian_rhs(R, L, L, 6)
+    hier = A.setup(torch.from_numpy(Uh).to(DEV), m0, A.make_params([4, 4], precision=A.SOLVE_MIXED))
+    x = torch.empty(psi.shape, dtype=torch.complex128, device=DEV)
+    info = A.solve(hier, torch.from_numpy(psi).to(DEV), x)
+    assert all(i.status == A.OK and i.true_relres <= 1e-10 for i in info)
+    xs = x[:4].cpu().numpy()
+    D = W.dirac_matrix(Uh, m0)
+    for k in range(4):
+        b = W.to_flat(psi[k])
+        assert np.linalg.norm(b - D @ W.to_flat(xs[k])) / np.linalg.norm(b) <= 1e-10
+    gold = os.path.join(HERE, "golden", "c4_oracle.json")
+    if not os.path.exists(gold):
+        pytest.skip("oracle solves of the 1024^2 workload not written yet")
+    g = json.load(open(gold))
+    assert abs(g["m0"] - m0) <= 1e-15
+    for row in g["solves"]:
+        k = row["rhs"]
+        assert row["converged"]
+        assert abs(info[k].iterations - row["iterations"]) <= max(1, 0.1 * row["iterations"]), (k, info[k].iterations,
+                                                                                              row["iterations"])
+        want = np.array([[complex(*v) for v in site] for site in row["x_at_sites"]])
+        got = np.array([[xs[k][a, t, xx] for a in range(2)] for (t, xx) in g["sites"]])
+        bound = 2e-9 * np.linalg.norm(psi[k]) / dm
+        assert np.max(np.abs(got - want)) <= bound
+        print(f"c4 rhs {k}: {info[k].iterations} iterations (oracle {row['iterations']}), sampled max |dx| "
+              f"{np.max(np.abs(got - want)):.2e} (|x| {row['x_norm']:.3e})")
+    hier.destroy()
