@@ -77,6 +77,13 @@ typedef struct amamg_ctx* amamg_handle;
 #define AMAMG_COARSEST_GMRES  1      /* the paper's setting (Sec. 5): unpreconditioned GMRES(30) from a
                                         zero start to relative residual 0.1, on the device */
 
+/* arithmetic of the outer solver's Gram-Schmidt (inner products, updates, norms) */
+#define AMAMG_GS_FP64 0              /* FP64 (default) */
+#define AMAMG_GS_DF64 1              /* double-float: pairs of floats with about 48 significant bits, formed
+                                        with error-free transformations on the FP32 pipe; the basis is kept
+                                        in that form; mixed precision only.  A faster alternative on GPUs
+                                        with a narrow FP64 pipe; the true residual stays FP64 */
+
 /* which basket a border site takes its formula from ("the first aggregate it
  * was assigned to", Sec. 4.1) */
 #define AMAMG_OWNER_TILE      0      /* the basket of the tile containing the site, W(t/a, x/a) (default) */
@@ -101,6 +108,7 @@ typedef struct {
                                         GMRES no dense inverse is formed (no size limit on the coarsest
                                         level) and the V-cycle is no longer a fixed linear map (the
                                         outer FGMRES is flexible) */
+    int    gs_arith;                 /* AMAMG_GS_FP64 (default) or AMAMG_GS_DF64 (with AMAMG_SOLVE_MIXED) */
 } amamg_params;
 
 typedef struct {

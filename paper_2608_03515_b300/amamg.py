@@ -34,6 +34,8 @@ OWNER_TILE = 0
 OWNER_FIRST_LEX = 1
 COARSEST_DIRECT = 0
 COARSEST_GMRES = 1
+GS_FP64 = 0
+GS_DF64 = 1
 
 EXPORTED = [
     "amamg_default_params", "amamg_query_bytes", "amamg_setup", "amamg_solve", "amamg_apply_D",
@@ -59,6 +61,7 @@ class Params(ctypes.Structure):
         ("normalization", ctypes.c_int),
         ("edge_owner", ctypes.c_int),
         ("coarsest", ctypes.c_int),
+        ("gs_arith", ctypes.c_int),
     ]
 
 
@@ -169,11 +172,13 @@ def default_params() -> Params:
 
 def make_params(aggs: Sequence[int], precision: int = SOLVE_FP64, restart: int = 30, max_iter: int = 3000,
                 post_smooth: int = 2, tol: float = 1e-10, spin_split: bool = False,
-                normalization: str = "none", ownership: str = "tile", coarsest: str = "direct") -> Params:
+                normalization: str = "none", ownership: str = "tile", coarsest: str = "direct",
+                gs: str = "fp64") -> Params:
     """Parameters of amamg_setup; normalization "none" | "rowsum" and ownership
     "tile" | "first_lex" name the readings the oracle's build_hierarchy takes;
     coarsest "direct" | "gmres" the coarsest solver (the oracle's vcycle
-    coarsest="lu" | "gmres")."""
+    coarsest="lu" | "gmres"); gs "fp64" | "df64" the outer Gram-Schmidt's
+    arithmetic (df64 with mixed precision only)."""
     p = default_params()
     p.nlevels = len(aggs) + 1
     for i, a in enumerate(aggs):
@@ -187,6 +192,7 @@ def make_params(aggs: Sequence[int], precision: int = SOLVE_FP64, restart: int =
     p.normalization = {"none": NORM_NONE, "rowsum": NORM_ROWSUM}[normalization]
     p.edge_owner = {"tile": OWNER_TILE, "first_lex": OWNER_FIRST_LEX}[ownership]
     p.coarsest = {"direct": COARSEST_DIRECT, "gmres": COARSEST_GMRES}[coarsest]
+    p.gs_arith = {"fp64": GS_FP64, "df64": GS_DF64}[gs]
     return p
 
 

@@ -289,7 +289,7 @@ int ensure_solver_ws(amamg_ctx* h, int R) {
   const int m = h->prm.restart;
   if (R <= h->Rsolve && m <= h->mcap) return AMAMG_OK;
   clear_graphs(h);
-  dfree(h->V); dfree(h->Z64); dfree(h->Z32); dfree(h->v32); dfree(h->w); dfree(h->res);
+  dfree(h->V); dfree(h->Z64); dfree(h->Z32); dfree(h->v32); dfree(h->w); dfree(h->res); dfree(h->wdf); dfree(h->df_part);
   dfree(h->partial); dfree(h->d_h); dfree(h->d_inv); dfree(h->d_flag); dfree(h->d_y); dfree(h->d_tickets); dfree(h->d_npart);
   dfree(h->d_diag64); dfree(h->d_inv64); dfree(h->d_inv32);
   if (h->h_h) cudaFreeHost(h->h_h);
@@ -305,6 +305,10 @@ int ensure_solver_ws(amamg_ctx* h, int R) {
   }
   CKS(dalloc(h, &h->w, (size_t)R * len));
   CKS(dalloc(h, &h->res, (size_t)R * len));
+  if (h->prm.gs_arith == AMAMG_GS_DF64) {
+    CKS(dalloc(h, &h->wdf, (size_t)R * len));
+    CKS(dalloc(h, &h->df_part, (size_t)R * (2 * (m + 2) * df_partial_blocks((long)len) + df_norm_blocks((long)len))));
+  }
   h->partial_elems = (size_t)R * (m + 2) * dot_blocks((long)len);
   CKS(dalloc(h, &h->partial, h->partial_elems));
   CKS(dalloc(h, &h->d_h, (size_t)R * 3 * (m + 2)));
@@ -662,7 +666,7 @@ int arnoldi_step(amamg_ctx* h, int j, int R, cudaStream_t st) {
     float2* zj = h->Z32 + (size_t)j * vi;
     // v_j in FP32: cast here for j = 0; for j >= 1 the previous step's
     // normalisation wrote it
-    if (j == 0)
+    if (j == 0 && h->prm.gs_arith != AMAMG_GS_DF64)   // (double-float: the cycle start wrote it)
       CKS(launch(h, "cast_f64_f32", (double)R * len * 24.0, st,
                  [&] { return launch_cast<double2, float2>(vj, h->v32, (long)R * len, st); }));
     CKS(vcycle_from<float>(h, 0, h->v32, zj, handle_vecs<float>(h), R, st));
@@ -685,6 +689,35 @@ int arnoldi_step(amamg_ctx* h, int j, int R, cudaStream_t st) {
   const int nrm_off = 2 * (m + 2);
   unsigned* tk_dots = h->d_tickets;
   unsigned* tk_norm = h->d_tickets + (size_t)R * (m + 2);
+  if (h->prm.gs_arith == AMAMG_GS_DF64) {
+    // the same four Gram-Schmidt steps in double-float arithmetic on the
+    // double-float basis, then v_{j+1} = w / ||w|| and its FP32 rounding
+    const double dfb = (double)R * len * 16.0;
+    CKS(launch(h, "to_df", (double)R * len * 32.0, st, [&] { return launch_to_df(h->w, h->wdf, (long)R * len, st); }));
+    double* dpart = h->df_part;
+    double* npart = h->df_part + (size_t)R * 2 * (m + 2) * df_partial_blocks(len);
+    CKS(launch(h, "gs_dots_df", dfb * (J + 1), st, [&] {
+      return launch_dots_df(h->V, vi, vr, h->wdf, vr, len, J, R, true, nullptr, dpart, 2 * (m + 2), tk_dots, d_h1,
+                            ldh, 0, st);
+    }, (double)R * len * 8.0 * (J + 1)));
+    CKS(launch(h, "gs_update_norm_df", dfb * (J + 2), st, [&] {
+      return launch_axpy_norm_df(h->wdf, vr, h->V, vi, vr, d_h1, ldh, J, len, R, nullptr, npart, tk_norm, d_h1, ldh,
+                                 nrm_off, h->d_inv, h->d_flag, J, 0.5, 2, st);
+    }, (double)R * len * 8.0 * (J + 1)));
+    CKS(launch(h, "gs2_dots_gated_df", dfb * (J + 1), st, [&] {
+      return launch_dots_df(h->V, vi, vr, h->wdf, vr, len, J, R, false, h->d_flag, dpart, 2 * (m + 2), tk_dots, d_h1,
+                            ldh, m + 2, st);
+    }, (double)R * len * 8.0 * J));
+    CKS(launch(h, "gs2_update_norm_gated_df", dfb * (J + 2), st, [&] {
+      return launch_axpy_norm_df(h->wdf, vr, h->V, vi, vr, d_h1 + (m + 2), ldh, J, len, R, h->d_flag, npart, tk_norm,
+                                 d_h1, ldh, nrm_off, h->d_inv, nullptr, 0, 0.0, 1, st);
+    }, (double)R * len * 8.0 * (J + 1)));
+    CKS(launch(h, "scale_copy", (double)R * len * 40.0, st, [&] {
+      return launch_scale_copy_df(h->V + (size_t)(j + 1) * vi, h->v32, vr, h->wdf, nullptr, vr, h->d_inv, len, R, st);
+    }));
+    CK(cudaMemcpyAsync(h->h_h, h->d_h, sizeof(double2) * R * ldh, cudaMemcpyDeviceToHost, st));
+    return AMAMG_OK;
+  }
   CKS(launch(h, "gs_dots", (double)R * len * 16.0 * (J + 1), st, [&] {
     return launch_dots_fused(h->V, vi, vr, h->w, vr, len, J, R, h->partial, true, nullptr, tk_dots, d_h1, ldh, 0, st);
   }, (double)R * len * 8.0 * (J + 1)));
@@ -803,9 +836,14 @@ int fgmres_cycle(amamg_ctx* h, const double2* b, double2* x, int R, cudaStream_t
   if (!left) return AMAMG_OK;
   // V[0] = r / beta (zero for right-hand sides that are not building: their inv is
   // set by the norm of a zero or converged residual and they are ignored below)
-  CKS(launch(h, "scale_copy", (double)R * len * 32.0, st, [&] {
-    return launch_scale_copy<double2>(h->V, vr, h->res, vr, h->d_inv, len, R, st);
-  }));
+  if (h->prm.gs_arith == AMAMG_GS_DF64)
+    CKS(launch(h, "scale_copy", (double)R * len * 40.0, st, [&] {
+      return launch_scale_copy_df(h->V, h->v32, vr, nullptr, h->res, vr, h->d_inv, len, R, st);
+    }));
+  else
+    CKS(launch(h, "scale_copy", (double)R * len * 32.0, st, [&] {
+      return launch_scale_copy<double2>(h->V, vr, h->res, vr, h->d_inv, len, R, st);
+    }));
   int j = 0;
   for (; j < m; ++j) {
     CKS(run_step(h, j, R, st));
@@ -976,6 +1014,14 @@ int check_params(const amamg_params* p, int Nt, int Nx, std::string* why) {
     if (l >= 1 && (nt % 4 || nx % 4)) { *why = "smoothed coarse levels need extents divisible by 4"; return AMAMG_ERR_INVALID_ARG; }
     nt /= a; nx /= a;
   }
+  if (p->gs_arith != AMAMG_GS_FP64 && p->gs_arith != AMAMG_GS_DF64) {
+    *why = "gs_arith must be AMAMG_GS_FP64 or AMAMG_GS_DF64";
+    return AMAMG_ERR_INVALID_ARG;
+  }
+  if (p->gs_arith == AMAMG_GS_DF64 && p->precision != AMAMG_SOLVE_MIXED) {
+    *why = "AMAMG_GS_DF64 needs AMAMG_SOLVE_MIXED";
+    return AMAMG_ERR_INVALID_ARG;
+  }
   if (p->coarsest != AMAMG_COARSEST_DIRECT && p->coarsest != AMAMG_COARSEST_GMRES) {
     *why = "coarsest must be AMAMG_COARSEST_DIRECT or AMAMG_COARSEST_GMRES";
     return AMAMG_ERR_INVALID_ARG;
@@ -1003,7 +1049,7 @@ void free_all(amamg_ctx* h) {
   dfree(h->U64); dfree(h->U64s); dfree(h->U32); dfree(h->Ainv); dfree(h->Ainv32); dfree(h->d_err); dfree(h->d_sync); dfree(h->d_owner_flags);
   dfree(h->d_smax); dfree(h->d_rowsum_skipped);
   dfree(h->gm_V); dfree(h->gm_part); dfree(h->gm_st); dfree(h->gm_done); dfree(h->tc_bop);
-  dfree(h->V); dfree(h->Z64); dfree(h->Z32); dfree(h->v32); dfree(h->w); dfree(h->res);
+  dfree(h->V); dfree(h->Z64); dfree(h->Z32); dfree(h->v32); dfree(h->w); dfree(h->res); dfree(h->wdf); dfree(h->df_part);
   dfree(h->partial); dfree(h->d_h); dfree(h->d_inv); dfree(h->d_flag); dfree(h->d_y); dfree(h->d_tickets); dfree(h->d_npart);
   dfree(h->d_diag64); dfree(h->d_inv64); dfree(h->d_inv32);
   if (h->h_h) cudaFreeHost(h->h_h);
@@ -1158,7 +1204,7 @@ int do_setup(amamg_ctx* h, const void* Uin, cudaStream_t st) {
   const char* tc_env = std::getenv("AMAMG_COARSEST_TC");
   if (rc == AMAMG_OK && coarsest_tc_possible(h->nd, 8) && !(tc_env && std::strcmp(tc_env, "0") == 0) &&
       coarsest_tc_init() == cudaSuccess) {
-    rc = dalloc(h, &h->tc_bop, coarsest_tc_bop_elems(h->nd));
+    rc = dalloc(h, &h->tc_bop, coarsest_tc_scratch_elems(h->nd));
     h->tc_ok = rc == AMAMG_OK;
   }
   cudaGetLastError();

@@ -13,16 +13,18 @@
 // (x_im, x_re); Rp = R rounded up to a multiple of 8 (rows of padding are 0), so
 // N = 2 Rp is a multiple of 16 (<= 256).  y_c[i] = (D[i][c], D[i][Rp + c]).
 //
-// One CTA per 128 rows (M = 128, cta_group::1).  K runs in chunks of 32 floats
-// (128 bytes of every row); each chunk of A (128 rows) and Bop (N rows) is
-// copied with cp.async into the canonical no-swizzle K-major layout (8-row x
-// 16-byte core matrices, 128 bytes each: core (r/8, c) at (r/8) SBO + c LBO,
-// LBO = 128 B, SBO = 1024 B), up to CM_STAGES stages with S - 2 chunks in
-// flight ahead of the one being multiplied.  Thread 0 issues the four K = 8
-// MMAs of a chunk and commits them to the chunk's mbarrier, which the threads
-// wait on before refilling that stage two chunks later.  All waits are bounded; on a
-// time-out the kernel records it, lets its copies finish, frees its tensor
-// memory and returns.
+// Tiles are moved by TMA (cp.async.bulk.tensor, 2D boxes of 32 floats x rows,
+// 128-byte swizzle, which the shared-memory descriptors of the MMAs name):
+// one CTA per 128 rows (M = 128, cta_group::1) and per slice of K (small
+// levels split K so that every SM has a CTA; the slices' FP32 partials are
+// added in slice order by a second kernel).  One thread drives the pipeline:
+// TMA loads of a chunk of 32 floats of every row of A and of Bop into a stage
+// (its full barrier counts the bytes), the four K = 8 MMAs of a landed chunk,
+// their commit to the stage's empty barrier, which the next load into that
+// stage waits for.  All waits are bounded; on a time-out the kernel records
+// it, frees its tensor memory and returns.
+#include <cuda.h>
+
 #include "context.h"
 
 namespace {
@@ -136,26 +138,62 @@ __global__ void k_coarsest_bop(const float2* __restrict__ x, float4* __restrict_
   }
 }
 
+// 2D TMA load of a box at (x inner, y outer) into shared memory, completing
+// on mbarrier mbar (transaction bytes)
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// shared-memory matrix descriptor for the 128-byte swizzled K-major layout that
+// TMA writes with CU_TENSOR_MAP_SWIZZLE_128B (rows of 128 bytes, 8-row atoms of
+// 1024 bytes: stride byte offset 1024, leading byte offset unused)
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;                               // SWIZZLE_128B
+  return d;
+}
+
+// One CTA per 128 rows and K slice (blockIdx.y of gridDim.y slices).  Thread 0
+// drives the pipeline: TMA loads of the A and Bop chunks into stage s (full[s],
+// with the stage's byte count), MMAs of a landed chunk, commit to empty[s],
+// which the next load into that stage waits for.  Out: y directly (one slice)
+// or the slice's FP32 partial of D (part[slice][row][column], N columns).
 __global__ void __launch_bounds__(CM_THREADS, 1)
-k_coarsest_tc(const float* __restrict__ A, const float* __restrict__ Bop, float2* __restrict__ y, int nd, int R,
-              int Rp, uint32_t tmem_cols, int S, int* __restrict__ err) {
-  extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ uint64_t mbar[CM_STAGES];
+k_coarsest_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+              float2* __restrict__ y, float* __restrict__ part, int nd, int R, int Rp, uint32_t tmem_cols, int S,
+              int* __restrict__ err) {
+  extern __shared__ unsigned char sm_raw[];
+  __shared__ uint64_t full[CM_STAGES], empty[CM_STAGES];
   __shared__ uint32_t tmem_base;
   __shared__ int failed;
   const int N = 2 * Rp;
-  const int K = 2 * nd;                                  // floats per row
-  const int nk = K / CM_BK;
+  const int nk_all = (2 * nd) / CM_BK;
+  const int per = (nk_all + gridDim.y - 1) / gridDim.y;
+  const int kt0 = blockIdx.y * per;
+  const int nk = max(0, min(nk_all, kt0 + per) - kt0);
   const int row0 = blockIdx.x * CM_BM;
-  const uint32_t a_bytes = CM_BM * CM_BK * 4;            // 16 KB
+  const uint32_t a_bytes = CM_BM * CM_BK * 4;             // 16 KB
   const uint32_t b_bytes = (uint32_t)N * CM_BK * 4;
-  const uint32_t stage_bytes = a_bytes + b_bytes;
-  const uint32_t sbase = smem_u32(sm);
+  const uint32_t stage_bytes = a_bytes + b_bytes;        // a multiple of 1024
+  const uint32_t sbase = (smem_u32(sm_raw) + 1023u) & ~1023u;   // 1024-byte aligned stages (swizzle atoms)
   const int tid = threadIdx.x, warp = tid >> 5;
 
   if (tid == 0) {
     failed = 0;
-    for (int s = 0; s < S; ++s) mbar_init(smem_u32(&mbar[s]), 1);
+    for (int s = 0; s < S; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
@@ -169,70 +207,61 @@ k_coarsest_tc(const float* __restrict__ A, const float* __restrict__ Bop, float2
   tc_fence_after();
   const uint32_t dtmem = tmem_base;
 
-  // copies of chunk kt into stage s: A rows row0..row0+127, Bop rows 0..N-1,
-  // K floats [kt 32, kt 32 + 32), as 16-byte pieces (row r, piece c of 8)
-  auto load_stage = [&](int kt, int s) {
-    const uint32_t sa = sbase + s * stage_bytes, sb = sa + a_bytes;
-    const int k0 = kt * CM_BK;
-    for (int q = tid; q < CM_BM * 8; q += CM_THREADS) {
-      const int r = q >> 3, c = q & 7;
-      cp_async16(sa + (r >> 3) * CM_SBO + c * CM_LBO + (r & 7) * 16, A + (size_t)(row0 + r) * K + k0 + 4 * c);
-    }
-    for (int q = tid; q < N * 8; q += CM_THREADS) {
-      const int r = q >> 3, c = q & 7;
-      cp_async16(sb + (r >> 3) * CM_SBO + c * CM_LBO + (r & 7) * 16, Bop + (size_t)r * K + k0 + 4 * c);
-    }
-  };
-
-  // S stages, P = S - 2 chunks prefetched ahead: a refill goes to the stage
-  // whose MMAs were issued two chunks earlier, so it rarely waits for them
-  const int P = S - 2;
-  for (int c = 0; c < P; ++c) {
-    if (c < nk) load_stage(c, c);
-    cp_async_commit();
-  }
-  const uint32_t idesc = idesc_tf32(CM_BM, N);
-  for (int kt = 0; kt < nk; ++kt) {
-    const int s = kt % S;
-    cp_async_wait_n(P - 1);                              // at most P - 1 newer groups pending: chunk kt landed
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();                                     // ... for every thread's copies
-    if (tid == 0) {
+  if (tid == 0 && nk > 0) {
+    auto load = [&](int c, int st) {
+      const uint32_t sa = sbase + st * stage_bytes;
+      const uint32_t fb = smem_u32(&full[st]);
+      mbar_expect_tx(fb, stage_bytes);
+      tma_load_2d(sa, &mapA, (kt0 + c) * CM_BK, row0, fb);
+      tma_load_2d(sa + a_bytes, &mapB, (kt0 + c) * CM_BK, 0, fb);
+    };
+    const int P = S - 1;                                  // chunks in flight ahead of the one multiplied
+    for (int c = 0; c < P && c < nk; ++c) load(c, c);
+    const uint32_t idesc = idesc_tf32(CM_BM, N);
+    for (int kt = 0; kt < nk; ++kt) {
+      const int st = kt % S;
+      if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((kt / S) & 1))) { failed = 1; break; }
       tc_fence_after();
-      const uint32_t sa = sbase + s * stage_bytes, sb = sa + a_bytes;
+      const uint32_t sa = sbase + st * stage_bytes, sb = sa + a_bytes;
 #pragma unroll
-      for (int k8 = 0; k8 < CM_BK / 8; ++k8)             // K = 8 TF32 per MMA = two core matrices
-        tc_mma_tf32(dtmem, smem_desc(sa + k8 * 2 * CM_LBO), smem_desc(sb + k8 * 2 * CM_LBO), idesc,
+      for (int k8 = 0; k8 < CM_BK / 8; ++k8)              // K = 8 TF32 = 32 bytes of the 128-byte row
+        tc_mma_tf32(dtmem, smem_desc_sw128(sa + 32 * k8), smem_desc_sw128(sb + 32 * k8), idesc,
                     (kt > 0 || k8 > 0) ? 1u : 0u);
-      tc_commit(smem_u32(&mbar[s]));
+      tc_commit(smem_u32(&empty[st]));
+      const int next = kt + P;
+      if (next < nk) {
+        const int sn = next % S;
+        // the stage's previous chunk (next - S) must have been multiplied
+        if (next >= S && !mbar_wait(smem_u32(&empty[sn]), (uint32_t)(((next / S) - 1) & 1))) { failed = 1; break; }
+        load(next, sn);
+      }
     }
-    // chunk kt + P goes to the stage of chunk kt - 2 once that chunk's MMAs are done
-    const int next = kt + P;
-    if (next < nk) {
-      const int sn = next % S;
-      if (kt >= 2 && !mbar_wait(smem_u32(&mbar[sn]), (uint32_t)(((kt - 2) / S) & 1))) failed = 1;
-      __syncthreads();
-      if (failed) break;
-      load_stage(next, sn);
-    }
-    cp_async_commit();
+    // the last chunk's MMAs (committed to its stage's empty barrier) end the accumulation
+    if (!failed && !mbar_wait(smem_u32(&empty[(nk - 1) % S]), (uint32_t)(((nk - 1) / S) & 1))) failed = 1;
   }
-  // the last chunk's MMAs (committed to its stage's barrier) end the accumulation
-  if (!failed && !mbar_wait(smem_u32(&mbar[(nk - 1) % S]), (uint32_t)(((nk - 1) / S) & 1))) failed = 1;
-  cp_async_wait_all();
   __syncthreads();
   tc_fence_after();
-  if (!failed && warp < 4) {
-    // warp w reads TMEM lanes 32 w .. 32 w + 31 (rows of D); columns c and Rp + c
+  if (!failed && nk > 0 && warp < 4) {
+    // warp w reads TMEM lanes 32 w .. 32 w + 31 (rows of D)
     const int row = row0 + 32 * warp + (tid & 31);
     const uint32_t lane_base = dtmem + ((uint32_t)(32 * warp) << 16);
     for (int c0 = 0; c0 < Rp; c0 += 32) {
       float re[32], im[32];
       tc_ld32(lane_base + (uint32_t)c0, re);
       tc_ld32(lane_base + (uint32_t)(Rp + c0), im);
+      if (gridDim.y == 1) {
 #pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (c0 + j < R) y[(size_t)(c0 + j) * nd + row] = make_float2(re[j], im[j]);
+        for (int j = 0; j < 32; ++j)
+          if (c0 + j < R) y[(size_t)(c0 + j) * nd + row] = make_float2(re[j], im[j]);
+      } else {
+        float* pr = part + ((size_t)blockIdx.y * nd + row) * N;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (c0 + j < Rp) {
+            pr[c0 + j] = re[j];
+            pr[Rp + c0 + j] = im[j];
+          }
+      }
     }
   }
   if (failed && tid == 0) atomicExch(err, 1);
@@ -242,26 +271,105 @@ k_coarsest_tc(const float* __restrict__ A, const float* __restrict__ Bop, float2
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(dtmem), "r"(tmem_cols) : "memory");
 }
 
+// y_c[i] = sum over slices (in slice order) of (D[i][c], D[i][Rp + c])
+__global__ void k_coarsest_tc_reduce(const float* __restrict__ part, float2* __restrict__ y, int nd, int R, int Rp,
+                                     int slices) {
+  const long total = (long)R * nd;
+  const int N = 2 * Rp;
+  for (long g = (long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
+    const int c = (int)(g / nd), i = (int)(g - (long)c * nd);
+    float re = 0.f, im = 0.f;
+    for (int sl = 0; sl < slices; ++sl) {
+      const float* pr = part + ((size_t)sl * nd + i) * N;
+      re += pr[c];
+      im += pr[Rp + c];
+    }
+    y[(size_t)c * nd + i] = make_float2(re, im);
+  }
+}
+
 }  // namespace
 
 bool coarsest_tc_possible(int nd, int R) { return nd % CM_BM == 0 && nd >= CM_BM && R >= 8; }
 
+// K slices: enough CTAs for one wave over the SMs (at most 16 slices)
+static int tc_slices(int nd) {
+  int sms = 148, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                 cudaSuccess) {
+    cudaGetLastError();
+    sms = 148;
+  }
+  const int tiles = nd / CM_BM;
+  int s = sms / tiles;
+  s = s < 1 ? 1 : (s > 16 ? 16 : s);
+  const int nk = 2 * nd / CM_BK;
+  if (s > nk) s = nk;
+  const int per = (nk + s - 1) / s;                     // chunks per slice; every slice gets at least one
+  return (nk + per - 1) / per;
+}
+
+size_t coarsest_tc_scratch_elems(int nd) {
+  // Bop for up to 128 right-hand sides per launch, then the slices' partial D
+  return (size_t)2 * 128 * 2 * nd + (size_t)tc_slices(nd) * nd * 256;
+}
+
 // stages for N columns of Bop: as many as fit CM_SMEM, at most CM_STAGES (at least 3)
 static int tc_stages(int N) {
   const int stage = CM_BM * CM_BK * 4 + N * CM_BK * 4;
-  const int S = CM_SMEM / stage;
+  const int S = (CM_SMEM - 1024) / stage;
   return S > CM_STAGES ? CM_STAGES : (S < 3 ? 3 : S);
 }
 
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiled encode_fn();
+
 cudaError_t coarsest_tc_init() {
+  if (!encode_fn()) return cudaErrorNotSupported;       // no tensor-map encoder: the CUDA-core apply runs
   return cudaFuncSetAttribute(k_coarsest_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, CM_SMEM);
 }
 
-size_t coarsest_tc_bop_elems(int nd) { return (size_t)2 * 128 * 2 * nd; }   // floats for up to 128 RHS per launch
+static EncodeTiled encode_fn() {
+  static EncodeTiled fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+    cudaGetLastError();
+  }
+  return fn;
+}
 
-cudaError_t launch_coarsest_tc(const float2* A, const float2* x, float2* y, int nd, int R, float* bop, int* err,
+// row-major FP32 matrix rows x cols (cols contiguous), boxes of 32 x box_rows,
+// 128-byte swizzle
+static bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int box_rows) {
+  EncodeTiled fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)cols * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)CM_BK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+cudaError_t launch_coarsest_tc(const float2* A, const float2* x, float2* y, int nd, int R, float* scratch, int* err,
                                cudaStream_t st) {
   if (!coarsest_tc_possible(nd, R)) return cudaErrorInvalidValue;
+  float* bop = scratch;
+  float* part = scratch + (size_t)2 * 128 * 2 * nd;
+  const int slices = tc_slices(nd);
+  CUtensorMap mapA;
+  if (!make_map(&mapA, A, nd, 2 * nd, CM_BM)) return cudaErrorNotSupported;
   for (int r0 = 0; r0 < R; r0 += 128) {
     const int Rc = R - r0 < 128 ? R - r0 : 128;
     const int Rp = (Rc + 7) & ~7;
@@ -277,12 +385,21 @@ cudaError_t launch_coarsest_tc(const float2* A, const float2* x, float2* y, int 
         x + (size_t)r0 * nd, reinterpret_cast<float4*>(bop), nd, Rc, Rp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    CUtensorMap mapB;
+    if (!make_map(&mapB, bop, N, 2 * nd, N)) return cudaErrorNotSupported;
     const int S = tc_stages(N);
-    const size_t smem = (size_t)S * (CM_BM * CM_BK * 4 + (size_t)N * CM_BK * 4);
-    k_coarsest_tc<<<nd / CM_BM, CM_THREADS, smem, st>>>(reinterpret_cast<const float*>(A), bop, y + (size_t)r0 * nd,
-                                                       nd, Rc, Rp, cols, S, err);
+    const size_t smem = (size_t)S * (CM_BM * CM_BK * 4 + (size_t)N * CM_BK * 4) + 1024;
+    k_coarsest_tc<<<dim3(nd / CM_BM, slices), CM_THREADS, smem, st>>>(mapA, mapB, y + (size_t)r0 * nd, part, nd, Rc,
+                                                                      Rp, cols, S, err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (slices > 1) {
+      const long total = (long)Rc * nd;
+      k_coarsest_tc_reduce<<<(unsigned)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096), 256, 0, st>>>(
+          part, y + (size_t)r0 * nd, nd, Rc, Rp, slices);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
   }
   return cudaSuccess;
 }

@@ -152,6 +152,8 @@ struct amamg_ctx {
   float2* v32 = nullptr;     // [R][len]
   double2* w = nullptr;      // [R][len]
   double2* res = nullptr;    // [R][len]
+  double2* wdf = nullptr;    // [R][len] w in double-float form (AMAMG_GS_DF64; 16 bytes per entry)
+  double* df_part = nullptr; // its inner-product and norm partial sums (pairs of floats, 8 bytes each)
   double2* partial = nullptr;
   size_t partial_elems = 0;
   double2* d_h = nullptr;    // [R][3 (m+2)] device: h1 | h2 | norms

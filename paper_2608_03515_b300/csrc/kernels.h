@@ -217,12 +217,28 @@ cudaError_t launch_coarsest_gmres(const typename cplx<T>::type* r, typename cplx
                                   unsigned* sync, int* all_done, int max_blocks, cudaStream_t s);
 
 // coarsest_tc.cu: y_r = Ainv32 x_r for R >= 8 right-hand sides on the tensor
-// cores (tcgen05.mma kind::tf32, FP32 accumulation in tensor memory); nd a
-// multiple of 128.  bop: coarsest_tc_bop_elems(nd) floats of scratch; err: a
-// word set when a bounded wait ran out.  coarsest_tc_init: once per process
-// (opts the kernel in to its shared-memory size), outside stream capture.
+// cores (tcgen05.mma kind::tf32 fed by TMA, FP32 accumulation in tensor
+// memory, K split over CTAs for small levels); nd a multiple of 128.  scratch:
+// coarsest_tc_scratch_elems(nd) floats; err: a word set when a bounded wait ran
+// out.  coarsest_tc_init: once per process (opts the kernel in to its
+// shared-memory size), outside stream capture.
 bool coarsest_tc_possible(int nd, int R);
-size_t coarsest_tc_bop_elems(int nd);
+size_t coarsest_tc_scratch_elems(int nd);
 cudaError_t coarsest_tc_init();
-cudaError_t launch_coarsest_tc(const float2* A, const float2* x, float2* y, int nd, int R, float* bop, int* err,
+cudaError_t launch_coarsest_tc(const float2* A, const float2* x, float2* y, int nd, int R, float* scratch, int* err,
                                cudaStream_t st);
+
+// gs_df.cu: the outer solver's Gram-Schmidt in double-float arithmetic (basis
+// stored as double-float complex entries, 16 bytes each; see the file header)
+cudaError_t launch_to_df(const double2* w, void* wd, long n, cudaStream_t st);
+int df_partial_blocks(long len);   // inner-product partial sums: R (2 (m + 2)) df_partial_blocks(len) pairs
+int df_norm_blocks(long len);      // norm partial sums: R df_norm_blocks(len) pairs
+cudaError_t launch_dots_df(const void* V, size_t vi, size_t vr, const void* w, size_t wr, long len, int J, int R,
+                           bool with_self, const int* gate, void* partial, int ps, unsigned* tickets, double2* out,
+                           int ldo, int off, cudaStream_t st);
+cudaError_t launch_axpy_norm_df(void* w, size_t wr, const void* V, size_t vi, size_t vr, const double2* coef, int ldc,
+                                int J, long len, int R, const int* gate, void* partial, unsigned* tickets,
+                                double2* out, int ldo, int nrm_off, double* inv, int* flag, int ref_off, double eta2,
+                                int mode, cudaStream_t st);
+cudaError_t launch_scale_copy_df(void* dst, float2* dst32, size_t dr, const void* src_df, const double2* src_d,
+                                 size_t sr, const double* scale, long len, int R, cudaStream_t st);
