@@ -43,7 +43,7 @@ FP64_PEAK_GFLOPS = 1250.0      # nominal B300 FP64 rate
 # FP64 level-1 coarse Gauss-Seidel (k_coarse_sweeps_owner<double>, two sweeps of
 # the 64x64 level of this workload), from one ncu capture of that kernel; set to
 # None when that kernel changes
-COARSE_SMOOTH_F64_DRAM_BYTES = 5798315
+COARSE_SMOOTH_F64_DRAM_BYTES = None
 WORKLOAD = ("256x256 Wilson-Dirac (periodic x, antiperiodic t), quenched U(1) beta=6 seed 2, "
             "m0 = m_crit + {0.1, 0.02, 0.005}, 3-level SM-AMG (tiles 4, 2), FGMRES(30) to 1e-10, 1 RHS per mass")
 
@@ -603,6 +603,31 @@ def main():
                              "max_iterations": its}
         del psib, xb
 
+    # the opt-in double-float Gram-Schmidt (mixed form): one right-hand side per
+    # call over the three masses, then 16 per call, same inputs as above
+    hs_df = [A.setup(U, m0, A.make_params(AGGS, precision=A.SOLVE_MIXED, restart=RESTART, tol=TOL, gs="df64"))
+             for m0 in masses]
+    run(hs_df, nst=args.warmup)
+    st_df, sv_df, it_df, rr_df = run(hs_df, nst=nsteps, skip=args.warmup)
+    gs_df64 = {"solves_per_s": round(len(sv_df) / (np.sum(st_df) * 1e-3), 3), "iterations": it_df[-len(masses):],
+               "true_relres_max": max(rr_df)}
+    psib = [torch.from_numpy(fx.gaussian_rhs(16, L, L, RHS_SEED0 + 50000 + 1600 + i)).to(dev) for i in range(2)]
+    xb = torch.empty_like(psib[0])
+    for h in hs_df:
+        A.solve(h, psib[0], xb)
+    flush.zero_()
+    eb = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    eb[0].record(stream)
+    for h in hs_df:
+        info = A.solve(h, psib[1], xb)
+        assert all(i.status == A.OK and i.true_relres <= TOL for i in info)
+    eb[1].record(stream)
+    torch.cuda.synchronize()
+    gs_df64["R16_solves_per_s"] = round(16 * len(hs_df) / (eb[0].elapsed_time(eb[1]) * 1e-3), 3)
+    for h in hs_df:
+        A.destroy(h)
+    del psib, xb
+
     # the opt-in spin-split hierarchy (spin-diagonal interpolation weights; a
     # comparison beside the method as read): one warm-up and one timed step
     hs_ss = []
@@ -782,6 +807,7 @@ def main():
                       "latency_ms": {"p50": round(float(np.percentile(sv32, 50)), 3),
                                      "p99": round(float(np.percentile(sv32, 99)), 3)},
                       "setup_ms": [round(s, 2) for s in setup32]},
+            "mixed_gs_df64": gs_df64,
             "latency_ms": {"p50": round(float(np.percentile(solve_ms, 50)), 3),
                            "p99": round(float(np.percentile(solve_ms, 99)), 3)},
             "batched_mixed": batched,

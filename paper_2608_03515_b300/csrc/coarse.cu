@@ -365,58 +365,169 @@ k_coarse_sweeps_grid(typename cplx<T>::type* __restrict__ e, const typename cplx
 // memory; e lives in global memory.  At start every block lists the other
 // blocks that own a neighbour of one of its sites (the operator's offsets are
 // symmetric, so these are also the blocks that read its sites).  Instead of a
-// barrier over the whole grid, a block starts colour phase p once every
-// listed block has published phase p - 1: no neighbour value it reads is
-// stale, and no neighbour still reads a value it is about to overwrite.
+// barrier over the whole grid, a block updates its sites of colour phase p
+// once every listed block has published phase p - 1: no neighbour value it
+// reads is stale, and no neighbour still reads a value it is about to
+// overwrite.
+//
+// Split of a site's update around that wait.  When phase p starts, only the
+// neighbours of the previous phase's colour can still change (all other
+// colours were published at phase p - 2 or earlier, and none changes again
+// before this block publishes phase p).  So a site's sum over offsets splits
+// into an "early" part over every other offset, which needs no wait, and a
+// "late" part over the at most S (4 or 8) offsets of the previous colour.
+// The block has three roles:
+//   early warps (LE lanes per site, several offsets per lane) form the early
+//     sums of phase p + 1 into a double-buffered shared array while phase p
+//     runs;
+//   post warps (4 S lanes per site: S late slots for each of the four real
+//     components of the 2x2 product) wait for phase p's release, load the
+//     late neighbours, add the early sum, form
+//     e_v = A_vv^{-1} (r_v - sum) and store it;
+//   the synchronising warp polls the listed blocks' counters with acquire
+//     loads, releases phase p through named barrier 1 (with the early warps'
+//     sums of phase p), collects the post warps' stores through named barrier
+//     2 and publishes with a release add.
+// The early sums of phase p + 1 read only colours other than those of phases
+// p and p + 1, which no block writes before this block publishes phase p + 1.
+// Few lanes per site keep the FP64 instruction count of a phase low: on this
+// GPU's narrow FP64 pipe it sets the time of the early sums and slows the post
+// warps that share the pipe.  LE = 8 (four sites per warp, three offsets per
+// lane) has the fewest FP64 instructions and is taken when several blocks
+// share an SM; with one block per SM, LE = 16 (two sites per warp) spreads the
+// early sums over two warps and measured faster (a warp's FP64 instructions
+// issue on its own SM sub-partition).
 // Phase counters are flags[block] = base + phases done, base = sync[3]
-// (advanced by the last block to finish through the ticket sync[4]), so they
-// need no reset between launches.  Polls are bounded (OWNER_SPIN_LIMIT, about
-// half a second); a block that times out sets sync[2] and stops waiting, so
-// the launch always ends.  withhold >= 0 names a block that never publishes
+// (advanced by the last block to finish through the ticket sync[4]; every
+// block sets its counter to base when it starts, before any neighbour can
+// need a value above base).  Polls are bounded (OWNER_SPIN_LIMIT, about
+// half a second); a block whose wait times out sets sync[2] and stops waiting,
+// so the launch always ends.  withhold >= 0 names a block that never publishes
 // (self-test of that time-out path; -1 in every normal launch).
+// The sum over offsets is the same as in the other sweeps; its rounding order
+// differs (early tree, then late tree).
 constexpr unsigned OWNER_SPIN_LIMIT = 1u << 20;
-// lanes per site: FP64 32 (one offset per lane: the shortest chain of
-// dependent FP64 instructions, which bounds a colour phase on this GPU's
-// narrow FP64 pipe), FP32 8
-#ifndef AMAMG_OWNER_LPS64
-#define AMAMG_OWNER_LPS64 32
-#endif
-#ifndef AMAMG_OWNER_LPS32
-#define AMAMG_OWNER_LPS32 8
-#endif
-template <typename T> struct OwnerLanes { static constexpr int value = AMAMG_OWNER_LPS32; };
-template <> struct OwnerLanes<double> { static constexpr int value = AMAMG_OWNER_LPS64; };
+constexpr int OWNER_EARLY_WARPS = 2;   // at most
+constexpr int OWNER_POST_WARPS = 4;    // at most
 
-template <typename T, typename BT, bool BSMEM>
-__global__ void __launch_bounds__(256, 1)
+__device__ __forceinline__ void bar_sync_n(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_arrive_n(int id, int n) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_gpu_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Early sums of the warp's sites jb + (lane / LPS) < cnt of colour
+// `colour` over their offsets not in lm (all offsets when !use_mask): lane g of
+// a site's group takes offsets 1 + g, 1 + g + LPS, ...; the group's
+// reduce-scatter leaves component q = 2 h1 + h2 of the sum in lanes with
+// (h1, h2) = (bit 2, bit 1) of g, whose even lane writes out[4 jj + q].
+template <typename T, typename BT, bool BSMEM, int LPS>
+__device__ __forceinline__ void owner_early(const typename cplx<T>::type* __restrict__ e0, const BT* __restrict__ Bc,
+                                            const float* __restrict__ Sc, const BT* bs, const float* ss,
+                                            const unsigned* lm, bool use_mask, const Offsets& off, int Nt, int Nx,
+                                            int ncol, int m, int K1, int cnt, int colour, int j0, int jb, int lane,
+                                            T* out) {
+  using C = typename cplx<T>::type;
+  constexpr int IT = (GS_MAX_OFFDIAG + LPS - 1) / LPS;
+  const int n = Nt * Nx;
+  const int g = lane & (LPS - 1), jj = jb + lane / LPS;
+  const bool valid = jj < cnt;
+  const int jjc = valid ? jj : 0, j = j0 + jjc;
+  const unsigned mask = use_mask ? lm[colour * cnt + jjc] : 0u;
+  int t, x;
+  colour_site(ncol, colour, j, Nx, t, x);
+  C xv[IT][2], bb[IT][4];
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int k = 1 + g + it * LPS;
+    if (valid && k < off.K && !((mask >> (k - 1)) & 1u)) {
+      int tw = t + off.dt[k]; tw -= (tw >= Nt) ? Nt : 0;
+      int xw = x + off.dx[k]; xw -= (xw >= Nx) ? Nx : 0;
+      const int w = tw * Nx + xw;
+      xv[it][0] = __ldcg(e0 + w);
+      xv[it][1] = __ldcg(e0 + n + w);
+      if constexpr (BSMEM) {
+        const int li = (colour * K1 + (k - 1)) * cnt + jj;
+        if constexpr (sizeof(T) == 4) {
+#pragma unroll
+          for (int d = 0; d < 4; ++d) bb[it][d] = h2c<float>(bs[4 * li + d], ss[li]);
+        } else {
+#pragma unroll
+          for (int d = 0; d < 4; ++d) bb[it][d] = to_c(bs[4 * li + d], T());
+        }
+      } else {
+        cm_block<T, BT>(Bc, Sc, ((size_t)colour * K1 + (k - 1)) * m + j, bb[it]);
+      }
+    } else {
+      xv[it][0] = xv[it][1] = czero<C>();
+      bb[it][0] = bb[it][1] = bb[it][2] = bb[it][3] = czero<C>();
+    }
+  }
+  C s0 = czero<C>(), s1 = czero<C>();
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    cmac(s0, bb[it][0], xv[it][0]);
+    cmac(s0, bb[it][1], xv[it][1]);
+    cmac(s1, bb[it][2], xv[it][0]);
+    cmac(s1, bb[it][3], xv[it][1]);
+  }
+  constexpr int o1 = LPS / 2, o2 = LPS / 4;
+  const bool h1 = (g & o1) != 0, h2 = (g & o2) != 0;
+  T ka = h1 ? s1.x : s0.x, kb = h1 ? s1.y : s0.y;
+  ka += __shfl_xor_sync(0xffffffffu, h1 ? s0.x : s1.x, o1);
+  kb += __shfl_xor_sync(0xffffffffu, h1 ? s0.y : s1.y, o1);
+  T sq = h2 ? kb : ka;
+  sq += __shfl_xor_sync(0xffffffffu, h2 ? ka : kb, o2);
+#pragma unroll
+  for (int o = o2 / 2; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if (valid && (g & (o2 - 1)) == 0) out[4 * jj + 2 * h1 + h2] = sq;
+}
+
+template <typename T, typename BT, bool BSMEM, int S, int LE>
+__global__ void __launch_bounds__(32 * (OWNER_EARLY_WARPS + OWNER_POST_WARPS + 1), 1)
 k_coarse_sweeps_owner(typename cplx<T>::type* __restrict__ e, const typename cplx<T>::type* __restrict__ r,
                       const BT* __restrict__ Bc, const float* __restrict__ Sc,
                       const typename cplx<T>::type* __restrict__ Dc, Offsets off, int Nt, int Nx, int ncol,
-                      int sweeps, int cnt, unsigned* __restrict__ flags, unsigned* __restrict__ sync,
-                      int withhold) {
+                      int sweeps, int cnt, int nearly, int late_half, unsigned* __restrict__ flags,
+                      unsigned* __restrict__ sync, int withhold) {
   using C = typename cplx<T>::type;
-  constexpr int LPS = OwnerLanes<T>::value;
-  static_assert(LPS >= 4 && LPS <= 32 && (LPS & (LPS - 1)) == 0, "lanes per site: a power of two, 4..32");
-  constexpr int IT = (GS_MAX_OFFDIAG + LPS - 1) / LPS;
+  static_assert(S == 4 || S == 8, "late slots per component: 4 or 8");
+  static_assert(LE == 8 || LE == 16, "early lanes per site: 8 or 16");
+  constexpr int LPP = 4 * S, SPP = 32 / LPP;                 // post lanes per site, sites per post warp
+  constexpr int SPE = 32 / LE;                               // sites per early warp
   const int n = Nt * Nx, m = n / ncol, K1 = off.K - 1;
   const int nbpr = m / cnt;                                  // owner blocks per right-hand side
   const int rhs = blockIdx.x / nbpr, b = blockIdx.x - rhs * nbpr;
   const int j0 = b * cnt;
   const int own = ncol * cnt;
+  const int NT = blockDim.x;
+  const int npost = NT / 32 - 1 - nearly;                    // warps: post, then early, then synchronising
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* rs = reinterpret_cast<C*>(smem_raw);                    // [ncol][cnt][2]
   C* ds = rs + 2 * own;                                      // [ncol][cnt][4]
   BT* bs = reinterpret_cast<BT*>(ds + 4 * own);              // [ncol][K1][cnt][4]   (BSMEM)
-  float* ss = reinterpret_cast<float*>(bs + (BSMEM ? 4 * K1 * own : 0));   // [ncol][K1][cnt] (BSMEM, FP16)
+  T* pre = reinterpret_cast<T*>(bs + (BSMEM ? 4 * K1 * own : 0));   // [2][cnt][4] early sums
+  unsigned* lm = reinterpret_cast<unsigned*>(pre + 8 * cnt);         // [ncol][cnt] late-offset bits
+  float* ss = reinterpret_cast<float*>(lm + own);                    // [ncol][K1][cnt] (BSMEM, FP16)
   __shared__ unsigned bm[OWNER_MAX_BLOCKS / 32];             // blocks owning a neighbour
   __shared__ short wl[OWNER_MAX_WAIT];                       // ... as a list
-  __shared__ int nwait, alive;
+  __shared__ int nwait;
   const size_t roff = (size_t)rhs * 2 * n;
   C* e0 = e + roff;
   const C* r0 = r + roff;
   const int words = (nbpr + 31) / 32;
-  for (int i = threadIdx.x; i < words; i += blockDim.x) bm[i] = 0u;
-  for (int i = threadIdx.x; i < own; i += blockDim.x) {
+  for (int i = threadIdx.x; i < words; i += NT) bm[i] = 0u;
+  for (int i = threadIdx.x; i < own; i += NT) {
     const int c = i / cnt, j = j0 + (i - c * cnt);
     int t, x;
     colour_site(ncol, c, j, Nx, t, x);
@@ -424,9 +535,10 @@ k_coarse_sweeps_owner(typename cplx<T>::type* __restrict__ e, const typename cpl
     rs[2 * i] = r0[v]; rs[2 * i + 1] = r0[n + v];
 #pragma unroll
     for (int d = 0; d < 4; ++d) ds[4 * i + d] = Dc[((size_t)c * m + j) * 4 + d];
+    lm[i] = 0u;
   }
   if constexpr (BSMEM) {
-    for (int i = threadIdx.x; i < K1 * own; i += blockDim.x) {
+    for (int i = threadIdx.x; i < K1 * own; i += NT) {
       const int ck = i / cnt, jj = i - ck * cnt;                // ck = c K1 + (k - 1)
       const size_t src = (size_t)ck * m + j0 + jj;
 #pragma unroll
@@ -435,7 +547,7 @@ k_coarse_sweeps_owner(typename cplx<T>::type* __restrict__ e, const typename cpl
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < K1 * own; i += blockDim.x) {
+  for (int i = threadIdx.x; i < K1 * own; i += NT) {
     const int site = i / K1, k = 1 + (i - site * K1);
     const int c = site / cnt, j = j0 + (site - c * cnt);
     int t, x;
@@ -446,6 +558,7 @@ k_coarse_sweeps_owner(typename cplx<T>::type* __restrict__ e, const typename cpl
     site_colour(ncol, tw, xw, Nx, cw, jw);
     const int ob = jw / cnt;
     if (ob != b) atomicOr(&bm[ob >> 5], 1u << (ob & 31));
+    if (cw == (c == 0 ? ncol - 1 : c - 1)) atomicOr(&lm[site], 1u << (k - 1));
   }
   __syncthreads();
   if (threadIdx.x < 32) {
@@ -471,125 +584,148 @@ k_coarse_sweeps_owner(typename cplx<T>::type* __restrict__ e, const typename cpl
     }
     if (threadIdx.x == 0) {
       nwait = total < OWNER_MAX_WAIT ? total : OWNER_MAX_WAIT;
-      alive = 1;
-      if (total > OWNER_MAX_WAIT) { atomicExch(sync + 2, 1u); alive = 0; }
+      if (total > OWNER_MAX_WAIT) atomicExch(sync + 2, 1u);
     }
   }
   const unsigned base = *reinterpret_cast<volatile unsigned*>(sync + 3);
   __syncthreads();
-  const int g = threadIdx.x & (LPS - 1);
-  const int groups = blockDim.x / LPS;
-  int p = 0;
-  for (int sw = 0; sw < sweeps; ++sw) {
-    for (int colour = 0; colour < ncol; ++colour, ++p) {
-      if (p > 0 && alive && threadIdx.x < nwait) {
+  const int phases = sweeps * ncol;
+  const int n_done = 32 * (npost + 1);                       // barrier 2: post warps + synchronising warp
+
+  if (warp == npost + nearly) {
+    // synchronising warp
+    bool alive = true;
+    // the block's counter starts the launch at base (a block withheld in a
+    // self-test is behind by a launch's phases until here)
+    if (lane == 0) *reinterpret_cast<volatile unsigned*>(flags + blockIdx.x) = base;
+    for (int p = 0; p < phases; ++p) {
+      if (p > 0 && alive) {
         const unsigned want = base + (unsigned)p;
-        for (int q = threadIdx.x; q < nwait; q += blockDim.x) {
-          const volatile unsigned* f = flags + rhs * nbpr + wl[q];
+        bool late = false;
+        for (int q = lane; q < nwait && !late; q += 32) {
+          const unsigned* f = flags + rhs * nbpr + wl[q];
           unsigned it = 0;
-          while ((int)(*f - want) < 0) {
-            if (++it == OWNER_SPIN_LIMIT) {
-              atomicExch(sync + 2, 1u);
-              alive = 0;
-              break;
-            }
+          while ((int)(ld_acquire_gpu(f) - want) < 0) {
+            if (++it == OWNER_SPIN_LIMIT) { late = true; break; }
           }
         }
-        __threadfence();
-      }
-      __syncthreads();
-      for (int base_i = 0; base_i < cnt; base_i += groups) {
-        const int jj = base_i + threadIdx.x / LPS;
-        const bool valid = jj < cnt;
-        const int j = j0 + (valid ? jj : 0);
-        int t, x;
-        colour_site(ncol, colour, j, Nx, t, x);
-        C xv[IT][2], bb[IT][4];
-#pragma unroll
-        for (int it = 0; it < IT; ++it) {
-          const int k = 1 + g + it * LPS;
-          if (valid && k < off.K) {
-            int tw = t + off.dt[k]; tw -= (tw >= Nt) ? Nt : 0;
-            int xw = x + off.dx[k]; xw -= (xw >= Nx) ? Nx : 0;
-            const int w = tw * Nx + xw;
-            xv[it][0] = __ldcg(e0 + w);
-            xv[it][1] = __ldcg(e0 + n + w);
-            if constexpr (BSMEM) {
-              const int li = (colour * K1 + (k - 1)) * cnt + jj;
-              if constexpr (sizeof(T) == 4) {
-#pragma unroll
-                for (int d = 0; d < 4; ++d) bb[it][d] = h2c<float>(bs[4 * li + d], ss[li]);
-              } else {
-#pragma unroll
-                for (int d = 0; d < 4; ++d) bb[it][d] = to_c(bs[4 * li + d], T());
-              }
-            } else {
-              cm_block<T, BT>(Bc, Sc, ((size_t)colour * K1 + (k - 1)) * m + j, bb[it]);
-            }
-          } else {
-            xv[it][0] = xv[it][1] = czero<C>();
-            bb[it][0] = bb[it][1] = bb[it][2] = bb[it][3] = czero<C>();
-          }
-        }
-        C s0 = czero<C>(), s1 = czero<C>();
-#pragma unroll
-        for (int it = 0; it < IT; ++it) {
-          cmac(s0, bb[it][0], xv[it][0]);
-          cmac(s0, bb[it][1], xv[it][1]);
-          cmac(s1, bb[it][2], xv[it][0]);
-          cmac(s1, bb[it][3], xv[it][1]);
-        }
-        // Reduce-scatter of (s0.x, s0.y, s1.x, s1.y) over the group's lanes:
-        // after it, lane g holds the full sum of component q = 2 h1 + h2
-        // (h1 = bit o1 of g, h2 = bit o2), with log2(LPS) + 1 dependent adds
-        // instead of 4 log2(LPS).
-        constexpr int o1 = LPS / 2, o2 = LPS / 4;
-        const bool h1 = (g & o1) != 0, h2 = (g & o2) != 0;
-        T ka = h1 ? s1.x : s0.x, kb = h1 ? s1.y : s0.y;
-        ka += __shfl_xor_sync(0xffffffffu, h1 ? s0.x : s1.x, o1);
-        kb += __shfl_xor_sync(0xffffffffu, h1 ? s0.y : s1.y, o1);
-        T sq = h2 ? kb : ka;
-        sq += __shfl_xor_sync(0xffffffffu, h2 ? ka : kb, o2);
-#pragma unroll
-        for (int o = o2 / 2; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-        // a = r - s, component q here; every lane gathers all four, and the
-        // four lanes (h1, h2) each form one real component of
-        // e = [d0 d1; d2 d3] a  (e_0 = d0 a_0 + d1 a_1, e_1 = d2 a_0 + d3 a_1)
-        const int i = colour * cnt + jj;
-        const int q = 2 * h1 + h2;
-        const T aq = reinterpret_cast<const T*>(rs)[4 * i + q] - sq;
-        const int gb = (threadIdx.x & 31) & ~(LPS - 1);
-        const T A0 = __shfl_sync(0xffffffffu, aq, gb);
-        const T A1 = __shfl_sync(0xffffffffu, aq, gb + o2);
-        const T A2 = __shfl_sync(0xffffffffu, aq, gb + o1);
-        const T A3 = __shfl_sync(0xffffffffu, aq, gb + o1 + o2);
-        if (valid && (g & ~(o1 | o2)) == 0) {
-          const C dA = ds[4 * i + (h1 ? 2 : 0)], dB = ds[4 * i + (h1 ? 3 : 1)];
-          // real part (h2 = 0): dA.x A0 - dA.y A1 + dB.x A2 - dB.y A3;
-          // imaginary part (h2 = 1): dA.x A1 + dA.y A0 + dB.x A3 + dB.y A2
-          const T p0 = h2 ? A1 : A0, p1 = h2 ? A0 : A1, q0 = h2 ? A3 : A2, q1 = h2 ? A2 : A3;
-          T out = dA.x * p0;
-          out = fma(h2 ? dA.y : -dA.y, p1, out);
-          out = fma(dB.x, q0, out);
-          out = fma(h2 ? dB.y : -dB.y, q1, out);
-          const int v = t * Nx + x;
-          __stcg(reinterpret_cast<T*>(e0) + 2 * (v + (h1 ? n : 0)) + h2, out);
+        if (__any_sync(0xffffffffu, late)) {
+          if (lane == 0) atomicExch(sync + 2, 1u);
+          alive = false;
         }
       }
-      __syncthreads();
-      if (threadIdx.x == 0 && (int)blockIdx.x != withhold) {
-        __threadfence();
-        atomicExch(flags + blockIdx.x, base + (unsigned)p + 1u);
-      }
+      __syncwarp();
+      bar_arrive_n(1, NT);                                   // phase p may start
+      bar_sync_n(2, n_done);                                 // the post warps stored phase p
+      if (lane == 0 && (int)blockIdx.x != withhold) red_release_gpu_add(flags + blockIdx.x, 1u);
     }
-  }
-  if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(sync + 4, 1u) == gridDim.x - 1) {
-      sync[4] = 0;
+    if (lane == 0) {
       __threadfence();
-      atomicExch(sync + 3, base + (unsigned)p);
+      if (atomicAdd(sync + 4, 1u) == gridDim.x - 1) {
+        sync[4] = 0;
+        __threadfence();
+        atomicExch(sync + 3, base + (unsigned)phases);
+      }
     }
+    return;
+  }
+
+  if (warp >= npost) {
+    // early warps: phase 0 in full (nothing is late yet), then phase p + 1
+    // during phase p
+    const int ew = warp - npost;
+    for (int jb = ew * SPE; jb < cnt; jb += nearly * SPE)
+      owner_early<T, BT, BSMEM, LE>(e0, Bc, Sc, bs, ss, lm, false, off, Nt, Nx, ncol, m, K1, cnt, 0, j0, jb, lane, pre);
+    for (int p = 0; p < phases; ++p) {
+      bar_sync_n(1, NT);
+      if (p + 1 < phases) {
+        T* out = pre + 4 * cnt * ((p + 1) & 1);
+        for (int jb = ew * SPE; jb < cnt; jb += nearly * SPE)
+          owner_early<T, BT, BSMEM, LE>(e0, Bc, Sc, bs, ss, lm, true, off, Nt, Nx, ncol, m, K1, cnt, (p + 1) % ncol,
+                                    j0, jb, lane, out);
+      }
+    }
+    return;
+  }
+
+  // post warps
+  const int sub = lane / LPP, slot = lane & (S - 1), q = (lane % LPP) / S;
+  const bool h1 = (q & 2) != 0, h2 = (q & 1) != 0;
+  const int gb = sub * LPP;                                  // first lane of this site's group
+  for (int p = 0; p < phases; ++p) {
+    const int colour = p % ncol;
+    const T* prep = pre + 4 * cnt * (p & 1);
+    bool first = true;
+    for (int jb = warp * SPP; jb < cnt; jb += npost * SPP) {
+      // address work first; the first sites' runs before the wait
+      const int jj = jb + sub;
+      const bool valid = jj < cnt;
+      const int jjc = valid ? jj : 0;
+      const int i = colour * cnt + jjc, j = j0 + jjc;
+      const unsigned mask = p > 0 ? lm[i] : 0u;
+      int t, x;
+      colour_site(ncol, colour, j, Nx, t, x);
+      const bool has = valid && slot < __popc(mask);
+      int w = 0;
+      C bA = czero<C>(), bB = czero<C>();                    // row h1 of the late block
+      if (has) {
+        const int k = 1 + (int)__fns(mask, 0u, slot + 1);
+        int tw = t + off.dt[k]; tw -= (tw >= Nt) ? Nt : 0;
+        int xw = x + off.dx[k]; xw -= (xw >= Nx) ? Nx : 0;
+        w = tw * Nx + xw;
+        if constexpr (BSMEM) {
+          const int li = (colour * K1 + (k - 1)) * cnt + jj;
+          if constexpr (sizeof(T) == 4) {
+            bA = h2c<float>(bs[4 * li + 2 * h1], ss[li]);
+            bB = h2c<float>(bs[4 * li + 2 * h1 + 1], ss[li]);
+          } else {
+            bA = to_c(bs[4 * li + 2 * h1], T());
+            bB = to_c(bs[4 * li + 2 * h1 + 1], T());
+          }
+        } else {
+          C bb[4];
+          cm_block<T, BT>(Bc, Sc, ((size_t)colour * K1 + (k - 1)) * m + j, bb);
+          bA = h1 ? bb[2] : bb[0];
+          bB = h1 ? bb[3] : bb[1];
+        }
+      }
+      if (first) {
+        bar_sync_n(1, NT);                                   // neighbours published p - 1; early sums ready
+        first = false;
+      }
+      T cq = T(0);
+      if (has) {
+        const C x0 = __ldcg(e0 + w), x1 = __ldcg(e0 + n + w);
+        // real part (h2 = 0): bA.x x0.x - bA.y x0.y + bB.x x1.x - bB.y x1.y;
+        // imaginary part (h2 = 1): bA.x x0.y + bA.y x0.x + bB.x x1.y + bB.y x1.x
+        T ca = bA.x * (h2 ? x0.y : x0.x);
+        ca = fma(h2 ? bA.y : -bA.y, h2 ? x0.x : x0.y, ca);
+        T cb = bB.x * (h2 ? x1.y : x1.x);
+        cb = fma(h2 ? bB.y : -bB.y, h2 ? x1.x : x1.y, cb);
+        cq = ca + cb;
+      }
+      for (int o = late_half; o > 0; o >>= 1) cq += __shfl_xor_sync(0xffffffffu, cq, o);
+      const T sq = prep[4 * jjc + q] + cq;
+      // a = r - s, component q here; every lane gathers all four, and the
+      // four slot-0 lanes of the site each form one real component of
+      // e = [d0 d1; d2 d3] a  (e_0 = d0 a_0 + d1 a_1, e_1 = d2 a_0 + d3 a_1)
+      const T aq = reinterpret_cast<const T*>(rs)[4 * i + q] - sq;
+      const T A0 = __shfl_sync(0xffffffffu, aq, gb);
+      const T A1 = __shfl_sync(0xffffffffu, aq, gb + S);
+      const T A2 = __shfl_sync(0xffffffffu, aq, gb + 2 * S);
+      const T A3 = __shfl_sync(0xffffffffu, aq, gb + 3 * S);
+      if (valid && slot == 0) {
+        const C dA = ds[4 * i + (h1 ? 2 : 0)], dB = ds[4 * i + (h1 ? 3 : 1)];
+        const T p0 = h2 ? A1 : A0, p1 = h2 ? A0 : A1, q0 = h2 ? A3 : A2, q1 = h2 ? A2 : A3;
+        T oa = dA.x * p0;
+        oa = fma(h2 ? dA.y : -dA.y, p1, oa);
+        T ob = dB.x * q0;
+        ob = fma(h2 ? dB.y : -dB.y, q1, ob);
+        const int v = t * Nx + x;
+        __stcg(reinterpret_cast<T*>(e0) + 2 * (v + (h1 ? n : 0)) + h2, oa + ob);
+      }
+    }
+    bar_arrive_n(2, n_done);                                 // this warp's stores of phase p are done
   }
 }
 
@@ -935,15 +1071,39 @@ cudaError_t launch_coarse_sweeps_grid(typename cplx<T>::type* e, const typename 
 // Owner sweep configuration for a level: the fewest sites per block and colour
 // (cnt, a divisor of m = n / ncol, at least OWNER_MIN_CNT) whose R m / cnt
 // blocks can all be resident (cooperative launch) and whose neighbour-owner
-// lists fit OWNER_MAX_WAIT; threads = LPS cnt (at most 256, more sites take
-// several passes); blocks in shared memory when that stays within 100 KB.
+// lists fit OWNER_MAX_WAIT; enough early warps (4 sites each) and post warps
+// (2 or 1 sites each) for the block's sites of a colour, up to
+// OWNER_EARLY_WARPS and OWNER_POST_WARPS (more sites take several passes), plus
+// the synchronising warp; blocks in shared
+// memory when that stays within 100 KB.  Levels with more than 8 late offsets
+// per site, or more than 32 off-diagonal offsets, have no owner sweep.
 #ifndef AMAMG_OWNER_MIN_CNT
 #define AMAMG_OWNER_MIN_CNT 4
 #endif
-static size_t owner_smem(int own, int K1, size_t cb, bool bsmem, size_t btb) {
-  size_t s = (size_t)own * 6 * cb;
+static size_t owner_smem(int own, int cnt, int K1, size_t cb, bool bsmem, size_t btb) {
+  size_t s = (size_t)own * 6 * cb + (size_t)cnt * 4 * cb + (size_t)own * 4;
   if (bsmem) s += (size_t)own * K1 * (4 * btb + 4);
   return s;
+}
+
+// largest number of offsets of a site whose neighbour has the previous colour
+// (the late offsets of the owner sweep)
+static int owner_max_late(int Nt, int Nx, int ncol, const Offsets& off) {
+  int worst = 0;
+  for (int t = 0; t < Nt; ++t)
+    for (int x = 0; x < Nx; ++x) {
+      int c, j;
+      site_colour(ncol, t, x, Nx, c, j);
+      const int prev = c == 0 ? ncol - 1 : c - 1;
+      int count = 0;
+      for (int k = 1; k < off.K; ++k) {
+        int cw, jw;
+        site_colour(ncol, (t + off.dt[k]) % Nt, (x + off.dx[k]) % Nx, Nx, cw, jw);
+        count += cw == prev;
+      }
+      worst = std::max(worst, count);
+    }
+  return worst;
 }
 
 // largest number of other blocks owning a neighbour of one block's sites
@@ -969,6 +1129,16 @@ static int owner_max_wait(int Nt, int Nx, int ncol, const Offsets& off, int cnt)
   return worst;
 }
 
+template <typename T, typename BT, int LE>
+static auto owner_kernel_le(bool bsmem, int slots) {
+  return bsmem ? (slots == 4 ? k_coarse_sweeps_owner<T, BT, true, 4, LE> : k_coarse_sweeps_owner<T, BT, true, 8, LE>)
+               : (slots == 4 ? k_coarse_sweeps_owner<T, BT, false, 4, LE> : k_coarse_sweeps_owner<T, BT, false, 8, LE>);
+}
+template <typename T, typename BT>
+static auto owner_kernel(bool bsmem, int slots, int le) {
+  return le == 16 ? owner_kernel_le<T, BT, 16>(bsmem, slots) : owner_kernel_le<T, BT, 8>(bsmem, slots);
+}
+
 template <typename T, typename BT>
 static bool owner_sweep_search(int Nt, int Nx, int K, int ncol, const Offsets& off, int R, OwnerConfig* cfg) {
   int dev = 0, sms = 0, coop = 0;
@@ -979,17 +1149,26 @@ static bool owner_sweep_search(int Nt, int Nx, int K, int ncol, const Offsets& o
   }
   const int m = Nt * Nx / ncol;
   const size_t cb = sizeof(typename cplx<T>::type);
+  const int max_late = owner_max_late(Nt, Nx, ncol, off);
+  if (K - 1 > 32 || max_late > 8) return false;
+  const int S = max_late <= 4 ? 4 : 8;
+  int late_half = 0;                                         // first xor offset of the late-slot reduction
+  while (2 * late_half < max_late) late_half = late_half ? 2 * late_half : 1;
+  if (max_late == 1) late_half = 0;
   for (int cnt = std::min(AMAMG_OWNER_MIN_CNT, m); cnt <= m; ++cnt) {
     if (m % cnt) continue;
     const int nbpr = m / cnt;
     const long blocks = (long)R * nbpr;
     if (nbpr > OWNER_MAX_BLOCKS || blocks > OWNER_MAX_BLOCKS) continue;
     const int own = ncol * cnt;
-    int threads = cnt * OwnerLanes<T>::value;
-    threads = threads > 256 ? 256 : ((threads + 31) / 32) * 32;
-    const bool bsmem = owner_smem(own, K - 1, cb, true, sizeof(BT)) <= 100 * 1024;
-    const size_t smem = owner_smem(own, K - 1, cb, bsmem, sizeof(BT));
-    auto kern = bsmem ? k_coarse_sweeps_owner<T, BT, true> : k_coarse_sweeps_owner<T, BT, false>;
+    const int le = blocks <= sms ? 16 : 8;                     // one block per SM: spread the early sums
+    const int spe = 32 / le, spp = 32 / (4 * S);
+    const int nearly = std::min((cnt + spe - 1) / spe, OWNER_EARLY_WARPS);
+    const int npost = std::min((cnt + spp - 1) / spp, OWNER_POST_WARPS);
+    const int threads = 32 * (nearly + npost + 1);
+    const bool bsmem = owner_smem(own, cnt, K - 1, cb, true, sizeof(BT)) <= 100 * 1024;
+    const size_t smem = owner_smem(own, cnt, K - 1, cb, bsmem, sizeof(BT));
+    auto kern = owner_kernel<T, BT>(bsmem, S, le);
     int occ = 0;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem) != cudaSuccess) {
@@ -999,6 +1178,10 @@ static bool owner_sweep_search(int Nt, int Nx, int K, int ncol, const Offsets& o
     if (blocks > (long)occ * sms) continue;
     if (owner_max_wait(Nt, Nx, ncol, off, cnt) > OWNER_MAX_WAIT) continue;
     cfg->cnt = cnt;
+    cfg->late_half = late_half;
+    cfg->slots = S;
+    cfg->nearly = nearly;
+    cfg->early_lanes = le;
     cfg->threads = threads;
     cfg->smem = smem;
     cfg->bsmem = bsmem;
@@ -1035,7 +1218,7 @@ cudaError_t launch_coarse_sweeps_owner(typename cplx<T>::type* e, const typename
                                        cudaStream_t st, int withhold) {
   OwnerConfig oc;
   if (!owner_sweep_config<T, BT>(Nt, Nx, off.K, ncol, off, R, &oc)) return cudaErrorNotSupported;
-  auto kern = oc.bsmem ? k_coarse_sweeps_owner<T, BT, true> : k_coarse_sweeps_owner<T, BT, false>;
+  auto kern = owner_kernel<T, BT>(oc.bsmem, oc.slots, oc.early_lanes);
   // the attribute is per kernel, and another level may have set a smaller one
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oc.smem);
   if (err != cudaSuccess) return err;
@@ -1049,8 +1232,8 @@ cudaError_t launch_coarse_sweeps_owner(typename cplx<T>::type* e, const typename
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, e, r, Bc, Sc, Dc, off, Nt, Nx, ncol, sweeps, oc.cnt, flags, sync,
-                            withhold);
+  return cudaLaunchKernelEx(&cfg, kern, e, r, Bc, Sc, Dc, off, Nt, Nx, ncol, sweeps, oc.cnt, oc.nearly,
+                            oc.late_half, flags, sync, withhold);
 }
 
 // the distributed-shared-memory sweep needs per = n / (16 ncol) whole sites per

@@ -96,7 +96,7 @@ cudaError_t launch_coarse_sweeps_grid(typename cplx<T>::type* e, const typename 
 constexpr int OWNER_MAX_BLOCKS = 4096;
 constexpr int OWNER_MAX_WAIT = 256;
 struct OwnerConfig {
-  int cnt = 0, threads = 0, blocks = 0;
+  int cnt = 0, threads = 0, blocks = 0, late_half = 0, slots = 4, nearly = 1, early_lanes = 8;
   size_t smem = 0;
   bool bsmem = false;
 };
