@@ -41,9 +41,10 @@ RHS_SEED0 = 1000
 FP64_PEAK_GFLOPS = 1250.0      # nominal B300 FP64 rate
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # FP64 level-1 coarse Gauss-Seidel (k_coarse_sweeps_owner<double>, two sweeps of
-# the 64x64 level of this workload), from one ncu capture of that kernel; set to
-# None when that kernel changes
-COARSE_SMOOTH_F64_DRAM_BYTES = None
+# a 64x64 level with 21 offsets, the shape of this workload's level 1), from one
+# ncu capture of that kernel on the smooth1 probe; set to None when that kernel
+# changes
+COARSE_SMOOTH_F64_DRAM_BYTES = 5818368
 WORKLOAD = ("256x256 Wilson-Dirac (periodic x, antiperiodic t), quenched U(1) beta=6 seed 2, "
             "m0 = m_crit + {0.1, 0.02, 0.005}, 3-level SM-AMG (tiles 4, 2), FGMRES(30) to 1e-10, 1 RHS per mass")
 
