@@ -292,9 +292,14 @@ int ensure_solver_ws(amamg_ctx* h, int R) {
   dfree(h->V); dfree(h->Z64); dfree(h->Z32); dfree(h->v32); dfree(h->w); dfree(h->res); dfree(h->wdf); dfree(h->df_part);
   dfree(h->partial); dfree(h->d_h); dfree(h->d_inv); dfree(h->d_flag); dfree(h->d_y); dfree(h->d_tickets); dfree(h->d_npart);
   dfree(h->d_diag64); dfree(h->d_inv64); dfree(h->d_inv32);
+  dfree(h->ls_H); dfree(h->ls_Q); dfree(h->ls_R); dfree(h->ls_g); dfree(h->ls_bnorm); dfree(h->ls_st);
+  dfree(h->d_lsout); dfree(h->d_lsinit);
   if (h->h_h) cudaFreeHost(h->h_h);
-  if (h->h_y) cudaFreeHost(h->h_y);
-  h->h_h = h->h_y = nullptr;
+  if (h->h_lsout) cudaFreeHost(h->h_lsout);
+  if (h->h_lsinit) cudaFreeHost(h->h_lsinit);
+  h->h_h = nullptr;
+  h->h_lsout = nullptr;
+  h->h_lsinit = nullptr;
   const size_t len = 2 * (size_t)h->lv[0].n;
   CKS(dalloc(h, &h->V, (size_t)(m + 1) * R * len));
   if (h->prm.precision == AMAMG_SOLVE_MIXED) {
@@ -321,8 +326,17 @@ int ensure_solver_ws(amamg_ctx* h, int R) {
   CKS(dalloc(h, &h->d_inv64, (size_t)R));
   CKS(dalloc(h, &h->d_inv32, (size_t)R));
   CKS(dalloc(h, &h->d_y, (size_t)R * m));
+  CKS(dalloc(h, &h->ls_H, (size_t)R * (m + 1) * m));
+  CKS(dalloc(h, &h->ls_Q, (size_t)R * (m + 1) * (m + 1)));
+  CKS(dalloc(h, &h->ls_R, (size_t)R * m * m));
+  CKS(dalloc(h, &h->ls_g, (size_t)R * (m + 1)));
+  CKS(dalloc(h, &h->ls_bnorm, (size_t)R));
+  CKS(dalloc(h, &h->ls_st, (size_t)R * 4));
+  CKS(dalloc(h, &h->d_lsout, (size_t)R));
+  CKS(dalloc(h, &h->d_lsinit, (size_t)R));
   CK(cudaMallocHost((void**)&h->h_h, sizeof(double2) * (size_t)R * 3 * (m + 2)));
-  CK(cudaMallocHost((void**)&h->h_y, sizeof(double2) * (size_t)R * m));
+  CK(cudaMallocHost((void**)&h->h_lsout, sizeof(LsOut) * (size_t)R));
+  CK(cudaMallocHost((void**)&h->h_lsinit, sizeof(LsInit) * (size_t)R));
   h->Rsolve = R;
   h->mcap = m;
   return AMAMG_OK;
@@ -639,15 +653,26 @@ int norms(amamg_ctx* h, const double2* X, size_t xr, long len, int R, double2* o
                 [&] { return launch_reduce(h->partial, nb, 1, R, out, ldo, off, 1, inv, st); });
 }
 
-// solve the upper-triangular k x k system of the rotated Hessenberg matrix
-void back_solve(const std::vector<double2>& H, int ldh, const std::vector<double2>& g, int k, double2* y) {
-  for (int i = k - 1; i >= 0; --i) {
-    double2 s = g[i];
-    for (int j = i + 1; j < k; ++j) s -= cmul(H[(size_t)i * ldh + j], y[j]);
-    const double2 d = H[(size_t)i * ldh + i];
-    const double dd = d.x * d.x + d.y * d.y;
-    y[i] = make_double2((s.x * d.x + s.y * d.y) / dd, (s.y * d.x - s.x * d.y) / dd);
-  }
+// The least-squares update of Arnoldi step j on the device (the rotation of
+// the new Hessenberg column, g, the residual estimate and the stopping test per
+// right-hand side, in FP64) and the copy of the per-RHS progress to pinned
+// host memory, on the side stream ws2 once the step's norms are in d_h, so
+// that it overlaps the normalisation of v_{j+1}; ls_join makes st wait for it.
+int ls_fork(amamg_ctx* h, int j, int R, cudaStream_t st) {
+  const int m = h->prm.restart;
+  CK(cudaEventRecord(h->ev_fork, st));
+  CK(cudaStreamWaitEvent(h->ws2, h->ev_fork, 0));
+  CKS(launch(h, "ls_update", (double)R * (2.0 * (j + 2) * 16.0 * 3 + 64.0), h->ws2, [&] {
+    return launch_ls_step(h->ls(), h->d_h, 3 * (m + 2), 2 * (m + 2), j, R, m, h->prm.tol, h->prm.max_iter, h->d_lsout,
+                          h->ws2);
+  }));
+  CK(cudaMemcpyAsync(h->h_lsout, h->d_lsout, sizeof(LsOut) * R, cudaMemcpyDeviceToHost, h->ws2));
+  CK(cudaEventRecord(h->ev_join, h->ws2));
+  return AMAMG_OK;
+}
+int ls_join(amamg_ctx* h, cudaStream_t st) {
+  CK(cudaStreamWaitEvent(st, h->ev_join, 0));
+  return AMAMG_OK;
 }
 
 // One Arnoldi step j for all R right-hand sides, entirely on the device:
@@ -712,11 +737,11 @@ int arnoldi_step(amamg_ctx* h, int j, int R, cudaStream_t st) {
       return launch_axpy_norm_df(h->wdf, vr, h->V, vi, vr, d_h1 + (m + 2), ldh, J, len, R, h->d_flag, npart, tk_norm,
                                  d_h1, ldh, nrm_off, h->d_inv, nullptr, 0, 0.0, 1, st);
     }, (double)R * len * 8.0 * (J + 1)));
+    CKS(ls_fork(h, j, R, st));
     CKS(launch(h, "scale_copy", (double)R * len * 40.0, st, [&] {
       return launch_scale_copy_df(h->V + (size_t)(j + 1) * vi, h->v32, vr, h->wdf, nullptr, vr, h->d_inv, len, R, st);
     }));
-    CK(cudaMemcpyAsync(h->h_h, h->d_h, sizeof(double2) * R * ldh, cudaMemcpyDeviceToHost, st));
-    return AMAMG_OK;
+    return ls_join(h, st);
   }
   CKS(launch(h, "gs_dots", (double)R * len * 16.0 * (J + 1), st, [&] {
     return launch_dots_fused(h->V, vi, vr, h->w, vr, len, J, R, h->partial, true, nullptr, tk_dots, d_h1, ldh, 0, st);
@@ -735,6 +760,7 @@ int arnoldi_step(amamg_ctx* h, int j, int R, cudaStream_t st) {
     return launch_axpy_norm(h->w, vr, h->V, vi, vr, d_h1 + (m + 2), ldh, J, len, R, h->d_flag, h->d_npart, tk_norm,
                             d_h1, ldh, nrm_off, h->d_inv, nullptr, 0, 0.0, 1, st);
   }, (double)R * len * 8.0 * (J + 1)));
+  CKS(ls_fork(h, j, R, st));
   if (mixed)
     CKS(launch(h, "scale_copy", (double)R * len * 40.0, st, [&] {
       return launch_scale_copy_dual(h->V + (size_t)(j + 1) * vi, h->v32, vr, h->w, vr, h->d_inv, len, R, st);
@@ -743,8 +769,7 @@ int arnoldi_step(amamg_ctx* h, int j, int R, cudaStream_t st) {
     CKS(launch(h, "scale_copy", (double)R * len * 32.0, st, [&] {
       return launch_scale_copy<double2>(h->V + (size_t)(j + 1) * vi, vr, h->w, vr, h->d_inv, len, R, st);
     }));
-  CK(cudaMemcpyAsync(h->h_h, h->d_h, sizeof(double2) * R * ldh, cudaMemcpyDeviceToHost, st));
-  return AMAMG_OK;
+  return ls_join(h, st);
 }
 
 // Runs Arnoldi step j: replays its captured graph (capturing it on first use),
@@ -827,13 +852,20 @@ int fgmres_cycle(amamg_ctx* h, const double2* b, double2* x, int R, cudaStream_t
     q.relres = q.bnorm > 0 ? beta / q.bnorm : 0.0;
     if (q.relres <= tol) { q.done = 1; q.status = AMAMG_OK; continue; }
     if (q.iters >= h->prm.max_iter) { q.done = 1; q.status = AMAMG_NOT_CONVERGED; continue; }
-    o.g[r].assign(m + 1, make_double2(0.0, 0.0));
-    o.g[r][0] = make_double2(beta, 0.0);
     o.building[r] = 1;
     left = true;
   }
   *any_left = left;
   if (!left) return AMAMG_OK;
+  // the device least-squares state: g = beta e_1, Q^H = I, progress counters
+  for (int r = 0; r < R; ++r) {
+    const SlotState& q = sl[r];
+    h->h_lsinit[r] = LsInit{o.building[r] ? h->h_h[(size_t)r * ldh + nrm_off].x : 0.0, q.bnorm, o.building[r],
+                            q.iters};
+  }
+  CK(cudaMemcpyAsync(h->d_lsinit, h->h_lsinit, sizeof(LsInit) * R, cudaMemcpyHostToDevice, st));
+  CKS(launch(h, "ls_update", (double)R * (m + 1) * (m + 2) * 16.0, st,
+             [&] { return launch_ls_init(h->ls(), h->d_lsinit, R, m, st); }));
   // V[0] = r / beta (zero for right-hand sides that are not building: their inv is
   // set by the norm of a zero or converged residual and they are ignored below)
   if (h->prm.gs_arith == AMAMG_GS_DF64)
@@ -852,50 +884,20 @@ int fgmres_cycle(amamg_ctx* h, const double2* b, double2* x, int R, cudaStream_t
     for (int r = 0; r < R; ++r) {
       if (!o.building[r]) continue;
       SlotState& q = sl[r];
-      const double2* hh = h->h_h + (size_t)r * ldh;
-      std::vector<double2>& Hr = o.H[r];
-      for (int i = 0; i <= j; ++i) Hr[(size_t)i * m + j] = hh[i] + hh[(m + 2) + i];
-      const double hn = hh[nrm_off].x;
-      if (!std::isfinite(hn)) { q.status = AMAMG_ERR_NONFINITE; q.done = 1; o.building[r] = 0; o.k[r] = 0; continue; }
-      // earlier rotations, then a new one that annihilates H[j+1][j]
-      for (int i = 0; i < j; ++i) {
-        const double2 a = Hr[(size_t)i * m + j], bb = Hr[(size_t)(i + 1) * m + j];
-        Hr[(size_t)i * m + j] = o.cs[r][i] * a + cmul(o.sn[r][i], bb);
-        Hr[(size_t)(i + 1) * m + j] = o.cs[r][i] * bb - cmulc(o.sn[r][i], a);
-      }
-      const double2 a = Hr[(size_t)j * m + j];
-      const double aa = std::sqrt(a.x * a.x + a.y * a.y);
-      double c;
-      double2 sv;
-      if (hn == 0.0) { c = 1.0; sv = make_double2(0.0, 0.0); }
-      else if (aa == 0.0) { c = 0.0; sv = make_double2(1.0, 0.0); }
-      else {
-        const double rr = std::hypot(aa, hn);
-        c = aa / rr;
-        sv = make_double2(a.x / aa * hn / rr, a.y / aa * hn / rr);   // (a/|a|) conj(hn) / r, hn real
-      }
-      o.cs[r][j] = c;
-      o.sn[r][j] = sv;
-      Hr[(size_t)j * m + j] = c * a + hn * sv;
-      const double2 gj = o.g[r][j];
-      o.g[r][j + 1] = -1.0 * cmulc(sv, gj);
-      o.g[r][j] = c * gj;
-      q.iters++;
-      o.k[r] = j + 1;
-      const double est = std::sqrt(cabs2(o.g[r][j + 1]));
-      if (est <= tol * q.bnorm || hn == 0.0 || q.iters >= h->prm.max_iter) o.building[r] = 0;
+      const LsOut& u = h->h_lsout[r];
+      q.iters = u.iters;
+      o.k[r] = u.k;
+      if (u.nonfinite) { q.status = AMAMG_ERR_NONFINITE; q.done = 1; o.building[r] = 0; o.k[r] = 0; continue; }
+      o.building[r] = u.building;
       if (o.building[r]) any = true;
     }
     if (!any) { ++j; break; }
   }
-  // x += Z y  (per right-hand side k[r] columns; the rest zero)
+  // x += Z y  (per right-hand side k[r] columns; the rest zero), y from the
+  // triangular factor and solve on the device
   const int jmax = j < m ? j : m;
-  for (int r = 0; r < R; ++r) {
-    double2* y = h->h_y + (size_t)r * m;
-    for (int i = 0; i < m; ++i) y[i] = make_double2(0.0, 0.0);
-    if (o.k[r] > 0 && sl[r].status != AMAMG_ERR_NONFINITE) back_solve(o.H[r], m, o.g[r], o.k[r], y);
-  }
-  CK(cudaMemcpyAsync(h->d_y, h->h_y, sizeof(double2) * R * m, cudaMemcpyHostToDevice, st));
+  CKS(launch(h, "ls_update", (double)R * m * (m + 1) * 16.0 * 2, st,
+             [&] { return launch_ls_solve(h->ls(), h->d_y, R, m, st); }));
   if (mixed)
     CKS(launch(h, "x_update", (double)R * len * (8.0 * jmax + 32.0), st, [&] {
       return launch_multi_axpy<float2>(x, vr, h->Z32, vi, vr, h->d_y, m, jmax, 1.0, len, R, st);
@@ -1046,15 +1048,24 @@ void free_all(amamg_ctx* h) {
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
   h->ws = nullptr; h->ev_in = h->ev_out = nullptr;
+  if (h->ws2) cudaStreamDestroy(h->ws2);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  h->ws2 = nullptr; h->ev_fork = h->ev_join = nullptr;
   dfree(h->U64); dfree(h->U64s); dfree(h->U32); dfree(h->Ainv); dfree(h->Ainv32); dfree(h->d_err); dfree(h->d_sync); dfree(h->d_owner_flags);
   dfree(h->d_smax); dfree(h->d_rowsum_skipped);
   dfree(h->gm_V); dfree(h->gm_part); dfree(h->gm_st); dfree(h->gm_done); dfree(h->tc_bop);
   dfree(h->V); dfree(h->Z64); dfree(h->Z32); dfree(h->v32); dfree(h->w); dfree(h->res); dfree(h->wdf); dfree(h->df_part);
   dfree(h->partial); dfree(h->d_h); dfree(h->d_inv); dfree(h->d_flag); dfree(h->d_y); dfree(h->d_tickets); dfree(h->d_npart);
   dfree(h->d_diag64); dfree(h->d_inv64); dfree(h->d_inv32);
+  dfree(h->ls_H); dfree(h->ls_Q); dfree(h->ls_R); dfree(h->ls_g); dfree(h->ls_bnorm); dfree(h->ls_st);
+  dfree(h->d_lsout); dfree(h->d_lsinit);
   if (h->h_h) cudaFreeHost(h->h_h);
-  if (h->h_y) cudaFreeHost(h->h_y);
-  h->h_h = h->h_y = nullptr;
+  if (h->h_lsout) cudaFreeHost(h->h_lsout);
+  if (h->h_lsinit) cudaFreeHost(h->h_lsinit);
+  h->h_h = nullptr;
+  h->h_lsout = nullptr;
+  h->h_lsinit = nullptr;
   for (auto e : h->ev_pool) cudaEventDestroy(e);
   h->ev_pool.clear();
 }
@@ -1070,6 +1081,9 @@ int do_setup(amamg_ctx* h, const void* Uin, cudaStream_t st) {
   CK(cudaStreamCreateWithFlags(&h->ws, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+  CK(cudaStreamCreateWithFlags(&h->ws2, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   CKS(dalloc(h, &h->U64, nl));
   CKS(dalloc(h, &h->U64s, nl));
   CKS(dalloc(h, &h->U32, nl));

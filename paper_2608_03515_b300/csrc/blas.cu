@@ -323,3 +323,189 @@ template cudaError_t launch_scale_copy<float2>(float2*, size_t, const double2*, 
                                                cudaStream_t);
 template cudaError_t launch_cast<double2, float2>(const double2*, float2*, long, cudaStream_t);
 template cudaError_t launch_cast<float2, double2>(const float2*, double2*, long, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Least squares of the outer FGMRES (Saad, Iterative Methods for Sparse Linear
+// Systems, Sec. 6.5.3: Givens rotations on the Hessenberg matrix).  A rotation
+// that annihilates the subdiagonal entry hn (real, >= 0) of column j, whose
+// entry j after the earlier rotations is t, is c = |t| / rho,
+// s = (t / |t|) hn / rho, rho = (|t|^2 + hn^2)^(1/2), applied to rows (j, j+1)
+// as [c s; -conj(s) c]; g_{j+1} = -conj(s) g_j, g_j = c g_j, and |g_{j+1}| is
+// the residual norm of the least-squares solution.  Instead of rotating every
+// stored column again, the product Q^H of the rotations is kept: step j needs
+// only t = (row j of Q^H) . (column j) (a warp-wide dot product) and updates
+// rows j and j+1 of Q^H; at the end of the cycle R = Q^H H and the triangular
+// solve give y.  On this GPU's narrow FP64 pipe that is a few dozen FP64
+// instructions per step instead of a chain of about 12 j.
+namespace {
+
+__device__ __forceinline__ double2 warp_sum_c(double2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+__global__ void k_ls_init(LsView v, const LsInit* __restrict__ init, int m) {
+  const int r = blockIdx.x;
+  const LsInit q = init[r];
+  const int n1 = m + 1;
+  double2* Q = v.Q + (size_t)r * n1 * n1;
+  for (int i = threadIdx.x; i < n1 * n1; i += blockDim.x)
+    Q[i] = make_double2(i / n1 == i % n1 ? 1.0 : 0.0, 0.0);
+  double2* g = v.g + (size_t)r * n1;
+  for (int i = threadIdx.x; i < n1; i += blockDim.x) g[i] = make_double2(i == 0 ? q.beta : 0.0, 0.0);
+  if (threadIdx.x == 0) {
+    int* s = v.st + 4 * r;
+    s[0] = q.building; s[1] = 0; s[2] = q.iters; s[3] = 0;
+    v.bnorm[r] = q.bnorm;
+  }
+}
+
+// one warp per right-hand side; every load is issued first (one round trip),
+// lane l handles rows l, l + 32 and l + 64 of the column
+__global__ void __launch_bounds__(32) k_ls_step(LsView v, const double2* __restrict__ hcol, int ldh, int nrm_off,
+                                                int j, int m, double tol, int max_iter, LsOut* __restrict__ out) {
+  const int r = blockIdx.x, lane = threadIdx.x;
+  const int n1 = m + 1;
+  int* s = v.st + 4 * r;
+  const int4 st0 = *reinterpret_cast<const int4*>(s);        // building, k, iters, nonfinite
+  const double2* hh = hcol + (size_t)r * ldh;
+  double2* Q = v.Q + (size_t)r * n1 * n1;
+  double2* g = v.g + (size_t)r * n1;
+  const double hn = hh[nrm_off].x;
+  const double bnorm = v.bnorm[r];
+  const double2 gj = g[j];
+  double2 h[3], q[3];
+#pragma unroll
+  for (int u = 0; u < 3; ++u) {
+    const int i = lane + 32 * u;
+    h[u] = q[u] = make_double2(0.0, 0.0);
+    if (i <= j) {
+      h[u] = hh[i] + hh[(m + 2) + i];
+      q[u] = Q[(size_t)j * n1 + i];
+    }
+  }
+  int4 st1 = st0;
+  if (st0.x) {
+    double2* Hr = v.Hraw + (size_t)r * n1 * m;
+    double2 part = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int i = lane + 32 * u;
+      if (i <= j) Hr[(size_t)i * m + j] = h[u];
+      if (32 * u <= j) part += cmul(q[u], h[u]);            // warp-uniform: FP64 issue is the cost here
+    }
+    if (lane == 0) Hr[(size_t)(j + 1) * m + j] = make_double2(hn, 0.0);
+    const double2 t = warp_sum_c(part);                      // entry j of the column after the earlier rotations
+    if (!isfinite(hn)) {
+      st1.x = 0; st1.y = 0; st1.w = 1;
+    } else {
+      const double a2 = t.x * t.x + t.y * t.y;
+      double c;
+      double2 sv;
+      if (hn == 0.0) { c = 1.0; sv = make_double2(0.0, 0.0); }
+      else if (a2 == 0.0) { c = 0.0; sv = make_double2(1.0, 0.0); }
+      else {
+        // c = |t| / rho, s = t hn / (|t| rho), with two reciprocal square roots
+        const double ia = rsqrt(a2), irho = rsqrt(fma(hn, hn, a2));
+        c = a2 * ia * irho;
+        const double f = hn * irho * ia;
+        sv = make_double2(t.x * f, t.y * f);
+      }
+      // rows j and j+1 of Q^H: [c s; -conj(s) c] applied to (row j, e_{j+1})
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int i = lane + 32 * u;
+        if (i <= j + 1) {
+          const double e1 = i == j + 1 ? 1.0 : 0.0;
+          Q[(size_t)j * n1 + i] = c * q[u] + e1 * sv;
+          Q[(size_t)(j + 1) * n1 + i] = make_double2(e1 * c, 0.0) - cmulc(sv, q[u]);
+        }
+      }
+      const double2 g1 = -1.0 * cmulc(sv, gj);
+      const double est2 = cabs2(g1), tb = tol * bnorm;
+      st1.y = j + 1;
+      st1.z += 1;
+      if (est2 <= tb * tb || hn == 0.0 || st1.z >= max_iter) st1.x = 0;
+      if (lane == 0) {
+        g[j + 1] = g1;
+        g[j] = c * gj;
+        out[r].est2 = est2;
+      }
+    }
+    if (lane == 0) *reinterpret_cast<int4*>(s) = st1;
+  }
+  if (lane == 0) {
+    out[r].building = st1.x;
+    out[r].k = st1.y;
+    out[r].iters = st1.z;
+    out[r].nonfinite = st1.w;
+  }
+}
+
+// R[i][c] = sum_{l <= c+1} Q^H[i][l] Hraw[l][c] for i <= c < k: block (c, r),
+// lanes over rows
+__global__ void __launch_bounds__(64) k_ls_rmat(LsView v, int m) {
+  const int c = blockIdx.x, r = blockIdx.y;
+  const int* s = v.st + 4 * r;
+  const int k = s[3] ? 0 : s[1];
+  if (c >= k) return;
+  const int n1 = m + 1;
+  const double2* Q = v.Q + (size_t)r * n1 * n1;
+  const double2* Hr = v.Hraw + (size_t)r * n1 * m;
+  double2* Rm = v.Rm + (size_t)r * m * m;
+  for (int i = threadIdx.x; i <= c; i += blockDim.x) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int l = 0; l <= c + 1; ++l) acc += cmul(Q[(size_t)i * n1 + l], Hr[(size_t)l * m + c]);
+    Rm[(size_t)i * m + c] = acc;
+  }
+}
+
+// back substitution, one warp per right-hand side (column oriented)
+__global__ void __launch_bounds__(32) k_ls_backsolve(LsView v, double2* __restrict__ y, int m) {
+  const int r = blockIdx.x, lane = threadIdx.x;
+  const int* s = v.st + 4 * r;
+  const int k = s[3] ? 0 : s[1];
+  const double2* Rm = v.Rm + (size_t)r * m * m;
+  const double2* g = v.g + (size_t)r * (m + 1);
+  double2* yr = y + (size_t)r * m;
+  __shared__ double2 tt[64];
+  for (int i = lane; i < m; i += 32) {
+    tt[i] = i < k ? g[i] : make_double2(0.0, 0.0);
+    if (i >= k) yr[i] = make_double2(0.0, 0.0);
+  }
+  __syncwarp();
+  for (int i = k - 1; i >= 0; --i) {
+    const double2 d = Rm[(size_t)i * m + i];
+    const double idd = 1.0 / (d.x * d.x + d.y * d.y);
+    const double2 ti = tt[i];
+    const double2 yi = make_double2((ti.x * d.x + ti.y * d.y) * idd, (ti.y * d.x - ti.x * d.y) * idd);
+    if (lane == 0) yr[i] = yi;
+    for (int l = lane; l < i; l += 32) tt[l] -= cmul(Rm[(size_t)l * m + i], yi);
+    __syncwarp();
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_ls_init(LsView v, const LsInit* init, int R, int m, cudaStream_t st) {
+  k_ls_init<<<R, 128, 0, st>>>(v, init, m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ls_step(LsView v, const double2* hcol, int ldh, int nrm_off, int j, int R, int m, double tol,
+                           int max_iter, LsOut* out, cudaStream_t st) {
+  k_ls_step<<<R, 32, 0, st>>>(v, hcol, ldh, nrm_off, j, m, tol, max_iter, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ls_solve(LsView v, double2* y, int R, int m, cudaStream_t st) {
+  k_ls_rmat<<<dim3(m, R), 64, 0, st>>>(v, m);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_ls_backsolve<<<R, 32, 0, st>>>(v, y, m);
+  return cudaGetLastError();
+}

@@ -66,18 +66,14 @@ struct SlotState {
 };
 
 // Arnoldi scratch of one restart cycle (host side), R right-hand sides x m steps
+// host mirror of the per-RHS progress of a restart cycle (the least-squares
+// state itself lives on the device, LsView)
 struct OuterState {
   int R = 0, m = 0;
-  std::vector<std::vector<double2>> H, g, sn;
-  std::vector<std::vector<double>> cs;
   std::vector<int> k, building;
   void resize(int R_, int m_) {
     if (R_ == R && m_ == m) return;
     R = R_; m = m_;
-    H.assign(R, std::vector<double2>((size_t)(m + 1) * m));
-    g.assign(R, std::vector<double2>(m + 1));
-    sn.assign(R, std::vector<double2>(m));
-    cs.assign(R, std::vector<double>(m));
     k.assign(R, 0);
     building.assign(R, 0);
   }
@@ -170,13 +166,28 @@ struct amamg_ctx {
   const float* cur_inv32 = nullptr;
   OuterState outer;
   double2* d_y = nullptr;    // [R][m]
-  double2* h_h = nullptr;    // pinned host mirror of d_h
-  double2* h_y = nullptr;    // pinned host mirror of d_y
+  double2* h_h = nullptr;    // pinned host mirror of d_h (norms at the start of a cycle)
+  // device least-squares state of the outer FGMRES and its host exchange
+  double2* ls_H = nullptr;   // [R][m + 1][m] raw Hessenberg columns
+  double2* ls_Q = nullptr;   // [R][m + 1][m + 1] accumulated rotations
+  double2* ls_R = nullptr;   // [R][m][m] triangular factor
+  double2* ls_g = nullptr;   // [R][m + 1]
+  double* ls_bnorm = nullptr;  // [R]
+  int* ls_st = nullptr;      // [R][4]
+  LsOut* d_lsout = nullptr;  // [R] per-step progress, copied to h_lsout
+  LsOut* h_lsout = nullptr;  // pinned
+  LsInit* d_lsinit = nullptr;  // [R] cycle start, copied from h_lsinit
+  LsInit* h_lsinit = nullptr;  // pinned
+  LsView ls() const { return LsView{ls_H, ls_Q, ls_R, ls_g, ls_bnorm, ls_st}; }
 
   // work stream of the solver (graph capture needs a non-default stream) and the
   // per-step CUDA graphs of one Arnoldi step j (captured once, replayed)
   cudaStream_t ws = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // side branch of an Arnoldi step: the least-squares update runs on ws2 beside
+  // the normalisation of the new basis vector
+  cudaStream_t ws2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::vector<cudaGraphExec_t> step_graphs;
   std::vector<long long> step_graph_kernels;
   int graph_R = 0;

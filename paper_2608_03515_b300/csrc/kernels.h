@@ -160,6 +160,32 @@ cudaError_t launch_scale_copy_dual(double2* dst, float2* dst32, size_t dr, const
                                    const double* scale, long len, int R, cudaStream_t st);
 template <typename Cs, typename Cd>
 cudaError_t launch_cast(const Cs* src, Cd* dst, long len, cudaStream_t st);
+// Least-squares part of the outer FGMRES on the device, per right-hand side:
+// the raw Hessenberg columns, the accumulated rotations Q^H (the product of
+// the Givens rotations so far, (m + 1) x (m + 1), identity beyond the current
+// step), the rotated right-hand side g = Q^H beta e_1 and st = {building, k,
+// iters, nonfinite}.
+struct LsView {
+  double2* Hraw;    // [R][m + 1][m]: column j = (h_0j .. h_jj, h_{j+1,j})
+  double2* Q;       // [R][m + 1][m + 1] accumulated Q^H (row i, column c at i (m + 1) + c)
+  double2* Rm;      // [R][m][m] triangular factor Q^H H at the end of a cycle
+  double2* g;       // [R][m + 1]
+  double* bnorm;    // [R]
+  int* st;          // [R][4]
+};
+struct LsOut { double est2; int building, k, iters, nonfinite; };  // per RHS (est2 = |g_{j+1}|^2), read each step
+struct LsInit { double beta, bnorm; int building, iters; };        // per RHS, written by the host each cycle
+cudaError_t launch_ls_init(LsView v, const LsInit* init, int R, int m, cudaStream_t st);
+// Arnoldi step j: column j = h1 + h2 (the two Gram-Schmidt passes, rows 0..j of
+// hcol[r]) and h_{j+1,j} = ||w|| (hcol[r][nrm_off].x); the rotation that
+// annihilates h_{j+1,j} after the earlier ones, Q^H and g updated; the RHS
+// stops building when |g_{j+1}| <= tol ||b||, on breakdown or after max_iter
+// steps in total
+cudaError_t launch_ls_step(LsView v, const double2* hcol, int ldh, int nrm_off, int j, int R, int m, double tol,
+                           int max_iter, LsOut* out, cudaStream_t st);
+// end of a cycle: R = Q^H H (k_r x k_r upper triangle), y_r = R^-1 g_r,
+// zero-padded to m
+cudaError_t launch_ls_solve(LsView v, double2* y, int R, int m, cudaStream_t st);
 
 // setup.cu
 // own: edge-ownership rule (OwnerRule, row_basket)
