@@ -304,6 +304,9 @@ def field_angles(Lf, beta, seed):
     return fx.metropolis_u1(Lf, Lf, beta, SWEEPS, seed)
 
 
+SERVING_SWEEP_REQUESTS = 400
+
+
 def run_serving(n_requests, rate, dev, mem_budget, thetas):
     """The serving stream: n_requests Poisson arrivals over the resident fields
     whose critical mass is tabulated (thetas[(L, k)]: futures of their angles)."""
@@ -317,12 +320,14 @@ def run_serving(n_requests, rate, dev, mem_budget, thetas):
         U = torch.from_numpy(fx.links_from_angles(thetas[(L, k)].result())).to(dev)
         fields[(L, k)] = (U, mc + 0.005)            # hierarchy at the lowest serving mass
         mcrit[(L, k)] = mc
+    saturated = None
     if rate <= 0:
         # calibration: a saturated burst (all requests at t = 0) measures the service rate
         calib = serving.poisson_requests(min(40, n_requests), 1e9, list(avail), mcrit, seed=99)
         srv = serving.Server(fields, mem_budget)
         c = serving.serve(srv, calib)
-        rate = 0.8 * c["requests_per_s"]
+        saturated = c["requests_per_s"]
+        rate = 0.8 * saturated
     srv = serving.Server(fields, mem_budget)
     reqs = serving.poisson_requests(n_requests, rate, list(avail), mcrit, seed=100)
     out = serving.serve(srv, reqs)
@@ -332,6 +337,19 @@ def run_serving(n_requests, rate, dev, mem_budget, thetas):
                           "(L, field) uniformly from the resident fields, m0 = m_crit + U[0.005, 0.1], "
                           "R ~ U{1..16}; mixed precision to 1e-10",
                 "sizes_missing": [Lm for Lm in SERVING_SIZES if Lm not in sizes]})
+    if saturated is not None:
+        # load sweep: shorter streams at 0.5 x and 1.0 x the saturated rate, same
+        # resident hierarchies (the 0.8 x stream above is the headline)
+        sweep = {}
+        for frac in (0.5, 1.0):
+            n_s = min(SERVING_SWEEP_REQUESTS, n_requests)
+            rq = serving.poisson_requests(n_s, frac * saturated, list(avail), mcrit, seed=int(100 + 10 * frac))
+            o = serving.serve(srv, rq)
+            sweep[f"{frac:g}x"] = {k: o[k] for k in ("requests", "solves_per_s", "requests_per_s", "latency_p50_ms",
+                                                     "latency_p99_ms", "not_converged")}
+            sweep[f"{frac:g}x"]["rate_req_per_s"] = frac * saturated
+        out["load_sweep"] = sweep
+        out["saturated_req_per_s"] = saturated
     return out
 
 

@@ -201,10 +201,14 @@ class Server:
             sb, rb = need[key]
             slots = int(max(1, min(max_slots, per_group // rb)))
             self.groups[key] = Group(self, key, U, m_setup, slots, precision, restart, tol, max_iter)
-        self.threads = [threading.Thread(target=g.run, daemon=True) for g in self.groups.values()]
+        self.threads = []
 
     def start(self):
+        """Starts one worker per resident hierarchy (again after close(): the
+        hierarchies stay resident between request streams)."""
+        self.closing = False
         self.t0 = time.perf_counter()
+        self.threads = [threading.Thread(target=g.run, daemon=True) for g in self.groups.values()]
         for t in self.threads:
             t.start()
 

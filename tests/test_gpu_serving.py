@@ -77,3 +77,9 @@ def test_server_stream_converges_and_reports_latency():
     assert out["max_true_relres"] <= 1e-10
     assert out["latency_p99_ms"] >= out["latency_p50_ms"] > 0
     assert all(r.done_units == r.R for r in reqs)
+    # a second stream on the same resident hierarchies (the server restarts its workers)
+    reqs2 = serving.poisson_requests(6, rate=200.0, pairs=list(fields), mcrit=mcrit, seed=8, max_rhs=2,
+                                     dm=(0.05, 0.1))
+    out2 = serving.serve(srv, reqs2)
+    assert out2["requests"] == 6 and out2["not_converged"] == 0 and out2["max_true_relres"] <= 1e-10
+    assert all(r.done_units == r.R for r in reqs2)
