@@ -355,18 +355,23 @@ def run_serving(n_requests, rate, dev, mem_budget, thetas):
 
 # ----------------------------------------------------------------------------- many right-hand sides
 
-C4_L, C4_BETA, C4_SEED, C4_DM, C4_AGGS, C4_R, C4_RHS_SEED = 1024, 12.0, 5, 0.005, [4, 4], 64, 6
+C4_L, C4_BETA, C4_SEED, C4_DM, C4_AGGS, C4_R, C4_RHS_SEED = 1024, 12.0, 5, 0.01, [4, 4], 64, 6
+# the 1024^2 field's own critical mass is not tabulated (the oracle's Arnoldi
+# route does not finish on the host in hours); the mass is set from the 256^2
+# beta = 12 field's, as in tests/golden/make_c4_oracle.py
+C4_MASS_REF = "L256_b12_s17"
 
 
 def c4_mcrit():
     table = json.load(open(os.path.join(ROOT, "tests", "golden", "mcrit.json")))
-    e = table.get(f"L{C4_L}_b{C4_BETA:g}_s{C4_SEED}")
+    e = table.get(C4_MASS_REF)
     return None if e is None else e["m_crit"]
 
 
 def run_c4(dev, theta_future):
-    """64 right-hand sides on the 1024^2 beta = 12 field at m_crit + 0.005, 3
-    levels (tiles 4, 4; coarsest 64^2 = 8192 unknowns, FP64 inverse), mixed
+    """64 right-hand sides on the 1024^2 beta = 12 field at m0 = (critical mass
+    of the 256^2 beta = 12 field) + 0.01, 3 levels (tiles 4, 4; coarsest
+    64^2 = 8192 unknowns, FP64 inverse, tensor-core apply), mixed
     precision, FGMRES(30) to 1e-10: one warm-up and one timed solve of all 64;
     beside it the plain FP64 form on the first right-hand side alone; and the
     oracle's iteration counts and sampled solution entries for the first four
@@ -376,17 +381,19 @@ def run_c4(dev, theta_future):
     from paper_2608_03515_b300 import fixtures as fx
     mc = c4_mcrit()
     if mc is None:
-        return {"skipped": "critical mass of the 1024^2 beta=12 field not tabulated"}
+        return {"skipped": f"reference critical mass {C4_MASS_REF} not tabulated"}
     m0 = mc + C4_DM
     U = torch.from_numpy(fx.links_from_angles(theta_future.result())).to(dev)
     psi = torch.from_numpy(fx.gaussian_rhs(C4_R, C4_L, C4_L, C4_RHS_SEED)).to(dev)
     x = torch.empty_like(psi)
     stream = torch.cuda.current_stream()
-    out = {"workload": f"{C4_L}x{C4_L} quenched U(1) beta={C4_BETA:g} seed {C4_SEED}, m0 = m_crit + {C4_DM}, "
+    out = {"workload": f"{C4_L}x{C4_L} quenched U(1) beta={C4_BETA:g} seed {C4_SEED}, m0 = m_crit(256^2 beta=12) "
+                       f"+ {C4_DM}, "
                        f"tiles {C4_AGGS} (coarsest 64^2, FP64 inverse), FGMRES(30) to 1e-10, {C4_R} RHS per call",
            "m0": m0}
-    h = A.setup(U, m0, A.make_params(C4_AGGS, precision=A.SOLVE_MIXED, restart=RESTART, tol=TOL))
+    h = A.setup(U, m0, A.make_params(C4_AGGS, precision=A.SOLVE_MIXED, restart=RESTART, tol=TOL, autotune=True))
     out["setup_ms"] = round(1e3 * A.setup_seconds(h), 1)
+    out["smoother_fixed_rule"] = A.query_smoother(h, 1, A.F32, C4_R)
     A.solve(h, psi, x)                                       # warm-up (captures the 64-wide graphs)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     ev[0].record(stream)
@@ -399,6 +406,7 @@ def run_c4(dev, theta_future):
                             "iterations": {"min": min(its), "max": max(its), "mean": round(float(np.mean(its)), 1)},
                             "true_relres_max": max(i.true_relres for i in info),
                             "all_converged": all(i.status == A.OK for i in info)}
+    out["smoother_autotuned"] = A.query_smoother(h, 1, A.F32, C4_R)
     xh = x[:4].cpu().numpy()
     A.destroy(h)
     del x
@@ -417,7 +425,7 @@ def run_c4(dev, theta_future):
                                                         out["fp64_single"]["solves_per_s"], 2)
     A.destroy(h64)
     gold = os.path.join(ROOT, "tests", "golden", "c4_oracle.json")
-    if os.path.exists(gold):
+    if os.path.exists(gold) and abs(json.load(open(gold))["m0"] - m0) <= 1e-15:
         g = json.load(open(gold))
         cmp = []
         for row in g["solves"]:
@@ -647,6 +655,22 @@ def main():
         A.destroy(h)
     del psib, xb
 
+    # the coarse-smoother autotuner (amamg_params.autotune): the same solves with
+    # the kernel and shape of the level-1 Gauss-Seidel timed and picked at the
+    # first solve (warm-up), FP64 and mixed
+    autotuned = {}
+    for name, prec, vp in (("fp64", A.SOLVE_FP64, A.F64), ("mixed", A.SOLVE_MIXED, A.F32)):
+        hs_at = [A.setup(U, m0, A.make_params(AGGS, precision=prec, restart=RESTART, tol=TOL, autotune=True))
+                 for m0 in masses]
+        fixed = A.query_smoother(hs_at[0], 1, vp, 1)
+        run(hs_at, nst=1)
+        st_at, _, it_at, _ = run(hs_at, nst=1 + args.steps, skip=1)
+        autotuned[name] = {"solves_per_s": round(len(masses) * args.steps / (np.sum(st_at) * 1e-3), 3),
+                           "iterations": it_at[-len(masses):], "level1_fixed_rule": fixed,
+                           "level1_autotuned": [A.query_smoother(h, 1, vp, 1) for h in hs_at]}
+        for h in hs_at:
+            A.destroy(h)
+
     # the opt-in spin-split hierarchy (spin-diagonal interpolation weights; a
     # comparison beside the method as read): one warm-up and one timed step
     hs_ss = []
@@ -827,6 +851,7 @@ def main():
                                      "p99": round(float(np.percentile(sv32, 99)), 3)},
                       "setup_ms": [round(s, 2) for s in setup32]},
             "mixed_gs_df64": gs_df64,
+            "autotuned": autotuned,
             "latency_ms": {"p50": round(float(np.percentile(solve_ms, 50)), 3),
                            "p99": round(float(np.percentile(solve_ms, 99)), 3)},
             "batched_mixed": batched,

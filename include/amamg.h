@@ -109,6 +109,13 @@ typedef struct {
                                         level) and the V-cycle is no longer a fixed linear map (the
                                         outer FGMRES is flexible) */
     int    gs_arith;                 /* AMAMG_GS_FP64 (default) or AMAMG_GS_DF64 (with AMAMG_SOLVE_MIXED) */
+    int    autotune;                 /* 0 (default): fixed rules pick each coarse level's Gauss-Seidel
+                                        kernel and its shape; 1: the first solve, batch cycle or
+                                        amamg_vcycle of each right-hand-side count times the
+                                        candidates on the handle's work vectors (CUDA events, before
+                                        any graph capture) and keeps the fastest; the candidates
+                                        compute the same sweeps up to rounding order.  Not part of
+                                        the paper's method. */
 } amamg_params;
 
 typedef struct {
@@ -240,6 +247,21 @@ int amamg_coarsest_solve(amamg_handle h, const void* r, void* e, int R, void* st
  * when R >= 8 and 2 Nt_L Nx_L is a multiple of 128, or GMRES in FP32 with
  * AMAMG_COARSEST_GMRES. */
 int amamg_coarsest_apply(amamg_handle h, const void* r, void* e, int R, int precision, void* stream);
+
+/* coarse Gauss-Seidel kernels (amamg_query_smoother) */
+#define AMAMG_SMOOTHER_COLOUR  0     /* one launch per colour */
+#define AMAMG_SMOOTHER_CLUSTER 1     /* all phases on an 8-block cluster, e in L2 (FP32) */
+#define AMAMG_SMOOTHER_DSMEM   2     /* all phases on a 16-block cluster, the level in distributed shared memory */
+#define AMAMG_SMOOTHER_GRID    3     /* all phases in one cooperative launch, a grid barrier per phase */
+#define AMAMG_SMOOTHER_OWNER   4     /* all phases in one cooperative launch of site-owning blocks */
+
+/* The coarse Gauss-Seidel kernel (AMAMG_SMOOTHER_*) and owner-sweep shape
+ * variant (0: the fixed rule; bits 0-1: early-sum lanes 8 (1) or 16 (2); bit
+ * 2: twice the fewest sites per block) that a smoothing of level `level`
+ * (1 .. nlevels-2, the smoothed coarse levels) with R right-hand sides in
+ * `precision` (AMAMG_F64 / AMAMG_F32) uses now: the autotuner's pick where it
+ * ran for that R, else the fixed rule.  Host-only; no GPU work. */
+int amamg_query_smoother(amamg_handle h, int level, int precision, int R, int* kernel, int* variant);
 
 /* e = M(r): one V-cycle of Algorithm 1 on the fine level with start vector 0,
  * no pre-smoothing and post_smooth sweeps per level. */

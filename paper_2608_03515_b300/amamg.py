@@ -39,7 +39,7 @@ GS_DF64 = 1
 
 EXPORTED = [
     "amamg_default_params", "amamg_query_bytes", "amamg_setup", "amamg_solve", "amamg_apply_D",
-    "amamg_apply_Ddag", "amamg_cgnr", "amamg_coarsest_apply",
+    "amamg_apply_Ddag", "amamg_cgnr", "amamg_coarsest_apply", "amamg_query_smoother",
     "amamg_apply_P", "amamg_apply_PH", "amamg_apply_coarse", "amamg_smooth", "amamg_coarsest_solve",
     "amamg_vcycle", "amamg_vcycle_noalloc", "amamg_selftest_sync_timeout", "amamg_sync_status", "amamg_export_structure", "amamg_level_info", "amamg_export_P", "amamg_export_coarse",
     "amamg_profile_enable", "amamg_profile_reset", "amamg_profile_get", "amamg_launch_count",
@@ -62,6 +62,7 @@ class Params(ctypes.Structure):
         ("edge_owner", ctypes.c_int),
         ("coarsest", ctypes.c_int),
         ("gs_arith", ctypes.c_int),
+        ("autotune", ctypes.c_int),
     ]
 
 
@@ -94,6 +95,7 @@ def _load() -> ctypes.CDLL:
         "amamg_smooth": ([vp, ci, vp, vp, ci, ci, ci, vp], ci),
         "amamg_coarsest_solve": ([vp, vp, vp, ci, vp], ci),
         "amamg_coarsest_apply": ([vp, vp, vp, ci, ci, vp], ci),
+        "amamg_query_smoother": ([vp, ci, ci, ci, ctypes.POINTER(ci), ctypes.POINTER(ci)], ci),
         "amamg_vcycle": ([vp, vp, vp, ci, ci, vp], ci),
         "amamg_vcycle_noalloc": ([vp, vp, vp, ci, ci, vp], ci),
         "amamg_selftest_sync_timeout": ([vp, ci, ci, vp], ci),
@@ -173,12 +175,13 @@ def default_params() -> Params:
 def make_params(aggs: Sequence[int], precision: int = SOLVE_FP64, restart: int = 30, max_iter: int = 3000,
                 post_smooth: int = 2, tol: float = 1e-10, spin_split: bool = False,
                 normalization: str = "none", ownership: str = "tile", coarsest: str = "direct",
-                gs: str = "fp64") -> Params:
+                gs: str = "fp64", autotune: bool = False) -> Params:
     """Parameters of amamg_setup; normalization "none" | "rowsum" and ownership
     "tile" | "first_lex" name the readings the oracle's build_hierarchy takes;
     coarsest "direct" | "gmres" the coarsest solver (the oracle's vcycle
     coarsest="lu" | "gmres"); gs "fp64" | "df64" the outer Gram-Schmidt's
-    arithmetic (df64 with mixed precision only)."""
+    arithmetic (df64 with mixed precision only); autotune: time the coarse
+    Gauss-Seidel candidates at the first solve of each right-hand-side count."""
     p = default_params()
     p.nlevels = len(aggs) + 1
     for i, a in enumerate(aggs):
@@ -193,6 +196,7 @@ def make_params(aggs: Sequence[int], precision: int = SOLVE_FP64, restart: int =
     p.edge_owner = {"tile": OWNER_TILE, "first_lex": OWNER_FIRST_LEX}[ownership]
     p.coarsest = {"direct": COARSEST_DIRECT, "gmres": COARSEST_GMRES}[coarsest]
     p.gs_arith = {"fp64": GS_FP64, "df64": GS_DF64}[gs]
+    p.autotune = 1 if autotune else 0
     return p
 
 
@@ -344,6 +348,18 @@ def selftest_sync_timeout(hier: Hierarchy, level: int, precision: int = None, st
     enqueued; sync_status then reports the time-out)."""
     prec = F64 if precision is None else precision
     return int(_lib.amamg_selftest_sync_timeout(hier.h, level, prec, _stream(stream)))
+
+
+SMOOTHER_NAMES = {0: "colour", 1: "cluster", 2: "dsmem", 3: "grid", 4: "owner"}
+
+
+def query_smoother(hier: Hierarchy, level: int, precision: int, R: int = 1):
+    """amamg_query_smoother: (kernel name, owner-shape variant) that a smoothing
+    of `level` with R right-hand sides in `precision` (F64 / F32) uses now."""
+    k, v = ctypes.c_int(), ctypes.c_int()
+    hier._check(_lib.amamg_query_smoother(hier.h, level, precision, R, ctypes.byref(k), ctypes.byref(v)),
+                "amamg_query_smoother")
+    return SMOOTHER_NAMES[k.value], v.value
 
 
 def sync_status(hier: Hierarchy, stream=None) -> int:

@@ -396,7 +396,8 @@ int smooth_impl(amamg_ctx* h, int l, typename cplx<T>::type* e, const typename c
   const int nc = L.ncol;
   const double bytes = (double)L.n / nc * ((L.off.K - 1) * blk + 4 * cb + R * 2 * 3 * cb);
   const double flops = (double)L.n / nc * R * ((L.off.K - 1) * 32.0 + 36.0);   // one colour
-  const int kind = gs_kind_for<T>(L, R);
+  const std::pair<int, int> choice = gs_choice<T>(L, R);
+  const int kind = choice.first, variant = choice.second;
   if (sweeps > 0 && kind == GS_DSMEM) {
     // every colour of every sweep on one 16-block cluster, level in shared memory
     const bool bsm = dsmem_blocks_in_smem<T>(L.n, L.off.K);
@@ -416,12 +417,12 @@ int smooth_impl(amamg_ctx* h, int l, typename cplx<T>::type* e, const typename c
     if constexpr (f64)
       return launch(h, "coarse_smooth_f64", bytes * nc * sweeps, st, [&] {
         return launch_coarse_sweeps_owner<double, double2>(e, r, L.Bc64, nullptr, L.Dc64, L.off, L.Nt, L.Nx, nc,
-                                                          sweeps, R, h->d_owner_flags, h->d_sync, st);
+                                                          sweeps, R, h->d_owner_flags, h->d_sync, st, -1, variant);
       }, flops * nc * sweeps);
     else
       return launch(h, "coarse_smooth_f32", bytes * nc * sweeps, st, [&] {
         return launch_coarse_sweeps_owner<float, __half2>(e, r, L.Bc16, L.Bcs, L.Dc32, L.off, L.Nt, L.Nx, nc, sweeps,
-                                                         R, h->d_owner_flags, h->d_sync, st);
+                                                         R, h->d_owner_flags, h->d_sync, st, -1, variant);
       }, flops * nc * sweeps);
   }
   if (sweeps > 0 && kind == GS_GRID) {
@@ -940,6 +941,81 @@ int check_grid_sync(amamg_ctx* h, cudaStream_t st) {
   return AMAMG_ERR_TIMEOUT;
 }
 
+// ----------------------------------------------------------------- autotuner
+// With amamg_params.autotune, the first V-cycle of each right-hand-side count R
+// (outside graph capture) times the coarse Gauss-Seidel candidates of every
+// smoothed coarse level in the precision the V-cycle runs in -- the owner sweep
+// in its shape variants (early-sum lanes 8 or 16, the fewest or twice the
+// fewest sites per block), the grid sweep and the distributed-shared-memory
+// cluster sweep, where each fits -- with CUDA events on the level's own work
+// vectors (2 warm-up and 5 timed launches each), and keeps the fastest for
+// that R.  The candidates compute the same sweeps; they differ only in the
+// rounding order of the owner sweep's split sums.
+template <typename T>
+int tune_level(amamg_ctx* h, int l, int R, cudaStream_t st) {
+  Level& L = h->lv[l];
+  constexpr bool f64 = sizeof(T) == 8;
+  using BT = typename std::conditional<f64, double2, __half2>::type;
+  auto& tm = f64 ? L.tune64 : L.tune32;
+  if (tm.count(R)) return AMAMG_OK;
+  std::vector<std::pair<int, int>> cand;
+  std::vector<OwnerConfig> seen;
+  for (const int v : {0, 1, 2, 4, 5, 6}) {
+    OwnerConfig oc;
+    if (!owner_sweep_config<T, BT>(L.Nt, L.Nx, L.off.K, L.ncol, L.off, R, &oc, v)) continue;
+    bool dup = false;
+    for (const auto& o : seen) dup |= o.cnt == oc.cnt && o.early_lanes == oc.early_lanes && o.slots == oc.slots;
+    if (dup) continue;
+    seen.push_back(oc);
+    cand.push_back({GS_OWNER, v});
+  }
+  if (grid_sweep_blocks<T, BT>(L.n, L.ncol, R) > 0) cand.push_back({GS_GRID, 0});
+  if (dsmem_sweeps_possible<T, BT>(L.n, L.off.K, L.ncol, dsmem_blocks_in_smem<T>(L.n, L.off.K)))
+    cand.push_back({GS_DSMEM, 0});
+  if (cand.size() < 2) return AMAMG_OK;                      // nothing to choose: the fixed rule stands
+  typename cplx<T>::type* e = f64 ? (typename cplx<T>::type*)L.e64 : (typename cplx<T>::type*)L.e32;
+  typename cplx<T>::type* r = f64 ? (typename cplx<T>::type*)L.r64 : (typename cplx<T>::type*)L.r32;
+  const size_t nb = sizeof(typename cplx<T>::type) * (size_t)R * 2 * L.n;
+  CK(cudaMemsetAsync(r, 0, nb, st));
+  CK(cudaMemsetAsync(e, 0, nb, st));
+  cudaEvent_t a = nullptr, b = nullptr;
+  CK(cudaEventCreate(&a));
+  if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); h->err = "cudaEventCreate"; return AMAMG_ERR_CUDA; }
+  const bool prof = h->prof;
+  h->prof = false;
+  const int sweeps = h->prm.post_smooth > 0 ? h->prm.post_smooth : 2;
+  float best = 1e30f;
+  std::pair<int, int> pick = cand[0];
+  int rc = AMAMG_OK;
+  for (const auto& c : cand) {
+    tm[R] = c;
+    for (int w = 0; w < 2 && rc == AMAMG_OK; ++w) rc = smooth_impl<T>(h, l, e, r, R, sweeps, st);
+    if (rc == AMAMG_OK && cudaEventRecord(a, st) != cudaSuccess) rc = AMAMG_ERR_CUDA;
+    for (int w = 0; w < 5 && rc == AMAMG_OK; ++w) rc = smooth_impl<T>(h, l, e, r, R, sweeps, st);
+    if (rc == AMAMG_OK && (cudaEventRecord(b, st) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess))
+      rc = AMAMG_ERR_CUDA;
+    if (rc != AMAMG_OK) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    if (ms < best) { best = ms; pick = c; }
+  }
+  h->prof = prof;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  tm[R] = pick;
+  if (rc != AMAMG_OK) return rc;
+  return check_grid_sync(h, st);
+}
+
+// Tunes every smoothed coarse level for R right-hand sides in precision prec
+// (AMAMG_F64 or AMAMG_F32) when the handle asks for it.
+int tune_smoothers(amamg_ctx* h, int R, int prec, cudaStream_t st) {
+  if (!h->prm.autotune) return AMAMG_OK;
+  for (int l = 1; l + 1 < (int)h->lv.size(); ++l)
+    CKS(prec == AMAMG_F64 ? tune_level<double>(h, l, R, st) : tune_level<float>(h, l, R, st));
+  return AMAMG_OK;
+}
+
 // Solver kernels read the per-RHS mass arrays while this guard is alive.
 struct MassGuard {
   amamg_ctx* h;
@@ -955,6 +1031,7 @@ int fgmres_on(amamg_ctx* h, const double2* psi, double2* x, int R, cudaStream_t 
   const long len = 2L * h->lv[0].n;
   CKS(ensure_vcycle_ws(h, R));
   CKS(ensure_solver_ws(h, R));
+  CKS(tune_smoothers(h, R, h->prm.precision == AMAMG_SOLVE_MIXED ? AMAMG_F32 : AMAMG_F64, st));
   std::vector<double> masses(R, h->m0);
   CKS(set_masses(h, masses.data(), R, st));
   MassGuard guard(h);
@@ -997,6 +1074,7 @@ int check_params(const amamg_params* p, int Nt, int Nx, std::string* why) {
   if (p->nlevels < 2 || p->nlevels > AMAMG_MAX_LEVELS) { *why = "nlevels must be 2..4"; return AMAMG_ERR_INVALID_ARG; }
   if (p->precision != AMAMG_SOLVE_FP64 && p->precision != AMAMG_SOLVE_MIXED) { *why = "bad precision"; return AMAMG_ERR_INVALID_ARG; }
   if (p->restart < 1 || p->restart > 64) { *why = "restart must be 1..64"; return AMAMG_ERR_INVALID_ARG; }
+  if (p->autotune != 0 && p->autotune != 1) { *why = "autotune must be 0 or 1"; return AMAMG_ERR_INVALID_ARG; }
   if (p->max_iter < 1 || p->post_smooth < 0 || !(p->tol > 0.0)) { *why = "bad max_iter/post_smooth/tol"; return AMAMG_ERR_INVALID_ARG; }
   if (p->spin_split != 0 && p->spin_split != 1) { *why = "spin_split must be 0 or 1"; return AMAMG_ERR_INVALID_ARG; }
   if (p->normalization != AMAMG_NORM_NONE && p->normalization != AMAMG_NORM_ROWSUM) {
@@ -1406,7 +1484,8 @@ int amamg_batch_cycle(amamg_batch_handle b, void* stream, amamg_slot_info* info)
   if (rc != AMAMG_OK) return rc;
   CK(cudaEventRecord(h->ev_in, st));
   CK(cudaStreamWaitEvent(h->ws, h->ev_in, 0));
-  rc = set_masses(h, b->mass.data(), R, h->ws);
+  rc = tune_smoothers(h, R, h->prm.precision == AMAMG_SOLVE_MIXED ? AMAMG_F32 : AMAMG_F64, h->ws);
+  if (rc == AMAMG_OK) rc = set_masses(h, b->mass.data(), R, h->ws);
   bool left = false;
   if (rc == AMAMG_OK) {
     MassGuard guard(h);
@@ -1535,9 +1614,22 @@ int amamg_coarsest_apply(amamg_handle h, const void* r, void* e, int R, int prec
   return AMAMG_ERR_INVALID_ARG;
 }
 
+int amamg_query_smoother(amamg_handle h, int level, int precision, int R, int* kernel, int* variant) {
+  if (!h || !kernel || !variant || level < 1 || level + 1 >= (int)h->lv.size() || R < 1) return AMAMG_ERR_INVALID_ARG;
+  std::pair<int, int> c;
+  if (precision == AMAMG_F64) c = gs_choice<double>(h->lv[level], R);
+  else if (precision == AMAMG_F32) c = gs_choice<float>(h->lv[level], R);
+  else return AMAMG_ERR_INVALID_ARG;
+  *kernel = c.first;
+  *variant = c.second;
+  return AMAMG_OK;
+}
+
 int amamg_vcycle(amamg_handle h, const void* r, void* e, int R, int precision, void* stream) {
   if (!h || !r || !e || R < 1) return AMAMG_ERR_INVALID_ARG;
+  if (precision != AMAMG_F64 && precision != AMAMG_F32) return AMAMG_ERR_INVALID_ARG;
   int rc = ensure_vcycle_ws(h, R);
+  if (rc == AMAMG_OK) rc = tune_smoothers(h, R, precision, S(stream));
   if (rc != AMAMG_OK) return rc;
   if (precision == AMAMG_F64)
     return vcycle_from<double>(h, 0, (const double2*)r, (double2*)e, handle_vecs<double>(h), R, S(stream));

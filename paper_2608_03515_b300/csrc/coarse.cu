@@ -1140,7 +1140,8 @@ static auto owner_kernel(bool bsmem, int slots, int le) {
 }
 
 template <typename T, typename BT>
-static bool owner_sweep_search(int Nt, int Nx, int K, int ncol, const Offsets& off, int R, OwnerConfig* cfg) {
+static bool owner_sweep_search(int Nt, int Nx, int K, int ncol, const Offsets& off, int R, OwnerConfig* cfg,
+                               int variant) {
   int dev = 0, sms = 0, coop = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) || !coop) {
@@ -1155,13 +1156,16 @@ static bool owner_sweep_search(int Nt, int Nx, int K, int ncol, const Offsets& o
   int late_half = 0;                                         // first xor offset of the late-slot reduction
   while (2 * late_half < max_late) late_half = late_half ? 2 * late_half : 1;
   if (max_late == 1) late_half = 0;
+  const int le_force = (variant & 3) == 1 ? 8 : (variant & 3) == 2 ? 16 : 0;
+  int first_fit = 0;                                         // variant & 4: at least twice the first fitting cnt
   for (int cnt = std::min(AMAMG_OWNER_MIN_CNT, m); cnt <= m; ++cnt) {
     if (m % cnt) continue;
+    if (first_fit && cnt < 2 * first_fit) continue;
     const int nbpr = m / cnt;
     const long blocks = (long)R * nbpr;
     if (nbpr > OWNER_MAX_BLOCKS || blocks > OWNER_MAX_BLOCKS) continue;
     const int own = ncol * cnt;
-    const int le = blocks <= sms ? 16 : 8;                     // one block per SM: spread the early sums
+    const int le = le_force ? le_force : blocks <= sms ? 16 : 8;   // one block per SM: spread the early sums
     const int spe = 32 / le, spp = 32 / (4 * S);
     const int nearly = std::min((cnt + spe - 1) / spe, OWNER_EARLY_WARPS);
     const int npost = std::min((cnt + spp - 1) / spp, OWNER_POST_WARPS);
@@ -1177,6 +1181,10 @@ static bool owner_sweep_search(int Nt, int Nx, int K, int ncol, const Offsets& o
     }
     if (blocks > (long)occ * sms) continue;
     if (owner_max_wait(Nt, Nx, ncol, off, cnt) > OWNER_MAX_WAIT) continue;
+    if ((variant & 4) && !first_fit) {
+      first_fit = cnt;
+      continue;
+    }
     cfg->cnt = cnt;
     cfg->late_half = late_half;
     cfg->slots = S;
@@ -1191,20 +1199,23 @@ static bool owner_sweep_search(int Nt, int Nx, int K, int ncol, const Offsets& o
   return false;
 }
 
-// Cached per (element type, device, level shape, offsets, R).
+// Cached per (element type, device, level shape, offsets, R, variant).
+// variant (the autotuner's candidates): bits 0-1 force the early-sum lanes
+// (1: 8, 2: 16; 0: by blocks per SM), bit 2 takes at least twice the fewest
+// sites per block that fit.
 template <typename T, typename BT>
-bool owner_sweep_config(int Nt, int Nx, int K, int ncol, const Offsets& off, int R, OwnerConfig* cfg) {
+bool owner_sweep_config(int Nt, int Nx, int K, int ncol, const Offsets& off, int R, OwnerConfig* cfg, int variant) {
   static std::mutex mu;
   static std::map<std::vector<int>, std::pair<bool, OwnerConfig>> cache;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return false; }
-  std::vector<int> key = {dev, Nt, Nx, K, ncol, R};
+  std::vector<int> key = {dev, Nt, Nx, K, ncol, R, variant};
   for (int k = 0; k < off.K; ++k) { key.push_back(off.dt[k]); key.push_back(off.dx[k]); }
   std::lock_guard<std::mutex> lock(mu);
   auto it = cache.find(key);
   if (it == cache.end()) {
     OwnerConfig oc;
-    const bool ok = owner_sweep_search<T, BT>(Nt, Nx, K, ncol, off, R, &oc);
+    const bool ok = owner_sweep_search<T, BT>(Nt, Nx, K, ncol, off, R, &oc, variant);
     it = cache.emplace(key, std::make_pair(ok, oc)).first;
   }
   *cfg = it->second.second;
@@ -1215,9 +1226,9 @@ template <typename T, typename BT>
 cudaError_t launch_coarse_sweeps_owner(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* Bc,
                                        const float* Sc, const typename cplx<T>::type* Dc, const Offsets& off,
                                        int Nt, int Nx, int ncol, int sweeps, int R, unsigned* flags, unsigned* sync,
-                                       cudaStream_t st, int withhold) {
+                                       cudaStream_t st, int withhold, int variant) {
   OwnerConfig oc;
-  if (!owner_sweep_config<T, BT>(Nt, Nx, off.K, ncol, off, R, &oc)) return cudaErrorNotSupported;
+  if (!owner_sweep_config<T, BT>(Nt, Nx, off.K, ncol, off, R, &oc, variant)) return cudaErrorNotSupported;
   auto kern = owner_kernel<T, BT>(oc.bsmem, oc.slots, oc.early_lanes);
   // the attribute is per kernel, and another level may have set a smaller one
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oc.smem);
@@ -1355,14 +1366,15 @@ template cudaError_t launch_coarse_colour<float, __half2>(float2*, const float2*
 template cudaError_t launch_coarse_sweeps_cluster<float, __half2>(float2*, const float2*, const __half2*, const float*,
                                                                   const float2*, const Offsets&, int, int, int, int,
                                                                   int, cudaStream_t);
-template bool owner_sweep_config<double, double2>(int, int, int, int, const Offsets&, int, OwnerConfig*);
-template bool owner_sweep_config<float, __half2>(int, int, int, int, const Offsets&, int, OwnerConfig*);
+template bool owner_sweep_config<double, double2>(int, int, int, int, const Offsets&, int, OwnerConfig*, int);
+template bool owner_sweep_config<float, __half2>(int, int, int, int, const Offsets&, int, OwnerConfig*, int);
 template cudaError_t launch_coarse_sweeps_owner<double, double2>(double2*, const double2*, const double2*,
                                                                 const float*, const double2*, const Offsets&, int, int,
-                                                                int, int, int, unsigned*, unsigned*, cudaStream_t, int);
+                                                                int, int, int, unsigned*, unsigned*, cudaStream_t, int,
+                                                                int);
 template cudaError_t launch_coarse_sweeps_owner<float, __half2>(float2*, const float2*, const __half2*, const float*,
                                                                const float2*, const Offsets&, int, int, int, int, int,
-                                                               unsigned*, unsigned*, cudaStream_t, int);
+                                                               unsigned*, unsigned*, cudaStream_t, int, int);
 template int grid_sweep_blocks<double, double2>(int, int, int);
 template int grid_sweep_blocks<float, __half2>(int, int, int);
 template cudaError_t launch_coarse_sweeps_grid<double, double2>(double2*, const double2*, const double2*, const float*,

@@ -1,5 +1,6 @@
 // Host-side state of one hierarchy (the object behind amamg_handle).
 #pragma once
+#include <map>
 #include <string>
 #include <vector>
 
@@ -23,6 +24,8 @@ struct Level {
   // coarse Gauss-Seidel kernel of this level in FP64 and in FP32 (GsKernel),
   // chosen in setup
   int gs64 = 0, gs32 = 0;
+  // the autotuner's (kernel, owner variant) per right-hand-side count
+  std::map<int, std::pair<int, int>> tune64, tune32;
   // colour-major copies for the Gauss-Seidel kernels (smoothed coarse levels)
   double2* Bc64 = nullptr;
   __half2* Bc16 = nullptr;
@@ -99,6 +102,16 @@ inline int gs_kind_for(const Level& L, int R) {
   const bool ok = f64 ? owner_sweep_config<double, double2>(L.Nt, L.Nx, L.off.K, L.ncol, L.off, R, &rc)
                       : owner_sweep_config<float, __half2>(L.Nt, L.Nx, L.off.K, L.ncol, L.off, R, &rc);
   return ok ? GS_OWNER : GS_GRID;
+}
+
+// (kernel, owner-sweep variant) of a smoothing launch: the autotuner's pick
+// for this R where it ran (amamg_params.autotune), else the fixed rule above
+template <typename T>
+inline std::pair<int, int> gs_choice(const Level& L, int R) {
+  const auto& tm = sizeof(T) == 8 ? L.tune64 : L.tune32;
+  const auto it = tm.find(R);
+  if (it != tm.end()) return it->second;
+  return {gs_kind_for<T>(L, R), 0};
 }
 
 // Coarse-level work vectors of one V-cycle: r_l and e_l of level l >= 1

@@ -100,13 +100,15 @@ struct OwnerConfig {
   size_t smem = 0;
   bool bsmem = false;
 };
+// variant: the autotuner's shape candidates (0: the fixed rule; see coarse.cu)
 template <typename T, typename BT>
-bool owner_sweep_config(int Nt, int Nx, int K, int ncol, const Offsets& off, int R, OwnerConfig* cfg);
+bool owner_sweep_config(int Nt, int Nx, int K, int ncol, const Offsets& off, int R, OwnerConfig* cfg,
+                        int variant = 0);
 template <typename T, typename BT>
 cudaError_t launch_coarse_sweeps_owner(typename cplx<T>::type* e, const typename cplx<T>::type* r, const BT* Bc,
                                        const float* Sc, const typename cplx<T>::type* Dc, const Offsets& off,
                                        int Nt, int Nx, int ncol, int sweeps, int R, unsigned* flags, unsigned* sync,
-                                       cudaStream_t st, int withhold = -1);
+                                       cudaStream_t st, int withhold = -1, int variant = 0);
 // Coarse Gauss-Seidel kernel choice.  Levels with n = 16 ncol per sites (per <= 64)
 // run all colours on one 16-block cluster with the level in distributed shared
 // memory; in FP32 also the off-diagonal blocks live in shared memory when they

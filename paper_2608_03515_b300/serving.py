@@ -66,14 +66,14 @@ class Request:
 class Group:
     """One resident hierarchy and its slot batch, served by one thread."""
 
-    def __init__(self, server, key, U, m_setup, slots, precision, restart, tol, max_iter):
+    def __init__(self, server, key, U, m_setup, slots, precision, restart, tol, max_iter, autotune=False):
         import torch
         self.server = server
         self.key = key
         self.L = key[0]
         self.stream = torch.cuda.Stream()
         self.params = A.make_params(aggregates_for(self.L), precision=precision, restart=restart, tol=tol,
-                                    max_iter=max_iter)
+                                    max_iter=max_iter, autotune=autotune)
         with torch.cuda.stream(self.stream):
             self.hier = A.setup(U, m_setup, self.params, stream=self.stream)
             self.batch = A.Batch(self.hier, slots)
@@ -177,8 +177,10 @@ class Server:
 
     def __init__(self, fields: Dict[Tuple[int, int], Tuple[object, float]], mem_budget_bytes: int,
                  max_slots: int = 16, precision: int = A.SOLVE_MIXED, restart: int = 30, tol: float = 1e-10,
-                 max_iter: int = 3000, device=None):
-        """fields[(L, k)] = (U on the device, setup mass)."""
+                 max_iter: int = 3000, device=None, autotune: bool = True):
+        """fields[(L, k)] = (U on the device, setup mass); autotune: each
+        hierarchy's coarse smoother is timed and picked at its first batch
+        cycle (amamg_params.autotune)."""
         import torch
         self.device = device or torch.device("cuda:0")
         self.closing = False
@@ -200,7 +202,7 @@ class Server:
         for key, (U, m_setup) in fields.items():
             sb, rb = need[key]
             slots = int(max(1, min(max_slots, per_group // rb)))
-            self.groups[key] = Group(self, key, U, m_setup, slots, precision, restart, tol, max_iter)
+            self.groups[key] = Group(self, key, U, m_setup, slots, precision, restart, tol, max_iter, autotune)
         self.threads = []
 
     def start(self):
