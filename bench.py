@@ -409,6 +409,23 @@ def run_c4(dev, theta_future):
     out["smoother_autotuned"] = A.query_smoother(h, 1, A.F32, C4_R)
     xh = x[:4].cpu().numpy()
     A.destroy(h)
+    # the same batch with the opt-in double-float Gram-Schmidt (FP64 Gram-Schmidt
+    # bounds the step above)
+    hd = A.setup(U, m0, A.make_params(C4_AGGS, precision=A.SOLVE_MIXED, restart=RESTART, tol=TOL, autotune=True,
+                                      gs="df64"))
+    A.solve(hd, psi, x)
+    ev[0].record(stream)
+    info_d = A.solve(hd, psi, x)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms_d = ev[0].elapsed_time(ev[1])
+    its_d = [i.iterations for i in info_d]
+    out["mixed_batched_gs_df64"] = {"solves_per_s": round(C4_R / (ms_d * 1e-3), 3), "ms": round(ms_d, 1),
+                                    "iterations": {"min": min(its_d), "max": max(its_d),
+                                                   "mean": round(float(np.mean(its_d)), 1)},
+                                    "true_relres_max": max(i.true_relres for i in info_d),
+                                    "all_converged": all(i.status == A.OK for i in info_d)}
+    A.destroy(hd)
     del x
     # the plain FP64 form, one right-hand side per call
     h64 = A.setup(U, m0, A.make_params(C4_AGGS, precision=A.SOLVE_FP64, restart=RESTART, tol=TOL))

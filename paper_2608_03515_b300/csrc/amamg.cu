@@ -232,10 +232,12 @@ int gs_colours(const Level& L) {
 
 // Coarse Gauss-Seidel kernel of a smoothed coarse level, per precision.
 // FP64: the owner sweep (all SMs, neighbour waits only), else the grid sweep,
-// since one 16-block cluster has the FP64 throughput of only 16 SMs.  FP32: one
-// 16-block cluster with the level in distributed shared memory where it fits,
-// else the owner sweep, else the grid sweep, else the L2 cluster sweep, else
-// one launch per colour.  AMAMG_COARSE_GS = colour | cluster | dsmem | grid |
+// since one 16-block cluster has the FP64 throughput of only 16 SMs.  FP32, one
+// right-hand side: the owner sweep, else the 16-block cluster with the level
+// in distributed shared memory, else the grid sweep, else the L2 cluster
+// sweep, else one launch per colour; FP32 with R >= 2: the cluster sweep where
+// it fits (one cluster per right-hand side, 37 us at 64^2 against 47 us for the
+// owner sweep at R = 4), else the R = 1 choice.  AMAMG_COARSE_GS = colour | cluster | dsmem | grid |
 // owner forces a kernel where it is available (for measurement); results are
 // the same.
 void choose_gs_kernels(Level& C) {
@@ -249,7 +251,8 @@ void choose_gs_kernels(Level& C) {
                                                             dsmem_blocks_in_smem<float>(C.n, C.off.K));
   const bool clu32 = use_cluster_sweeps<float>(C.n, C.ncol);
   C.gs64 = owner64 ? GS_OWNER : grid64 ? GS_GRID : dsm64 ? GS_DSMEM : GS_COLOUR;
-  C.gs32 = dsm32 ? GS_DSMEM : owner32 ? GS_OWNER : grid32 ? GS_GRID : clu32 ? GS_CLUSTER : GS_COLOUR;
+  C.gs32 = owner32 ? GS_OWNER : dsm32 ? GS_DSMEM : grid32 ? GS_GRID : clu32 ? GS_CLUSTER : GS_COLOUR;
+  C.gs32_multi = dsm32 ? GS_DSMEM : C.gs32;
   const char* env = getenv("AMAMG_COARSE_GS");
   if (!env) return;
   const std::string want(env);
@@ -258,6 +261,7 @@ void choose_gs_kernels(Level& C) {
   else if (want == "dsmem") { C.gs64 = dsm64 ? GS_DSMEM : C.gs64; C.gs32 = dsm32 ? GS_DSMEM : C.gs32; }
   else if (want == "grid") { C.gs64 = grid64 ? GS_GRID : C.gs64; C.gs32 = grid32 ? GS_GRID : C.gs32; }
   else if (want == "owner") { C.gs64 = owner64 ? GS_OWNER : C.gs64; C.gs32 = owner32 ? GS_OWNER : C.gs32; }
+  C.gs32_multi = C.gs32 == GS_OWNER && dsm32 && want != "owner" ? GS_DSMEM : C.gs32;
 }
 
 // ----------------------------------------------------------------- workspace

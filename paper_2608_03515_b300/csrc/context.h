@@ -24,6 +24,7 @@ struct Level {
   // coarse Gauss-Seidel kernel of this level in FP64 and in FP32 (GsKernel),
   // chosen in setup
   int gs64 = 0, gs32 = 0;
+  int gs32_multi = 0;        // FP32 with R >= 2 right-hand sides
   // the autotuner's (kernel, owner variant) per right-hand-side count
   std::map<int, std::pair<int, int>> tune64, tune32;
   // colour-major copies for the Gauss-Seidel kernels (smoothed coarse levels)
@@ -91,12 +92,12 @@ struct OuterState {
 enum GsKernel : int { GS_COLOUR = 0, GS_CLUSTER = 1, GS_DSMEM = 2, GS_GRID = 3, GS_OWNER = 4 };
 
 // The kernel a smoothing launch of R right-hand sides uses on level L: the one
-// chosen in setup (for R = 1), or the whole-GPU grid sweep when the owner sweep
-// has no resident shape for this R.
+// chosen in setup (FP32: one for R = 1, one for R >= 2), or the whole-GPU grid
+// sweep when the owner sweep has no resident shape for this R.
 template <typename T>
 inline int gs_kind_for(const Level& L, int R) {
   constexpr bool f64 = sizeof(T) == 8;
-  const int kind = f64 ? L.gs64 : L.gs32;
+  const int kind = f64 ? L.gs64 : (R == 1 ? L.gs32 : L.gs32_multi);
   if (kind != GS_OWNER || R == 1) return kind;
   OwnerConfig rc;
   const bool ok = f64 ? owner_sweep_config<double, double2>(L.Nt, L.Nx, L.off.K, L.ncol, L.off, R, &rc)
