@@ -991,23 +991,46 @@ int tune_level(amamg_ctx* h, int l, int R, cudaStream_t st) {
   float best = 1e30f;
   std::pair<int, int> pick = cand[0];
   int rc = AMAMG_OK;
+  const bool log = getenv("AMAMG_TUNE_LOG") != nullptr;
+  bool any = false, sticky = false;
   for (const auto& c : cand) {
     tm[R] = c;
+    rc = AMAMG_OK;
     for (int w = 0; w < 2 && rc == AMAMG_OK; ++w) rc = smooth_impl<T>(h, l, e, r, R, sweeps, st);
     if (rc == AMAMG_OK && cudaEventRecord(a, st) != cudaSuccess) rc = AMAMG_ERR_CUDA;
     for (int w = 0; w < 5 && rc == AMAMG_OK; ++w) rc = smooth_impl<T>(h, l, e, r, R, sweeps, st);
     if (rc == AMAMG_OK && (cudaEventRecord(b, st) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess))
       rc = AMAMG_ERR_CUDA;
-    if (rc != AMAMG_OK) break;
+    if (rc != AMAMG_OK) {
+      // a candidate the driver refuses at launch (a configuration error, not a
+      // fault) is dropped; a sticky error ends the tuning
+      const cudaError_t le = cudaGetLastError();
+      if (log) fprintf(stderr, "amamg autotune: level %d R %d kernel %d variant %d refused: %s\n", l, R, c.first,
+                       c.second, h->err.c_str());
+      if (cudaStreamSynchronize(st) != cudaSuccess) { (void)le; sticky = true; break; }
+      h->err.clear();
+      continue;
+    }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, a, b);
+    if (log) fprintf(stderr, "amamg autotune: level %d %s R %d kernel %d variant %d: %.1f us\n", l, f64 ? "f64" : "f32",
+                     R, c.first, c.second, 1e3 * ms / 5);
+    any = true;
     if (ms < best) { best = ms; pick = c; }
   }
   h->prof = prof;
   cudaEventDestroy(a);
   cudaEventDestroy(b);
+  if (sticky) {
+    tm.erase(R);
+    if (h->err.empty()) h->err = "autotune: the stream failed";
+    return AMAMG_ERR_CUDA;
+  }
+  if (!any) {
+    tm.erase(R);                                             // nothing ran: the fixed rule stands
+    return AMAMG_OK;
+  }
   tm[R] = pick;
-  if (rc != AMAMG_OK) return rc;
   return check_grid_sync(h, st);
 }
 

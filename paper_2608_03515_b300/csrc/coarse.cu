@@ -1028,19 +1028,29 @@ size_t dsmem_sweep_bytes(int n, int K, size_t cbytes, bool bsmem, size_t bt_byte
 constexpr int GRID_SWEEP_THREADS = AMAMG_GRID_THREADS;
 template <typename T, typename BT>
 int grid_sweep_blocks(int n, int ncol, int R) {
-  static int cap[2] = {-1, -1};                       // per element type, first device queried
-  int& c = cap[sizeof(T) == 8 ? 1 : 0];
-  if (c < 0) {
-    int dev = 0, sms = 0, occ = 0, coop = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_coarse_sweeps_grid<T, BT>, GRID_SWEEP_THREADS, 0) !=
-            cudaSuccess) {
-      cudaGetLastError();
-      c = 0;
+  // co-resident blocks of the grid sweep, per device (several host threads may ask)
+  static std::mutex mu;
+  static std::map<int, int> cap;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return 0; }
+  int c;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cap.find(dev);
+    if (it == cap.end()) {
+      int sms = 0, occ = 0, coop = 0;
+      if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_coarse_sweeps_grid<T, BT>, GRID_SWEEP_THREADS, 0) !=
+              cudaSuccess) {
+        cudaGetLastError();
+        c = 0;
+      } else {
+        c = coop ? sms * occ : 0;
+      }
+      cap[dev] = c;
     } else {
-      c = coop ? sms * occ : 0;
+      c = it->second;
     }
   }
   if (c <= 0) return 0;
@@ -1080,6 +1090,34 @@ cudaError_t launch_coarse_sweeps_grid(typename cplx<T>::type* e, const typename 
 #ifndef AMAMG_OWNER_MIN_CNT
 #define AMAMG_OWNER_MIN_CNT 4
 #endif
+// The dynamic shared memory cap of a kernel is one setting per function and
+// device, shared by every host thread of the process.  Setting it to each
+// launch's own size lets one thread (a serving worker) lower it between
+// another's setting and launch, and a cooperative launch then fails its
+// residency check.  So it is raised once, to the device's opt-in maximum
+// minus the kernel's static shared memory, and never lowered; occupancy
+// follows the size each launch requests.
+static cudaError_t allow_max_dyn_smem(const void* kern) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, cudaError_t> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_pair(dev, kern);
+  const auto it = done.find(key);
+  if (it != done.end()) return it->second;
+  int mx = 0;
+  cudaFuncAttributes fa;
+  e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - (int)fa.sharedSizeBytes);
+  if (e != cudaSuccess) cudaGetLastError();
+  done[key] = e;
+  return e;
+}
+
 static size_t owner_smem(int own, int cnt, int K1, size_t cb, bool bsmem, size_t btb) {
   size_t s = (size_t)own * 6 * cb + (size_t)cnt * 4 * cb + (size_t)own * 4;
   if (bsmem) s += (size_t)own * K1 * (4 * btb + 4);
@@ -1174,7 +1212,7 @@ static bool owner_sweep_search(int Nt, int Nx, int K, int ncol, const Offsets& o
     const size_t smem = owner_smem(own, cnt, K - 1, cb, bsmem, sizeof(BT));
     auto kern = owner_kernel<T, BT>(bsmem, S, le);
     int occ = 0;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+    if (allow_max_dyn_smem((const void*)kern) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem) != cudaSuccess) {
       cudaGetLastError();
       return false;
@@ -1230,8 +1268,8 @@ cudaError_t launch_coarse_sweeps_owner(typename cplx<T>::type* e, const typename
   OwnerConfig oc;
   if (!owner_sweep_config<T, BT>(Nt, Nx, off.K, ncol, off, R, &oc, variant)) return cudaErrorNotSupported;
   auto kern = owner_kernel<T, BT>(oc.bsmem, oc.slots, oc.early_lanes);
-  // the attribute is per kernel, and another level may have set a smaller one
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oc.smem);
+  // the shared memory cap of the kernel, raised once to the device maximum
+  cudaError_t err = allow_max_dyn_smem((const void*)kern);
   if (err != cudaSuccess) return err;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(oc.blocks);
@@ -1264,7 +1302,7 @@ bool dsmem_sweeps_possible(int n, int K, int ncol, bool bsmem) {
   if (smem > 200 * 1024) return false;
   auto kern = bsmem ? k_coarse_sweeps_dsmem<T, BT, true> : k_coarse_sweeps_dsmem<T, BT, false>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      allow_max_dyn_smem((const void*)kern) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
@@ -1300,7 +1338,7 @@ cudaError_t launch_coarse_sweeps_dsmem(typename cplx<T>::type* e, const typename
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   auto kern = bsmem ? k_coarse_sweeps_dsmem<T, BT, true> : k_coarse_sweeps_dsmem<T, BT, false>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  if (err == cudaSuccess) err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err == cudaSuccess) err = allow_max_dyn_smem((const void*)kern);
   if (err != cudaSuccess) return err;
   const int per = n / ncol / DSMEM_CLUSTER;
   int threads = ((per * 8 + 31) / 32) * 32;

@@ -333,18 +333,18 @@ cudaError_t coarsest_tc_init() {
 }
 
 static EncodeTiled encode_fn() {
-  static EncodeTiled fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  // looked up once (a function-local static is initialised once, thread-safely)
+  static const EncodeTiled fn = []() -> EncodeTiled {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
+    EncodeTiled f = nullptr;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiled>(p);
+      f = reinterpret_cast<EncodeTiled>(p);
     cudaGetLastError();
-  }
+    return f;
+  }();
   return fn;
 }
 

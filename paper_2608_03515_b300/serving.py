@@ -30,6 +30,7 @@ from . import amamg as A
 # status of a request withdrawn by Server.cancel (a serving-level status, not a
 # library code)
 CANCELLED = -100
+FAILED = -101          # the worker of the request's hierarchy stopped on a library error
 
 
 def aggregates_for(L: int) -> List[int]:
@@ -86,9 +87,14 @@ class Group:
         self.cycles = 0
         self.busy_s = 0.0
         self.cancelling: List[Request] = []
+        self.error: Optional[str] = None
 
     def submit(self, req: Request):
         with self.cv:
+            if self.error is not None:
+                req.status = FAILED
+                req.finish = time.perf_counter() - self.server.t0
+                return
             for i in range(req.R):
                 self.queue.append((req, i))
             self.cv.notify()
@@ -117,6 +123,23 @@ class Group:
                 self.cancelling.remove(req)
 
     def run(self):
+        """Worker loop; an exception (a library error) fails every request this
+        group holds or will receive, so that no caller waits forever."""
+        try:
+            self._run()
+        except Exception as exc:                        # noqa: BLE001 - reported through the requests
+            with self.cv:
+                self.error = repr(exc)
+                pending = [r for (r, _) in self.queue] + [r for (r, _) in self.where.values()]
+                self.queue.clear()
+                self.where.clear()
+            now = time.perf_counter() - self.server.t0
+            for r in pending:
+                if r.finish is None:
+                    r.status = FAILED
+                    r.finish = now
+
+    def _run(self):
         import torch
         from . import fixtures as fx
         torch.cuda.set_device(self.server.device)
@@ -209,6 +232,7 @@ class Server:
         """Starts one worker per resident hierarchy (again after close(): the
         hierarchies stay resident between request streams)."""
         self.closing = False
+        self.stalled = False
         self.t0 = time.perf_counter()
         self.threads = [threading.Thread(target=g.run, daemon=True) for g in self.groups.values()]
         for t in self.threads:
@@ -228,16 +252,20 @@ class Server:
                 req.finish = time.perf_counter() - self.t0
 
     def close(self):
+        """Stops the workers after the work they hold (a stalled stream's workers
+        are left to finish on their own: daemon threads)."""
         self.closing = True
         for g in self.groups.values():
             with g.cv:
                 g.cv.notify()
         for t in self.threads:
-            t.join()
+            t.join(timeout=None if not getattr(self, "stalled", False) else 1.0)
 
 
-def serve(server: Server, requests: List[Request], time_scale: float = 1.0) -> dict:
-    """Releases requests at their arrival times, waits for all, returns metrics."""
+def serve(server: Server, requests: List[Request], time_scale: float = 1.0, max_idle_s: float = 900.0) -> dict:
+    """Releases requests at their arrival times, waits for all, returns metrics.
+    If no request finishes for max_idle_s seconds while some are open, the
+    open ones are marked FAILED (a watchdog: the caller never waits forever)."""
     server.start()
     for req in sorted(requests, key=lambda r: r.arrival):
         delay = req.arrival * time_scale - (time.perf_counter() - server.t0)
@@ -245,7 +273,21 @@ def serve(server: Server, requests: List[Request], time_scale: float = 1.0) -> d
             time.sleep(delay)
         req.arrival = time.perf_counter() - server.t0
         server.submit(req)
-    while any(r.finish is None for r in requests):
+    last_done, last_t = -1, time.perf_counter()
+    while True:
+        open_ = [r for r in requests if r.finish is None]
+        if not open_:
+            break
+        done = len(requests) - len(open_)
+        if done != last_done:
+            last_done, last_t = done, time.perf_counter()
+        elif time.perf_counter() - last_t > max_idle_s:
+            now = time.perf_counter() - server.t0
+            for r in open_:
+                r.status = FAILED
+                r.finish = now
+            server.stalled = True
+            break
         time.sleep(0.005)
     wall = time.perf_counter() - server.t0
     server.close()
@@ -255,9 +297,11 @@ def serve(server: Server, requests: List[Request], time_scale: float = 1.0) -> d
         "requests": len(requests), "solves": solves, "wall_s": wall,
         "solves_per_s": solves / wall, "requests_per_s": len(requests) / wall,
         "latency_p50_ms": float(np.percentile(lat, 50) * 1e3), "latency_p99_ms": float(np.percentile(lat, 99) * 1e3),
-        "not_converged": sum(1 for r in requests if r.status not in (A.OK, CANCELLED)),
+        "not_converged": sum(1 for r in requests if r.status not in (A.OK, CANCELLED, FAILED)),
+        "failed": sum(1 for r in requests if r.status == FAILED),
+        "errors": sorted({g.error for g in server.groups.values() if g.error is not None}),
         "cancelled": sum(1 for r in requests if r.status == CANCELLED),
-        "max_true_relres": float(max(max(r.relres) for r in requests if r.relres)),
+        "max_true_relres": float(max([max(r.relres) for r in requests if r.relres], default=0.0)),
         "slots": {f"{k[0]}/{k[1]}": g.slots for k, g in server.groups.items()},
         "cycles": sum(g.cycles for g in server.groups.values()),
     }
