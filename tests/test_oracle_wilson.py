@@ -136,3 +136,19 @@ def test_free_field_critical_mass(Nt, Nx):
 def test_arnoldi_critical_mass_matches_dense(L, beta, seed):
     U = fx.links_from_angles(fx.metropolis_u1(L, L, beta, 200, seed))
     assert abs(spectrum.critical_mass(U, dense=False) - spectrum.critical_mass(U, dense=True)) < 1e-6
+
+
+def test_arnoldi_critical_mass_matches_dense_at_64():
+    """The Arnoldi route that tabulates the fields of 128^2 and more, against
+    all eigenvalues of the dense 8192 x 8192 operator of two 64^2 fields (the
+    benchmark coupling and the weak coupling of the 1024^2 workload), at both
+    tolerances it is used with (tests/golden/make_mcrit_dense.py)."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "mcrit_dense.json")
+    table = json.load(open(path))
+    assert len(table) >= 1
+    for key, e in table.items():
+        assert e["m_crit"] < 0.0
+        for tol, mc in e["arpack"].items():
+            assert abs(mc - e["m_crit"]) < 1e-9, (key, tol, mc, e["m_crit"])
