@@ -787,6 +787,11 @@ def main():
                 c[3] += fl
         tot = sum(c[1] for c in cats.values())
         share = {k: round(v[1] / tot, 4) for k, v in sorted(cats.items(), key=lambda kv: -kv[1][1])}
+        # the analytic operation count of a solve (the per-kernel FLOP formulas
+        # x launches, averaged over the replay's solves): the paper's GFLOP metric
+        flop_count[len(flop_count)] = {"gflop_per_solve": round(sum(c[3] for c in cats.values()) / 1e9 /
+                                                                (nsteps * len(hs)), 3),
+                                       "solves": nsteps * len(hs)}
         dname, (dn, dms, dby, dfl) = max(cats.items(), key=lambda kv: kv[1][1])
         gbs = dby / (dms * 1e-3) / 1e9
         gflops = dfl / (dms * 1e-3) / 1e9
@@ -805,8 +810,11 @@ def main():
             roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch (64x64 owner sweep)"
         return roof, share
 
+    flop_count = {}
     roofline, kernel_share = profile(hs64)
     roofline_mixed, kernel_share_mixed = profile(hs32)
+    flop_count = {"fp64": flop_count[0], "mixed": flop_count[1],
+                  "note": "mean over the three masses' solves; per-kernel formulas in the library's profile"}
 
     # stencil bandwidth on working sets larger than L2 (1024^2, random-phase links)
     d_apply = {}
@@ -871,6 +879,7 @@ def main():
             "kernel_share": kernel_share,
             "roofline_mixed": roofline_mixed,
             "kernel_share_mixed": kernel_share_mixed,
+            "flop_count": flop_count,
             "cpu_baseline": cpu,
             "clocks": clk,
             "error_vs_oracle": ({"x": "||x_gpu - x_oracle|| / ||x_oracle||, m_crit+0.1 mass, first timed RHS",

@@ -25,6 +25,20 @@ from paper_2608_03515_b300 import amamg as A  # noqa: E402
 DEV = torch.device("cuda:0")
 
 
+def canary(*shape_and_dtype):
+    """canary(d0, d1, ..., dtype) or canary(shape, dtype): an output buffer
+    filled with NaN (a canary): an element the kernel does not write stays NaN
+    and fails the element-wise comparison."""
+    *shape, dtype = shape_and_dtype
+    if len(shape) == 1 and not isinstance(shape[0], int):
+        shape = tuple(shape[0])
+    return torch.full(tuple(shape), complex(float("nan"), float("nan")), dtype=dtype, device=DEV)
+
+
+def canary_like(t):
+    return canary(t.shape, t.dtype)
+
+
 def random_links(Nt, Nx, seed):
     rng = np.random.Generator(np.random.PCG64(seed))
     return np.exp(1j * rng.uniform(-np.pi, np.pi, size=(2, Nt, Nx)))
@@ -83,7 +97,7 @@ def test_apply_D_fp64_and_fp32(Nt, Nx, R):
     U = random_links(Nt, Nx, 3)
     hier = A.setup(dev(U), 0.07, A.make_params([2]))
     psi = fx.gaussian_rhs(R, Nt, Nx, 4)
-    out = torch.empty(R, 2, Nt, Nx, dtype=torch.complex128, device=DEV)
+    out = canary(R, 2, Nt, Nx, torch.complex128)
     A.apply_D(hier, dev(psi), out)
     got = host(out)
     want = np.stack([W.apply_dirac(U, 0.07, psi[r]) for r in range(R)])
@@ -93,7 +107,7 @@ def test_apply_D_fp64_and_fp32(Nt, Nx, R):
         assert relerr(got[r], lattice_vec(D @ W.to_flat(psi[r]), Nt, Nx)) <= 1e-13
     # FP32: inputs rounded to complex64, reference in FP64 on the rounded inputs
     psi32 = psi.astype(np.complex64)
-    out32 = torch.empty(R, 2, Nt, Nx, dtype=torch.complex64, device=DEV)
+    out32 = canary(R, 2, Nt, Nx, torch.complex64)
     A.apply_D(hier, dev(psi32, torch.complex64), out32)
     U32 = U.astype(np.complex64).astype(np.complex128)
     want32 = np.stack([W.apply_dirac(U32, 0.07, psi32[r].astype(np.complex128)) for r in range(R)])
@@ -107,7 +121,7 @@ def test_apply_D_full_size_256_properties():
     U = fx.links_from_angles(theta)
     hier = A.setup(dev(U), 0.03, A.make_params([4, 2]))
     psi = fx.gaussian_rhs(1, Nt, Nx, 3)
-    out = torch.empty(1, 2, Nt, Nx, dtype=torch.complex128, device=DEV)
+    out = canary(1, 2, Nt, Nx, torch.complex128)
     A.apply_D(hier, dev(psi), out)
     assert relerr(host(out)[0], W.apply_dirac(U, 0.03, psi[0])) <= 1e-13
 
@@ -133,13 +147,13 @@ def test_interpolator_and_galerkin_fp64(Nt, Nx, aggs):
     for l, a in enumerate(aggs):
         L = levels[l]
         want = oracle_P_tiles(L.P, L.Nt, L.Nx, a)
-        got = torch.empty(want.shape, dtype=torch.complex128, device=DEV)
+        got = canary(want.shape, torch.complex128)
         A.export_P(hier, l, got)
         assert relerr(host(got), want) <= 1e-12
         C = levels[l + 1]
         Bw = amg.block_stencil(C.A, C.offsets, C.Nt, C.Nx)            # [K, n, 2, 2]
         Bw = np.transpose(Bw.reshape(len(C.offsets), C.Nt * C.Nx, 4), (0, 2, 1))
-        Bg = torch.empty(Bw.shape, dtype=torch.complex128, device=DEV)
+        Bg = canary(Bw.shape, torch.complex128)
         A.export_coarse(hier, l + 1, Bg)
         assert relerr(host(Bg), Bw) <= 1e-12
 
@@ -162,17 +176,17 @@ def test_spin_split_hierarchy_matches_oracle():
     for l, a in enumerate(aggs):
         L = levels[l]
         want = oracle_P_tiles(L.P, L.Nt, L.Nx, a)
-        got = torch.empty(want.shape, dtype=torch.complex128, device=DEV)
+        got = canary(want.shape, torch.complex128)
         A.export_P(hier, l, got)
         assert relerr(host(got), want) <= 1e-12
         C = levels[l + 1]
         Bw = amg.block_stencil(C.A, C.offsets, C.Nt, C.Nx)
         Bw = np.transpose(Bw.reshape(len(C.offsets), C.Nt * C.Nx, 4), (0, 2, 1))
-        Bg = torch.empty(Bw.shape, dtype=torch.complex128, device=DEV)
+        Bg = canary(Bw.shape, torch.complex128)
         A.export_coarse(hier, l + 1, Bg)
         assert relerr(host(Bg), Bw) <= 1e-12
     psi = fx.gaussian_rhs(1, Nt, Nx, 1)
-    x = torch.empty(psi.shape, dtype=torch.complex128, device=DEV)
+    x = canary(psi.shape, torch.complex128)
     info = A.solve(hier, dev(psi), x)
     ref = krylov.fgmres(lambda v: D @ v, lambda r: amg.vcycle(levels, r), W.to_flat(psi[0]), 30, 1e-10, 5000)
     b = W.to_flat(psi[0])
@@ -191,8 +205,8 @@ def test_transfers_and_coarse_apply_fp64(Nt, Nx, aggs, R):
         F, C = levels[l], levels[l + 1]
         ec = rng.standard_normal((R, 2, C.Nt, C.Nx)) + 1j * rng.standard_normal((R, 2, C.Nt, C.Nx))
         ef = rng.standard_normal((R, 2, F.Nt, F.Nx)) + 1j * rng.standard_normal((R, 2, F.Nt, F.Nx))
-        out_f = torch.empty(R, 2, F.Nt, F.Nx, dtype=torch.complex128, device=DEV)
-        out_c = torch.empty(R, 2, C.Nt, C.Nx, dtype=torch.complex128, device=DEV)
+        out_f = canary(R, 2, F.Nt, F.Nx, torch.complex128)
+        out_c = canary(R, 2, C.Nt, C.Nx, torch.complex128)
         A.apply_P(hier, l, dev(ec), out_f)
         A.apply_PH(hier, l, dev(ef), out_c)
         gf, gc = host(out_f), host(out_c)
@@ -312,8 +326,8 @@ def test_fused_fine_post_smoother_equals_separate_launches(monkeypatch, R):
     for fused in ("1", "0"):
         monkeypatch.setenv("AMAMG_FINE_FUSED", fused)
         hier = A.setup(dev(U), 0.1, A.make_params(aggs))
-        e64 = torch.empty(psi.shape, dtype=torch.complex128, device=DEV)
-        e32 = torch.empty(psi.shape, dtype=torch.complex64, device=DEV)
+        e64 = canary(psi.shape, torch.complex128)
+        e32 = canary(psi.shape, torch.complex64)
         A.vcycle(hier, dev(psi), e64)
         A.vcycle(hier, dev(psi, torch.complex64), e32)
         out[fused] = (host(e64), host(e32))
@@ -357,7 +371,7 @@ def test_coarsest_solve_and_vcycle_fp64():
     C = levels[-1]
     rng = np.random.Generator(np.random.PCG64(11))
     rc = rng.standard_normal((2, 2, C.Nt, C.Nx)) + 1j * rng.standard_normal((2, 2, C.Nt, C.Nx))
-    ec = torch.empty(rc.shape, dtype=torch.complex128, device=DEV)
+    ec = canary(rc.shape, torch.complex128)
     A.coarsest_solve(hier, dev(rc), ec)
     import scipy.linalg as sla
     got = host(ec)
@@ -366,7 +380,7 @@ def test_coarsest_solve_and_vcycle_fp64():
         want = lattice_vec(sla.lu_solve(C.lu, W.to_flat(rc[r])), C.Nt, C.Nx)
         assert relerr(got[r], want) <= 1e-15 * cond * 10
     psi = fx.gaussian_rhs(2, Nt, Nx, 12)
-    e = torch.empty(psi.shape, dtype=torch.complex128, device=DEV)
+    e = canary(psi.shape, torch.complex128)
     A.vcycle(hier, dev(psi), e)
     got = host(e)
     for r in range(2):
@@ -389,7 +403,7 @@ def test_solve_fp64_matches_oracle_c1_field(aggs):
     m0 = -0.1383495190759743 + 0.05
     U_, D, hier, levels = make(Nt, Nx, aggs, m0=m0, U=U)
     psi = fx.gaussian_rhs(1, Nt, Nx, 1)
-    x = torch.empty(psi.shape, dtype=torch.complex128, device=DEV)
+    x = canary(psi.shape, torch.complex128)
     info = A.solve(hier, dev(psi), x)
     ref = oracle_solve(D, levels, W.to_flat(psi[0]), 30)
     assert info[0].status == A.OK
@@ -405,11 +419,11 @@ def test_solve_multi_rhs_each_equals_single():
     Nt = Nx = 16
     U, D, hier, levels = make(Nt, Nx, [2, 2], m0=0.05, seed=13)
     psi = fx.gaussian_rhs(3, Nt, Nx, 14)
-    x = torch.empty(psi.shape, dtype=torch.complex128, device=DEV)
+    x = canary(psi.shape, torch.complex128)
     info = A.solve(hier, dev(psi), x)
     xb = host(x)
     for r in range(3):
-        x1 = torch.empty((1,) + psi.shape[1:], dtype=torch.complex128, device=DEV)
+        x1 = canary((1,) + psi.shape[1:], torch.complex128)
         i1 = A.solve(hier, dev(psi[r:r + 1]), x1)
         assert i1[0].iterations == info[r].iterations
         assert relerr(host(x1)[0], xb[r]) <= 1e-12
@@ -424,8 +438,8 @@ def test_solve_mixed_precision_reaches_tolerance():
     hier64 = A.setup(dev(U), m0, A.make_params([4, 2]))
     hier32 = A.setup(dev(U), m0, A.make_params([4, 2], precision=A.SOLVE_MIXED))
     psi = fx.gaussian_rhs(1, Nt, Nx, 1)
-    x64 = torch.empty(psi.shape, dtype=torch.complex128, device=DEV)
-    x32 = torch.empty(psi.shape, dtype=torch.complex128, device=DEV)
+    x64 = canary(psi.shape, torch.complex128)
+    x32 = canary(psi.shape, torch.complex128)
     i64 = A.solve(hier64, dev(psi), x64)
     i32 = A.solve(hier32, dev(psi), x32)
     assert i32[0].status == A.OK and i32[0].true_relres <= 1e-10
@@ -484,8 +498,8 @@ def test_fp32_transfers_coarse_and_smoothers_match_emulated_storage(Nt):
         Pq = mixed.quantise_tiles(oracle_P_tiles(F.P, F.Nt, F.Nx, a))
         ec = mixed.round32(rng.standard_normal((R, 2, C.Nt, C.Nx)) + 1j * rng.standard_normal((R, 2, C.Nt, C.Nx)))
         ef = mixed.round32(rng.standard_normal((R, 2, F.Nt, F.Nx)) + 1j * rng.standard_normal((R, 2, F.Nt, F.Nx)))
-        out_f = torch.empty(R, 2, F.Nt, F.Nx, dtype=torch.complex64, device=DEV)
-        out_c = torch.empty(R, 2, C.Nt, C.Nx, dtype=torch.complex64, device=DEV)
+        out_f = canary(R, 2, F.Nt, F.Nx, torch.complex64)
+        out_c = canary(R, 2, C.Nt, C.Nx, torch.complex64)
         A.apply_P(hier, l, dev(ec, torch.complex64), out_f)
         A.apply_PH(hier, l, dev(ef, torch.complex64), out_c)
         gf, gc = host(out_f), host(out_c)
@@ -567,8 +581,8 @@ def test_graph_replay_matches_eager_profiled_solve():
     Nt = Nx = 32
     U, D, hier, levels = make(Nt, Nx, [4, 2], m0=0.05, seed=25)
     psi = fx.gaussian_rhs(2, Nt, Nx, 26)
-    x1 = torch.empty(psi.shape, dtype=torch.complex128, device=DEV)
-    x2 = torch.empty(psi.shape, dtype=torch.complex128, device=DEV)
+    x1 = canary(psi.shape, torch.complex128)
+    x2 = canary(psi.shape, torch.complex128)
     i1 = A.solve(hier, dev(psi), x1)
     A.profile_enable(hier, True)
     i2 = A.solve(hier, dev(psi), x2)
@@ -594,11 +608,11 @@ def test_coarse_apply_many_rhs_loads_blocks_once_same_result(R):
         for dt in (torch.complex128, torch.complex64):
             xin = rng.standard_normal((R, 2, C.Nt, C.Nx)) + 1j * rng.standard_normal((R, 2, C.Nt, C.Nx))
             xd = dev(xin, dt)
-            out = torch.empty_like(xd)
+            out = canary_like(xd)
             A.apply_coarse(hier, l, xd, out)
             got = host(out)
             for r in range(R):
-                one = torch.empty_like(xd[r:r + 1])
+                one = canary_like(xd[r:r + 1])
                 A.apply_coarse(hier, l, xd[r:r + 1].contiguous(), one)
                 assert np.array_equal(host(one)[0], got[r])
                 if dt == torch.complex128:
