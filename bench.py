@@ -212,8 +212,9 @@ def run_probe(args):
     prec = A.SOLVE_MIXED if args.prec == "f32" else A.SOLVE_FP64
     h = A.setup(U, 0.1, A.make_params(aggs, precision=prec))
     dt = torch.complex64 if args.prec == "f32" else torch.complex128
-    x = torch.randn(args.rhs, 2, Lp, Lp, dtype=dt, device=dev)
-    y = torch.empty_like(x)
+    fine = args.probe in ("apply_D", "vcycle", "solve")
+    x = torch.randn(args.rhs, 2, Lp, Lp, dtype=dt, device=dev) if fine else None
+    y = torch.empty_like(x) if fine else None
     nt1, nx1, _ = h.level_info(1)
     r1 = torch.randn(args.rhs, 2, nt1, nx1, dtype=dt, device=dev)
     e1 = torch.zeros_like(r1)
@@ -228,6 +229,8 @@ def run_probe(args):
             A.vcycle(h, x, y)
         elif args.probe == "smooth1":
             A.smooth(h, 1, r1, e1, 2)
+        elif args.probe == "coarse_apply":
+            A.apply_coarse(h, 1, r1, e1)
         elif args.probe in ("coarsest", "coarsest_f32"):
             nt, nx, _ = h.level_info(len(aggs))
             cdt = torch.complex64 if args.probe == "coarsest_f32" else torch.complex128
@@ -382,6 +385,32 @@ def c4_mcrit():
     return None if e is None else e["m_crit"]
 
 
+def time_coarse_apply(A, h, xc, yc, reps=20):
+    """CUDA-event time of amamg_apply_coarse on level 1 (3 warm-up calls), with
+    the library's algorithmic bytes and FLOPs of the call (profile records)."""
+    import torch
+    for _ in range(3):
+        A.apply_coarse(h, 1, xc, yc)
+    A.profile_reset(h)
+    A.profile_enable(h, True)
+    A.apply_coarse(h, 1, xc, yc)
+    A.profile_enable(h, False)
+    name, _, _, nbytes, flops = [c for c in A.profile_get(h) if c[0].startswith("coarse_apply")][-1]
+    A.profile_reset(h)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(reps):
+        A.apply_coarse(h, 1, xc, yc)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    us = 1e3 * ev[0].elapsed_time(ev[1]) / reps
+    return {"kernel": name, "us": round(us, 1), "algorithmic_GB/s": round(nbytes / us / 1e3, 1),
+            "hbm_frac": round(nbytes / us / 1e3 / measured_peaks()[0], 3),
+            "useful_TFLOP/s": round(flops / us / 1e6, 2)}
+
+
 def run_c4(dev, theta_future):
     """64 right-hand sides on the 1024^2 beta = 12 field at m0 = (critical mass
     of the 256^2 beta = 12 field) + 0.01, 3 levels (tiles 4, 4; coarsest
@@ -422,6 +451,15 @@ def run_c4(dev, theta_future):
                             "all_converged": all(i.status == A.OK for i in info)}
     out["smoother_autotuned"] = A.query_smoother(h, 1, A.F32, C4_R)
     xh = x[:4].cpu().numpy()
+    # the level-1 operator (256^2 coarse sites, 21 offsets) applied to the 64
+    # right-hand sides: tensor cores (FP16 super-block GEMMs) here, the CUDA-core
+    # FP32 kernel on the FP64 handle below (same links, mass, tiles: same operator)
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    n1 = C4_L // C4_AGGS[0]
+    xc = torch.randn(C4_R, 2, n1, n1, dtype=torch.complex64, device=dev, generator=g)
+    yc_tc = torch.empty_like(xc)
+    ca_tc = time_coarse_apply(A, h, xc, yc_tc)
     A.destroy(h)
     # the same batch with the opt-in double-float Gram-Schmidt (FP64 Gram-Schmidt
     # bounds the step above)
@@ -443,6 +481,22 @@ def run_c4(dev, theta_future):
     del x
     # the plain FP64 form, one right-hand side per call
     h64 = A.setup(U, m0, A.make_params(C4_AGGS, precision=A.SOLVE_FP64, restart=RESTART, tol=TOL))
+    yc_cc = torch.empty_like(xc)
+    prev = os.environ.get("AMAMG_COARSE_TC")
+    os.environ["AMAMG_COARSE_TC"] = "0"                      # read at a level's first apply
+    ca_cc = time_coarse_apply(A, h64, xc, yc_cc)
+    if prev is None:
+        del os.environ["AMAMG_COARSE_TC"]
+    else:
+        os.environ["AMAMG_COARSE_TC"] = prev
+    d = (yc_tc - yc_cc).abs().max().item() / yc_cc.abs().max().item()
+    out["coarse_apply_level1"] = {
+        "workload": f"level 1 of the {C4_L}^2 hierarchy ({n1}x{n1} coarse sites, 21 offsets), {C4_R} RHS, "
+                    "FP32 vectors, Gaussian inputs",
+        "tensor_core": ca_tc, "cuda_core": ca_cc,
+        "speedup": round(ca_cc["us"] / ca_tc["us"], 2),
+        "max_rel_diff_tc_vs_cuda_core": d}
+    del xc, yc_tc, yc_cc
     x1 = torch.empty_like(psi[:1])
     A.solve(h64, psi[:1], x1)
     ev[0].record(stream)
@@ -479,7 +533,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--probe", default=None,
-                    choices=["apply_D", "vcycle", "smooth1", "solve", "coarsest", "coarsest_f32"],
+                    choices=["apply_D", "vcycle", "smooth1", "coarse_apply", "solve", "coarsest", "coarsest_f32"],
                     help="time one kernel family on a small random-phase case (for profiler captures)")
     ap.add_argument("--lattice", type=int, default=512)
     ap.add_argument("--tiles", default="", help="probe: tile sides, e.g. 4,4")

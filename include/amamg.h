@@ -217,7 +217,21 @@ int amamg_apply_P(amamg_handle h, int level, const void* coarse_in, void* fine_o
 int amamg_apply_PH(amamg_handle h, int level, const void* fine_in, void* coarse_out,
                    int R, int precision, void* stream);
 
-/* out = A_l in with the Galerkin operator of level l >= 1 (A_l = P^H A_{l-1} P). */
+/* out = A_l in with the Galerkin operator of level l >= 1 (A_l = P^H A_{l-1} P,
+ * Sec. 2), a block stencil of 2x2 complex blocks.  in, out: level-l vectors
+ * [R][2][Nt_l][Nx_l], complex128 (AMAMG_F64: FP64 blocks) or complex64
+ * (AMAMG_F32).  With AMAMG_F32 and R >= 32 on a level with even Nt_l >= 8,
+ * Nx_l >= 8 a multiple of 4 and block offsets within 2 sites, the product runs
+ * on the tensor cores: 2 x 4-site super-blocks of the operator as dense
+ * 16 x 96 complex tiles in FP16 with one FP32 scale per operator row, the
+ * right-hand sides in FP16 with one power-of-two scale each, FP32 accumulation
+ * (relative error about 5e-4 against the FP64 product, like the FP16 block
+ * storage of the CUDA-core FP32 kernel, whose scale is per 2x2 block).  Its
+ * first use on a level builds that level's FP16 images (6 KB per 8 coarse
+ * sites) and a staging buffer of 2 bytes per complex entry of in, owned by the
+ * handle; AMAMG_COARSE_TC=0 in the environment keeps the CUDA-core kernel.
+ * A bounded wait of the tensor-core kernel that runs out is reported by
+ * amamg_sync_status. */
 int amamg_apply_coarse(amamg_handle h, int level, const void* in, void* out,
                        int R, int precision, void* stream);
 

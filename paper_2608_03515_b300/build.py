@@ -16,7 +16,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libamamg.so")
-SOURCES = ["amamg.cu", "dslash.cu", "transfer.cu", "coarse.cu", "blas.cu", "setup.cu", "noalloc.cu", "cg.cu", "coarsest_gmres.cu", "coarsest_tc.cu", "gs_df.cu"]
+SOURCES = ["amamg.cu", "dslash.cu", "transfer.cu", "coarse.cu", "blas.cu", "setup.cu", "noalloc.cu", "cg.cu", "coarsest_gmres.cu", "coarsest_tc.cu", "coarse_tc.cu", "gs_df.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--cudart", "shared",
          "-Xcompiler", "-Wall", "-Wno-deprecated-gpu-targets"]

@@ -539,6 +539,54 @@ int op_restrict(amamg_ctx* h, int l, const typename cplx<T>::type* ef, typename 
     }, (double)L.nT * L.nrows * 64.0 * R);
 }
 
+// Right-hand-side count from which the FP32 coarse apply runs on the tensor
+// cores (64 right-hand sides fill the MMA's 128 rows with both planes).
+constexpr int COARSE_TC_MIN_R = 32;
+
+// The tensor-core coarse apply of level l for R right-hand sides: builds the
+// level's FP16 super-block images at the first use and grows the staging
+// buffers.  Returns false (the CUDA-core kernel runs) where the level's shape
+// or the device does not allow it, or AMAMG_COARSE_TC=0.
+bool ensure_coarse_tc(amamg_ctx* h, int l, int R, cudaStream_t st, int* rc) {
+  Level& L = h->lv[l];
+  *rc = AMAMG_OK;
+  if (L.ct_state == 0) {
+    const char* env = std::getenv("AMAMG_COARSE_TC");
+    L.ct_state = -1;
+    if (!(env && std::strcmp(env, "0") == 0) && coarse_tc_possible(L.Nt, L.Nx, L.off) &&
+        coarse_tc_init() == cudaSuccess) {
+      *rc = dalloc(h, &L.ctW, coarse_tc_image_halves(L.Nt, L.Nx));
+      if (*rc == AMAMG_OK) *rc = dalloc(h, &L.ctWs, coarse_tc_scale_floats(L.Nt, L.Nx));
+      if (*rc == AMAMG_OK)
+        *rc = launch(h, "coarse_tc_images", 0.0, st, [&] {
+          return launch_coarse_tc_pack_w(L.B64, L.off, L.Nt, L.Nx, L.ctW, L.ctWs, st);
+        });
+      if (*rc != AMAMG_OK) {
+        dfree(L.ctW);
+        dfree(L.ctWs);
+        return false;
+      }
+      L.ct_state = 1;
+    }
+    cudaGetLastError();
+  }
+  if (L.ct_state != 1) return false;
+  const size_t need = coarse_tc_stage_halves(L.Nt, L.Nx, R);
+  if (need > h->ct_stage_cap) {
+    dfree(h->ct_stage);
+    h->ct_stage_cap = 0;
+    if ((*rc = dalloc(h, &h->ct_stage, need)) != AMAMG_OK) return false;
+    h->ct_stage_cap = need;
+  }
+  if (R > h->ct_amax_cap) {
+    dfree(h->ct_amax);
+    h->ct_amax_cap = 0;
+    if ((*rc = dalloc(h, &h->ct_amax, (size_t)R)) != AMAMG_OK) return false;
+    h->ct_amax_cap = R;
+  }
+  return true;
+}
+
 template <typename T>
 int op_coarse(amamg_ctx* h, int l, const typename cplx<T>::type* in, typename cplx<T>::type* out,
               const typename cplx<T>::type* b, int R, cudaStream_t st) {
@@ -547,6 +595,17 @@ int op_coarse(amamg_ctx* h, int l, const typename cplx<T>::type* in, typename cp
   const double cb = f64 ? 16.0 : 8.0;
   const double blk = f64 ? 16.0 * 4 : (4.0 * 4 + 4.0);
   const double bytes = (double)L.n * (L.off.K * blk + R * 2 * (b ? 3 : 2) * cb);
+  if constexpr (!f64) {
+    if (!b && R >= COARSE_TC_MIN_R) {
+      int rc = AMAMG_OK;
+      if (ensure_coarse_tc(h, l, R, st, &rc))
+        return launch(h, "coarse_apply_tc", bytes, st, [&] {
+          return launch_coarse_tc(in, out, L.ctW, L.ctWs, L.Nt, L.Nx, R, h->ct_stage, h->ct_amax,
+                                  reinterpret_cast<int*>(h->d_sync + 2), st);
+        }, (double)L.n * R * L.off.K * 32.0);
+      if (rc != AMAMG_OK) return rc;
+    }
+  }
   if constexpr (f64)
     return launch(h, "coarse_apply_f64", bytes, st, [&] {
       return launch_coarse_apply<double, double2>(in, out, b, L.B64, nullptr, L.off, L.Nt, L.Nx, R, st);
@@ -1147,7 +1206,9 @@ void free_all(amamg_ctx* h) {
     dfree(L.Bc64); dfree(L.Bc16); dfree(L.Bcs); dfree(L.Dc64); dfree(L.Dc32);
     dfree(L.P64); dfree(L.P16); dfree(L.Ps);
     dfree(L.r64); dfree(L.e64); dfree(L.r32); dfree(L.e32);
+    dfree(L.ctW); dfree(L.ctWs);
   }
+  dfree(h->ct_stage); dfree(h->ct_amax);
   clear_graphs(h);
   if (h->ws) cudaStreamDestroy(h->ws);
   if (h->ev_in) cudaEventDestroy(h->ev_in);

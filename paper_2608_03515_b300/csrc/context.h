@@ -33,6 +33,12 @@ struct Level {
   float* Bcs = nullptr;
   double2* Dc64 = nullptr;
   float2* Dc32 = nullptr;
+  // tensor-core apply of this level's operator to many right-hand sides:
+  // FP16 super-block images with per-row scales (built at the first use);
+  // ct_state 0: not yet tried, 1: built, -1: not available for this level
+  __half* ctW = nullptr;
+  float* ctWs = nullptr;
+  int ct_state = 0;
   // interpolation to the next level
   double2* P64 = nullptr;
   __half2* P16 = nullptr;
@@ -143,6 +149,10 @@ struct amamg_ctx {
   float2* Ainv32 = nullptr;  // its FP32 rounding, applied by the mixed-precision V-cycle
   float* tc_bop = nullptr;   // tensor-core coarsest apply: its right-hand-side operand (scratch)
   bool tc_ok = false;        // the tensor-core coarsest apply is available (AMAMG_COARSEST_TC=0: off)
+  __half* ct_stage = nullptr;  // tensor-core coarse apply: FP16 staging of the right-hand sides
+  size_t ct_stage_cap = 0;     // (halves)
+  unsigned* ct_amax = nullptr; // their largest components (FP32 bits)
+  int ct_amax_cap = 0;
   int nd = 0;
   int* d_err = nullptr;
   // coarse Gauss-Seidel synchronisation: [0] grid-barrier count, [1] its

@@ -256,6 +256,23 @@ cudaError_t coarsest_tc_init();
 cudaError_t launch_coarsest_tc(const float2* A, const float2* x, float2* y, int nd, int R, float* scratch, int* err,
                                cudaStream_t st);
 
+// coarse_tc.cu: y_r = A_l x_r for many right-hand sides on the tensor cores
+// (tcgen05.mma kind::f16 over 2 x 4-site super-blocks, FP32 accumulation in
+// tensor memory).  Operator images (coarse_tc_image_halves FP16 + scale floats)
+// from the FP64 blocks by launch_coarse_tc_pack_w; per call the right-hand
+// sides are staged in FP16 (stage: coarse_tc_stage_halves, amax: R words).
+// coarse_tc_possible: even Nt >= 8, Nx >= 8 a multiple of 4, offsets within
+// |dt|, |dx| <= 2.  coarse_tc_init: once per process, outside stream capture.
+bool coarse_tc_possible(int Nt, int Nx, const Offsets& off);
+size_t coarse_tc_image_halves(int Nt, int Nx);
+size_t coarse_tc_scale_floats(int Nt, int Nx);
+size_t coarse_tc_stage_halves(int Nt, int Nx, int R);
+cudaError_t coarse_tc_init();
+cudaError_t launch_coarse_tc_pack_w(const double2* B, const Offsets& off, int Nt, int Nx, __half* W, float* Ws,
+                                    cudaStream_t st);
+cudaError_t launch_coarse_tc(const float2* x, float2* y, const __half* W, const float* Ws, int Nt, int Nx, int R,
+                             __half* stage, unsigned* amax, int* err, cudaStream_t st);
+
 // gs_df.cu: the outer solver's Gram-Schmidt in double-float arithmetic (basis
 // stored as double-float complex entries, 16 bytes each; see the file header)
 cudaError_t launch_to_df(const double2* w, void* wd, long n, cudaStream_t st);
