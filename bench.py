@@ -56,6 +56,24 @@ def arm_config(world):
             "l2": "flushed (256 MB write) between steps"}
 
 
+def replica_rhs_seed(rank: int, i: int) -> int:
+    """Seed of the i-th right-hand side of replica `rank` (replicas solve their own)."""
+    return RHS_SEED0 + 100000 * rank + i
+
+
+def reduce_over_ranks(total_ms: float, solves_per_rank: int, world: int, dev):
+    """Whole-job throughput of `world` replicas: the slowest rank's timed
+    milliseconds (an all-reduce MAX; the only collective, off the data path)
+    and every rank's solves over that time.  Returns (max_ms, solves/s)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, solves_per_rank * world / (total_ms * 1e-3)
+
+
 def load_mcrit():
     path = os.path.join(ROOT, "tests", "golden", "mcrit.json")
     table = json.load(open(path))
@@ -594,7 +612,7 @@ def main():
     masses = [mcrit + d for d in MASS_OFFSETS]
     nsteps = args.warmup + args.steps
     # right-hand sides resident in HBM before the timed region (replicas draw their own)
-    psis = [torch.from_numpy(fx.gaussian_rhs(1, L, L, RHS_SEED0 + 100000 * rank + i)).to(dev) for i in range(nsteps)]
+    psis = [torch.from_numpy(fx.gaussian_rhs(1, L, L, replica_rhs_seed(rank, i))).to(dev) for i in range(nsteps)]
     x = torch.empty_like(psis[0])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
 
@@ -668,13 +686,7 @@ def main():
     torch.cuda.nvtx.range_pop()
     clk = clocks.stop()
     launches = sum(A.launch_count(h) for h in hs64) - launches0
-    total_ms = float(np.sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    solves = args.steps * len(masses) * world
-    value = solves / (total_ms * 1e-3)
+    total_ms, value = reduce_over_ranks(float(np.sum(step_ms)), args.steps * len(masses), world, dev)
 
     # mixed precision on the same inputs
     run(hs32, nst=args.warmup)
