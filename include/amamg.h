@@ -84,6 +84,12 @@ typedef struct amamg_ctx* amamg_handle;
                                         in that form; mixed precision only.  A faster alternative on GPUs
                                         with a narrow FP64 pipe; the true residual stays FP64 */
 
+/* variant of the outer solver's Gram-Schmidt (FP64 arithmetic) */
+#define AMAMG_GS_CGS2 0              /* classical, with a second pass wherever the DGKS test asks for it
+                                        (default): four kernels per Arnoldi step */
+#define AMAMG_GS_MGS  1              /* modified (the oracle's variant): one stage per basis vector, each
+                                        a fused update and inner product, half the FP64 work of CGS2 */
+
 /* which basket a border site takes its formula from ("the first aggregate it
  * was assigned to", Sec. 4.1) */
 #define AMAMG_OWNER_TILE      0      /* the basket of the tile containing the site, W(t/a, x/a) (default) */
@@ -116,6 +122,7 @@ typedef struct {
                                         any graph capture) and keeps the fastest; the candidates
                                         compute the same sweeps up to rounding order.  Not part of
                                         the paper's method. */
+    int    gs_method;                /* AMAMG_GS_CGS2 (default) or AMAMG_GS_MGS (with AMAMG_GS_FP64) */
 } amamg_params;
 
 typedef struct {

@@ -36,6 +36,8 @@ COARSEST_DIRECT = 0
 COARSEST_GMRES = 1
 GS_FP64 = 0
 GS_DF64 = 1
+GS_CGS2 = 0
+GS_MGS = 1
 
 EXPORTED = [
     "amamg_default_params", "amamg_query_bytes", "amamg_setup", "amamg_solve", "amamg_apply_D",
@@ -63,6 +65,7 @@ class Params(ctypes.Structure):
         ("coarsest", ctypes.c_int),
         ("gs_arith", ctypes.c_int),
         ("autotune", ctypes.c_int),
+        ("gs_method", ctypes.c_int),
     ]
 
 
@@ -175,12 +178,14 @@ def default_params() -> Params:
 def make_params(aggs: Sequence[int], precision: int = SOLVE_FP64, restart: int = 30, max_iter: int = 3000,
                 post_smooth: int = 2, tol: float = 1e-10, spin_split: bool = False,
                 normalization: str = "none", ownership: str = "tile", coarsest: str = "direct",
-                gs: str = "fp64", autotune: bool = False) -> Params:
+                gs: str = "fp64", autotune: bool = False, gs_method: str = "cgs2") -> Params:
     """Parameters of amamg_setup; normalization "none" | "rowsum" and ownership
     "tile" | "first_lex" name the readings the oracle's build_hierarchy takes;
     coarsest "direct" | "gmres" the coarsest solver (the oracle's vcycle
     coarsest="lu" | "gmres"); gs "fp64" | "df64" the outer Gram-Schmidt's
-    arithmetic (df64 with mixed precision only); autotune: time the coarse
+    arithmetic (df64 with mixed precision only); gs_method "cgs2" | "mgs" its
+    variant (classical with DGKS-gated second pass, or modified as in the
+    oracle; mgs with fp64 arithmetic only); autotune: time the coarse
     Gauss-Seidel candidates at the first solve of each right-hand-side count."""
     p = default_params()
     p.nlevels = len(aggs) + 1
@@ -197,6 +202,7 @@ def make_params(aggs: Sequence[int], precision: int = SOLVE_FP64, restart: int =
     p.coarsest = {"direct": COARSEST_DIRECT, "gmres": COARSEST_GMRES}[coarsest]
     p.gs_arith = {"fp64": GS_FP64, "df64": GS_DF64}[gs]
     p.autotune = 1 if autotune else 0
+    p.gs_method = {"cgs2": GS_CGS2, "mgs": GS_MGS}[gs_method]
     return p
 
 

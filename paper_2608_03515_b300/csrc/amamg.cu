@@ -807,6 +807,18 @@ int arnoldi_step(amamg_ctx* h, int j, int R, cudaStream_t st) {
     }));
     return ls_join(h, st);
   }
+  if (h->prm.gs_method == AMAMG_GS_MGS) {
+    // modified Gram-Schmidt: stage i subtracts the projection on v_{i-1} and
+    // forms the inner product with v_i (the last stage the norm); J + 1 stages
+    for (int i = 0; i <= J; ++i) {
+      const double nvec = i == 0 ? 2.0 : (i < J ? 4.0 : 3.0);      // w, v_{i-1}, v_i read; w written
+      const double fl = (i >= 1 ? 8.0 : 0.0) + (i < J ? 8.0 : 4.0);
+      CKS(launch(h, i < J ? "mgs_stage" : "mgs_norm", (double)R * len * 16.0 * nvec, st, [&] {
+        return launch_mgs_stage(h->w, vr, h->V, vi, vr, len, i, J, R, h->partial, m + 2, tk_dots, d_h1, ldh, m + 2,
+                                nrm_off, h->d_inv, st);
+      }, (double)R * len * fl));
+    }
+  } else {
   CKS(launch(h, "gs_dots", (double)R * len * 16.0 * (J + 1), st, [&] {
     return launch_dots_fused(h->V, vi, vr, h->w, vr, len, J, R, h->partial, true, nullptr, tk_dots, d_h1, ldh, 0, st);
   }, (double)R * len * 8.0 * (J + 1)));
@@ -824,6 +836,7 @@ int arnoldi_step(amamg_ctx* h, int j, int R, cudaStream_t st) {
     return launch_axpy_norm(h->w, vr, h->V, vi, vr, d_h1 + (m + 2), ldh, J, len, R, h->d_flag, h->d_npart, tk_norm,
                             d_h1, ldh, nrm_off, h->d_inv, nullptr, 0, 0.0, 1, st);
   }, (double)R * len * 8.0 * (J + 1)));
+  }
   CKS(ls_fork(h, j, R, st));
   if (mixed)
     CKS(launch(h, "scale_copy", (double)R * len * 40.0, st, [&] {
@@ -1186,6 +1199,14 @@ int check_params(const amamg_params* p, int Nt, int Nx, std::string* why) {
   }
   if (p->gs_arith == AMAMG_GS_DF64 && p->precision != AMAMG_SOLVE_MIXED) {
     *why = "AMAMG_GS_DF64 needs AMAMG_SOLVE_MIXED";
+    return AMAMG_ERR_INVALID_ARG;
+  }
+  if (p->gs_method != AMAMG_GS_CGS2 && p->gs_method != AMAMG_GS_MGS) {
+    *why = "gs_method must be AMAMG_GS_CGS2 or AMAMG_GS_MGS";
+    return AMAMG_ERR_INVALID_ARG;
+  }
+  if (p->gs_method == AMAMG_GS_MGS && p->gs_arith != AMAMG_GS_FP64) {
+    *why = "AMAMG_GS_MGS runs in FP64 arithmetic (gs_arith AMAMG_GS_FP64)";
     return AMAMG_ERR_INVALID_ARG;
   }
   if (p->coarsest != AMAMG_COARSEST_DIRECT && p->coarsest != AMAMG_COARSEST_GMRES) {

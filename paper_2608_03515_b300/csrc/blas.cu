@@ -232,6 +232,74 @@ k_axpy_norm(double2* __restrict__ y, size_t yr, const double2* __restrict__ X, s
   }
 }
 
+// Stage i (0 <= i <= J) of modified Gram-Schmidt of w_r against v_0..v_{J-1}
+// (the inner loop of the Arnoldi step in Saad's flexible GMRES): for i >= 1,
+// w_r -= h_{i-1,r} v_{i-1,r} with the previous stage's coefficient; then for
+// i < J the inner product h_{i,r} = v_{i,r}^H w_r, for i = J the norm ||w_r||,
+// each with the fixed-order last-block reduction of k_dots_fused.  h_{i,r} goes
+// to out[r*ldo + i] and a zero to out[r*ldo + off2 + i] (the second-pass slot
+// that the least-squares step adds); the norm to out[r*ldo + nrm_off] and its
+// inverse to inv[r].  One stage reads w and at most two basis vectors.
+__global__ void __launch_bounds__(DOT_THREADS)
+k_mgs_stage(double2* __restrict__ w, size_t wr, const double2* __restrict__ V, size_t vi, size_t vr, long len,
+            long chunk, int i, int J, double2* __restrict__ partial, int pslots, unsigned* __restrict__ tickets,
+            double2* __restrict__ out, int ldo, int off2, int nrm_off, double* __restrict__ inv) {
+  __shared__ double2 sh[32];
+  __shared__ double shr[32];
+  __shared__ bool last;
+  const int r = blockIdx.y, nb = gridDim.x;
+  double2* y = w + r * wr;
+  const double2 c = i >= 1 ? out[(size_t)r * ldo + i - 1] : make_double2(0.0, 0.0);
+  const double2* vp = V + (size_t)(i >= 1 ? i - 1 : 0) * vi + r * vr;
+  const double2* vn = V + (size_t)(i < J ? i : 0) * vi + r * vr;
+  const long start = (long)blockIdx.x * chunk;
+  const long end = min(start + chunk, len);
+  double2 acc = make_double2(0.0, 0.0);
+  double ss = 0.0;
+  for (long k = start + threadIdx.x; k < end; k += blockDim.x) {
+    double2 yk = y[k];
+    if (i >= 1) {
+      double2 t = make_double2(0.0, 0.0);
+      cmac(t, c, vp[k]);
+      yk = yk - t;
+      y[k] = yk;
+    }
+    if (i < J) cmacc(acc, vn[k], yk);
+    else ss = fma(yk.x, yk.x, fma(yk.y, yk.y, ss));
+  }
+  const size_t slot = (size_t)r * pslots + i;
+  if (i < J) {
+    acc = block_reduce(acc, sh);
+  } else {
+    ss = block_reduce_real(ss, shr);
+    acc = make_double2(ss, 0.0);
+  }
+  if (threadIdx.x == 0) {
+    partial[slot * nb + blockIdx.x] = acc;
+    __threadfence();
+    last = atomicAdd(&tickets[slot], 1u) == (unsigned)(nb - 1);
+  }
+  __syncthreads();
+  if (last) {
+    double2 t = make_double2(0.0, 0.0);
+    for (int bb = threadIdx.x; bb < nb; bb += blockDim.x) t += __ldcg(&partial[slot * nb + bb]);
+    t = block_reduce(t, sh);
+    if (threadIdx.x == 0) {
+      if (i < J) {
+        out[(size_t)r * ldo + i] = t;
+        out[(size_t)r * ldo + off2 + i] = make_double2(0.0, 0.0);
+      } else {
+        // NaN propagates (a NaN or Inf entry must surface as a non-finite norm)
+        const double q = t.x;
+        const double nrm = (q >= 0.0) ? sqrt(q) : ((q < 0.0) ? 0.0 : q);
+        out[(size_t)r * ldo + nrm_off] = make_double2(nrm, 0.0);
+        inv[r] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+      }
+      tickets[slot] = 0;
+    }
+  }
+}
+
 inline int grid_for(long len) {
   long g = (len + 255) / 256;
   if (g > 148 * 16) g = 148 * 16;
@@ -273,6 +341,16 @@ cudaError_t launch_dots_fused(const double2* V, size_t vi, size_t vr, const doub
 }
 
 int axpy_norm_blocks(long len) { return grid_for(len); }
+
+cudaError_t launch_mgs_stage(double2* w, size_t wr, const double2* V, size_t vi, size_t vr, long len, int i, int J,
+                             int R, double2* partial, int pslots, unsigned* tickets, double2* out, int ldo, int off2,
+                             int nrm_off, double* inv, cudaStream_t st) {
+  const int nb = dot_blocks(len);
+  const long chunk = (len + nb - 1) / nb;
+  k_mgs_stage<<<dim3(nb, R), DOT_THREADS, 0, st>>>(w, wr, V, vi, vr, len, chunk, i, J, partial, pslots, tickets, out,
+                                                   ldo, off2, nrm_off, inv);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_axpy_norm(double2* y, size_t yr, const double2* X, size_t xi, size_t xr, const double2* coef,
                              int ldc, int J, long len, int R, const int* gate, double* partial, unsigned* tickets,

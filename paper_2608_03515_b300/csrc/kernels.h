@@ -146,6 +146,11 @@ cudaError_t launch_reduce(const double2* partial, int nb, int J, int R, double2*
 cudaError_t launch_dots_fused(const double2* V, size_t vi, size_t vr, const double2* w, size_t wr, long len, int J,
                               int R, double2* partial, bool with_self, const int* gate, unsigned* tickets,
                               double2* out, int ldo, int off, cudaStream_t st);
+// stage i of modified Gram-Schmidt (w -= h_{i-1} v_{i-1}, then h_i = v_i^H w,
+// or ||w|| at i = J); partial: pslots x dot_blocks(len) double2 per RHS
+cudaError_t launch_mgs_stage(double2* w, size_t wr, const double2* V, size_t vi, size_t vr, long len, int i, int J,
+                             int R, double2* partial, int pslots, unsigned* tickets, double2* out, int ldo, int off2,
+                             int nrm_off, double* inv, cudaStream_t st);
 int axpy_norm_blocks(long len);
 cudaError_t launch_axpy_norm(double2* y, size_t yr, const double2* X, size_t xi, size_t xr, const double2* coef,
                              int ldc, int J, long len, int R, const int* gate, double* partial, unsigned* tickets,
