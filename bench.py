@@ -932,6 +932,15 @@ def main():
         gbs = by / (ms * 1e-3) / 1e9
         d_apply[prec] = {"lattice": f"{Nd}x{Nd}", "rhs": R, "ms": round(ms, 4), "GB/s": round(gbs, 1),
                          "frac_of_hbm": round(gbs / peak, 3), "bytes_per_launch": by}
+        if prec == "f64":
+            # 56 FLOPs per site and right-hand side (the stencil's complex
+            # multiply-adds): on B300 the FP64 form is bound by the FP64 pipe
+            gfl = Nd * Nd * R * 56.0 / (ms * 1e-3) / 1e9
+            d_apply[prec].update({"bound": "alu (FP64 pipe)", "GFLOP/s": round(gfl, 1),
+                                  "frac_of_fp64_peak": round(gfl / FP64_PEAK_GFLOPS, 3),
+                                  "fp64_peak": f"{FP64_PEAK_GFLOPS:g} GFLOP/s nominal"})
+        else:
+            d_apply[prec]["bound"] = "hbm"
         del xin, yout
     del hd
 

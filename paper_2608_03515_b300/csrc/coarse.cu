@@ -218,6 +218,84 @@ __device__ __forceinline__ void gs_site(typename cplx<T>::type* __restrict__ e0,
   }
 }
 
+// gs_site for the same site of nr <= RB right-hand sides (e0, r0: the first
+// one's vectors, the others rs elements apart): the lanes load the site's
+// blocks and diagonal inverse once and the neighbour values of all nr
+// right-hand sides together, then form each right-hand side's update in
+// gs_site's order (same sums, same shuffle tree), so every right-hand side
+// gets gs_site's result bit for bit.
+template <typename T, typename BT, int LPS, int RB>
+__device__ __forceinline__ void gs_site_rb(typename cplx<T>::type* __restrict__ e0,
+                                           const typename cplx<T>::type* __restrict__ r0, size_t rs, int nr,
+                                           const BT* __restrict__ Bc, const float* __restrict__ Sc,
+                                           const typename cplx<T>::type* __restrict__ Dc, const Offsets& off,
+                                           int Nt, int Nx, int ncol, int colour, int j, int g, bool valid) {
+  using C = typename cplx<T>::type;
+  const int n = Nt * Nx;
+  const int m = n / ncol;
+  if (!valid) j = 0;
+  int t, x;
+  colour_site(ncol, colour, j, Nx, t, x);
+  const int v = t * Nx + x;
+  const int K1 = off.K - 1;
+  C d[4] = {czero<C>(), czero<C>(), czero<C>(), czero<C>()};
+  C rv[RB][2];
+#pragma unroll
+  for (int q = 0; q < RB; ++q) rv[q][0] = rv[q][1] = czero<C>();
+  if (valid && g == 0) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) d[e] = Dc[((size_t)colour * m + j) * 4 + e];
+#pragma unroll
+    for (int q = 0; q < RB; ++q)
+      if (q < nr) { rv[q][0] = r0[q * rs + v]; rv[q][1] = r0[q * rs + n + v]; }
+  }
+  constexpr int IT = (GS_MAX_OFFDIAG + LPS - 1) / LPS;
+  C bb[IT][4], xv[RB][IT][2];
+#pragma unroll
+  for (int i = 0; i < IT; ++i) {
+    const int k = 1 + g + i * LPS;
+    if (valid && k < off.K) {
+      int tw = t + off.dt[k]; tw -= (tw >= Nt) ? Nt : 0;
+      int xw = x + off.dx[k]; xw -= (xw >= Nx) ? Nx : 0;
+      const int w = tw * Nx + xw;
+#pragma unroll
+      for (int q = 0; q < RB; ++q) {
+        if (q < nr) { xv[q][i][0] = __ldcg(e0 + q * rs + w); xv[q][i][1] = __ldcg(e0 + q * rs + n + w); }
+        else xv[q][i][0] = xv[q][i][1] = czero<C>();
+      }
+      cm_block<T, BT>(Bc, Sc, ((size_t)colour * K1 + (k - 1)) * m + j, bb[i]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < RB; ++q) xv[q][i][0] = xv[q][i][1] = czero<C>();
+      bb[i][0] = bb[i][1] = bb[i][2] = bb[i][3] = czero<C>();
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < RB; ++q) {
+    C s0 = czero<C>(), s1 = czero<C>();
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+      cmac(s0, bb[i][0], xv[q][i][0]);
+      cmac(s0, bb[i][1], xv[q][i][1]);
+      cmac(s1, bb[i][2], xv[q][i][0]);
+      cmac(s1, bb[i][3], xv[q][i][1]);
+    }
+#pragma unroll
+    for (int o = LPS / 2; o > 0; o >>= 1) {
+      s0.x += __shfl_xor_sync(0xffffffffu, s0.x, o);
+      s0.y += __shfl_xor_sync(0xffffffffu, s0.y, o);
+      s1.x += __shfl_xor_sync(0xffffffffu, s1.x, o);
+      s1.y += __shfl_xor_sync(0xffffffffu, s1.y, o);
+    }
+    if (valid && g == 0 && q < nr) {
+      const C a0 = rv[q][0] - s0, a1 = rv[q][1] - s1;
+      const C y0 = cmul(d[0], a0) + cmul(d[1], a1), y1 = cmul(d[2], a0) + cmul(d[3], a1);
+      __stcg(e0 + q * rs + v, y0);
+      __stcg(e0 + q * rs + n + v, y1);
+    }
+  }
+}
+
 // Lanes per site: 8 in FP64 (B300's FP64 pipe is narrow: the sites of a colour
 // spread over many SMs, three offsets per lane), 32 in FP32 (all offsets of a
 // site loaded at once: the clustered sweep is latency bound).
@@ -327,7 +405,10 @@ __device__ __forceinline__ bool grid_barrier(unsigned* sync, unsigned nblocks) {
 template <typename T> struct GridLanes { static constexpr int value = 32; };
 template <> struct GridLanes<double> { static constexpr int value = AMAMG_GRID_LPS64; };
 
-template <typename T, typename BT>
+// RB > 1: a work unit is a site and a group of RB right-hand sides (gs_site_rb:
+// the site's blocks loaded once per group), with each right-hand side's
+// result unchanged.
+template <typename T, typename BT, int RB>
 __global__ void __launch_bounds__(256)
 k_coarse_sweeps_grid(typename cplx<T>::type* __restrict__ e, const typename cplx<T>::type* __restrict__ r,
                      const BT* __restrict__ B, const float* __restrict__ Bs,
@@ -336,7 +417,8 @@ k_coarse_sweeps_grid(typename cplx<T>::type* __restrict__ e, const typename cplx
   constexpr int LPS = GridLanes<T>::value;
   const int n = Nt * Nx;
   const int per_colour = n / ncol;
-  const long units = (long)R * per_colour;
+  const int ngrp = (R + RB - 1) / RB;
+  const long units = (long)ngrp * per_colour;
   const int g = threadIdx.x & (LPS - 1);
   const int gpb = blockDim.x / LPS;
   const long stride = (long)gridDim.x * gpb;
@@ -346,10 +428,16 @@ k_coarse_sweeps_grid(typename cplx<T>::type* __restrict__ e, const typename cplx
       for (long base = 0; base < units; base += stride) {
         const long u = base + (long)blockIdx.x * gpb + threadIdx.x / LPS;
         const bool valid = u < units;
-        const int rhs = valid ? (int)(u / per_colour) : 0;
-        const int idx = valid ? (int)(u - (long)rhs * per_colour) : 0;
-        const size_t roff = (size_t)rhs * 2 * n;
-        gs_site<T, BT, LPS, false>(e + roff, r + roff, B, Bs, Dinv, off, Nt, Nx, ncol, colour, idx, g, valid);
+        const int grp = valid ? (int)(u / per_colour) : 0;
+        const int idx = valid ? (int)(u - (long)grp * per_colour) : 0;
+        const size_t roff = (size_t)grp * RB * 2 * n;
+        if constexpr (RB == 1) {
+          gs_site<T, BT, LPS, false>(e + roff, r + roff, B, Bs, Dinv, off, Nt, Nx, ncol, colour, idx, g, valid);
+        } else {
+          const int nr = R - grp * RB < RB ? R - grp * RB : RB;
+          gs_site_rb<T, BT, LPS, RB>(e + roff, r + roff, (size_t)2 * n, nr, B, Bs, Dinv, off, Nt, Nx, ncol, colour,
+                                     idx, g, valid);
+        }
       }
       if (!grid_barrier(sync, gridDim.x)) return;
     }
@@ -1026,35 +1114,39 @@ size_t dsmem_sweep_bytes(int n, int K, size_t cbytes, bool bsmem, size_t bt_byte
 #define AMAMG_GRID_THREADS 64
 #endif
 constexpr int GRID_SWEEP_THREADS = AMAMG_GRID_THREADS;
+constexpr int GRID_RB = 4;       // right-hand sides per work unit of the grid sweep from 4 on
 template <typename T, typename BT>
 int grid_sweep_blocks(int n, int ncol, int R) {
-  // co-resident blocks of the grid sweep, per device (several host threads may ask)
+  // co-resident blocks of the grid sweep variant for R (right-hand sides in
+  // groups of GRID_RB from GRID_RB on), per device (several host threads may ask)
   static std::mutex mu;
-  static std::map<int, int> cap;
+  static std::map<std::pair<int, int>, int> cap;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return 0; }
+  const int rb = R >= GRID_RB ? GRID_RB : 1;
   int c;
   {
     std::lock_guard<std::mutex> lock(mu);
-    auto it = cap.find(dev);
+    auto it = cap.find({dev, rb});
     if (it == cap.end()) {
       int sms = 0, occ = 0, coop = 0;
+      const void* kern = rb == 1 ? (const void*)k_coarse_sweeps_grid<T, BT, 1>
+                                 : (const void*)k_coarse_sweeps_grid<T, BT, GRID_RB>;
       if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
           cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_coarse_sweeps_grid<T, BT>, GRID_SWEEP_THREADS, 0) !=
-              cudaSuccess) {
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, GRID_SWEEP_THREADS, 0) != cudaSuccess) {
         cudaGetLastError();
         c = 0;
       } else {
         c = coop ? sms * occ : 0;
       }
-      cap[dev] = c;
+      cap[{dev, rb}] = c;
     } else {
       c = it->second;
     }
   }
   if (c <= 0) return 0;
-  const long groups = (long)R * (n / ncol);
+  const long groups = (long)((R + rb - 1) / rb) * (n / ncol);
   const long want = (groups * GridLanes<T>::value + GRID_SWEEP_THREADS - 1) / GRID_SWEEP_THREADS;
   return (int)(want < c ? want : c);
 }
@@ -1075,7 +1167,11 @@ cudaError_t launch_coarse_sweeps_grid(typename cplx<T>::type* e, const typename 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_coarse_sweeps_grid<T, BT>, e, r, B, Bs, Dinv, off, Nt, Nx, ncol, sweeps, R, sync);
+  if (R >= GRID_RB)
+    return cudaLaunchKernelEx(&cfg, k_coarse_sweeps_grid<T, BT, GRID_RB>, e, r, B, Bs, Dinv, off, Nt, Nx, ncol,
+                              sweeps, R, sync);
+  return cudaLaunchKernelEx(&cfg, k_coarse_sweeps_grid<T, BT, 1>, e, r, B, Bs, Dinv, off, Nt, Nx, ncol, sweeps, R,
+                            sync);
 }
 
 // Owner sweep configuration for a level: the fewest sites per block and colour

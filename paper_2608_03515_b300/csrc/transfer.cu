@@ -66,6 +66,61 @@ k_prolong(const typename cplx<T>::type* __restrict__ ec, typename cplx<T>::type*
   f0[(size_t)alpha * nf + (p * a + i) * Nxf + q * a + j] = acc;
 }
 
+// k_prolong for many right-hand sides: a thread loads its row's 8 entries of P
+// once and applies them to RB right-hand sides (blockIdx.y selects the group);
+// per right-hand side the arithmetic of k_prolong.
+template <typename T, typename PT, int RB>
+__global__ void __launch_bounds__(256)
+k_prolong_rb(const typename cplx<T>::type* __restrict__ ec, typename cplx<T>::type* __restrict__ ef,
+             const PT* __restrict__ P, const float* __restrict__ Pscale,
+             int Nxf, int a, int nrows, int Np, int Nq, int own, int R) {
+  using C = typename cplx<T>::type;
+  const int rows_tot = nrows + 2;
+  const int nc = Np * Nq;
+  const int nf = nc * a * a;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nc * rows_tot) return;
+  const int r0 = blockIdx.y * RB;
+  const int nr = R - r0 < RB ? R - r0 : RB;
+  const int tile = g / rows_tot;
+  const int lr = g - tile * rows_tot;
+  const int p = tile / Nq, q = tile - (tile / Nq) * Nq;
+  if (lr >= nrows) {
+    const int alpha = lr - nrows;
+#pragma unroll
+    for (int k = 0; k < RB; ++k)
+      if (k < nr)
+        ef[(size_t)(r0 + k) * 2 * nf + (size_t)alpha * nf + (p * a) * Nxf + q * a] =
+            ec[(size_t)(r0 + k) * 2 * nc + (size_t)alpha * nc + tile];
+    return;
+  }
+  const int l = (lr >> 1) + 1, alpha = lr & 1;
+  const int i = l / a, j = l - (l / a) * a;
+  int dp, dq;
+  row_basket(own, p, q, i, j, dp, dq);
+  const int pb = (p + dp < 0) ? Np - 1 : p + dp, qb = (q + dq < 0) ? Nq - 1 : q + dq;
+  const int p1 = (pb + 1 == Np) ? 0 : pb + 1, q1 = (qb + 1 == Nq) ? 0 : qb + 1;
+  const int vtx[4] = {pb * Nq + qb, pb * Nq + q1, p1 * Nq + qb, p1 * Nq + q1};
+  const size_t base = (size_t)tile * 8 * nrows + lr;
+  C pc[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) pc[c] = p_load<T, PT>(P, Pscale, base + (size_t)c * nrows, tile);
+  const size_t fo = (size_t)alpha * nf + (p * a + i) * Nxf + q * a + j;
+#pragma unroll
+  for (int k = 0; k < RB; ++k) {
+    if (k < nr) {
+      const C* e0 = ec + (size_t)(r0 + k) * 2 * nc;
+      C acc = czero<C>();
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        cmac(acc, pc[2 * c], e0[vtx[c]]);
+        cmac(acc, pc[2 * c + 1], e0[nc + vtx[c]]);
+      }
+      ef[(size_t)(r0 + k) * 2 * nf + fo] = acc;
+    }
+  }
+}
+
 // e_coarse = P^H e_fine.  One warp per coarse vertex v = (p, q): it gathers the
 // rows of the four tiles that have v as a corner (tile (p-di, q-dj) sees v as
 // its corner c = 2 di + dj) plus v's own fine site (identity row), so every
@@ -141,6 +196,77 @@ k_restrict(const typename cplx<T>::type* __restrict__ ef, typename cplx<T>::type
     const T* fv = reinterpret_cast<const T*>(f0 + (h1 ? nf : 0) + sv);
     T* e0 = reinterpret_cast<T*>(ec + (size_t)blockIdx.y * 2 * nc + (h1 ? nc : 0) + warp);
     e0[h2] = sq + fv[h2];
+  }
+}
+
+// k_restrict for many right-hand sides: a warp's lanes load their entries of P
+// once (a <= 4: at most RESTRICT_UNROLL pairs per lane) and apply them to RB
+// right-hand sides (blockIdx.y selects the group); per right-hand side the
+// loads, the accumulation order and the reduce-scatter of k_restrict, so every
+// right-hand side gets that kernel's result bit for bit.
+template <typename T, typename PT, int RB>
+__global__ void __launch_bounds__(256)
+k_restrict_rb(const typename cplx<T>::type* __restrict__ ef, typename cplx<T>::type* __restrict__ ec,
+              const PT* __restrict__ P, const float* __restrict__ Pscale,
+              int Nxf, int a, int nrows, int Np, int Nq, int R) {
+  using C = typename cplx<T>::type;
+  const int nc = Np * Nq;
+  const int nf = nc * a * a;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= nc) return;                      // whole warps leave together
+  const int r0 = blockIdx.y * RB;
+  const int nr = R - r0 < RB ? R - r0 : RB;
+  const int p = warp / Nq, q = warp - (warp / Nq) * Nq;
+  C pa[RESTRICT_UNROLL], pb[RESTRICT_UNROLL];
+  size_t fidx[RESTRICT_UNROLL];
+  bool use[RESTRICT_UNROLL];
+#pragma unroll
+  for (int u = 0; u < RESTRICT_UNROLL; ++u) {
+    const int idx = lane + 32 * u;
+    use[u] = idx < 4 * nrows;
+    pa[u] = pb[u] = czero<C>();
+    fidx[u] = 0;
+    if (use[u]) {
+      const int c = idx / nrows, lr = idx - c * nrows;
+      const int di = c >> 1, dj = c & 1;
+      const int pT = (p - di < 0) ? Np - 1 : p - di;
+      const int qT = (q - dj < 0) ? Nq - 1 : q - dj;
+      const int tile = pT * Nq + qT;
+      const size_t base = (size_t)tile * 8 * nrows + (size_t)(2 * c) * nrows;
+      const int l = (lr >> 1) + 1, alpha = lr & 1;
+      const int i = l / a, j = l - (l / a) * a;
+      fidx[u] = (size_t)alpha * nf + (pT * a + i) * Nxf + qT * a + j;
+      pa[u] = p_load<T, PT>(P, Pscale, base + lr, tile);
+      pb[u] = p_load<T, PT>(P, Pscale, base + nrows + lr, tile);
+    }
+  }
+  const bool h1 = (lane & 16) != 0, h2 = (lane & 8) != 0;
+  const int sv = (p * a) * Nxf + q * a;
+#pragma unroll 1
+  for (int k = 0; k < nr; ++k) {
+    const C* f0 = ef + (size_t)(r0 + k) * 2 * nf;
+    C fv[RESTRICT_UNROLL];
+#pragma unroll
+    for (int u = 0; u < RESTRICT_UNROLL; ++u) fv[u] = use[u] ? f0[fidx[u]] : czero<C>();
+    C acc0 = czero<C>(), acc1 = czero<C>();
+#pragma unroll
+    for (int u = 0; u < RESTRICT_UNROLL; ++u) {
+      cmacc(acc0, pa[u], fv[u]);
+      cmacc(acc1, pb[u], fv[u]);
+    }
+    T ka = h1 ? acc1.x : acc0.x, kb = h1 ? acc1.y : acc0.y;
+    ka += __shfl_xor_sync(0xffffffffu, h1 ? acc0.x : acc1.x, 16);
+    kb += __shfl_xor_sync(0xffffffffu, h1 ? acc0.y : acc1.y, 16);
+    T sq = h2 ? kb : ka;
+    sq += __shfl_xor_sync(0xffffffffu, h2 ? ka : kb, 8);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if ((lane & 7) == 0) {
+      const T* fvv = reinterpret_cast<const T*>(f0 + (h1 ? nf : 0) + sv);
+      T* e0 = reinterpret_cast<T*>(ec + (size_t)(r0 + k) * 2 * nc + (h1 ? nc : 0) + warp);
+      e0[h2] = sq + fvv[h2];
+    }
   }
 }
 
@@ -231,6 +357,12 @@ cudaError_t launch_prolong(const typename cplx<T>::type* ec, typename cplx<T>::t
                            const float* Pscale, int Nxf, int a, int Np, int Nq, int R, cudaStream_t st, int own) {
   const int nrows = 2 * (a * a - 1);
   const int total = Np * Nq * (nrows + 2);
+  constexpr int RB = sizeof(T) == 8 ? 4 : 8;       // right-hand sides per group of the blocked kernel
+  if (R >= 4) {
+    dim3 grid((total + 255) / 256, (R + RB - 1) / RB);
+    k_prolong_rb<T, PT, RB><<<grid, 256, 0, st>>>(ec, ef, P, Pscale, Nxf, a, nrows, Np, Nq, own, R);
+    return cudaGetLastError();
+  }
   dim3 grid((total + 255) / 256, R);
   k_prolong<T, PT><<<grid, 256, 0, st>>>(ec, ef, P, Pscale, Nxf, a, nrows, Np, Nq, own);
   return cudaGetLastError();
@@ -241,6 +373,12 @@ cudaError_t launch_restrict(const typename cplx<T>::type* ef, typename cplx<T>::
                             const float* Pscale, int Nxf, int a, int Np, int Nq, int R, cudaStream_t st, int own) {
   const int nrows = 2 * (a * a - 1);
   const int nc = Np * Nq;
+  constexpr int RB = sizeof(T) == 8 ? 4 : 8;       // right-hand sides per group of the blocked kernel
+  if (own == OWN_TILE && R >= 4 && 4 * nrows <= 32 * RESTRICT_UNROLL) {
+    dim3 grid((nc * 32 + 255) / 256, (R + RB - 1) / RB);
+    k_restrict_rb<T, PT, RB><<<grid, 256, 0, st>>>(ef, ec, P, Pscale, Nxf, a, nrows, Np, Nq, R);
+    return cudaGetLastError();
+  }
   dim3 grid((nc * 32 + 255) / 256, R);
   if (own == OWN_TILE) k_restrict<T, PT><<<grid, 256, 0, st>>>(ef, ec, P, Pscale, Nxf, a, nrows, Np, Nq);
   else k_restrict_owned<T, PT><<<grid, 256, 0, st>>>(ef, ec, P, Pscale, Nxf, a, nrows, Np, Nq, own);

@@ -618,3 +618,69 @@ def test_coarse_apply_many_rhs_loads_blocks_once_same_result(R):
                 if dt == torch.complex128:
                     want = lattice_vec(C.A @ W.to_flat(xin[r]), C.Nt, C.Nx)
                     assert relerr(got[r], want) <= 1e-12
+
+
+@pytest.mark.parametrize("R", [4, 9, 17])
+def test_transfers_many_rhs_load_P_once_same_result(R):
+    """The right-hand-side-blocked prolongation and restriction (R >= 4: each
+    entry of P loaded once per group of right-hand sides) give every
+    right-hand side bit for bit the one-right-hand-side kernels' result, and
+    the oracle's P and P^H to 1e-13 (FP64)."""
+    U, D, hier, levels = make(32, 32, [4, 2], m0=0.2, seed=7)
+    rng = np.random.Generator(np.random.PCG64(9))
+    for l in (0, 1):
+        F, C = levels[l], levels[l + 1]
+        for dt in (torch.complex128, torch.complex64):
+            ec = rng.standard_normal((R, 2, C.Nt, C.Nx)) + 1j * rng.standard_normal((R, 2, C.Nt, C.Nx))
+            ef = rng.standard_normal((R, 2, F.Nt, F.Nx)) + 1j * rng.standard_normal((R, 2, F.Nt, F.Nx))
+            ecd, efd = dev(ec, dt), dev(ef, dt)
+            out_f, out_c = canary_like(efd), canary_like(ecd)
+            A.apply_P(hier, l, ecd, out_f)
+            A.apply_PH(hier, l, efd, out_c)
+            gf, gc = host(out_f), host(out_c)
+            for r in range(R):
+                one_f, one_c = canary_like(efd[r:r + 1]), canary_like(ecd[r:r + 1])
+                A.apply_P(hier, l, ecd[r:r + 1].contiguous(), one_f)
+                A.apply_PH(hier, l, efd[r:r + 1].contiguous(), one_c)
+                assert np.array_equal(host(one_f)[0], gf[r])
+                assert np.array_equal(host(one_c)[0], gc[r])
+                if dt == torch.complex128:
+                    wf = lattice_vec(F.P @ W.to_flat(ec[r]), F.Nt, F.Nx)
+                    wc = lattice_vec(F.P.conj().T @ W.to_flat(ef[r]), C.Nt, C.Nx)
+                    assert relerr(gf[r], wf) <= 1e-13
+                    assert relerr(gc[r], wc) <= 1e-13
+
+
+@pytest.mark.parametrize("R", [4, 6])
+def test_grid_sweep_groups_of_right_hand_sides_same_result(monkeypatch, R):
+    """The cooperative grid sweep with R >= 4 takes a site and a group of 4
+    right-hand sides per work unit (the site's blocks loaded once per group; a
+    ragged last group at R = 6); every right-hand side gets the one-at-a-time
+    sweep's result bit for bit, and the oracle's sequential Gauss-Seidel to
+    1e-12 (FP64)."""
+    monkeypatch.setenv("AMAMG_COARSE_GS", "grid")
+    Nt = Nx = 64
+    aggs = [2, 2, 2]
+    U = random_links(Nt, Nx, 33)
+    levels = amg.build_hierarchy(W.dirac_matrix(U, 0.1), Nt, Nx, aggs)
+    hier = A.setup(dev(U), 0.1, A.make_params(aggs))
+    rng = np.random.Generator(np.random.PCG64(34))
+    for l in (1, 2):
+        L = levels[l]
+        shape = (R, 2, L.Nt, L.Nx)
+        r = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+        e0 = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+        for dt in (torch.complex128, torch.complex64):
+            e = dev(e0, dt)
+            A.smooth(hier, l, dev(r, dt), e, 2)
+            g = host(e)
+            for q in range(R):
+                e1 = dev(e0[q:q + 1], dt)
+                A.smooth(hier, l, dev(r[q:q + 1], dt), e1, 2)
+                assert np.array_equal(host(e1)[0], g[q]), (l, q, dt)
+                if dt == torch.complex128:
+                    want = W.to_flat(e0[q])
+                    for _ in range(2):
+                        want = amg.gs_sweep(L.A, L.dinv, L.colour, want, W.to_flat(r[q]))
+                    assert relerr(g[q], lattice_vec(want, L.Nt, L.Nx)) <= 1e-12
+    hier.destroy()
