@@ -60,6 +60,10 @@ typedef struct amamg_ctx* amamg_handle;
 /* vector precision of apply-style calls */
 #define AMAMG_F64 0                  /* complex128 vectors, FP64 operators */
 #define AMAMG_F32 1                  /* complex64 vectors, FP32 links, FP16+scale P and coarse blocks */
+#define AMAMG_F32_F64 2              /* amamg_apply_D only: complex64 input, complex128 output, FP64 links
+                                        and arithmetic (the product w = D z of the mixed solve, z from the
+                                        FP32 V-cycle); equal to the FP64 stencil of the input widened to
+                                        complex128 */
 
 /* solve precision */
 #define AMAMG_SOLVE_FP64  0          /* every step in FP64 */
@@ -194,7 +198,9 @@ int amamg_batch_cycle(amamg_batch_handle b, void* stream, amamg_slot_info* info)
 int amamg_batch_retire(amamg_batch_handle b, int slot, void* x, void* stream);
 int amamg_batch_destroy(amamg_batch_handle b);
 
-/* out = D in on the fine lattice, Eq. (3).  precision AMAMG_F64 or AMAMG_F32. */
+/* out = D in on the fine lattice, Eq. (3).  precision AMAMG_F64 (complex128 in
+ * and out), AMAMG_F32 (complex64 in and out, FP32 links) or AMAMG_F32_F64
+ * (complex64 in, complex128 out, FP64 links and arithmetic). */
 int amamg_apply_D(amamg_handle h, const void* in, void* out, int R, int precision, void* stream);
 
 /* out = D^H in = sigma_3 D sigma_3 in (sigma_3-hermiticity, Eq. (6)) on the

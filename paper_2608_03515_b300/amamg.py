@@ -34,6 +34,7 @@ OWNER_TILE = 0
 OWNER_FIRST_LEX = 1
 COARSEST_DIRECT = 0
 COARSEST_GMRES = 1
+F32_F64 = 2
 GS_FP64 = 0
 GS_DF64 = 1
 GS_CGS2 = 0
@@ -296,8 +297,12 @@ def solve(hier: Hierarchy, psi, x, stream=None) -> List[Info]:
 
 
 def apply_D(hier: Hierarchy, inp, out, stream=None):
+    """out = D inp; complex64 inp with complex128 out is the FP64 stencil of the
+    widened input (AMAMG_F32_F64), else both of one precision."""
+    import torch
     R = int(inp.shape[0])
-    hier._check(_lib.amamg_apply_D(hier.h, _ptr(inp), _ptr(out), R, _prec(inp), _stream(stream)), "amamg_apply_D")
+    prec = F32_F64 if (inp.dtype == torch.complex64 and out.dtype == torch.complex128) else _prec(inp)
+    hier._check(_lib.amamg_apply_D(hier.h, _ptr(inp), _ptr(out), R, prec, _stream(stream)), "amamg_apply_D")
 
 
 def apply_P(hier: Hierarchy, level: int, coarse_in, fine_out, stream=None):

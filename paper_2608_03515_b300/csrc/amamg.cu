@@ -1642,6 +1642,14 @@ int amamg_apply_D(amamg_handle h, const void* in, void* out, int R, int precisio
   if (!h || !in || !out || R < 1) return AMAMG_ERR_INVALID_ARG;
   if (precision == AMAMG_F64) return op_dslash<double>(h, (const double2*)in, (double2*)out, nullptr, R, S(stream));
   if (precision == AMAMG_F32) return op_dslash<float>(h, (const float2*)in, (float2*)out, nullptr, R, S(stream));
+  if (precision == AMAMG_F32_F64) {
+    const Level& L = h->lv[0];
+    cudaStream_t st = S(stream);
+    return launch(h, "dslash_mixed", (double)L.n * (R * (16.0 + 32.0) + 32.0), st, [&] {
+      return launch_dslash<float2, double2, double>((const float2*)in, (double2*)out, nullptr, h->U64s, h->m0 + 2.0,
+                                                    L.Nt, L.Nx, R, st);
+    }, (double)L.n * R * 56.0);
+  }
   return AMAMG_ERR_INVALID_ARG;
 }
 

@@ -684,3 +684,31 @@ def test_grid_sweep_groups_of_right_hand_sides_same_result(monkeypatch, R):
                         want = amg.gs_sweep(L.A, L.dinv, L.colour, want, W.to_flat(r[q]))
                     assert relerr(g[q], lattice_vec(want, L.Nt, L.Nx)) <= 1e-12
     hier.destroy()
+
+
+def test_apply_D_fp32_input_fp64_output_equals_fp64_on_widened_input():
+    """AMAMG_F32_F64 (the product w = D z of the mixed solve) widens its
+    complex64 input exactly, so it equals the FP64 stencil of the widened input
+    bit for bit, here with zeros, subnormals and entries from 1e-30 to 1e30
+    among Gaussian ones."""
+    Nt, Nx, R = 16, 32, 3
+    U = random_links(Nt, Nx, 61)
+    hier = A.setup(dev(U), 0.07, A.make_params([4]))
+    rng = np.random.Generator(np.random.PCG64(62))
+    z = (rng.standard_normal((R, 2, Nt, Nx)) + 1j * rng.standard_normal((R, 2, Nt, Nx))).astype(np.complex64)
+    flat = z.reshape(-1)
+    flat[:40] = 0
+    flat[40:80] = np.float32(1e-41) * (1 + 1j)                       # subnormal in FP32
+    flat[80:120] *= np.float32(1e30)
+    flat[120:160] *= np.float32(1e-30)
+    flat[160:170] = -0.0 + 0j
+    zd = torch.from_numpy(z).to(DEV)
+    out_mixed = canary(R, 2, Nt, Nx, torch.complex128)
+    A.apply_D(hier, zd, out_mixed)
+    out64 = canary(R, 2, Nt, Nx, torch.complex128)
+    A.apply_D(hier, zd.to(torch.complex128), out64)
+    assert np.array_equal(host(out_mixed), host(out64))
+    for r in range(R):
+        ref = W.apply_dirac(U, 0.07, z[r].astype(np.complex128))
+        assert relerr(host(out_mixed)[r], ref) <= 1e-13
+    hier.destroy()
