@@ -74,3 +74,23 @@ def test_status_strings(lib):
     assert L.amamg_status_string(0) == b"ok"
     assert b"singular" in L.amamg_status_string(lib.ERR_SINGULAR)
     assert L.amamg_launch_count(None) == -1
+
+
+def test_gram_schmidt_variant_parameters_are_validated(lib):
+    """gs_method: classical (default) or modified, the modified one in FP64
+    arithmetic only; gs_arith double-float needs the mixed solve."""
+    ok = [lib.make_params([4, 2]), lib.make_params([4, 2], gs_method="mgs"),
+          lib.make_params([4, 2], precision=lib.SOLVE_MIXED, gs_method="mgs"),
+          lib.make_params([4, 2], precision=lib.SOLVE_MIXED, gs="df64")]
+    for p in ok:
+        lib.query_bytes(p, 64, 64, 1)
+    bad = [lib.make_params([4, 2], precision=lib.SOLVE_MIXED, gs="df64", gs_method="mgs"),
+           lib.make_params([4, 2], gs="df64")]
+    p = lib.make_params([4, 2])
+    p.gs_method = 7
+    bad.append(p)
+    for p in bad:
+        with pytest.raises(lib.AmamgError) as ei:
+            lib.query_bytes(p, 64, 64, 1)
+        assert ei.value.status == lib.ERR_INVALID_ARG
+    assert lib.default_params().gs_method == lib.GS_CGS2
