@@ -196,6 +196,8 @@ int amamg_batch_admit(amamg_batch_handle b, int slot, const void* psi, double m0
 int amamg_batch_cycle(amamg_batch_handle b, void* stream, amamg_slot_info* info);
 /* Copies the slot's iterate to x (device complex128 [2][Nt][Nx]) and frees it. */
 int amamg_batch_retire(amamg_batch_handle b, int slot, void* x, void* stream);
+/* Synchronises the device and frees the batch's buffers (slots not retired
+ * are dropped); the hierarchy stays.  AMAMG_ERR_INVALID_ARG for NULL. */
 int amamg_batch_destroy(amamg_batch_handle b);
 
 /* out = D in on the fine lattice, Eq. (3).  precision AMAMG_F64 (complex128 in
@@ -222,11 +224,16 @@ int amamg_cgnr(amamg_handle h, const void* psi, void* x, int R, int max_iter, do
                amamg_solve_info* info);
 
 /* fine_out = P_l coarse_in: interpolation from level l+1 to level l
- * (Eq. (16) rows for owned edge/interior sites, identity on vertices). */
+ * (Eq. (16) rows for owned edge/interior sites, identity on vertices).
+ * coarse_in: level-(l+1) vectors, fine_out: level-l vectors ([R][2][Nt][Nx]
+ * of that level), complex128 with AMAMG_F64 (FP64 P) or complex64 with
+ * AMAMG_F32 (P in FP16 with one FP32 scale per tile); caller-owned, not
+ * aliased.  AMAMG_ERR_INVALID_ARG for a level without a coarser one. */
 int amamg_apply_P(amamg_handle h, int level, const void* coarse_in, void* fine_out,
                   int R, int precision, void* stream);
 
-/* coarse_out = P_l^H fine_in: restriction from level l to level l+1 (Sec. 2). */
+/* coarse_out = P_l^H fine_in: restriction from level l to level l+1 (Sec. 2);
+ * layouts, precisions and errors as amamg_apply_P. */
 int amamg_apply_PH(amamg_handle h, int level, const void* fine_in, void* coarse_out,
                    int R, int precision, void* stream);
 
@@ -370,6 +377,7 @@ int amamg_export_coarse(amamg_handle h, int level, void* out, void* stream);
  * floating-point operations done (each input read once, each output written
  * once).  Returns AMAMG_ERR_INVALID_ARG past the last category. */
 int amamg_profile_enable(amamg_handle h, int on);
+/* Collects outstanding records and forgets every category. */
 int amamg_profile_reset(amamg_handle h);
 int amamg_profile_get(amamg_handle h, int idx, const char** name, long long* launches,
                       double* total_ms, double* bytes, double* flops);
@@ -380,8 +388,14 @@ long long amamg_launch_count(amamg_handle h);
 /* Seconds of device time of the last amamg_setup (measured with events). */
 double amamg_setup_seconds(amamg_handle h);
 
+/* Synchronises the device and frees everything the handle owns (hierarchy,
+ * solver workspace, graphs, streams); caller buffers are untouched.
+ * AMAMG_ERR_INVALID_ARG for NULL. */
 int amamg_destroy(amamg_handle h);
+/* A static string naming an AMAMG_* status code. */
 const char* amamg_status_string(int status);
+/* The message of the last failure on h (empty when none), valid until the
+ * next call on h; "null handle" for NULL. */
 const char* amamg_last_error(amamg_handle h);
 
 #ifdef __cplusplus
