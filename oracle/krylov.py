@@ -6,8 +6,11 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 Right-preconditioned flexible GMRES with restart length m (Saad's FGMRES):
 the preconditioned directions z_j = M(v_j) are kept in a second basis Z so that
 M may change between steps (the V-cycle is not a fixed linear operator once it
-runs in reduced precision).  Arnoldi uses modified Gram-Schmidt; the small
-least-squares problem is solved with complex Givens rotations.
+runs in reduced precision).  Arnoldi uses modified Gram-Schmidt (gs="mgs",
+default), or classical Gram-Schmidt with a second pass where the first one
+cancelled much of w (gs="cgs2": the criterion of Daniel, Gragg, Kaufman and
+Stewart, 1976, ||w after|| < ||w before|| / sqrt(2)); the small least-squares
+problem is solved with complex Givens rotations.
 
 Readings (the paper fixes none of them): start vector x0 = 0; residual measured
 as ||b - A x||_2 / ||b||_2; the iteration count is the total number of Arnoldi
@@ -31,6 +34,7 @@ class FgmresResult:
     converged: bool
     estimates: List[float] = field(default_factory=list)   # |g_{j+1}| / ||b|| after each step
     restarts: int = 0
+    second_passes: int = 0                                   # gs="cgs2": steps that reorthogonalised
 
 
 def givens(a: complex, b: complex):
@@ -47,8 +51,11 @@ def givens(a: complex, b: complex):
 
 def fgmres(apply_A: Callable[[np.ndarray], np.ndarray],
            precond: Callable[[np.ndarray], np.ndarray],
-           b: np.ndarray, m: int, tol: float, max_iter: int) -> FgmresResult:
+           b: np.ndarray, m: int, tol: float, max_iter: int, gs: str = "mgs") -> FgmresResult:
+    if gs not in ("mgs", "cgs2"):
+        raise ValueError(f"gs must be 'mgs' or 'cgs2', got {gs!r}")
     n = b.shape[0]
+    second = 0
     x = np.zeros(n, dtype=np.complex128)
     bnorm = np.linalg.norm(b)
     if bnorm == 0:
@@ -60,9 +67,9 @@ def fgmres(apply_A: Callable[[np.ndarray], np.ndarray],
         r = b - apply_A(x)
         beta = np.linalg.norm(r)
         if beta <= tol * bnorm:
-            return FgmresResult(x, iters, beta / bnorm, True, estimates, restarts)
+            return FgmresResult(x, iters, beta / bnorm, True, estimates, restarts, second)
         if iters >= max_iter:
-            return FgmresResult(x, iters, beta / bnorm, False, estimates, restarts)
+            return FgmresResult(x, iters, beta / bnorm, False, estimates, restarts, second)
         V = np.zeros((m + 1, n), dtype=np.complex128)
         Z = np.zeros((m, n), dtype=np.complex128)
         H = np.zeros((m + 1, m), dtype=np.complex128)
@@ -75,9 +82,22 @@ def fgmres(apply_A: Callable[[np.ndarray], np.ndarray],
         for j in range(m):
             Z[j] = precond(V[j])
             w = apply_A(Z[j])
-            for i in range(j + 1):                       # modified Gram-Schmidt
-                H[i, j] = np.vdot(V[i], w)
-                w = w - H[i, j] * V[i]
+            if gs == "mgs":
+                for i in range(j + 1):                   # modified Gram-Schmidt
+                    H[i, j] = np.vdot(V[i], w)
+                    w = w - H[i, j] * V[i]
+            else:
+                # classical Gram-Schmidt: all projections from the same w, then
+                # once more if the pass removed more than 1 - 1/sqrt(2) of ||w||
+                w0 = np.linalg.norm(w)
+                h = V[:j + 1].conj() @ w
+                w = w - V[:j + 1].T @ h
+                if np.linalg.norm(w) < w0 / np.sqrt(2.0):
+                    h2 = V[:j + 1].conj() @ w
+                    w = w - V[:j + 1].T @ h2
+                    h = h + h2
+                    second += 1
+                H[:j + 1, j] = h
             H[j + 1, j] = np.linalg.norm(w)
             breakdown = H[j + 1, j] == 0
             if not breakdown:

@@ -101,3 +101,43 @@ def test_cgnr_equals_cg_on_the_normal_equations_and_solves_the_system():
     res3 = krylov.cgnr(lambda v: D @ v, lambda v: s3 @ (D @ (s3 @ v)), b, 1e-10, 5000)
     assert res3.iterations == res.iterations
     assert np.linalg.norm(res3.x - res.x) <= 1e-10 * np.linalg.norm(res.x)
+
+
+def test_classical_gram_schmidt_with_second_pass_pins():
+    """gs="cgs2" (the GPU's default variant): with M = I it is GMRES like the
+    modified form (same Krylov spaces, so the same solution and step count as
+    scipy's GMRES); its second pass runs exactly when the first pass removed
+    more than 1 - 1/sqrt(2) of ||w||; with the V-cycle it takes the modified
+    form's step count on a Wilson problem."""
+    Nt = Nx = 8
+    D = W.dirac_matrix(random_links(Nt, Nx, 40), 0.4)
+    b = W.to_flat(fx.gaussian_rhs(1, Nt, Nx, 41)[0])
+    r_m = krylov.fgmres(lambda v: D @ v, lambda v: v, b, 10, 1e-10, 2000)
+    r_c = krylov.fgmres(lambda v: D @ v, lambda v: v, b, 10, 1e-10, 2000, gs="cgs2")
+    assert r_c.converged and r_c.true_relres <= 1e-10
+    assert r_c.iterations == r_m.iterations
+    assert np.allclose(r_c.estimates, r_m.estimates, rtol=1e-8)
+    xs = np.linalg.solve(D.toarray(), b)
+    assert np.linalg.norm(r_c.x - xs) <= 1e-8 * np.linalg.norm(xs)
+    assert r_m.second_passes == 0
+    # the criterion: an operator that maps v to (1 - eps) v + eps u leaves
+    # about eps of w after projecting out v (second pass), the identity plus a
+    # large orthogonal part leaves most of it (no second pass)
+    n = 6
+    e = np.eye(n, dtype=complex)
+    for eps, want in ((1e-3, 1), (0.9, 0)):
+        A = (1 - eps) * np.eye(n) + eps * np.roll(np.eye(n), 1, axis=0)
+        res = krylov.fgmres(lambda v: A @ v, lambda v: v, e[0], 1, 1e-300, 1, gs="cgs2")
+        assert res.second_passes == want, (eps, res.second_passes)
+    with pytest.raises(ValueError):
+        krylov.fgmres(lambda v: v, lambda v: v, e[0], 1, 1e-10, 1, gs="cgs1")
+    # preconditioned by the V-cycle on a 16^2 Wilson problem: same step count
+    Nt = Nx = 16
+    D = W.dirac_matrix(random_links(Nt, Nx, 42), 0.05)
+    levels = amg.build_hierarchy(D, Nt, Nx, [2, 2])
+    b = W.to_flat(fx.gaussian_rhs(1, Nt, Nx, 43)[0])
+    m1 = krylov.fgmres(lambda v: D @ v, lambda r: amg.vcycle(levels, r), b, 30, 1e-10, 500)
+    c1 = krylov.fgmres(lambda v: D @ v, lambda r: amg.vcycle(levels, r), b, 30, 1e-10, 500, gs="cgs2")
+    assert m1.converged and c1.converged
+    assert c1.iterations == m1.iterations
+    assert np.linalg.norm(c1.x - m1.x) <= 1e-8 * np.linalg.norm(m1.x)
