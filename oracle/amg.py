@@ -55,6 +55,8 @@ import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
 
+from .wilson import dirac_rows
+
 ROLE_VERTEX, ROLE_EDGE, ROLE_INTERIOR = 0, 1, 2
 
 
@@ -247,6 +249,66 @@ def build_interpolator(A: sp.csr_matrix, Nt: int, Nx: int, a: int, route: str = 
         P = (0.5 * (P + s3f @ P @ s3c)).tocsr()
         P.eliminate_zeros()
     return P, pattern
+
+
+def galerkin_rows(U: np.ndarray, m0: float, a: int, vertices):
+    """Rows of the first coarse operator A_1 = P^H D P (Sec. 2; tile edge
+    ownership, N the identity) for the coarse sites `vertices` ((p, q) pairs),
+    from the baskets near them only: row v of A_1 involves P's column v (the
+    owned rows of the four tiles around v and v's own site) and, through the
+    nearest-neighbour D, the columns of every coarse site whose tiles reach a
+    neighbour of those rows, all within three tiles of v.  Returns
+    {(p, q): {w: 2x2 block A_1[(v, alpha), (w, beta)]}} with w the coarse site
+    index p_w (Nx / a) + q_w.  For lattices too large to assemble D and P whole;
+    equal to the rows of galerkin(P, D) (pinned)."""
+    _, Nt, Nx = U.shape
+    check_tiling(Nt, Nx, a)
+    Np, Nq = Nt // a, Nx // a
+    vertices = [(int(p) % Np, int(q) % Nq) for p, q in vertices]
+    tiles = sorted({((p + dp) % Np, (q + dq) % Nq) for (p, q) in vertices
+                    for dp in range(-3, 3) for dq in range(-3, 3)})
+    sites = {(t, x) for (tp, tq) in tiles for (t, x, _, _) in basket_sites(Nt, Nx, a, tp, tq)}
+    D = dirac_rows(U, m0, sites)
+    # rows of P owned by the tiles in reach: fine DOF -> {coarse DOF: weight}
+    Prow = {}
+    for (tp, tq) in tiles:
+        F_sites, P_F = local_interpolation(D, Nt, Nx, a, tp, tq)
+        for k, (t, x, i, j) in enumerate(F_sites):
+            if owner_basket(t, x, Nt, Nx, a, "tile") != tp * Nq + tq:
+                continue
+            for alpha in range(2):
+                row = Prow.setdefault(2 * (t * Nx + x) + alpha, {})
+                for c in range(4):
+                    v = corner_vertex(Nt, Nx, a, tp, tq, c)
+                    for beta in range(2):
+                        row[2 * v + beta] = row.get(2 * v + beta, 0) + P_F[2 * k + alpha, 2 * c + beta]
+        for alpha in range(2):
+            Prow[2 * ((tp * a) * Nx + tq * a) + alpha] = {2 * (tp * Nq + tq) + alpha: 1.0 + 0j}
+    out = {}
+    for (p, q) in vertices:
+        v = p * Nq + q
+        blocks = {}
+        for alpha in range(2):
+            col = 2 * v + alpha
+            # column v of P: the fine rows that reference it
+            supp = [(i, r[col]) for i, r in Prow.items() if col in r]
+            # (P_v)^H D: a sparse fine row vector
+            acc = {}
+            for i, pv in supp:
+                lo, hi = D.indptr[i], D.indptr[i + 1]
+                if lo == hi:
+                    raise ValueError("row of D outside the window")
+                for jj, dij in zip(D.indices[lo:hi], D.data[lo:hi]):
+                    acc[jj] = acc.get(jj, 0) + np.conj(pv) * dij
+            # times P
+            for j, val in acc.items():
+                if j not in Prow:
+                    raise ValueError("row of P outside the window")
+                for cdof, pw in Prow[j].items():
+                    w, beta = divmod(cdof, 2)
+                    blocks.setdefault(w, np.zeros((2, 2), dtype=np.complex128))[alpha, beta] += val * pw
+        out[(p, q)] = blocks
+    return out
 
 
 # --------------------------------------------------------------------------- Galerkin / sparsity

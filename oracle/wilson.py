@@ -35,14 +35,9 @@ def site_index(t, x, Nx):
     return t * Nx + x
 
 
-def dirac_matrix(U: np.ndarray, m0: float, t_sign: float = -1.0) -> sp.csr_matrix:
-    """Assemble D of Eq. (3) as a sparse (2 V) x (2 V) complex matrix, one entry at a time.
-
-    t_sign is the factor on hops across the t boundary: -1 (antiperiodic, Eq. (7);
-    the method's case) or +1 (periodic, used only by the normalisation pin)."""
+def _add_site_row(U: np.ndarray, m0: float, t: int, x: int, t_sign: float, rows, cols, vals) -> None:
+    """Entries of D's two rows of site (t, x) (Eq. (3)), appended to rows/cols/vals."""
     _, Nt, Nx = U.shape
-    V = Nt * Nx
-    rows, cols, vals = [], [], []
 
     def add_block(s_row, s_col, block):
         for a in range(2):
@@ -52,28 +47,53 @@ def dirac_matrix(U: np.ndarray, m0: float, t_sign: float = -1.0) -> sp.csr_matri
                     cols.append(2 * s_col + b)
                     vals.append(block[a, b])
 
+    n = site_index(t, x, Nx)
+    add_block(n, n, (m0 + 2.0) * IDENT2)
+    for mu in (0, 1):
+        # forward neighbour n + mu_hat, with the Eq. (7) sign when it wraps in t
+        if mu == 0:
+            tf, xf = (t + 1) % Nt, x
+            sign_f = t_sign if t == Nt - 1 else 1.0
+            tb, xb = (t - 1) % Nt, x
+            sign_b = t_sign if t == 0 else 1.0
+        else:
+            tf, xf = t, (x + 1) % Nx
+            sign_f = 1.0
+            tb, xb = t, (x - 1) % Nx
+            sign_b = 1.0
+        m_f = site_index(tf, xf, Nx)
+        m_b = site_index(tb, xb, Nx)
+        u_f = U[mu, t, x]                 # U_mu(n)
+        u_b = np.conj(U[mu, tb, xb])      # U_mu(n - mu)^dagger
+        add_block(n, m_f, -0.5 * sign_f * u_f * (IDENT2 - SIGMAS[mu]))
+        add_block(n, m_b, -0.5 * sign_b * u_b * (IDENT2 + SIGMAS[mu]))
+
+
+def dirac_matrix(U: np.ndarray, m0: float, t_sign: float = -1.0) -> sp.csr_matrix:
+    """Assemble D of Eq. (3) as a sparse (2 V) x (2 V) complex matrix, one entry at a time.
+
+    t_sign is the factor on hops across the t boundary: -1 (antiperiodic, Eq. (7);
+    the method's case) or +1 (periodic, used only by the normalisation pin)."""
+    _, Nt, Nx = U.shape
+    V = Nt * Nx
+    rows, cols, vals = [], [], []
     for t in range(Nt):
         for x in range(Nx):
-            n = site_index(t, x, Nx)
-            add_block(n, n, (m0 + 2.0) * IDENT2)
-            for mu in (0, 1):
-                # forward neighbour n + mu_hat, with the Eq. (7) sign when it wraps in t
-                if mu == 0:
-                    tf, xf = (t + 1) % Nt, x
-                    sign_f = t_sign if t == Nt - 1 else 1.0
-                    tb, xb = (t - 1) % Nt, x
-                    sign_b = t_sign if t == 0 else 1.0
-                else:
-                    tf, xf = t, (x + 1) % Nx
-                    sign_f = 1.0
-                    tb, xb = t, (x - 1) % Nx
-                    sign_b = 1.0
-                m_f = site_index(tf, xf, Nx)
-                m_b = site_index(tb, xb, Nx)
-                u_f = U[mu, t, x]                 # U_mu(n)
-                u_b = np.conj(U[mu, tb, xb])      # U_mu(n - mu)^dagger
-                add_block(n, m_f, -0.5 * sign_f * u_f * (IDENT2 - SIGMAS[mu]))
-                add_block(n, m_b, -0.5 * sign_b * u_b * (IDENT2 + SIGMAS[mu]))
+            _add_site_row(U, m0, t, x, t_sign, rows, cols, vals)
+    D = sp.coo_matrix((vals, (rows, cols)), shape=(2 * V, 2 * V)).tocsr()
+    D.sum_duplicates()
+    return D
+
+
+def dirac_rows(U: np.ndarray, m0: float, sites, t_sign: float = -1.0) -> sp.csr_matrix:
+    """D of Eq. (3) restricted to the rows of the given (t, x) sites (other rows
+    zero), same shape as dirac_matrix: for local work on lattices too large to
+    assemble whole."""
+    _, Nt, Nx = U.shape
+    V = Nt * Nx
+    rows, cols, vals = [], [], []
+    for (t, x) in sorted(set((int(t), int(x)) for t, x in sites)):
+        _add_site_row(U, m0, t, x, t_sign, rows, cols, vals)
     D = sp.coo_matrix((vals, (rows, cols)), shape=(2 * V, 2 * V)).tocsr()
     D.sum_duplicates()
     return D

@@ -8,7 +8,8 @@ power-of-two scale per right-hand side, oracle.mixed.quantise_rhs_pow2): equal
 up to FP32 accumulation, 1e-5 of the output's largest entry.  Against the
 exact FP64 product: the FP16 rounding of both operands, 2e-3.  Sizes: coarse
 levels of 8 x 8 (the box wraps the whole x extent) to 32 x 16, one to two
-groups of 64 right-hand sides with a ragged last group."""
+groups of 64 right-hand sides with a ragged last group, and the benchmark's
+256^2 x 64 on sampled sites (oracle rows built locally)."""
 import numpy as np
 import pytest
 
@@ -113,3 +114,44 @@ def test_tensor_core_coarse_apply_agrees_with_cuda_core_kernels_and_repeats():
         assert relerr(g[r], one.cpu().numpy()[0]) <= 2e-3
         assert relerr(g[r], g64[r]) <= 2e-3
     hier.destroy()
+
+
+def test_tensor_core_coarse_apply_full_size_sampled_rows_against_oracle():
+    """At the benchmark's size and launch (level 1 of a 1024^2 lattice: 256^2
+    coarse sites, 64 right-hand sides in one group): sampled output sites,
+    including both periodic edges, against the oracle's Galerkin rows built
+    locally (oracle.amg.galerkin_rows) -- with the kernel's FP16 operands
+    emulated (row-scaled operator, power-of-two scaled right-hand sides) to
+    1e-5 of the sampled outputs' largest entry, and against exact FP64 to 2e-3."""
+    L, a, R, m0 = 1024, 4, 64, 0.1
+    U = random_links(L, L, 71)
+    hier = A.setup(torch.from_numpy(U).to(DEV), m0, A.make_params([4, 4, 2], precision=A.SOLVE_MIXED))
+    n1 = L // a
+    rng = np.random.Generator(np.random.PCG64(72))
+    x = (rng.standard_normal((R, 2, n1, n1)) + 1j * rng.standard_normal((R, 2, n1, n1))).astype(np.complex64)
+    y = torch.full(x.shape, complex(float("nan"), float("nan")), dtype=torch.complex64, device=DEV)
+    A.profile_enable(hier, True)
+    A.apply_coarse(hier, 1, torch.from_numpy(x).to(DEV), y)
+    A.profile_enable(hier, False)
+    assert any(name == "coarse_apply_tc" for name, *_ in A.profile_get(hier))
+    got = y.cpu().numpy()
+    hier.destroy()
+    verts = [(0, 0), (n1 - 1, n1 - 1), (1, n1 // 2), (n1 // 2, 0), (77, 200), (200, 31)]
+    rows = amg.galerkin_rows(U, m0, a, verts)
+    xf = x.astype(np.complex128).reshape(R, 2, -1)
+    xq = mixed.quantise_rhs_pow2(x).reshape(R, 2, -1)     # one scale per whole right-hand side
+    want, want_q, g = [], [], []
+    for (p, q) in verts:
+        ws = sorted(rows[(p, q)])
+        B = np.stack([rows[(p, q)][w] for w in ws])              # [K, 2, 2]
+        Bq = mixed.quantise_rows(B[:, None])[:, 0]               # the kernel's row-scaled FP16 storage
+        for r in range(R):
+            want.append(sum(B[k] @ xf[r][:, w] for k, w in enumerate(ws)))
+            want_q.append(sum(Bq[k] @ xq[r][:, w] for k, w in enumerate(ws)))
+            g.append(got[r][:, p, q])
+    want, want_q, g = np.array(want), np.array(want_q), np.array(g)
+    e_q, e_x = relerr(g, want_q), relerr(g, want)
+    print(f"1024^2 level 1 x 64 RHS, {len(verts)} sampled sites: vs emulated FP16 operands {e_q:.2e}, "
+          f"vs exact {e_x:.2e}")
+    assert e_q <= 1e-5
+    assert e_x <= 2e-3

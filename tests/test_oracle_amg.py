@@ -505,3 +505,46 @@ def test_vcycle_post_smoothing_placement_two_level_formula():
     assert np.linalg.norm(got - pre) > 1e-3 * np.linalg.norm(post)
     assert np.linalg.norm(got - coarse(r)) > 1e-3 * np.linalg.norm(post)
     assert np.linalg.norm(amg.vcycle(levels, r, post_smooth=0) - coarse(r)) <= 1e-12 * np.linalg.norm(post)
+
+
+@pytest.mark.parametrize("Nt,Nx", [(16, 16), (24, 32), (40, 24)])
+def test_local_galerkin_rows_equal_the_global_product(Nt, Nx):
+    """galerkin_rows builds rows of the first coarse operator from the baskets
+    near each coarse site and the rows of D at their sites only; they equal the
+    rows of the global Galerkin product P^H D P (16 x 16: the three-tile reach
+    wraps around the 4 x 4 coarse lattice)."""
+    rng = np.random.Generator(np.random.PCG64(90 + Nt))
+    U = np.exp(1j * rng.uniform(-np.pi, np.pi, size=(2, Nt, Nx)))
+    m0 = 0.13
+    a = 4
+    D = W.dirac_matrix(U, m0)
+    P, _ = amg.build_interpolator(D, Nt, Nx, a)
+    Ac = amg.galerkin(P, D).tocsr()
+    Nq = Nx // a
+    verts = [(0, 0), (Nt // a - 1, Nq - 1), (1, Nq // 2), (Nt // a // 2, 0)]
+    rows = amg.galerkin_rows(U, m0, a, verts)
+    scale = np.max(np.abs(Ac.data))
+    for (p, q) in verts:
+        v = p * Nq + q
+        blocks = rows[(p, q)]
+        dense = Ac[[2 * v, 2 * v + 1]].toarray()
+        got = np.zeros_like(dense)
+        for w, blk in blocks.items():
+            got[:, 2 * w:2 * w + 2] += blk
+        assert np.max(np.abs(got - dense)) <= 1e-13 * scale, (p, q)
+        # and only sites within two coarse sites carry blocks (21 offsets)
+        nz = [w for w, blk in blocks.items() if np.max(np.abs(blk)) > 1e-14 * scale]
+        assert len(nz) <= 21
+
+
+def test_dirac_rows_are_rows_of_the_matrix():
+    rng = np.random.Generator(np.random.PCG64(95))
+    U = np.exp(1j * rng.uniform(-np.pi, np.pi, size=(2, 8, 12)))
+    D = W.dirac_matrix(U, 0.2)
+    sites = [(0, 0), (7, 11), (3, 5), (0, 11)]
+    Dr = W.dirac_rows(U, 0.2, sites)
+    for (t, x) in sites:
+        for alpha in range(2):
+            r = 2 * (t * 12 + x) + alpha
+            assert (Dr[r] != D[r]).nnz == 0
+    assert Dr.nnz == sum(D[2 * (t * 12 + x) + al].nnz for (t, x) in sites for al in range(2))
